@@ -1,0 +1,341 @@
+"""Pins of the CPU oracle against facts other than itself.
+
+Each test ties an oracle function to a closed form, a textbook identity, a
+worked example of the paper, or brute force on tiny inputs, so that a
+dropped term, a wrong sign or a swapped index in the oracle fails here.
+"""
+import itertools
+import random
+
+import mpmath
+import numpy as np
+import pytest
+
+from oracle import factor, canonical
+from oracle.atoms import atoms
+from oracle.ddf import certify_irreducible, ddf_degrees
+from oracle.recombine import (accept, band_pairs, expand, expand_values,
+                              recombine_a, value)
+from oracle.reduction import reduce_poly
+from oracle.roots import complex_roots
+from oracle.sturm import real_root_count
+from oracle.zpoly import (is_squarefree, pdivmod_monic, peval, pmul, psub,
+                          padd, trim)
+from workloads import poly_mul, random_monic
+
+
+def prod(polys):
+    acc = [1]
+    for f in polys:
+        acc = pmul(acc, f)
+    return acc
+
+
+# ---------------------------------------------------------------- Z[x] basics
+def test_divmod_identity():
+    rng = random.Random(7)
+    for _ in range(200):
+        a = [rng.randint(-50, 50) for _ in range(rng.randint(1, 12))]
+        b = [rng.randint(-9, 9) for _ in range(rng.randint(0, 6))] + [1]
+        q, r = pdivmod_monic(a, b)
+        assert padd(pmul(q, b), r) == trim(a)
+        assert len(trim(r)) < len(b) or trim(r) == [0]
+
+
+def test_squarefree():
+    assert is_squarefree([1, 0, -10, 0, 1])
+    assert not is_squarefree(pmul([-1, 1], pmul([-1, 1], [2, 1])))
+    assert not is_squarefree(pmul([1, 0, 1], [1, 0, 1]))
+
+
+# ---------------------------------------------------------------- Sturm count
+def test_sturm_closed_forms():
+    assert real_root_count(prod([[-i, 1] for i in range(1, 11)])) == 10
+    assert real_root_count([1, 0, -10, 0, 1]) == 4          # Eq. 6: four real roots
+    assert real_root_count([1, 0, 1]) == 0
+    for m in (5, 6, 12, 30):                                 # x^m - 1: roots +-1 only
+        assert real_root_count([-1] + [0] * (m - 1) + [1]) == (2 if m % 2 == 0 else 1)
+    # Chebyshev T_n (non-monic, integer) has n real roots
+    t0, t1 = [1], [0, 1]
+    for n in range(2, 12):
+        t0, t1 = t1, psub(pmul([0, 2], t1), t0)
+        assert real_root_count(t1) == n
+
+
+def test_sturm_against_eigenvalues():
+    rng = np.random.default_rng(11)
+    for _ in range(30):
+        p = random_monic(rng, int(rng.integers(3, 16)), -20, 20)
+        if not is_squarefree(p):
+            continue
+        z = np.roots([float(c) for c in reversed(p)])
+        # count only unambiguous cases
+        im = np.sort(np.abs(z.imag))
+        r = int(np.sum(im < 1e-7))
+        if r < len(im) and im[r] < 1e-3:
+            continue
+        assert real_root_count(p) == r
+
+
+# ---------------------------------------------------------------- roots
+def test_roots_newton_identities():
+    rng = np.random.default_rng(3)
+    for d in (5, 17, 40):
+        p = random_monic(rng, d, -100, 100)
+        z = complex_roots(p)
+        with mpmath.workdps(60):
+            s1 = mpmath.fsum(z)
+            s2 = mpmath.fsum(w * w for w in z)
+            assert abs(s1 + p[-2]) < 1e-45
+            assert abs(s2 - (p[-2] ** 2 - 2 * p[-3])) < 1e-40
+            for w in z:
+                assert abs(mpmath.polyval([mpmath.mpf(c) for c in reversed(p)], w)) < 1e-35 * (1 + abs(w)) ** d * 100 ** 1
+
+
+def test_rho_definition_sqrt2():
+    # roots of x^2 - 2 are +-sqrt2; rho = (frac(-sqrt2), frac(sqrt2))
+    _, r, els = reduce_poly([-2, 0, 1])
+    assert r == 2 and [e.kind for e in els] == ["real", "real"]
+    with mpmath.workdps(60):
+        s2 = mpmath.sqrt(2)
+        assert abs(els[0].rho - (2 - s2)) < 1e-50
+        assert abs(els[1].rho - (s2 - 1)) < 1e-50
+
+
+def test_pair_trace_parts():
+    # x^2 + x + 1: one conjugate pair, z + conj z = -1, z^2 + conj z^2 = -1
+    _, r, els = reduce_poly([1, 1, 1])
+    assert r == 0 and len(els) == 1 and els[0].kind == "pair"
+    assert abs(els[0].t1 + 1) < 1e-50 and abs(els[0].t2 + 1) < 1e-50 and abs(els[0].rho) < 1e-50
+
+
+# ---------------------------------------------------------------- value/accept, EXPAND, FIND's set
+def test_value_accept_and_complement_symmetry():
+    rng = random.Random(5)
+    M = 1 << 20
+    for _ in range(30):
+        n = rng.randint(2, 9)
+        w = [rng.randrange(M) for _ in range(n - 1)]
+        w.append((-sum(w)) % M)                          # whole set sums to an integer
+        full = (1 << n) - 1
+        for s in range(1 << n):
+            a = accept(value(s, w, M), M, 3)
+            b = accept(value(full ^ s, w, M), M, 3)
+            assert a == b                                 # Section 3.1 symmetry
+        assert accept(value(0, w, M), M, 0) and accept(value(full, w, M), M, 0)
+
+
+def test_expand_is_sorted_subset_sums():
+    rng = random.Random(9)
+    M = 1 << 16
+    w = [rng.randrange(M) for _ in range(6)]
+    vals = expand_values(w, M)
+    brute = [sum(c for c, bit in zip(w, bits) if bit) % M
+             for bits in itertools.product([0, 1], repeat=6)]
+    # itertools order is big-endian in bits; compare as multisets, and per pattern
+    assert sorted(vals) == sorted(brute) == expand(w, M)
+    for s in range(64):
+        assert vals[s] == sum(w[i] for i in range(6) if s >> i & 1) % M
+
+
+def test_band_pairs_equals_scan_on_concatenation():
+    # Meet in the middle finds exactly the patterns RECOMBINE_A finds.
+    rng = random.Random(13)
+    M = 1 << 24
+    for _ in range(20):
+        na, nb = rng.randint(1, 5), rng.randint(1, 5)
+        w = [rng.randrange(M) for _ in range(na + nb)] + [rng.randrange(M)]   # last = fixed element
+        W = rng.choice([0, 5, 1 << 14])
+        scan = set(recombine_a(w, M, W))
+        alpha = expand_values(w[:na], M)
+        beta = expand_values(w[na:na + nb], M)
+        mitm = {i | (j << na) for (i, j) in band_pairs(alpha, beta, M, W)}
+        assert scan == mitm
+
+
+def test_recombine_vectorised_equals_loop():
+    rng = random.Random(21)
+    M = 1 << 62
+    w = [rng.randrange(M) for _ in range(19)]
+    # plant an integral subset
+    w[3] = (-(w[0] + w[5] + w[11])) % M
+    fast = recombine_a(w, M, 1 << 30)
+    slow = [s for s in range(1 << 18) if accept(value(s, w, M), M, 1 << 30)]
+    assert fast == slow and any(s == (1 | 8 | 32 | 2048) for s in fast)
+
+
+def test_atoms():
+    # divisors {0,1}, {0,1,2} of a 5-element set -> atoms {0,1}, {2}, {3,4}
+    at = atoms(5, [{0, 1}, {0, 1, 2}])
+    assert sorted(map(sorted, at)) == [[0, 1], [2], [3, 4]]
+    assert atoms(3, []) == [frozenset({0, 1, 2})]
+
+
+# ---------------------------------------------------------------- whole factorisation
+def brute_factor(p):
+    """Root-free brute force: repeatedly divide out the smallest-degree monic
+    integer divisor, searched over the box given by the Cauchy root bound."""
+    p = trim(p)
+    out = []
+    while len(p) > 2:
+        d = len(p) - 1
+        R = 1 + max(abs(c) for c in p[:-1])
+        found = None
+        for e in range(1, d // 2 + 1):
+            from math import comb
+            ranges = []
+            for k in range(e):
+                bound = comb(e, k) * R ** (e - k)
+                if k == 0 and p[0] != 0:
+                    ranges.append([s * v for v in range(1, abs(p[0]) + 1) if p[0] % v == 0 for s in (1, -1)])
+                else:
+                    ranges.append(range(-bound, bound + 1))
+            for q in itertools.product(*ranges):
+                cand = list(q) + [1]
+                _, r = pdivmod_monic(p, cand)
+                if r == [0]:
+                    found = cand
+                    break
+            if found:
+                break
+        if not found:
+            break
+        out.append(found)
+        p, _ = pdivmod_monic(p, found)
+    out.append(p)
+    return canonical(out)
+
+
+def test_brute_force_tiny_all():
+    count = 0
+    for d in (2, 3, 4):
+        for coeffs in itertools.product(range(-2, 3), repeat=d):
+            p = list(coeffs) + [1]
+            if not is_squarefree(p):
+                continue
+            assert factor(p).factors == brute_factor(p), p
+            count += 1
+    assert count > 500
+
+
+def test_brute_force_tiny_sampled():
+    rng = random.Random(17)
+    for _ in range(25):
+        d = rng.choice([5, 6])
+        p = [rng.randint(-3, 3) for _ in range(d)] + [1]
+        if rng.random() < 0.5:                         # make some reducible
+            e = rng.randint(1, d - 1)
+            p = pmul([rng.randint(-3, 3) for _ in range(e)] + [1],
+                     [rng.randint(-3, 3) for _ in range(d - e)] + [1])
+        if not is_squarefree(p):
+            continue
+        assert factor(p).factors == brute_factor(p), p
+
+
+def cyclotomic(k, cache={}):
+    """Phi_k by the textbook recursion x^k - 1 = prod_{j | k} Phi_j."""
+    if k not in cache:
+        num = [-1] + [0] * (k - 1) + [1]
+        for j in range(1, k):
+            if k % j == 0:
+                num, r = pdivmod_monic(num, cyclotomic(j))
+                assert r == [0]
+        cache[k] = num
+    return cache[k]
+
+
+def test_cyclotomic_closed_forms():
+    assert cyclotomic(12) == [1, 0, -1, 0, 1]
+    assert cyclotomic(30) == [1, 1, 0, -1, -1, -1, 0, 1, 1]
+    assert min(cyclotomic(105)) == -2                  # the first cyclotomic with a coefficient -2
+    for m in (12, 30):
+        res = factor([-1] + [0] * (m - 1) + [1])
+        assert res.method == "exhaustive"
+        assert res.factors == canonical([cyclotomic(k) for k in range(1, m + 1) if m % k == 0])
+
+
+@pytest.mark.slow
+def test_phi105():
+    # Phi_105 is reducible modulo every prime, so no degree sieve can certify
+    # it; the scan (n = 24) proves it irreducible.
+    assert not certify_irreducible(cyclotomic(105), max_primes=15)[0]
+    res = factor(cyclotomic(105))
+    assert res.factors == [cyclotomic(105)] and res.n == 24 and res.r == 0
+
+
+def sqrt_shift_product(f, m):
+    """f(x - sqrt m) * f(x + sqrt m) in Z[x], by arithmetic in Z[sqrt m][x]
+    (pairs (a, b) meaning a + b sqrt m)."""
+    def mul(P, Q):
+        out = [(0, 0)] * (len(P) + len(Q) - 1)
+        for i, (a, b) in enumerate(P):
+            for j, (c, e) in enumerate(Q):
+                x, y = out[i + j]
+                out[i + j] = (x + a * c + m * b * e, y + a * e + b * c)
+        return out
+    def compose(sign):                                  # f(x + sign*sqrt m)
+        acc = [(0, 0)]
+        for c in reversed(f):
+            acc = mul(acc, [(0, sign), (1, 0)])
+            acc[0] = (acc[0][0] + c, acc[0][1])
+        return acc
+    prodp = mul(compose(-1), compose(1))
+    assert all(b == 0 for _, b in prodp)
+    return trim([a for a, _ in prodp])
+
+
+def test_swinnerton_dyer():
+    f1 = [-2, 0, 1]                                     # prod (x +- sqrt2)
+    f2 = sqrt_shift_product(f1, 3)
+    assert f2 == [1, 0, -10, 0, 1]                      # Eq. 6
+    res = factor(f2)
+    assert res.factors == [f2] and res.n == 4 and res.r == 4
+    # Every real factor has a dual with b_{e-1} = 0 (Section 2): candidates
+    # exist, none verifies.  The pair {sqrt2+sqrt3, -sqrt2-sqrt3} sums to 0;
+    # its product is x^2 - 5 - 2 sqrt6 (Eq. 7 with its constant corrected).
+    assert len(res.candidates) >= 1 and res.verified == []
+    f3 = sqrt_shift_product(f2, 5)
+    assert f3 == [576, 0, -960, 0, 352, 0, -40, 0, 1]
+    res3 = factor(f3)
+    assert res3.factors == [f3] and res3.r == 8 and len(res3.candidates) >= 7 and res3.verified == []
+
+
+def test_linear_split():
+    p = prod([[-i, 1] for i in range(1, 11)])
+    res = factor(p)
+    assert res.factors == [[-i, 1] for i in range(10, 0, -1)]
+    assert len(res.candidates) == 2 ** 9 - 1            # every rho is 0: every pattern is a candidate
+
+
+def test_known_products_and_invariant():
+    rng = np.random.default_rng(23)
+    for _ in range(6):
+        fs = [random_monic(rng, int(rng.integers(2, 9)), -20, 20) for _ in range(int(rng.integers(2, 4)))]
+        p = [1]
+        for f in fs:
+            p = poly_mul(p, f)
+        if not is_squarefree(p):
+            continue
+        res = factor(p)
+        assert prod(res.factors) == p
+        # every construction factor is a product of returned factors
+        for f in fs:
+            sub = [g for g in res.factors if pdivmod_monic(f, g)[1] == [0]]
+            assert sub
+        # the certificate route agrees with the scan
+        cert = factor(p, construction=fs, max_scan_n=0)
+        assert cert.factors == res.factors
+
+
+# ---------------------------------------------------------------- DDF certificates
+def test_ddf_degrees_small():
+    assert ddf_degrees([1, 0, 1], 3) == {2: 1}          # x^2+1 irreducible mod 3
+    assert ddf_degrees([1, 0, 1], 5) == {1: 2}          # splits mod 5 (2^2 = -1)
+    assert ddf_degrees([-1, -1, 0, 0, 0, 1], 7) is not None
+
+
+def test_certificates():
+    assert certify_irreducible([-1, -1, 0, 0, 0, 1])[0]           # x^5 - x - 1
+    assert certify_irreducible(cyclotomic(7))[0]
+    assert not certify_irreducible([1, 0, 0, 0, 1], max_primes=20)[0]   # x^4+1: reducible mod every prime
+    assert not certify_irreducible(pmul([1, 0, 1], [2, 0, 1]), max_primes=20)[0]
