@@ -1,0 +1,178 @@
+/*
+ * rfr.h — C ABI of the RFR (Real-Factors-Recombination) factorisation library
+ * for NVIDIA B300 (sm_103a).
+ *
+ * The library factors a monic, square-free polynomial p in Z[x] into its
+ * monic irreducible factors by the method of "Integer polynomial
+ * factorization by recombination of real factors" (arXiv 2410.15880):
+ *   1. all complex roots of p (Section 2, "black box"; here a batched FP64
+ *      Aberth iteration with a double-double Newton polish and an inclusion
+ *      radius per root),
+ *   2. the real factorisation of Eq. 1 and the fractional parts rho of the
+ *      first traces (Section 2), scaled to 64-bit fixed point (Eq. 18),
+ *   3. the meet-in-the-middle subset-sum search of Section 3.3 (Horowitz-
+ *      Sahni): all half-subset sums of each half, sorted, and matched
+ *      against the integrality window of Eq. 9 / Eq. 19,
+ *   4. the candidate test of Algorithm FACTOR (q in Z[x]) by rounding and
+ *      exact integer division, and the irreducible factors as atoms of the
+ *      verified divisors.
+ * Every step runs in CUDA kernels on one GPU; the host code only validates,
+ * plans memory, launches and assembles results.
+ *
+ * Conventions shared by every call
+ *  - Polynomials are arrays of int64 coefficients in ASCENDING powers:
+ *    coeffs[0] = a_0 ... coeffs[degree] = a_degree.  The input must be monic
+ *    (coeffs[degree] == 1), 1 <= degree <= RFR_MAX_DEGREE and |a_i| < 2^53.
+ *  - Status codes: RFR_OK (0) on success, RFR_PENDING (> 0) for a request
+ *    still in flight, negative RFR_E_* values on error.  No call aborts the
+ *    process; every call is thread-safe with respect to one context.
+ *  - Input buffers are read (and copied where the call returns before the
+ *    work ends) before the call returns; the caller keeps ownership.
+ *  - Output factor lists are allocated by the library and released by the
+ *    caller with rfr_factors_free().
+ */
+#ifndef RFR_H_
+#define RFR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RFR_MAX_DEGREE 128
+
+/* ---- status codes ------------------------------------------------------ */
+#define RFR_OK                 0
+#define RFR_PENDING            1   /* rfr_poll: request not finished yet      */
+#define RFR_E_INVALID         -1   /* null pointer / bad argument / unknown ticket */
+#define RFR_E_NOT_MONIC       -2   /* coeffs[degree] != 1                     */
+#define RFR_E_RANGE           -3   /* degree outside [1,128] or |a_i| >= 2^53 */
+#define RFR_E_NOT_SQUAREFREE  -4   /* p and p' share a factor (Section 2 assumes square-free) */
+#define RFR_E_NO_CONVERGENCE  -5   /* root iteration did not converge         */
+#define RFR_E_ROOTS           -6   /* inclusion discs overlap or real/complex classification undecidable */
+#define RFR_E_WINDOW          -7   /* integrality window too wide for the search */
+#define RFR_E_CAND_OVERFLOW   -8   /* more candidate patterns than the configured cap */
+#define RFR_E_OVERFLOW        -9   /* a verified candidate needs more than int128 / |c| < 2^62 */
+#define RFR_E_OOM            -10   /* device or host allocation failed        */
+#define RFR_E_BUDGET         -11   /* the request's tables exceed the memory budget */
+#define RFR_E_TIMEOUT        -12   /* rfr_wait timed out (request still queued/running) */
+#define RFR_E_CUDA           -13   /* a CUDA runtime call failed              */
+#define RFR_E_CANCELLED      -14   /* request cancelled with rfr_cancel       */
+#define RFR_E_INTERNAL       -15   /* an internal consistency check failed    */
+
+/* ---- root finder precision (rfr_config.root_mode) ----------------------- */
+#define RFR_ROOTS_FP64       0     /* Aberth in FP64, then double-double polish */
+#define RFR_ROOTS_FP32_BULK  1     /* Aberth bulk in FP32, then FP64, then double-double polish */
+
+typedef struct rfr_ctx rfr_ctx;   /* opaque: owns streams, device memory, worker threads */
+
+/* Library configuration.  Fill with rfr_config_default() and override. */
+typedef struct {
+    int      device;            /* CUDA device ordinal                                   */
+    size_t   mem_budget_bytes;  /* device bytes the context may hold for tables; 0 = 85% of free memory at create */
+    int      max_inflight;      /* serving: batches that may run concurrently (streams), >= 1 */
+    int      max_batch;         /* serving: requests admitted into one batch                */
+    int      root_mode;         /* RFR_ROOTS_FP64 or RFR_ROOTS_FP32_BULK                    */
+    int      timing;            /* 1: record CUDA events per stage into rfr_diag.stage_us   */
+    uint64_t max_candidates;    /* per polynomial cap on candidate patterns (after the Tr_1/Tr_2 windows) */
+    double   eps_override;      /* > 0: integrality window eps (fraction of 1) replacing the derived one */
+} rfr_config;
+
+/* Per-polynomial diagnostics returned with each result. */
+typedef struct {
+    int      n, r, c;           /* n = r + c elements of Eq. 1: r real roots, c conjugate pairs */
+    int      n_a, n_b;          /* half sizes of the meet-in-the-middle split (one element fixed out) */
+    uint64_t window;            /* Tr_1 window W in units of 2^-64                          */
+    uint64_t half_sums;         /* 2^n_a + 2^n_b table entries enumerated                    */
+    uint64_t cand_coarse;       /* pairs within the coarse (prefix) window                   */
+    uint64_t cand_pre;          /* pairs within the exact Tr_1 window W                      */
+    uint64_t cand_post;         /* ... that also pass the Tr_2 window                        */
+    uint64_t verified;          /* candidates proven to divide p                             */
+    double   max_rel_residual;  /* max_i |p(z_i)| / sum_k |a_k||z_i|^k after the polish       */
+    double   max_root_err;      /* largest inclusion radius                                  */
+    double   stage_us[8];       /* roots, weights, enumerate(count+scan+scatter), match, verify, atoms, host, total */
+} rfr_diag;
+
+/* A factorisation: n_factors monic irreducible factors in canonical order
+ * (degree ascending, then (a_0, ..., a_{e-1}) lexicographic as signed int64).
+ * degrees[i] is the degree of factor i; coeffs holds the factors one after
+ * the other, each as degree+1 ascending coefficients (monic).  The product of
+ * the factors equals the input exactly. */
+typedef struct {
+    int      n_factors;
+    int*     degrees;
+    int64_t* coeffs;
+    rfr_diag diag;
+} rfr_factors;
+
+/* Device allocator hook (e.g. PyTorch's caching allocator).  alloc returns a
+ * device pointer of at least `bytes` bytes usable on `stream` (a
+ * cudaStream_t), or NULL; free releases it. */
+typedef void* (*rfr_alloc_fn)(size_t bytes, void* user, void* stream);
+typedef void  (*rfr_free_fn)(void* ptr, size_t bytes, void* user, void* stream);
+
+/* Fill *cfg with defaults: device 0, budget 0 (auto), max_inflight 2,
+ * max_batch 64, FP64 roots, timing off, 1<<16 candidates, no override.
+ * Returns RFR_E_INVALID if cfg is NULL. */
+int rfr_config_default(rfr_config* cfg);
+
+/* Create a context on cfg->device (cfg may be NULL for defaults).  Errors:
+ * RFR_E_INVALID (bad config), RFR_E_CUDA (device unusable). */
+int rfr_create(const rfr_config* cfg, rfr_ctx** out);
+
+/* Stop the serving workers (pending requests end RFR_E_CANCELLED), free all
+ * device memory and destroy the context.  NULL is accepted. */
+int rfr_destroy(rfr_ctx* ctx);
+
+/* Route the context's device allocations through alloc/free (both non-NULL),
+ * or back to the built-in stream-ordered pool (both NULL).  Must be called
+ * while no request is in flight; returns RFR_E_INVALID otherwise. */
+int rfr_set_allocator(rfr_ctx* ctx, rfr_alloc_fn alloc, rfr_free_fn free_fn, void* user);
+
+/* Factor one polynomial (blocking).  On RFR_OK *out holds the factors; on
+ * error *out is zeroed except out->diag.  Algorithm FACTOR, Section 2. */
+int rfr_factor(rfr_ctx* ctx, const int64_t* coeffs, int degree, rfr_factors* out);
+
+/* Factor `count` polynomials as one batch (blocking): the stages run once
+ * over the whole batch.  coeffs[i] points at degrees[i]+1 coefficients.
+ * outs[i] / statuses[i] receive each result.  The return value is RFR_OK if
+ * the batch ran (individual statuses may still be errors), else the error
+ * that stopped the whole batch. */
+int rfr_factor_batch(rfr_ctx* ctx, int count, const int64_t* const* coeffs,
+                     const int* degrees, rfr_factors* outs, int* statuses);
+
+/* Serving API (continuous batching).  rfr_submit copies the input and
+ * queues it; workers admit queued requests into batches as slots and device
+ * memory free up, and batches in flight overlap on the device.
+ * *ticket identifies the request.  Input errors (monic, range) are reported
+ * at submit time. */
+int rfr_submit(rfr_ctx* ctx, const int64_t* coeffs, int degree, uint64_t* ticket);
+
+/* Non-blocking: RFR_PENDING while queued or running; otherwise the
+ * request's final status, with *out filled on RFR_OK.  A finished ticket
+ * is released by the first rfr_poll/rfr_wait that returns its result. */
+int rfr_poll(rfr_ctx* ctx, uint64_t ticket, rfr_factors* out);
+
+/* Block until the request finishes or timeout_ms elapses (< 0: no limit);
+ * RFR_E_TIMEOUT leaves the request in place. */
+int rfr_wait(rfr_ctx* ctx, uint64_t ticket, int timeout_ms, rfr_factors* out);
+
+/* Cancel a queued request (it then finishes with RFR_E_CANCELLED).  A request
+ * already running completes normally.  RFR_E_INVALID for unknown tickets. */
+int rfr_cancel(rfr_ctx* ctx, uint64_t ticket);
+
+/* Release the arrays of a result; safe on a zeroed or already freed struct. */
+void rfr_factors_free(rfr_factors* f);
+
+/* Static English description of a status code. */
+const char* rfr_strerror(int status);
+
+/* Library version string. */
+const char* rfr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RFR_H_ */

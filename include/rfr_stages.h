@@ -1,0 +1,124 @@
+/*
+ * rfr_stages.h — stage-level C ABI of the RFR library (device pointers).
+ *
+ * These entry points run one stage of the hot path on buffers that already
+ * live in device memory, on the caller's CUDA stream (passed as void*, a
+ * cudaStream_t; NULL = the legacy default stream).  They exist so that each
+ * stage can be checked on its own against the CPU oracle and timed on its
+ * own; rfr_factor / rfr_factor_batch in rfr.h chain the same kernels.
+ * All pointers are device pointers unless named h_*; the caller owns every
+ * buffer.  Calls are asynchronous: they return after the launches are
+ * queued (RFR_OK) or with RFR_E_INVALID for bad sizes and RFR_E_CUDA if a
+ * launch failed.  Errors found by the kernels are written to the stated
+ * device status words.
+ */
+#ifndef RFR_STAGES_H_
+#define RFR_STAGES_H_
+
+#include <stddef.h>
+#include <stdint.h>
+#include "rfr.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Coefficient layout for the stages: int64 [batch][RFR_LDC], ascending
+ * powers, entries above each problem's degree ignored. */
+#define RFR_LDC (RFR_MAX_DEGREE + 1)
+
+/* Per-polynomial plan written by the weights stage (one per problem).
+ * Elements are the factors of Eq. 1 in canonical order: real roots
+ * ascending, then conjugate pairs by (Re z, Im z) of the member with
+ * Im z > 0.  The last element (index n-1) is fixed out of the search
+ * (complement symmetry, Section 3.1); elements 0..n_a-1 form half a and
+ * n_a..n_a+n_b-1 half b. */
+typedef struct {
+    int32_t  status;        /* RFR_OK or the first error of roots/weights     */
+    int32_t  degree;
+    int32_t  n, r, c;       /* elements, real roots, conjugate pairs          */
+    int32_t  n_a, n_b;      /* n_a = floor((n-1)/2), n_b = n-1-n_a            */
+    int32_t  pad0;
+    uint64_t window;        /* Tr_1 window W (units of 2^-64)                 */
+    uint64_t window2;       /* Tr_2 window W2 (units of 2^-64; >= 2^63 = off) */
+    double   max_radius;    /* largest root inclusion radius                  */
+    double   max_rel_residual;
+    double   sum_err1;      /* bound on |error| of any Tr_1 subset sum        */
+    double   sum_err2;      /* same for Tr_2                                  */
+    uint64_t w[RFR_MAX_DEGREE];    /* rho_k scaled: round(frac(Tr_1 part) * 2^64) mod 2^64 (Eq. 18) */
+    uint64_t w2[RFR_MAX_DEGREE];   /* Tr_2 part scaled the same way           */
+    uint8_t  kind[RFR_MAX_DEGREE]; /* 1 = real linear factor, 2 = real quadratic factor */
+    uint8_t  root0[RFR_MAX_DEGREE];/* root index (into the roots array) of element k    */
+    uint8_t  root1[RFR_MAX_DEGREE];/* conjugate partner's root index (pairs only)       */
+} rfr_plan;
+
+/* K-a roots.  For problem i (degree degrees[i]) writes its roots to
+ * roots[i*RFR_MAX_DEGREE*4 + 4*j + {0,1,2,3}] = (Re hi, Re lo, Im hi, Im lo)
+ * as double-double values, the inclusion radius of root j to
+ * radius[i*RFR_MAX_DEGREE + j] (a disc of that radius around the root
+ * contains exactly one root of p when the discs are disjoint), and RFR_OK,
+ * RFR_E_NO_CONVERGENCE or RFR_E_RANGE to status[i].
+ * root_mode: RFR_ROOTS_FP64 or RFR_ROOTS_FP32_BULK.  Section 2, Eq. 1. */
+int rfr_stage_roots(const int64_t* coeffs, const int32_t* degrees, int batch,
+                    int root_mode, double* roots, double* radius,
+                    int32_t* status, void* stream);
+
+/* K-b weights.  From the roots and radii of K-a, classify real roots and
+ * conjugate pairs (Eq. 1), order the elements, and write plans[i]: the
+ * fixed-point Tr_1 weights w (Eq. 18, rounded), Tr_2 weights w2, the
+ * windows W and W2 derived from the radii, and the half split.
+ * eps_override > 0 replaces W by ceil(eps_override * 2^64).  Section 2,
+ * Section 3.3. */
+int rfr_stage_weights(const int64_t* coeffs, const int32_t* degrees, int batch,
+                      const double* roots, const double* radius,
+                      const int32_t* root_status, double eps_override,
+                      rfr_plan* plans, void* stream);
+
+/* K-c, plain form: keys[s] = (sum of w[i] over the set bits i of s) mod 2^64
+ * for s = 0 .. 2^h - 1, written in pattern order with 128-bit stores
+ * (EXPAND before its sort, Section 3.3).  1 <= h <= 32 (h = 0 writes the
+ * single entry 0).  keys must hold 2^h entries, 16-byte aligned. */
+int rfr_stage_enumerate(const uint64_t* w, int h, uint64_t* keys, void* stream);
+
+/* Match workspace: bytes of device scratch rfr_stage_match needs for halves
+ * of n_a and n_b elements. */
+size_t rfr_stage_match_workspace(int n_a, int n_b);
+
+/* K-c + K-d + K-e for one problem given its weights: enumerate both halves
+ * (keys of half b negated), radix-partition them by key (first digit fused
+ * into the enumeration, second digit in shared memory inside the match),
+ * and write every pattern s = s_a | (s_b << n_a), s != 0, with
+ *   dist((sum_a w_a + sum_b w_b) mod 2^64) <= W   and
+ *   dist((sum_a w2_a + sum_b w2_b) mod 2^64) <= W2,
+ * dist(y) = min(y, 2^64 - y) (Eq. 9 / Eq. 19 made circular), to
+ * cand[0 .. min(count, cap)).  counters (device, uint64 [6]) receive
+ * {coarse pairs, pairs within W, pairs also within W2 (= count), trivial
+ * pattern seen (1/0), halo overflow (1/0), 0}.  w_a/w2_a hold n_a weights, w_b/w2_b n_b; 0 <= n_a,
+ * n_b <= 32.  workspace: rfr_stage_match_workspace(n_a, n_b) bytes,
+ * 256-byte aligned.  Section 3.3 (RECOMBINE_C's result set). */
+int rfr_stage_match(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
+                    const uint64_t* w_b, const uint64_t* w2_b, int n_b,
+                    uint64_t window, uint64_t window2,
+                    void* workspace, size_t workspace_bytes,
+                    uint64_t* cand, uint64_t cap, uint64_t* counters,
+                    void* stream);
+
+/* K-f verify.  For job j: problem prob[j], element pattern
+ * (pat_lo[j], pat_hi[j]) over that problem's n elements.  Builds the real
+ * factor of Eq. 2 for the pattern or its complement (whichever has the
+ * lower degree) in double-double arithmetic, rounds it, and divides p by it
+ * exactly in 128-bit integers.  result[j] = 1 if the pattern's polynomial is
+ * an integer divisor of p, 0 if not, RFR_E_OVERFLOW if the test needed more
+ * than the integer range; if coeffs_out is not NULL and result[j] == 1, the
+ * pattern's own polynomial (degree = sum of element degrees) is written to
+ * coeffs_out[j*RFR_LDC ...] ascending.  FACTOR, Section 2. */
+int rfr_stage_verify(const int64_t* coeffs, const int32_t* degrees,
+                     const double* roots, const rfr_plan* plans,
+                     const int32_t* prob, const uint64_t* pat_lo,
+                     const uint64_t* pat_hi, int jobs,
+                     int32_t* result, int64_t* coeffs_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RFR_STAGES_H_ */

@@ -59,8 +59,8 @@ def recombine_a(w, M: int = ORACLE_M, window: int | None = None):
     nbits = n - 1
     if nbits <= 16:
         return [s for s in range(1 << nbits) if accept(value(s, w, M), M, window)]
-    if M > (1 << 62):
-        raise ValueError("vectorised scan needs M <= 2^62")
+    if M > (1 << 62) and M != (1 << 64):
+        raise ValueError("vectorised scan needs M <= 2^62 or M = 2^64 (uint64 wrap-around)")
     mask = np.uint64(M - 1)
     low = min(nbits, 20)
     vals = np.zeros(1, dtype=np.uint64)

@@ -1,0 +1,322 @@
+"""ctypes declarations of the C ABI and small marshalling helpers."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "librfr.so")
+
+RFR_MAX_DEGREE = 128
+RFR_LDC = RFR_MAX_DEGREE + 1
+RFR_OK = 0
+RFR_PENDING = 1
+RFR_ROOTS_FP64 = 0
+RFR_ROOTS_FP32_BULK = 1
+
+_STATUS = {
+    0: "RFR_OK", 1: "RFR_PENDING", -1: "RFR_E_INVALID", -2: "RFR_E_NOT_MONIC",
+    -3: "RFR_E_RANGE", -4: "RFR_E_NOT_SQUAREFREE", -5: "RFR_E_NO_CONVERGENCE",
+    -6: "RFR_E_ROOTS", -7: "RFR_E_WINDOW", -8: "RFR_E_CAND_OVERFLOW",
+    -9: "RFR_E_OVERFLOW", -10: "RFR_E_OOM", -11: "RFR_E_BUDGET", -12: "RFR_E_TIMEOUT",
+    -13: "RFR_E_CUDA", -14: "RFR_E_CANCELLED", -15: "RFR_E_INTERNAL",
+}
+
+
+def status_name(st: int) -> str:
+    return _STATUS.get(int(st), f"status {st}")
+
+
+class RFRError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = int(status)
+        super().__init__(f"{what}: {status_name(status)}" if what else status_name(status))
+
+
+class Config(C.Structure):
+    _fields_ = [("device", C.c_int), ("mem_budget_bytes", C.c_size_t), ("max_inflight", C.c_int),
+                ("max_batch", C.c_int), ("root_mode", C.c_int), ("timing", C.c_int),
+                ("max_candidates", C.c_uint64), ("eps_override", C.c_double)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("n", C.c_int), ("r", C.c_int), ("c", C.c_int), ("n_a", C.c_int), ("n_b", C.c_int),
+                ("window", C.c_uint64), ("half_sums", C.c_uint64), ("cand_coarse", C.c_uint64),
+                ("cand_pre", C.c_uint64), ("cand_post", C.c_uint64), ("verified", C.c_uint64),
+                ("max_rel_residual", C.c_double), ("max_root_err", C.c_double),
+                ("stage_us", C.c_double * 8)]
+
+
+class Factors(C.Structure):
+    _fields_ = [("n_factors", C.c_int), ("degrees", C.POINTER(C.c_int)),
+                ("coeffs", C.POINTER(C.c_int64)), ("diag", Diag)]
+
+
+# rfr_plan as a numpy structured dtype (byte-exact with include/rfr_stages.h)
+PLAN_DTYPE = np.dtype([
+    ("status", "<i4"), ("degree", "<i4"), ("n", "<i4"), ("r", "<i4"), ("c", "<i4"),
+    ("n_a", "<i4"), ("n_b", "<i4"), ("pad0", "<i4"), ("window", "<u8"), ("window2", "<u8"),
+    ("max_radius", "<f8"), ("max_rel_residual", "<f8"), ("sum_err1", "<f8"), ("sum_err2", "<f8"),
+    ("w", "<u8", (RFR_MAX_DEGREE,)), ("w2", "<u8", (RFR_MAX_DEGREE,)),
+    ("kind", "u1", (RFR_MAX_DEGREE,)), ("root0", "u1", (RFR_MAX_DEGREE,)),
+    ("root1", "u1", (RFR_MAX_DEGREE,)),
+])
+
+_lib = None
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+def lib():
+    """The loaded librfr.so.  Raises if it was not built: there is no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"librfr.so is not built ({_LIB_PATH}); run "
+                           "`python -m paper_2410_15880_b300.build`")
+    L = C.CDLL(_LIB_PATH)
+    vp, i32, i64p, u64 = C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.c_uint64
+    sig = {
+        "rfr_version": (C.c_char_p, []),
+        "rfr_strerror": (C.c_char_p, [i32]),
+        "rfr_config_default": (i32, [C.POINTER(Config)]),
+        "rfr_create": (i32, [C.POINTER(Config), C.POINTER(vp)]),
+        "rfr_destroy": (i32, [vp]),
+        "rfr_set_allocator": (i32, [vp, ALLOC_FN, FREE_FN, vp]),
+        "rfr_factor": (i32, [vp, i64p, i32, C.POINTER(Factors)]),
+        "rfr_factor_batch": (i32, [vp, i32, C.POINTER(i64p), C.POINTER(C.c_int), C.POINTER(Factors), C.POINTER(C.c_int)]),
+        "rfr_submit": (i32, [vp, i64p, i32, C.POINTER(u64)]),
+        "rfr_poll": (i32, [vp, u64, C.POINTER(Factors)]),
+        "rfr_wait": (i32, [vp, u64, i32, C.POINTER(Factors)]),
+        "rfr_cancel": (i32, [vp, u64]),
+        "rfr_factors_free": (None, [C.POINTER(Factors)]),
+        "rfr_stage_roots": (i32, [vp, vp, i32, i32, vp, vp, vp, vp]),
+        "rfr_stage_weights": (i32, [vp, vp, i32, vp, vp, vp, C.c_double, vp, vp]),
+        "rfr_stage_enumerate": (i32, [vp, i32, vp, vp]),
+        "rfr_stage_match_workspace": (C.c_size_t, [i32, i32]),
+        "rfr_stage_match": (i32, [vp, vp, i32, vp, vp, i32, u64, u64, vp, C.c_size_t, vp, u64, vp, vp]),
+        "rfr_stage_verify": (i32, [vp, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+@dataclass
+class Result:
+    """One factorisation: canonical factor list plus diagnostics."""
+    status: int
+    factors: List[List[int]] = field(default_factory=list)
+    diag: dict = field(default_factory=dict)
+
+    @property
+    def ok(self) -> bool:
+        return self.status == RFR_OK
+
+
+def _diag_dict(d: Diag) -> dict:
+    return {k: (list(getattr(d, k)) if k == "stage_us" else getattr(d, k)) for k, _ in Diag._fields_}
+
+
+def _to_result(status: int, f: Factors) -> Result:
+    res = Result(status=int(status), diag=_diag_dict(f.diag))
+    if status == RFR_OK:
+        off = 0
+        for i in range(f.n_factors):
+            e = f.degrees[i]
+            res.factors.append([int(f.coeffs[off + k]) for k in range(e + 1)])
+            off += e + 1
+    lib().rfr_factors_free(C.byref(f))
+    return res
+
+
+def _coeff_array(coeffs: Sequence[int]):
+    arr = (C.c_int64 * len(coeffs))(*[int(c) for c in coeffs])
+    return arr
+
+
+class Context:
+    """A library context (rfr_create).  Thread-safe; use as a context manager."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_inflight: int = 2,
+                 max_batch: int = 64, root_mode: int = RFR_ROOTS_FP64, timing: bool = False,
+                 max_candidates: int = 1 << 16, eps_override: float = 0.0):
+        L = lib()
+        cfg = Config()
+        L.rfr_config_default(C.byref(cfg))
+        cfg.device, cfg.mem_budget_bytes, cfg.max_inflight = device, mem_budget_bytes, max_inflight
+        cfg.max_batch, cfg.root_mode, cfg.timing = max_batch, root_mode, int(bool(timing))
+        cfg.max_candidates, cfg.eps_override = max_candidates, eps_override
+        h = C.c_void_p()
+        st = L.rfr_create(C.byref(cfg), C.byref(h))
+        if st != RFR_OK:
+            raise RFRError(st, "rfr_create")
+        self._h = h
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rfr_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def use_torch_allocator(self):
+        """Route device allocations through PyTorch's caching allocator."""
+        import torch
+        dev = torch.cuda.current_device()
+
+        def _alloc(nbytes, user, stream):
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream or 0)
+
+        def _free(ptr, nbytes, user, stream):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        fa, ff = ALLOC_FN(_alloc), FREE_FN(_free)
+        self._keep = [fa, ff]
+        st = lib().rfr_set_allocator(self._h, fa, ff, None)
+        if st != RFR_OK:
+            raise RFRError(st, "rfr_set_allocator")
+
+    def factor(self, coeffs: Sequence[int]) -> Result:
+        f = Factors()
+        arr = _coeff_array(coeffs)
+        st = lib().rfr_factor(self._h, arr, len(coeffs) - 1, C.byref(f))
+        return _to_result(st, f)
+
+    def factor_batch(self, polys: Sequence[Sequence[int]]) -> List[Result]:
+        n = len(polys)
+        arrs = [_coeff_array(p) for p in polys]
+        ptrs = (C.POINTER(C.c_int64) * n)(*[C.cast(a, C.POINTER(C.c_int64)) for a in arrs])
+        degs = (C.c_int * n)(*[len(p) - 1 for p in polys])
+        outs = (Factors * n)()
+        sts = (C.c_int * n)()
+        rc = lib().rfr_factor_batch(self._h, n, ptrs, degs, outs, sts)
+        if rc != RFR_OK:
+            for i in range(n):
+                lib().rfr_factors_free(C.byref(outs[i]))
+            raise RFRError(rc, "rfr_factor_batch")
+        return [_to_result(sts[i], outs[i]) for i in range(n)]
+
+    def submit(self, coeffs: Sequence[int]) -> int:
+        t = C.c_uint64()
+        st = lib().rfr_submit(self._h, _coeff_array(coeffs), len(coeffs) - 1, C.byref(t))
+        if st != RFR_OK:
+            raise RFRError(st, "rfr_submit")
+        return int(t.value)
+
+    def poll(self, ticket: int) -> Optional[Result]:
+        f = Factors()
+        st = lib().rfr_poll(self._h, ticket, C.byref(f))
+        if st == RFR_PENDING:
+            return None
+        if st == -1 and f.n_factors == 0 and not f.degrees:
+            raise RFRError(st, "rfr_poll")
+        return _to_result(st, f)
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> Result:
+        f = Factors()
+        st = lib().rfr_wait(self._h, ticket, timeout_ms, C.byref(f))
+        if st == -12:
+            raise RFRError(st, "rfr_wait")
+        return _to_result(st, f)
+
+    def cancel(self, ticket: int) -> int:
+        return int(lib().rfr_cancel(self._h, ticket))
+
+
+# ---------------------------------------------------------------- stages (torch tensors on CUDA)
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check(st, what):
+    if st != RFR_OK:
+        raise RFRError(st, what)
+
+
+def stage_roots(coeffs, degrees, root_mode: int = RFR_ROOTS_FP64):
+    """coeffs: int64 [B, 129] cuda; degrees: int32 [B] cuda.
+    Returns (roots float64 [B, 128, 4], radius float64 [B, 128], status int32 [B])."""
+    import torch
+    B = coeffs.shape[0]
+    roots = torch.zeros((B, RFR_MAX_DEGREE, 4), dtype=torch.float64, device=coeffs.device)
+    radius = torch.zeros((B, RFR_MAX_DEGREE), dtype=torch.float64, device=coeffs.device)
+    status = torch.zeros((B,), dtype=torch.int32, device=coeffs.device)
+    _check(lib().rfr_stage_roots(_ptr(coeffs), _ptr(degrees), B, root_mode, _ptr(roots), _ptr(radius),
+                                 _ptr(status), _stream()), "rfr_stage_roots")
+    return roots, radius, status
+
+
+def stage_weights(coeffs, degrees, roots, radius, status, eps_override: float = 0.0):
+    """Returns the plans as a uint8 cuda tensor [B, sizeof(rfr_plan)] (view with PLAN_DTYPE)."""
+    import torch
+    B = coeffs.shape[0]
+    plans = torch.zeros((B, PLAN_DTYPE.itemsize), dtype=torch.uint8, device=coeffs.device)
+    _check(lib().rfr_stage_weights(_ptr(coeffs), _ptr(degrees), B, _ptr(roots), _ptr(radius), _ptr(status),
+                                   eps_override, _ptr(plans), _stream()), "rfr_stage_weights")
+    return plans
+
+
+def stage_enumerate(w, h: int):
+    """w: int64 cuda tensor holding uint64 weights bit-for-bit; returns keys int64 [2^h]."""
+    import torch
+    keys = torch.empty((1 << h,), dtype=torch.int64, device=w.device)
+    _check(lib().rfr_stage_enumerate(_ptr(w), h, _ptr(keys), _stream()), "rfr_stage_enumerate")
+    return keys
+
+
+def match_workspace_bytes(n_a: int, n_b: int) -> int:
+    return int(lib().rfr_stage_match_workspace(n_a, n_b))
+
+
+def stage_match(w_a, w2_a, w_b, w2_b, window: int, window2: int, cap: int):
+    """Weights as int64 cuda tensors (uint64 bits).  Returns (cand int64 [cap], counters int64 [6])."""
+    import torch
+    n_a, n_b = int(w_a.numel()), int(w_b.numel())
+    dev = w_b.device
+    ws_bytes = match_workspace_bytes(n_a, n_b)
+    ws = torch.empty((ws_bytes // 8 + 64,), dtype=torch.int64, device=dev)
+    base = ws.data_ptr()
+    aligned = (base + 255) & ~255
+    cand = torch.zeros((max(cap, 1),), dtype=torch.int64, device=dev)
+    ctr = torch.zeros((6,), dtype=torch.int64, device=dev)
+    _check(lib().rfr_stage_match(_ptr(w_a) if n_a else None, _ptr(w2_a) if n_a else None, n_a,
+                                 _ptr(w_b) if n_b else None, _ptr(w2_b) if n_b else None, n_b,
+                                 int(window), int(window2), C.c_void_p(aligned), ws_bytes,
+                                 _ptr(cand), int(cap), _ptr(ctr), _stream()), "rfr_stage_match")
+    return cand, ctr, ws
+
+
+def stage_verify(coeffs, degrees, roots, plans, prob, pat_lo, pat_hi, want_coeffs: bool = False):
+    import torch
+    J = int(prob.numel())
+    res = torch.zeros((J,), dtype=torch.int32, device=coeffs.device)
+    co = torch.zeros((J, RFR_LDC), dtype=torch.int64, device=coeffs.device) if want_coeffs else None
+    _check(lib().rfr_stage_verify(_ptr(coeffs), _ptr(degrees), _ptr(roots), _ptr(plans), _ptr(prob),
+                                  _ptr(pat_lo), _ptr(pat_hi), J, _ptr(res), _ptr(co) if co is not None else None,
+                                  _stream()), "rfr_stage_verify")
+    return res, co

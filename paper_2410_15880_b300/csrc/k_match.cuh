@@ -1,0 +1,72 @@
+// k_match.cuh — job descriptors shared by the enumerate / partition / match
+// kernels (K-c, K-d, K-e) and their host-side planners.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rfr {
+
+constexpr int SUB_BITS = 13;          // second radix digit, sorted in shared memory
+constexpr int JOIN_CAP = 9216;        // table-a entries per shared-memory chunk
+constexpr int JOIN_THREADS = 512;
+constexpr int PART_THREADS = 512;
+constexpr int MAX_D1 = 13;            // first radix digit, at most 8192 buckets
+
+// One half-table (a: keys = sum w; b: keys = -sum w) of one problem.
+struct HalfJob {
+    const uint64_t* w;      // h weights (device)
+    int h;                  // elements of this half (mask bits), 0..32
+    int neg;                // 1 for half b
+    int d1;                 // bucket bits (>= 2)
+    int ctas;               // CTAs of the count/scatter grids for this half (power of 2)
+    int cta_base;           // first CTA of this half in those grids
+    int scan_base;          // first CTA of this half in the column-scan grid
+    uint64_t wc;            // coarse window (halo test, half b)
+    uint32_t* hist;         // [ctas][NB]: counts, then per-CTA offsets
+    uint32_t* bstart;       // [NB + 1]: bucket starts in tab
+    uint64_t* tab;          // [2^h] records ((key << d1) & ~lowmask) | mask
+    uint32_t* halo_cnt;     // [NB + 1] (half b): halo counts, then starts
+    uint32_t* halo_cur;     // [NB]     (half b): halo write cursors
+    uint64_t* halo;         // [halo_cap][2] (half b): (coarse key, mask)
+    uint64_t halo_cap;
+    int* err;               // set to 1 on halo overflow
+};
+
+// One problem's match.
+struct ProbJob {
+    HalfJob A, B;
+    const uint64_t* w_a;  const uint64_t* w2_a;
+    const uint64_t* w_b;  const uint64_t* w2_b;
+    int n_a, n_b, d1;
+    int join_base;          // first CTA of this problem in the join grid (one per bucket)
+    uint64_t W, W2, Wc;
+    uint64_t* cand;
+    uint64_t cap;
+    unsigned long long* ctr;    // [4]: coarse pairs, pairs within W, candidates (within W and W2, non-trivial), trivial seen
+};
+
+// Host-side sizing of one problem's match.
+struct MatchGeom {
+    int n_a, n_b, d1, ctas_a, ctas_b;
+    uint64_t wc;
+    uint64_t hcap;          // halo capacity (entries)
+    size_t bytes;           // device workspace bytes (tables + histograms + halo)
+};
+
+// Choose bucket bits and coarse window; returns false if the window is too
+// wide for any bucket layout.
+bool match_geometry(int n_a, int n_b, uint64_t W, int ctas_a, int ctas_b, MatchGeom* g);
+
+// Bytes of one problem's buffers for geometry g (uses g.hcap).
+size_t match_bytes(const MatchGeom& g);
+
+// Lay out one problem's buffers inside `ws` (256-byte aligned pieces).
+void match_layout(const MatchGeom& g, char* ws, ProbJob* pj);
+
+// Assign grid bases, upload the job arrays (host_halves: 2*np scratch) and
+// launch count -> column scan -> bucket scan -> scatter -> join on stream s.
+// ev_mid, if given, is recorded between the scatter and the join.
+cudaError_t run_match(ProbJob* jobs, int np, ProbJob* dev_jobs, HalfJob* dev_halves,
+                      HalfJob* host_halves, cudaStream_t s, cudaEvent_t ev_mid);
+
+}  // namespace rfr

@@ -1,0 +1,275 @@
+// k_roots.cu — K-a: batched root finder (the "black box" of Section 2).
+//
+// One CTA per polynomial, one thread per root (d <= 128).
+//  1. Starting points from the Newton polygon of p (upper convex hull of
+//     (k, log|a_k|)): for each hull edge of width m, m points on a circle
+//     whose radius is the edge's geometric-mean root modulus (Bini 1996).
+//  2. Aberth-Ehrlich iteration (Jacobi form):
+//        z_i <- z_i - N_i / (1 - N_i * sum_{j != i} 1/(z_i - z_j)),
+//     N_i = p(z_i)/p'(z_i).  For |z| > 1 the reversed polynomial
+//     P(w) = w^d p(1/w) is evaluated at w = 1/z, so nothing overflows:
+//        p/p' = z P(w) / (d P(w) - w P'(w)).
+//     A root stops moving when its correction is below 4 ulp or |p(z_i)| is
+//     below the rounding-error bound of its evaluation.  In FP32-bulk mode
+//     the same iteration runs in FP32 first and FP64 finishes it.
+//  3. Two Newton steps with p evaluated in double-double arithmetic (the
+//     correction itself in FP64), so each root is kept as a DD value.
+//  4. Inclusion radius: r_i = d |p(z_i)| / prod_{j != i} |z_i - z_j|, with
+//     |p(z_i)| enlarged by the DD evaluation's error bound.  When the discs
+//     D(z_i, r_i) are pairwise disjoint each holds exactly one root of p
+//     (the Weierstrass / Braess-Hadeler inclusion theorem).
+#include "rfr_device.cuh"
+
+namespace rfr {
+
+template <typename T> struct cx { T x, y; };
+template <typename T> __device__ __forceinline__ cx<T> cxm(T x, T y) { return {x, y}; }
+template <typename T> __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T> __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T> __device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T> __device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return {a.x * s, a.y * s}; }
+template <typename T> __device__ __forceinline__ T cabs2(cx<T> a) { return a.x * a.x + a.y * a.y; }
+template <typename T> __device__ __forceinline__ T cabsv(cx<T> a);
+template <> __device__ __forceinline__ double cabsv(cx<double> a) { return hypot(a.x, a.y); }
+template <> __device__ __forceinline__ float cabsv(cx<float> a) { return hypotf(a.x, a.y); }
+template <typename T> __device__ __forceinline__ cx<T> cdivv(cx<T> a, cx<T> b) {
+    T s = fmax(fabs(b.x), fabs(b.y));
+    if (s == T(0)) return {T(0), T(0)};
+    T bx = b.x / s, by = b.y / s;
+    T m = (bx * bx + by * by) * s;
+    return {(a.x * bx + a.y * by) / m, (a.y * bx - a.x * by) / m};
+}
+template <typename T> struct eps_of;
+template <> struct eps_of<double> { static constexpr double v = 1.1102230246251565e-16; };
+template <> struct eps_of<float> { static constexpr float v = 5.9604645e-8f; };
+
+// Newton ratio p(z)/p'(z); *noise = |p(z)| is below its evaluation error bound.
+template <typename T>
+__device__ cx<T> newton_ratio(const T* a, int d, cx<T> z, bool* noise) {
+    T az = cabsv(z);
+    const T g = T(4 * (2 * d + 2)) * eps_of<T>::v;
+    if (az <= T(1)) {
+        cx<T> p = cxm<T>(a[d], 0), dp = cxm<T>(0, 0);
+        T mag = fabs(a[d]);
+        for (int k = d - 1; k >= 0; --k) {
+            dp = dp * z + p;
+            p = p * z + cxm<T>(a[k], 0);
+            mag = mag * az + fabs(a[k]);
+        }
+        *noise = cabsv(p) <= g * mag;
+        return cdivv(p, dp);
+    }
+    cx<T> w = cdivv(cxm<T>(1, 0), z);
+    T aw = cabsv(w);
+    cx<T> P = cxm<T>(a[0], 0), dP = cxm<T>(0, 0);
+    T mag = fabs(a[0]);
+    for (int k = 1; k <= d; ++k) {
+        dP = dP * w + P;
+        P = P * w + cxm<T>(a[k], 0);
+        mag = mag * aw + fabs(a[k]);
+    }
+    *noise = cabsv(P) <= g * mag;
+    cx<T> den = cscale(P, T(d)) - w * dP;
+    return cdivv(z * P, den);
+}
+
+// Aberth iterations on the shared approximations z[0..d); returns true when
+// every root stopped moving.
+template <typename T>
+__device__ bool aberth(const T* a, int d, cx<T>* z, int max_iter, int* s_flag) {
+    const int i = threadIdx.x;
+    bool done = i >= d;
+    for (int it = 0; it < max_iter; ++it) {
+        cx<T> zi = i < d ? z[i] : cxm<T>(0, 0);
+        cx<T> corr = cxm<T>(0, 0);
+        if (!done) {
+            bool noise;
+            cx<T> N = newton_ratio<T>(a, d, zi, &noise);
+            cx<T> S = cxm<T>(0, 0);
+            for (int j = 0; j < d; ++j) {
+                if (j == i) continue;
+                cx<T> df = zi - z[j];
+                T m = cabs2(df);
+                if (m > T(0)) S = S + cxm<T>(df.x / m, -df.y / m);
+            }
+            cx<T> den = cxm<T>(1, 0) - N * S;
+            corr = cdivv(N, den);
+            if (!(cabsv(corr) < T(1e30))) corr = N;               // degenerate denominator: Newton step
+            if (noise || cabsv(corr) <= T(4) * eps_of<T>::v * cabsv(zi)) done = true;
+        }
+        __syncthreads();
+        if (i < d) z[i] = zi - corr;
+        if (!__syncthreads_or(!done)) return true;
+    }
+    return false;
+}
+
+// p(Z) in double-double (|z| <= 1) or P(W), W = 1/Z (|z| > 1).
+__device__ cdd eval_dd(const double* a, int d, cdd Z, bool reversed) {
+    if (!reversed) {
+        cdd P = cdd_make(a[d], 0.0);
+        for (int k = d - 1; k >= 0; --k) P = cdd_add_d(cdd_mul(P, Z), a[k]);
+        return P;
+    }
+    cdd P = cdd_make(a[0], 0.0);
+    for (int k = 1; k <= d; ++k) P = cdd_add_d(cdd_mul(P, Z), a[k]);
+    return P;
+}
+
+__global__ void __launch_bounds__(DMAX)
+k_roots(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees,
+        int root_mode, double* __restrict__ roots, double* __restrict__ radius,
+        int32_t* __restrict__ status) {
+    __shared__ double a[DMAX + 1];
+    __shared__ float af[DMAX + 1];
+    __shared__ cx<double> z[DMAX];
+    __shared__ cx<float> zf[DMAX];
+    __shared__ int hull[DMAX + 2];
+    __shared__ int nhull, kmin, s_flag;
+    __shared__ double s_maxres;
+
+    const int prob = blockIdx.x, i = threadIdx.x;
+    const int d = degrees[prob];
+    const int64_t* c = coeffs + (size_t)prob * LDC;
+    if (i == 0) s_maxres = 0.0;
+    if (d < 1 || d > DMAX) {
+        if (i == 0) status[prob] = RFR_E_RANGE;
+        return;
+    }
+    for (int k = i; k <= d; k += blockDim.x) { a[k] = (double)c[k]; af[k] = (float)c[k]; }
+    __syncthreads();
+
+    // Newton polygon: upper hull of (k, log2|a_k|) over a_k != 0.
+    if (i == 0) {
+        int km = 0;
+        while (km < d && a[km] == 0.0) ++km;
+        kmin = km;
+        int h = 0;
+        for (int k = km; k <= d; ++k) {
+            if (a[k] == 0.0) continue;
+            double yk = log2(fabs(a[k]));
+            while (h >= 2) {
+                int o = hull[h - 2], p = hull[h - 1];
+                double yo = log2(fabs(a[o])), yp = log2(fabs(a[p]));
+                double cr = (double)(p - o) * (yk - yo) - (yp - yo) * (double)(k - o);
+                if (cr >= 0.0) --h; else break;
+            }
+            hull[h++] = k;
+        }
+        nhull = h;
+    }
+    __syncthreads();
+    if (i < d) {
+        cx<double> z0 = cxm<double>(0.0, 0.0);
+        if (i >= kmin) {
+            int e = 0;
+            while (e + 1 < nhull - 1 && hull[e + 1] <= i) ++e;
+            int k0 = hull[e], k1 = hull[e + 1], m = k1 - k0, j = i - k0;
+            double u = exp2((log2(fabs(a[k0])) - log2(fabs(a[k1]))) / (double)m);
+            double s, co;
+            sincospi(2.0 * ((double)j + 0.25) / (double)m + 0.22 * (double)e + 0.13, &s, &co);
+            z0 = cxm<double>(u * co, u * s);
+        }
+        z[i] = z0;
+        zf[i] = cxm<float>((float)z0.x, (float)z0.y);
+    }
+    __syncthreads();
+
+    bool conv;
+    if (root_mode == RFR_ROOTS_FP32_BULK) {
+        aberth<float>(af, d, zf, 400, &s_flag);
+        if (i < d) z[i] = cxm<double>((double)zf[i].x, (double)zf[i].y);
+        __syncthreads();
+        conv = aberth<double>(a, d, z, 200, &s_flag);
+    } else {
+        conv = aberth<double>(a, d, z, 600, &s_flag);
+    }
+
+    // Double-double Newton polish.
+    cdd Z = cdd_make(0.0, 0.0);
+    if (i < d) Z = cdd_make(z[i].x, z[i].y);
+    for (int it = 0; it < 2 && i < d; ++it) {
+        cx<double> zh = cxm<double>(Z.re.hi, Z.im.hi);
+        bool rev = cabsv(zh) > 1.0;
+        bool noise;
+        cx<double> Nf = newton_ratio<double>(a, d, zh, &noise);   // FP64 fallback for the derivative part
+        cx<double> N;
+        if (!rev) {
+            cdd P = eval_dd(a, d, Z, false);
+            // p'(z) in FP64
+            cx<double> p = cxm<double>(a[d], 0), dp = cxm<double>(0, 0);
+            for (int k = d - 1; k >= 0; --k) { dp = dp * zh + p; p = p * zh + cxm<double>(a[k], 0); }
+            N = cdivv(cxm<double>(P.re.hi, P.im.hi), dp);
+        } else {
+            cdd W = cdd_inv(Z);
+            cdd P = eval_dd(a, d, W, true);
+            cx<double> wh = cxm<double>(W.re.hi, W.im.hi);
+            cx<double> Pp = cxm<double>(a[0], 0), dP = cxm<double>(0, 0);
+            for (int k = 1; k <= d; ++k) { dP = dP * wh + Pp; Pp = Pp * wh + cxm<double>(a[k], 0); }
+            cx<double> Ph = cxm<double>(P.re.hi, P.im.hi);
+            N = cdivv(zh * Ph, cscale(Ph, (double)d) - wh * dP);
+        }
+        if (!(cabsv(N) < 1e300)) N = Nf;
+        Z.re = dd_add_d(Z.re, -N.x);
+        Z.im = dd_add_d(Z.im, -N.y);
+    }
+    __syncthreads();
+    if (i < d) z[i] = cxm<double>(Z.re.hi, Z.im.hi);
+    __syncthreads();
+
+    // Inclusion radius.
+    if (i < d) {
+        cx<double> zh = z[i];
+        double az = cabsv(zh);
+        bool rev = az > 1.0;
+        double lp, res;
+        if (!rev) {
+            cdd P = eval_dd(a, d, Z, false);
+            double mag = 0.0;
+            for (int k = d; k >= 0; --k) mag = mag * az + fabs(a[k]);
+            double pv = hypot(P.re.hi, P.im.hi);
+            double err = (double)(2 * d + 8) * 0x1p-100 * mag;
+            lp = log2(pv + err);
+            res = pv / mag;
+        } else {
+            cdd W = cdd_inv(Z);
+            cdd P = eval_dd(a, d, W, true);
+            double aw = 1.0 / az, mag = 0.0;
+            for (int k = 0; k <= d; ++k) mag = mag * aw + fabs(a[k]);
+            double pv = hypot(P.re.hi, P.im.hi);
+            double err = (double)(2 * d + 8) * 0x1p-100 * mag;
+            lp = (double)d * log2(az) + log2(pv + err);
+            res = pv / mag;
+        }
+        double lprod = 0.0;
+        bool coincide = false;
+        for (int j = 0; j < d; ++j) {
+            if (j == i) continue;
+            double dist = cabsv(zh - z[j]);
+            if (dist == 0.0) coincide = true; else lprod += log2(dist);
+        }
+        double r = coincide ? INFINITY : exp2(log2((double)d) + lp - lprod) * 1.01 + 0x1p-96 * az;
+        if (d == 1) r = 0x1p-96 * az + 0x1p-100;
+        double* out = roots + ((size_t)prob * DMAX + i) * 4;
+        out[0] = Z.re.hi; out[1] = Z.re.lo; out[2] = Z.im.hi; out[3] = Z.im.lo;
+        radius[(size_t)prob * DMAX + i] = r;
+        atomicMax((unsigned long long*)&s_maxres, __double_as_longlong(res));
+    }
+    __syncthreads();
+    if (i == 0) status[prob] = conv ? RFR_OK : RFR_E_NO_CONVERGENCE;
+}
+
+}  // namespace rfr
+
+using namespace rfr;
+
+extern "C" int rfr_stage_roots(const int64_t* coeffs, const int32_t* degrees, int batch,
+                               int root_mode, double* roots, double* radius,
+                               int32_t* status, void* stream) {
+    if (batch < 0 || !coeffs || !degrees || !roots || !radius || !status) return RFR_E_INVALID;
+    if (batch == 0) return RFR_OK;
+    k_roots<<<batch, DMAX, 0, (cudaStream_t)stream>>>(coeffs, degrees, root_mode, roots, radius, status);
+    return cudaGetLastError() == cudaSuccess ? RFR_OK : RFR_E_CUDA;
+}

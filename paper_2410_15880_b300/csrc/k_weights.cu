@@ -1,0 +1,180 @@
+// k_weights.cu — K-b: real factorisation (Eq. 1) and fixed-point weights.
+//
+// One CTA per polynomial, one thread per root.
+//  * Disjointness: every pair of inclusion discs must be disjoint, else the
+//    roots are not separated (RFR_E_ROOTS).
+//  * Real or not: a root whose disc misses the real axis (|Im z| > r) is not
+//    real.  A root with |Im z| <= r is real when no other disc comes within
+//    3r of it: the conjugate of its root lies within 3r of z, hence in the
+//    same disc, which holds only one root.  Anything else is undecidable
+//    (RFR_E_ROOTS).
+//  * Each root with Im z > 0 is paired with the Im z < 0 root nearest its
+//    conjugate; the pairing must be a bijection and the partner disc must
+//    meet the conjugate disc.
+//  * Elements in canonical order: real roots ascending, then pairs by
+//    (Re z, Im z).  Tr_1 part t1 = u or Re z + Re z' (Eq. 4), Tr_2 part
+//    t2 = u^2 or Re z^2 + Re z'^2, both in double-double; each is scaled to
+//    w = round(frac(t) * 2^64) mod 2^64, i.e. Eq. 18 with M = 2^64 and
+//    rounding in place of floor.
+//  * Windows: a subset sum of the w's differs from 2^64 x (the true Tr_1 of
+//    that subset) by at most 2^64 * sum_k err_k + n/2, with err_k the
+//    element's radius (or the two radii of a pair); W adds slack to that.
+//    W2 is the same bound for Tr_2, err2 = (2|z| + r) r per root.
+#include "rfr_device.cuh"
+
+namespace rfr {
+
+__global__ void __launch_bounds__(DMAX)
+k_weights(const int32_t* __restrict__ degrees, const double* __restrict__ roots,
+          const double* __restrict__ radius, const int32_t* __restrict__ root_status,
+          double eps_override, rfr_plan* __restrict__ plans) {
+    __shared__ double zx[DMAX], zy[DMAX], rr[DMAX];
+    __shared__ int cls[DMAX];        // 0 real, 1 upper, 2 lower
+    __shared__ int partner[DMAX], taken[DMAX];
+    __shared__ int s_err, s_r, s_c;
+    __shared__ double s_e1, s_e2, s_maxr;
+    const int prob = blockIdx.x, i = threadIdx.x;
+    const int d = degrees[prob];
+    rfr_plan* P = plans + prob;
+    const int rs = root_status[prob];
+    if (rs != RFR_OK || d < 1 || d > DMAX) {
+        if (i == 0) {
+            P->status = rs != RFR_OK ? rs : RFR_E_RANGE;
+            P->degree = d;
+            P->n = P->r = P->c = P->n_a = P->n_b = 0;
+        }
+        return;
+    }
+    const double* R = roots + (size_t)prob * DMAX * 4;
+    if (i < d) {
+        zx[i] = R[4 * i];
+        zy[i] = R[4 * i + 2];
+        rr[i] = radius[(size_t)prob * DMAX + i];
+        taken[i] = 0;
+        partner[i] = -1;
+    }
+    if (i == 0) { s_err = 0; s_r = 0; s_c = 0; s_e1 = 0.0; s_e2 = 0.0; s_maxr = 0.0; }
+    __syncthreads();
+
+    if (i < d) {
+        double ri = rr[i];
+        bool isolated = isfinite(ri), strong = true;
+        for (int j = 0; j < d; ++j) {
+            if (j == i) continue;
+            double dist = hypot(zx[i] - zx[j], zy[i] - zy[j]);
+            if (!(dist > ri + rr[j])) isolated = false;
+            if (!(dist > 3.0 * ri + rr[j])) strong = false;
+        }
+        int k;
+        if (!isolated) k = -1;
+        else if (fabs(zy[i]) > ri) k = zy[i] > 0.0 ? 1 : 2;
+        else k = strong ? 0 : -1;
+        cls[i] = k;
+        if (k < 0) atomicExch(&s_err, 1);
+        atomicMax((unsigned long long*)&s_maxr, __double_as_longlong(isfinite(ri) ? ri : 1e308));
+    }
+    __syncthreads();
+    if (s_err) {
+        if (i == 0) { P->status = RFR_E_ROOTS; P->degree = d; P->n = 0; P->max_radius = s_maxr; }
+        return;
+    }
+    if (i < d && cls[i] == 1) {
+        int best = -1;
+        double bd = INFINITY;
+        for (int j = 0; j < d; ++j) {
+            if (cls[j] != 2) continue;
+            double dist = hypot(zx[j] - zx[i], zy[j] + zy[i]);
+            if (dist < bd) { bd = dist; best = j; }
+        }
+        if (best < 0 || !(bd <= rr[i] + rr[best])) atomicExch(&s_err, 1);
+        else { partner[i] = best; atomicAdd(&taken[best], 1); }
+    }
+    __syncthreads();
+    if (i < d && cls[i] == 2 && taken[i] != 1) atomicExch(&s_err, 1);
+    if (i < d && cls[i] == 0) atomicAdd(&s_r, 1);
+    if (i < d && cls[i] == 1) atomicAdd(&s_c, 1);
+    __syncthreads();
+    if (s_err || s_r + 2 * s_c != d) {
+        if (i == 0) { P->status = RFR_E_ROOTS; P->degree = d; P->n = 0; P->max_radius = s_maxr; }
+        return;
+    }
+    const int r = s_r, c = s_c, n = r + c;
+
+    if (i < d && cls[i] != 2) {
+        // canonical position
+        int rank = 0;
+        for (int j = 0; j < d; ++j) {
+            if (j == i || cls[j] != cls[i]) continue;
+            bool before = cls[i] == 0
+                ? (zx[j] < zx[i] || (zx[j] == zx[i] && j < i))
+                : (zx[j] < zx[i] || (zx[j] == zx[i] && (zy[j] < zy[i] || (zy[j] == zy[i] && j < i))));
+            rank += before;
+        }
+        const int k = cls[i] == 0 ? rank : r + rank;
+        const double* Ri = R + 4 * i;
+        dd re = {Ri[0], Ri[1]}, im = {Ri[2], Ri[3]};
+        dd t1, t2;
+        double e1, e2;
+        if (cls[i] == 0) {
+            t1 = re;
+            t2 = dd_mul(re, re);
+            e1 = rr[i];
+            e2 = (2.0 * fabs(re.hi) + rr[i]) * rr[i];
+        } else {
+            const int j = partner[i];
+            const double* Rj = R + 4 * j;
+            dd rej = {Rj[0], Rj[1]}, imj = {Rj[2], Rj[3]};
+            t1 = dd_add(re, rej);
+            t2 = dd_add(dd_sub(dd_mul(re, re), dd_mul(im, im)), dd_sub(dd_mul(rej, rej), dd_mul(imj, imj)));
+            e1 = rr[i] + rr[j];
+            double azi = hypot(re.hi, im.hi), azj = hypot(rej.hi, imj.hi);
+            e2 = (2.0 * azi + rr[i]) * rr[i] + (2.0 * azj + rr[j]) * rr[j];
+        }
+        e1 += 0x1p-100 * (fabs(t1.hi) + 1.0);
+        e2 += 0x1p-98 * (fabs(t2.hi) + 1.0);
+        P->w[k] = dd_frac_fixed64(t1);
+        P->w2[k] = dd_frac_fixed64(t2);
+        P->kind[k] = cls[i] == 0 ? 1 : 2;
+        P->root0[k] = (uint8_t)i;
+        P->root1[k] = (uint8_t)(cls[i] == 0 ? i : partner[i]);
+        atomicAdd(&s_e1, e1);
+        atomicAdd(&s_e2, e2);
+    }
+    __syncthreads();
+    if (i == 0) {
+        // W = ceil(2^64 * sum err1 * (1 + 2^-20)) + n + 2, saturating at 2^62.
+        double w1 = ldexp(s_e1 * (1.0 + 0x1p-20), 64);
+        uint64_t W = w1 >= 0x1p62 ? (1ull << 62) : (uint64_t)ceil(w1) + (uint64_t)n + 2ull;
+        if (eps_override > 0.0) {
+            double wo = ldexp(eps_override, 64);
+            W = wo >= 0x1p62 ? (1ull << 62) : (uint64_t)ceil(wo);
+        }
+        double w2 = ldexp(s_e2 * (1.0 + 0x1p-20), 64);
+        uint64_t W2 = w2 >= 0x1p61 ? (1ull << 63) : (uint64_t)ceil(w2) + (uint64_t)n + 2ull;
+        P->status = RFR_OK;
+        P->degree = d;
+        P->n = n; P->r = r; P->c = c;
+        P->n_a = (n - 1) / 2;
+        P->n_b = (n - 1) - (n - 1) / 2;
+        P->window = W;
+        P->window2 = W2;
+        P->max_radius = s_maxr;
+        P->sum_err1 = s_e1;
+        P->sum_err2 = s_e2;
+    }
+}
+
+}  // namespace rfr
+
+using namespace rfr;
+
+extern "C" int rfr_stage_weights(const int64_t* coeffs, const int32_t* degrees, int batch,
+                                 const double* roots, const double* radius,
+                                 const int32_t* root_status, double eps_override,
+                                 rfr_plan* plans, void* stream) {
+    (void)coeffs;
+    if (batch < 0 || !degrees || !roots || !radius || !root_status || !plans) return RFR_E_INVALID;
+    if (batch == 0) return RFR_OK;
+    k_weights<<<batch, DMAX, 0, (cudaStream_t)stream>>>(degrees, roots, radius, root_status, eps_override, plans);
+    return cudaGetLastError() == cudaSuccess ? RFR_OK : RFR_E_CUDA;
+}

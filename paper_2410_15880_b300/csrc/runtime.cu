@@ -1,0 +1,823 @@
+// runtime.cu — host runtime of the RFR library: context, batch pipeline,
+// memory budget, serving queue (continuous batching) and the C ABI of rfr.h.
+//
+// Pipeline for a batch of polynomials on one stream:
+//   validate (monic, range, square-free mod primes)      host
+//   H2D coefficients                                     copy
+//   K-a roots, K-b weights                               kernels
+//   D2H plans -> per-problem table geometry             host (sync 1)
+//   K-c/K-d/K-e match for every problem, in sub-batches  kernels
+//     that fit the memory budget
+//   D2H candidate counts and candidates                  host (sync 2)
+//   K-f verify all candidates                            kernel
+//   D2H verdicts -> atoms of the verified divisors       host (sync 3)
+//   K-f on the atoms, returning their integer polynomials kernel
+//   D2H factors -> canonical order                       host (sync 4)
+#include "rfr_device.cuh"
+#include "k_match.cuh"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+extern "C" int rfr_stage_roots(const int64_t*, const int32_t*, int, int, double*, double*, int32_t*, void*);
+extern "C" int rfr_stage_weights(const int64_t*, const int32_t*, int, const double*, const double*,
+                                 const int32_t*, double, rfr_plan*, void*);
+extern "C" int rfr_stage_verify(const int64_t*, const int32_t*, const double*, const rfr_plan*,
+                                const int32_t*, const uint64_t*, const uint64_t*, int, int32_t*,
+                                int64_t*, void*);
+
+namespace rfr {
+
+// ---------------------------------------------------------------- helpers
+static uint64_t mulmod(uint64_t a, uint64_t b, uint64_t m) { return (uint64_t)((unsigned __int128)a * b % m); }
+static uint64_t powmod(uint64_t a, uint64_t e, uint64_t m) {
+    uint64_t r = 1;
+    for (a %= m; e; e >>= 1, a = mulmod(a, a, m)) if (e & 1) r = mulmod(r, a, m);
+    return r;
+}
+// gcd(p, p') over F_l is 1?  (p monic)
+static bool coprime_mod(const int64_t* p, int d, uint64_t l) {
+    std::vector<uint64_t> a(d + 1), b(d);
+    for (int i = 0; i <= d; ++i) { int64_t v = p[i] % (int64_t)l; a[i] = v < 0 ? v + l : v; }
+    for (int i = 1; i <= d; ++i) b[i - 1] = mulmod(a[i], (uint64_t)i % l, l);
+    auto trim = [](std::vector<uint64_t>& v) { while (v.size() > 1 && v.back() == 0) v.pop_back(); };
+    trim(a); trim(b);
+    if (b.size() == 1 && b[0] == 0) return false;
+    while (!(b.size() == 1 && b[0] == 0)) {
+        if (b.size() == 1) return true;                     // nonzero constant
+        uint64_t inv = powmod(b.back(), l - 2, l);
+        while (a.size() >= b.size() && !(a.size() == 1 && a[0] == 0)) {
+            uint64_t c = mulmod(a.back(), inv, l);
+            size_t sh = a.size() - b.size();
+            for (size_t j = 0; j < b.size(); ++j) a[sh + j] = (a[sh + j] + l - mulmod(c, b[j], l)) % l;
+            a.pop_back();
+            trim(a);
+            if (a.empty()) a.push_back(0);
+        }
+        std::swap(a, b);
+    }
+    return a.size() == 1;   // gcd is a nonzero constant
+}
+static bool squarefree_check(const int64_t* p, int d) {
+    static const uint64_t primes[] = {2147483647ull, 2147483629ull, 2147483587ull, 2147483579ull, 2147483563ull};
+    for (uint64_t l : primes)
+        if (coprime_mod(p, d, l)) return true;
+    return false;
+}
+
+struct Bits {
+    uint64_t lo = 0, hi = 0;
+    bool get(int k) const { return k < 64 ? (lo >> k) & 1 : (hi >> (k - 64)) & 1; }
+    void set(int k) { if (k < 64) lo |= 1ull << k; else hi |= 1ull << (k - 64); }
+    Bits operator&(const Bits& o) const { return {lo & o.lo, hi & o.hi}; }
+    Bits operator~() const { return {~lo, ~hi}; }
+    bool operator==(const Bits& o) const { return lo == o.lo && hi == o.hi; }
+};
+static Bits full_bits(int n) {
+    Bits b;
+    b.lo = n >= 64 ? ~0ull : (n ? (~0ull >> (64 - n)) : 0ull);
+    b.hi = n > 64 ? (~0ull >> (128 - n)) : 0ull;
+    return b;
+}
+
+// ---------------------------------------------------------------- allocation
+struct DevAlloc {
+    rfr_alloc_fn fa = nullptr;
+    rfr_free_fn ff = nullptr;
+    void* user = nullptr;
+    void* get(size_t bytes, cudaStream_t s) {
+        if (bytes == 0) bytes = 256;
+        if (fa) return fa(bytes, user, (void*)s);
+        void* p = nullptr;
+        if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+        return p;
+    }
+    void put(void* p, size_t bytes, cudaStream_t s) {
+        if (!p) return;
+        if (ff) ff(p, bytes, user, (void*)s);
+        else cudaFreeAsync(p, s);
+    }
+};
+
+struct Item {
+    const int64_t* coeffs;
+    int degree;
+    int status;
+    rfr_factors* out;
+};
+
+// Per-problem working state inside a batch.
+struct Work {
+    int item;                // index into the batch's items
+    int slot;                // index into the device arrays
+    rfr_plan plan;           // copied back after K-b
+    MatchGeom geom;
+    bool full_halo = false;
+    bool matched = false;
+    uint64_t ctr[6] = {0, 0, 0, 0, 0, 0};
+    std::vector<uint64_t> cand;
+    std::vector<Bits> verified;
+    std::vector<Bits> atoms;
+    std::vector<std::vector<int64_t>> factors;
+    int status = RFR_OK;
+};
+
+struct Ctx;
+
+// One pipeline = one stream plus its reusable buffers.
+struct Pipeline {
+    Ctx* ctx = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev[8] = {};
+    int cap = 0;                      // problems the device arrays hold
+    int64_t* d_coeffs = nullptr;
+    int32_t* d_deg = nullptr;
+    double* d_roots = nullptr;
+    double* d_radius = nullptr;
+    int32_t* d_rstat = nullptr;
+    rfr_plan* d_plans = nullptr;
+    int64_t* h_coeffs = nullptr;      // pinned
+    int32_t* h_deg = nullptr;         // pinned
+    rfr_plan* h_plans = nullptr;      // pinned
+    bool init(Ctx* c);
+    void destroy();
+    bool reserve(int n);
+    int run(std::vector<Item>& items);
+};
+
+struct Request {
+    uint64_t ticket;
+    std::vector<int64_t> coeffs;
+    int degree;
+    int status = RFR_PENDING;
+    bool cancelled = false, running = false, done = false;
+    rfr_factors result{};
+};
+
+struct Ctx {
+    rfr_config cfg;
+    int device = 0;
+    DevAlloc alloc;
+    size_t budget = 0;
+    std::mutex budget_mu;
+    std::condition_variable budget_cv;
+    size_t budget_used = 0;
+    std::mutex sync_mu;               // serialises rfr_factor / rfr_factor_batch
+    Pipeline sync_pipe;
+    // serving
+    std::mutex q_mu;
+    std::condition_variable q_cv, done_cv;
+    std::deque<Request*> pending;
+    std::unordered_map<uint64_t, Request*> reqs;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    int running_batches = 0;
+    std::vector<std::thread> workers;
+    std::vector<std::unique_ptr<Pipeline>> worker_pipes;
+
+    // Reserve `bytes` of the device budget; waits while other batches hold it.
+    bool reserve(size_t bytes) {
+        std::unique_lock<std::mutex> lk(budget_mu);
+        if (bytes > budget) return false;
+        budget_cv.wait(lk, [&] { return budget_used + bytes <= budget || stop; });
+        if (stop) return false;
+        budget_used += bytes;
+        return true;
+    }
+    void release(size_t bytes) {
+        std::lock_guard<std::mutex> lk(budget_mu);
+        budget_used -= bytes;
+        budget_cv.notify_all();
+    }
+};
+
+static int cuda_ok(cudaError_t e) { return e == cudaSuccess ? RFR_OK : RFR_E_CUDA; }
+
+bool Pipeline::init(Ctx* c) {
+    ctx = c;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return false;
+    for (auto& e : ev) if (cudaEventCreate(&e) != cudaSuccess) return false;
+    return true;
+}
+
+void Pipeline::destroy() {
+    if (s) cudaStreamSynchronize(s);
+    auto put = [&](void* p) { if (p) ctx->alloc.put(p, 0, s); };
+    put(d_coeffs); put(d_deg); put(d_roots); put(d_radius); put(d_rstat); put(d_plans);
+    if (s) cudaStreamSynchronize(s);
+    if (h_coeffs) cudaFreeHost(h_coeffs);
+    if (h_deg) cudaFreeHost(h_deg);
+    if (h_plans) cudaFreeHost(h_plans);
+    for (auto& e : ev) if (e) cudaEventDestroy(e);
+    if (s) cudaStreamDestroy(s);
+    s = nullptr;
+}
+
+bool Pipeline::reserve(int n) {
+    if (n <= cap) return true;
+    int nc = std::max(n, std::max(16, cap * 2));
+    cudaStreamSynchronize(s);
+    auto put = [&](void* p) { if (p) ctx->alloc.put(p, 0, s); };
+    put(d_coeffs); put(d_deg); put(d_roots); put(d_radius); put(d_rstat); put(d_plans);
+    if (h_coeffs) cudaFreeHost(h_coeffs);
+    if (h_deg) cudaFreeHost(h_deg);
+    if (h_plans) cudaFreeHost(h_plans);
+    d_coeffs = (int64_t*)ctx->alloc.get((size_t)nc * LDC * 8, s);
+    d_deg = (int32_t*)ctx->alloc.get((size_t)nc * 4, s);
+    d_roots = (double*)ctx->alloc.get((size_t)nc * DMAX * 32, s);
+    d_radius = (double*)ctx->alloc.get((size_t)nc * DMAX * 8, s);
+    d_rstat = (int32_t*)ctx->alloc.get((size_t)nc * 4, s);
+    d_plans = (rfr_plan*)ctx->alloc.get((size_t)nc * sizeof(rfr_plan), s);
+    bool ok = d_coeffs && d_deg && d_roots && d_radius && d_rstat && d_plans;
+    ok = ok && cudaMallocHost(&h_coeffs, (size_t)nc * LDC * 8) == cudaSuccess;
+    ok = ok && cudaMallocHost(&h_deg, (size_t)nc * 4) == cudaSuccess;
+    ok = ok && cudaMallocHost(&h_plans, (size_t)nc * sizeof(rfr_plan)) == cudaSuccess;
+    cap = ok ? nc : 0;
+    return ok;
+}
+
+static double ms_between(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) { cudaGetLastError(); return 0.0; }
+    return ms;
+}
+
+static void fill_factors(rfr_factors* out, const std::vector<std::vector<int64_t>>& fs) {
+    out->n_factors = (int)fs.size();
+    size_t tot = 0;
+    for (auto& f : fs) tot += f.size();
+    out->degrees = (int*)malloc(sizeof(int) * std::max<size_t>(1, fs.size()));
+    out->coeffs = (int64_t*)malloc(sizeof(int64_t) * std::max<size_t>(1, tot));
+    size_t o = 0;
+    for (size_t i = 0; i < fs.size(); ++i) {
+        out->degrees[i] = (int)fs[i].size() - 1;
+        memcpy(out->coeffs + o, fs[i].data(), fs[i].size() * 8);
+        o += fs[i].size();
+    }
+}
+
+static void canonical_sort(std::vector<std::vector<int64_t>>& fs) {
+    std::sort(fs.begin(), fs.end(), [](const std::vector<int64_t>& a, const std::vector<int64_t>& b) {
+        if (a.size() != b.size()) return a.size() < b.size();
+        for (size_t i = 0; i + 1 < a.size(); ++i) if (a[i] != b[i]) return a[i] < b[i];
+        return false;
+    });
+}
+
+// Candidate CTAs per half: spread about four CTAs per SM over the sub-batch.
+static int part_ctas(int h, double share_total_elems) {
+    const double target = 4.0 * 148.0;
+    double want = std::ldexp(1.0, h) * target / std::max(1.0, share_total_elems);
+    int c = 1;
+    while (c * 2 <= want && c < 512 && ((uint64_t)c * 2 * 64) <= (1ull << h)) c *= 2;
+    return c;
+}
+
+int Pipeline::run(std::vector<Item>& items) {
+    Ctx& C = *ctx;
+    const bool timing = C.cfg.timing != 0;
+    auto t_host0 = std::chrono::steady_clock::now();
+    std::vector<Work> work;
+    // ---- validate
+    for (size_t i = 0; i < items.size(); ++i) {
+        Item& it = items[i];
+        memset(it.out, 0, sizeof(rfr_factors));
+        it.status = RFR_OK;
+        if (!it.coeffs || it.degree < 1 || it.degree > DMAX) { it.status = it.coeffs ? RFR_E_RANGE : RFR_E_INVALID; continue; }
+        if (it.coeffs[it.degree] != 1) { it.status = RFR_E_NOT_MONIC; continue; }
+        bool range = true;
+        for (int k = 0; k <= it.degree; ++k)
+            if (it.coeffs[k] >= (1ll << 53) || it.coeffs[k] <= -(1ll << 53)) range = false;
+        if (!range) { it.status = RFR_E_RANGE; continue; }
+        if (it.degree == 1) {
+            std::vector<std::vector<int64_t>> f = {{it.coeffs[0], 1}};
+            fill_factors(it.out, f);
+            it.out->diag.n = 1; it.out->diag.r = 1;
+            continue;
+        }
+        if (!squarefree_check(it.coeffs, it.degree)) { it.status = RFR_E_NOT_SQUAREFREE; continue; }
+        Work w;
+        w.item = (int)i;
+        w.slot = (int)work.size();
+        work.push_back(std::move(w));
+    }
+    const int B = (int)work.size();
+    if (B == 0) return RFR_OK;
+    if (!reserve(B)) return RFR_E_OOM;
+    for (auto& w : work) {
+        const Item& it = items[w.item];
+        int64_t* row = h_coeffs + (size_t)w.slot * LDC;
+        memset(row, 0, LDC * 8);
+        memcpy(row, it.coeffs, (it.degree + 1) * 8);
+        h_deg[w.slot] = it.degree;
+    }
+    cudaEventRecord(ev[0], s);
+    int rc = cuda_ok(cudaMemcpyAsync(d_coeffs, h_coeffs, (size_t)B * LDC * 8, cudaMemcpyHostToDevice, s));
+    if (rc == RFR_OK) rc = cuda_ok(cudaMemcpyAsync(d_deg, h_deg, (size_t)B * 4, cudaMemcpyHostToDevice, s));
+    if (rc == RFR_OK) rc = rfr_stage_roots(d_coeffs, d_deg, B, C.cfg.root_mode, d_roots, d_radius, d_rstat, s);
+    cudaEventRecord(ev[1], s);
+    if (rc == RFR_OK) rc = rfr_stage_weights(d_coeffs, d_deg, B, d_roots, d_radius, d_rstat, C.cfg.eps_override, d_plans, s);
+    cudaEventRecord(ev[2], s);
+    if (rc == RFR_OK) rc = cuda_ok(cudaMemcpyAsync(h_plans, d_plans, (size_t)B * sizeof(rfr_plan), cudaMemcpyDeviceToHost, s));
+    if (rc == RFR_OK) rc = cuda_ok(cudaStreamSynchronize(s));
+    if (rc != RFR_OK) return rc;
+    double t_roots = timing ? ms_between(ev[0], ev[1]) : 0, t_weights = timing ? ms_between(ev[1], ev[2]) : 0;
+    double t_enum = 0, t_match = 0, t_verify = 0, t_atoms = 0;
+
+    // ---- plan the match
+    std::vector<int> todo;
+    for (auto& w : work) {
+        w.plan = h_plans[w.slot];
+        if (w.plan.status != RFR_OK) { w.status = w.plan.status; continue; }
+        if (w.plan.n <= 1) continue;                      // a single element: irreducible
+        if (w.plan.n_b > 32) { w.status = RFR_E_BUDGET; continue; }
+        todo.push_back(w.slot);
+    }
+    const uint64_t cap = std::max<uint64_t>(1, C.cfg.max_candidates);
+    while (!todo.empty()) {
+        // take a sub-batch that fits the budget
+        double tot_elems = 0;
+        for (int sl : todo) tot_elems += std::ldexp(1.0, work[sl].plan.n_a) + std::ldexp(1.0, work[sl].plan.n_b);
+        std::vector<int> sub, rest;
+        size_t bytes = 0;
+        for (int sl : todo) {
+            Work& w = work[sl];
+            MatchGeom g;
+            if (!match_geometry(w.plan.n_a, w.plan.n_b, w.plan.window, part_ctas(w.plan.n_a, tot_elems),
+                                part_ctas(w.plan.n_b, tot_elems), &g)) { w.status = RFR_E_WINDOW; continue; }
+            if (w.full_halo) { g.hcap = 1ull << g.n_b; g.bytes = match_bytes(g); }
+            const size_t need = g.bytes + (size_t)cap * 8 + 6 * 8 + 512;
+            if (need > C.budget) { w.status = RFR_E_BUDGET; continue; }
+            if (!sub.empty() && bytes + need > C.budget / std::max(1, C.cfg.max_inflight)) { rest.push_back(sl); continue; }
+            w.geom = g;
+            bytes += need;
+            sub.push_back(sl);
+        }
+        todo.swap(rest);
+        if (sub.empty()) continue;
+        if (!C.reserve(bytes)) { for (int sl : sub) work[sl].status = RFR_E_BUDGET; continue; }
+        const int np = (int)sub.size();
+        const size_t jobs_bytes = (size_t)np * sizeof(ProbJob) + 2 * (size_t)np * sizeof(HalfJob) + 1024;
+        char* ws = (char*)C.alloc.get(bytes + jobs_bytes, s);
+        if (!ws) { C.release(bytes); for (int sl : sub) work[sl].status = RFR_E_OOM; continue; }
+        std::vector<ProbJob> jobs(np);
+        std::vector<HalfJob> halves(2 * np);
+        char* p = ws;
+        ProbJob* d_jobs = (ProbJob*)p; p += ((np * sizeof(ProbJob)) + 255) & ~(size_t)255;
+        HalfJob* d_halves = (HalfJob*)p; p += ((2 * np * sizeof(HalfJob)) + 255) & ~(size_t)255;
+        for (int i = 0; i < np; ++i) {
+            Work& w = work[sub[i]];
+            ProbJob& pj = jobs[i];
+            memset(&pj, 0, sizeof(pj));
+            match_layout(w.geom, p, &pj);
+            p += w.geom.bytes;
+            uint64_t* cbuf = (uint64_t*)p; p += ((size_t)cap * 8 + 255) & ~(size_t)255;
+            uint64_t* ctr = (uint64_t*)p; p += 256;
+            const rfr_plan* dp = d_plans + w.slot;
+            pj.A.w = dp->w;                     pj.B.w = dp->w + w.plan.n_a;
+            pj.w_a = dp->w;                     pj.w2_a = dp->w2;
+            pj.w_b = dp->w + w.plan.n_a;        pj.w2_b = dp->w2 + w.plan.n_a;
+            pj.W = w.plan.window;               pj.W2 = w.plan.window2;
+            pj.cand = cbuf;                     pj.cap = cap;
+            pj.ctr = (unsigned long long*)ctr;
+            pj.A.err = pj.B.err = (int*)(ctr + 4);
+            cudaMemsetAsync(ctr, 0, 6 * 8, s);
+            cudaMemsetAsync(pj.B.halo_cnt, 0, (((size_t)1 << w.geom.d1) + 1) * 4, s);
+        }
+        cudaEventRecord(ev[3], s);
+        rc = cuda_ok(run_match(jobs.data(), np, d_jobs, d_halves, halves.data(), s, ev[4]));
+        cudaEventRecord(ev[5], s);
+        std::vector<uint64_t> h_ctr(6 * (size_t)np);
+        for (int i = 0; i < np && rc == RFR_OK; ++i)
+            rc = cuda_ok(cudaMemcpyAsync(&h_ctr[6 * i], jobs[i].ctr, 6 * 8, cudaMemcpyDeviceToHost, s));
+        if (rc == RFR_OK) rc = cuda_ok(cudaStreamSynchronize(s));
+        if (timing && rc == RFR_OK) { t_enum += ms_between(ev[3], ev[4]); t_match += ms_between(ev[4], ev[5]); }
+        for (int i = 0; i < np && rc == RFR_OK; ++i) {
+            Work& w = work[sub[i]];
+            memcpy(w.ctr, &h_ctr[6 * i], sizeof(w.ctr));
+            if (w.ctr[4]) { w.full_halo = true; todo.push_back(w.slot); continue; }   // retry with a full halo
+            if (w.ctr[3] == 0) { w.status = RFR_E_INTERNAL; continue; }               // empty pattern must match
+            if (w.ctr[2] > cap) { w.status = RFR_E_CAND_OVERFLOW; continue; }
+            w.cand.resize(w.ctr[2]);
+            if (w.ctr[2]) rc = cuda_ok(cudaMemcpyAsync(w.cand.data(), jobs[i].cand, w.ctr[2] * 8, cudaMemcpyDeviceToHost, s));
+            w.matched = true;
+        }
+        if (rc == RFR_OK) rc = cuda_ok(cudaStreamSynchronize(s));
+        C.alloc.put(ws, bytes + jobs_bytes, s);
+        C.release(bytes);
+        if (rc != RFR_OK) return rc;
+    }
+
+    // ---- verify candidates, then extract atoms (two K-f passes)
+    auto run_verify = [&](std::vector<int32_t>& jp, std::vector<uint64_t>& jlo, std::vector<uint64_t>& jhi,
+                          std::vector<int32_t>& res, std::vector<int64_t>* coeffs_out) -> int {
+        const int J = (int)jp.size();
+        res.assign(J, 0);
+        if (J == 0) return RFR_OK;
+        const size_t bytes = (size_t)J * (4 + 8 + 8 + 4) + (coeffs_out ? (size_t)J * LDC * 8 : 0) + 1024;
+        char* buf = (char*)C.alloc.get(bytes, s);
+        if (!buf) return RFR_E_OOM;
+        int32_t* dp = (int32_t*)buf;
+        uint64_t* dlo = (uint64_t*)(((uintptr_t)(dp + J) + 15) & ~(uintptr_t)15);
+        uint64_t* dhi = dlo + J;
+        int32_t* dres = (int32_t*)(dhi + J);
+        int64_t* dco = coeffs_out ? (int64_t*)(((uintptr_t)(dres + J) + 15) & ~(uintptr_t)15) : nullptr;
+        int r = cuda_ok(cudaMemcpyAsync(dp, jp.data(), J * 4, cudaMemcpyHostToDevice, s));
+        if (r == RFR_OK) r = cuda_ok(cudaMemcpyAsync(dlo, jlo.data(), J * 8, cudaMemcpyHostToDevice, s));
+        if (r == RFR_OK) r = cuda_ok(cudaMemcpyAsync(dhi, jhi.data(), J * 8, cudaMemcpyHostToDevice, s));
+        if (r == RFR_OK) r = rfr_stage_verify(d_coeffs, d_deg, d_roots, d_plans, dp, dlo, dhi, J, dres, dco, s);
+        if (r == RFR_OK) r = cuda_ok(cudaMemcpyAsync(res.data(), dres, J * 4, cudaMemcpyDeviceToHost, s));
+        if (r == RFR_OK && coeffs_out) {
+            coeffs_out->resize((size_t)J * LDC);
+            r = cuda_ok(cudaMemcpyAsync(coeffs_out->data(), dco, (size_t)J * LDC * 8, cudaMemcpyDeviceToHost, s));
+        }
+        if (r == RFR_OK) r = cuda_ok(cudaStreamSynchronize(s));
+        C.alloc.put(buf, bytes, s);
+        return r;
+    };
+    {
+        std::vector<int32_t> jp, res;
+        std::vector<uint64_t> jlo, jhi;
+        std::vector<std::pair<int, size_t>> owner;
+        for (auto& w : work) {
+            if (w.status != RFR_OK || !w.matched) continue;
+            for (size_t c = 0; c < w.cand.size(); ++c) {
+                jp.push_back(w.slot);
+                jlo.push_back(w.cand[c]);                // patterns over elements 0..n-2 (n-1 <= 64)
+                jhi.push_back(0);
+                owner.push_back({w.slot, c});
+            }
+        }
+        cudaEventRecord(ev[6], s);
+        rc = run_verify(jp, jlo, jhi, res, nullptr);
+        cudaEventRecord(ev[7], s);
+        if (rc != RFR_OK) return rc;
+        if (timing) { cudaEventSynchronize(ev[7]); t_verify = ms_between(ev[6], ev[7]); }
+        for (size_t j = 0; j < res.size(); ++j) {
+            Work& w = work[owner[j].first];
+            if (res[j] == 1) { Bits b; b.lo = jlo[j]; w.verified.push_back(b); }
+            else if (res[j] == RFR_E_OVERFLOW) w.status = RFR_E_OVERFLOW;
+        }
+    }
+    {
+        std::vector<int32_t> jp, res;
+        std::vector<uint64_t> jlo, jhi;
+        std::vector<std::pair<int, int>> owner;
+        for (auto& w : work) {
+            if (w.status != RFR_OK) continue;
+            const int n = w.plan.n;
+            if (n <= 1 || w.verified.empty()) continue;
+            const Bits full = full_bits(n);
+            std::vector<Bits> fam;
+            fam.push_back(full);
+            for (auto& v : w.verified) { fam.push_back(v); fam.push_back(full & ~v); }
+            for (int i = 0; i < n; ++i) {
+                Bits a = full;
+                for (auto& t : fam) if (t.get(i)) a = a & t;
+                bool seen = false;
+                for (auto& x : w.atoms) if (x == a) { seen = true; break; }
+                if (!seen) w.atoms.push_back(a);
+            }
+            if (w.atoms.size() < 2) { w.atoms.clear(); continue; }
+            for (size_t a = 0; a < w.atoms.size(); ++a) {
+                jp.push_back(w.slot); jlo.push_back(w.atoms[a].lo); jhi.push_back(w.atoms[a].hi);
+                owner.push_back({w.slot, (int)a});
+            }
+        }
+        std::vector<int64_t> co;
+        cudaEventRecord(ev[6], s);
+        rc = run_verify(jp, jlo, jhi, res, &co);
+        cudaEventRecord(ev[7], s);
+        if (rc != RFR_OK) return rc;
+        if (timing) { cudaEventSynchronize(ev[7]); t_atoms = ms_between(ev[6], ev[7]); }
+        for (size_t j = 0; j < res.size(); ++j) {
+            Work& w = work[owner[j].first];
+            if (res[j] != 1) { if (w.status == RFR_OK) w.status = res[j] == RFR_E_OVERFLOW ? RFR_E_OVERFLOW : RFR_E_INTERNAL; continue; }
+            int e = 0;
+            const Bits& a = w.atoms[owner[j].second];
+            for (int k = 0; k < w.plan.n; ++k) if (a.get(k)) e += w.plan.kind[k];
+            const int64_t* src = co.data() + j * LDC;
+            w.factors.emplace_back(src, src + e + 1);
+        }
+    }
+
+    // ---- results
+    const double t_host = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_host0).count();
+    for (auto& w : work) {
+        Item& it = items[w.item];
+        rfr_diag& dg = it.out->diag;
+        dg.n = w.plan.n; dg.r = w.plan.r; dg.c = w.plan.c; dg.n_a = w.plan.n_a; dg.n_b = w.plan.n_b;
+        dg.window = w.plan.window;
+        dg.half_sums = w.plan.n > 1 ? (1ull << w.plan.n_a) + (1ull << w.plan.n_b) : 0;
+        dg.cand_coarse = w.ctr[0]; dg.cand_pre = w.ctr[1]; dg.cand_post = w.ctr[2];
+        dg.verified = w.verified.size();
+        dg.max_rel_residual = w.plan.max_rel_residual;
+        dg.max_root_err = w.plan.max_radius;
+        dg.stage_us[0] = t_roots * 1e3; dg.stage_us[1] = t_weights * 1e3; dg.stage_us[2] = t_enum * 1e3;
+        dg.stage_us[3] = t_match * 1e3; dg.stage_us[4] = t_verify * 1e3; dg.stage_us[5] = t_atoms * 1e3;
+        dg.stage_us[7] = t_host * 1e3;
+        if (w.status != RFR_OK) { it.status = w.status; continue; }
+        std::vector<std::vector<int64_t>> fs;
+        if (!w.factors.empty()) {
+            fs = w.factors;
+        } else {
+            fs.emplace_back(it.coeffs, it.coeffs + it.degree + 1);
+        }
+        // exact check: product of the factors equals p (host, tiny)
+        std::vector<__int128> prod(1, 1);
+        for (auto& f : fs) {
+            std::vector<__int128> nx(prod.size() + f.size() - 1, 0);
+            for (size_t i = 0; i < prod.size(); ++i)
+                for (size_t j = 0; j < f.size(); ++j) nx[i + j] += prod[i] * (__int128)f[j];
+            prod.swap(nx);
+        }
+        bool same = (int)prod.size() == it.degree + 1;
+        for (int k = 0; same && k <= it.degree; ++k) same = prod[k] == (__int128)it.coeffs[k];
+        if (!same) { it.status = RFR_E_INTERNAL; continue; }
+        canonical_sort(fs);
+        fill_factors(it.out, fs);
+    }
+    return RFR_OK;
+}
+
+// ---------------------------------------------------------------- serving
+static void worker_loop(Ctx* C, Pipeline* P) {
+    cudaSetDevice(C->device);
+    for (;;) {
+        std::vector<Request*> batch;
+        {
+            std::unique_lock<std::mutex> lk(C->q_mu);
+            C->q_cv.wait(lk, [&] { return C->stop || !C->pending.empty(); });
+            if (C->stop) return;
+            while (!C->pending.empty() && (int)batch.size() < C->cfg.max_batch) {
+                Request* r = C->pending.front();
+                C->pending.pop_front();
+                if (r->cancelled) continue;
+                r->running = true;
+                batch.push_back(r);
+            }
+            ++C->running_batches;
+        }
+        std::vector<Item> items(batch.size());
+        for (size_t i = 0; i < batch.size(); ++i)
+            items[i] = {batch[i]->coeffs.data(), batch[i]->degree, RFR_OK, &batch[i]->result};
+        int rc = batch.empty() ? RFR_OK : P->run(items);
+        {
+            std::lock_guard<std::mutex> lk(C->q_mu);
+            for (size_t i = 0; i < batch.size(); ++i) {
+                batch[i]->status = rc == RFR_OK ? items[i].status : rc;
+                batch[i]->running = false;
+                batch[i]->done = true;
+            }
+            --C->running_batches;
+        }
+        C->done_cv.notify_all();
+    }
+}
+
+}  // namespace rfr
+
+using namespace rfr;
+
+struct rfr_ctx { Ctx c; };
+
+extern "C" {
+
+const char* rfr_version(void) { return "rfr-b300 0.1 (sm_103a)"; }
+
+const char* rfr_strerror(int st) {
+    switch (st) {
+        case RFR_OK: return "ok";
+        case RFR_PENDING: return "pending";
+        case RFR_E_INVALID: return "invalid argument";
+        case RFR_E_NOT_MONIC: return "polynomial is not monic";
+        case RFR_E_RANGE: return "degree or coefficient out of range";
+        case RFR_E_NOT_SQUAREFREE: return "polynomial is not square-free";
+        case RFR_E_NO_CONVERGENCE: return "root iteration did not converge";
+        case RFR_E_ROOTS: return "roots could not be separated or classified";
+        case RFR_E_WINDOW: return "integrality window too wide";
+        case RFR_E_CAND_OVERFLOW: return "too many candidate patterns";
+        case RFR_E_OVERFLOW: return "integer overflow in exact verification";
+        case RFR_E_OOM: return "out of memory";
+        case RFR_E_BUDGET: return "tables exceed the memory budget";
+        case RFR_E_TIMEOUT: return "timed out";
+        case RFR_E_CUDA: return "CUDA error";
+        case RFR_E_CANCELLED: return "cancelled";
+        case RFR_E_INTERNAL: return "internal consistency check failed";
+        default: return "unknown status";
+    }
+}
+
+int rfr_config_default(rfr_config* cfg) {
+    if (!cfg) return RFR_E_INVALID;
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->device = 0;
+    cfg->mem_budget_bytes = 0;
+    cfg->max_inflight = 2;
+    cfg->max_batch = 64;
+    cfg->root_mode = RFR_ROOTS_FP64;
+    cfg->timing = 0;
+    cfg->max_candidates = 1ull << 16;
+    cfg->eps_override = 0.0;
+    return RFR_OK;
+}
+
+int rfr_create(const rfr_config* cfg_in, rfr_ctx** out) {
+    if (!out) return RFR_E_INVALID;
+    *out = nullptr;
+    rfr_config cfg;
+    if (cfg_in) cfg = *cfg_in; else rfr_config_default(&cfg);
+    if (cfg.max_inflight < 1 || cfg.max_batch < 1 || (cfg.root_mode != RFR_ROOTS_FP64 && cfg.root_mode != RFR_ROOTS_FP32_BULK))
+        return RFR_E_INVALID;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg.device < 0 || cfg.device >= ndev) { cudaGetLastError(); return RFR_E_CUDA; }
+    if (cudaSetDevice(cfg.device) != cudaSuccess) return RFR_E_CUDA;
+    rfr_ctx* x = new (std::nothrow) rfr_ctx();
+    if (!x) return RFR_E_OOM;
+    Ctx& C = x->c;
+    C.cfg = cfg;
+    C.device = cfg.device;
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    C.budget = cfg.mem_budget_bytes ? cfg.mem_budget_bytes : (size_t)(fr * 0.85);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, cfg.device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    if (!C.sync_pipe.init(&C)) { delete x; return RFR_E_CUDA; }
+    for (int i = 0; i < cfg.max_inflight; ++i) {
+        C.worker_pipes.emplace_back(new Pipeline());
+        if (!C.worker_pipes.back()->init(&C)) { rfr_destroy(x); return RFR_E_CUDA; }
+    }
+    for (int i = 0; i < cfg.max_inflight; ++i) C.workers.emplace_back(worker_loop, &C, C.worker_pipes[i].get());
+    *out = x;
+    return RFR_OK;
+}
+
+int rfr_destroy(rfr_ctx* x) {
+    if (!x) return RFR_OK;
+    Ctx& C = x->c;
+    {
+        std::lock_guard<std::mutex> lk(C.q_mu);
+        C.stop = true;
+        for (Request* r : C.pending) { r->status = RFR_E_CANCELLED; r->done = true; }
+        C.pending.clear();
+    }
+    { std::lock_guard<std::mutex> lk(C.budget_mu); }
+    C.budget_cv.notify_all();
+    C.q_cv.notify_all();
+    for (auto& t : C.workers) t.join();
+    for (auto& p : C.worker_pipes) p->destroy();
+    C.sync_pipe.destroy();
+    for (auto& kv : C.reqs) { rfr_factors_free(&kv.second->result); delete kv.second; }
+    delete x;
+    return RFR_OK;
+}
+
+int rfr_set_allocator(rfr_ctx* x, rfr_alloc_fn a, rfr_free_fn f, void* user) {
+    if (!x || ((a == nullptr) != (f == nullptr))) return RFR_E_INVALID;
+    Ctx& C = x->c;
+    std::lock_guard<std::mutex> lk1(C.sync_mu);
+    std::lock_guard<std::mutex> lk2(C.q_mu);
+    if (C.running_batches || !C.pending.empty()) return RFR_E_INVALID;
+    // buffers owned by pipelines were made with the previous allocator: drop them
+    auto reset = [&](Pipeline& P) {
+        cudaStreamSynchronize(P.s);
+        auto put = [&](void* p) { if (p) C.alloc.put(p, 0, P.s); };
+        put(P.d_coeffs); put(P.d_deg); put(P.d_roots); put(P.d_radius); put(P.d_rstat); put(P.d_plans);
+        cudaStreamSynchronize(P.s);
+        P.d_coeffs = nullptr; P.d_deg = nullptr; P.d_roots = nullptr; P.d_radius = nullptr; P.d_rstat = nullptr; P.d_plans = nullptr;
+        if (P.h_coeffs) cudaFreeHost(P.h_coeffs);
+        if (P.h_deg) cudaFreeHost(P.h_deg);
+        if (P.h_plans) cudaFreeHost(P.h_plans);
+        P.h_coeffs = nullptr; P.h_deg = nullptr; P.h_plans = nullptr;
+        P.cap = 0;
+    };
+    reset(C.sync_pipe);
+    for (auto& p : C.worker_pipes) reset(*p);
+    C.alloc.fa = a; C.alloc.ff = f; C.alloc.user = user;
+    return RFR_OK;
+}
+
+int rfr_factor_batch(rfr_ctx* x, int count, const int64_t* const* coeffs, const int* degrees,
+                     rfr_factors* outs, int* statuses) {
+    if (!x || count < 0 || (count && (!coeffs || !degrees || !outs))) return RFR_E_INVALID;
+    Ctx& C = x->c;
+    std::lock_guard<std::mutex> lk(C.sync_mu);
+    cudaSetDevice(C.device);
+    std::vector<Item> items(count);
+    for (int i = 0; i < count; ++i) items[i] = {coeffs[i], degrees[i], RFR_OK, &outs[i]};
+    int rc = C.sync_pipe.run(items);
+    for (int i = 0; i < count; ++i) {
+        const int st = rc == RFR_OK ? items[i].status : rc;
+        if (statuses) statuses[i] = st;
+        if (st != RFR_OK) { rfr_factors_free(&outs[i]); }
+    }
+    return rc;
+}
+
+int rfr_factor(rfr_ctx* x, const int64_t* coeffs, int degree, rfr_factors* out) {
+    if (!x || !coeffs || !out) return RFR_E_INVALID;
+    int st = RFR_OK;
+    const int64_t* c[1] = {coeffs};
+    int rc = rfr_factor_batch(x, 1, c, &degree, out, &st);
+    return rc == RFR_OK ? st : rc;
+}
+
+int rfr_submit(rfr_ctx* x, const int64_t* coeffs, int degree, uint64_t* ticket) {
+    if (!x || !coeffs || !ticket) return RFR_E_INVALID;
+    if (degree < 1 || degree > DMAX) return RFR_E_RANGE;
+    if (coeffs[degree] != 1) return RFR_E_NOT_MONIC;
+    for (int k = 0; k <= degree; ++k)
+        if (coeffs[k] >= (1ll << 53) || coeffs[k] <= -(1ll << 53)) return RFR_E_RANGE;
+    Ctx& C = x->c;
+    Request* r = new (std::nothrow) Request();
+    if (!r) return RFR_E_OOM;
+    r->coeffs.assign(coeffs, coeffs + degree + 1);
+    r->degree = degree;
+    {
+        std::lock_guard<std::mutex> lk(C.q_mu);
+        if (C.stop) { delete r; return RFR_E_CANCELLED; }
+        r->ticket = C.next_ticket++;
+        C.reqs[r->ticket] = r;
+        C.pending.push_back(r);
+        *ticket = r->ticket;
+    }
+    C.q_cv.notify_one();
+    return RFR_OK;
+}
+
+static int take_result(Ctx& C, std::unordered_map<uint64_t, Request*>::iterator it, rfr_factors* out) {
+    Request* r = it->second;
+    const int st = r->status;
+    if (out) { *out = r->result; } else rfr_factors_free(&r->result);
+    memset(&r->result, 0, sizeof(r->result));
+    C.reqs.erase(it);
+    delete r;
+    return st;
+}
+
+int rfr_poll(rfr_ctx* x, uint64_t ticket, rfr_factors* out) {
+    if (!x) return RFR_E_INVALID;
+    Ctx& C = x->c;
+    std::lock_guard<std::mutex> lk(C.q_mu);
+    auto it = C.reqs.find(ticket);
+    if (it == C.reqs.end()) return RFR_E_INVALID;
+    if (!it->second->done) return RFR_PENDING;
+    return take_result(C, it, out);
+}
+
+int rfr_wait(rfr_ctx* x, uint64_t ticket, int timeout_ms, rfr_factors* out) {
+    if (!x) return RFR_E_INVALID;
+    Ctx& C = x->c;
+    std::unique_lock<std::mutex> lk(C.q_mu);
+    auto it = C.reqs.find(ticket);
+    if (it == C.reqs.end()) return RFR_E_INVALID;
+    Request* r = it->second;
+    auto pred = [&] { return r->done; };
+    if (timeout_ms < 0) C.done_cv.wait(lk, pred);
+    else if (!C.done_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred)) return RFR_E_TIMEOUT;
+    it = C.reqs.find(ticket);
+    return take_result(C, it, out);
+}
+
+int rfr_cancel(rfr_ctx* x, uint64_t ticket) {
+    if (!x) return RFR_E_INVALID;
+    Ctx& C = x->c;
+    {
+        std::lock_guard<std::mutex> lk(C.q_mu);
+        auto it = C.reqs.find(ticket);
+        if (it == C.reqs.end()) return RFR_E_INVALID;
+        Request* r = it->second;
+        if (r->done) return RFR_OK;
+        if (r->running) return RFR_PENDING;
+        r->cancelled = true;
+        r->status = RFR_E_CANCELLED;
+        r->done = true;
+        C.pending.erase(std::remove(C.pending.begin(), C.pending.end(), r), C.pending.end());
+    }
+    C.done_cv.notify_all();
+    return RFR_OK;
+}
+
+void rfr_factors_free(rfr_factors* f) {
+    if (!f) return;
+    free(f->degrees);
+    free(f->coeffs);
+    f->degrees = nullptr;
+    f->coeffs = nullptr;
+    f->n_factors = 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every
+function the headers declare, and its host-only entry points behave."""
+import ctypes
+import json
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in ("rfr.h", "rfr_stages.h"):
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(rfr_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(n for n in names if not n.endswith("_fn")))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2410_15880_b300.build import build
+    build()
+    import paper_2410_15880_b300 as P
+    return P.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_host_only_calls(L):
+    import paper_2410_15880_b300._native as N
+    assert L.rfr_version().startswith(b"rfr-b300")
+    assert L.rfr_strerror(-8) == b"too many candidate patterns"
+    assert L.rfr_strerror(12345) == b"unknown status"
+    cfg = N.Config()
+    assert L.rfr_config_default(ctypes.byref(cfg)) == 0
+    assert cfg.max_inflight == 2 and cfg.max_candidates == 1 << 16 and cfg.root_mode == 0
+    assert L.rfr_config_default(None) == -1
+    assert L.rfr_destroy(None) == 0
+    f = N.Factors()
+    L.rfr_factors_free(ctypes.byref(f))                 # zeroed struct is fine
+
+
+def test_struct_layout(L):
+    import paper_2410_15880_b300._native as N
+    assert N.PLAN_DTYPE.itemsize == 2512
+    assert ctypes.sizeof(N.Config) == 48 and ctypes.sizeof(N.Diag) == 152
+
+
+def test_create_without_gpu_fails_cleanly(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_2410_15880_b300._native as N
+    h = ctypes.c_void_p()
+    assert L.rfr_create(None, ctypes.byref(h)) == -13     # RFR_E_CUDA, no abort
+    assert not h.value
+
+
+def test_stage_argument_checks(L):
+    # invalid sizes are rejected on the host before any launch
+    assert L.rfr_stage_enumerate(None, 4, None, None) == -1
+    assert L.rfr_stage_match_workspace(5, 3) == 0          # n_b < n_a is not a valid split
+    assert L.rfr_stage_match_workspace(10, 11) > (1 << 11) * 8
+
+
+def test_golden_files_are_consistent():
+    from oracle.zpoly import pmul
+    for name in ("cfg1", "cfg2", "cfg3", "cfg4_sample", "cfg5", "special"):
+        recs = json.load(open(os.path.join(ROOT, "tests", "golden", f"{name}.json")))
+        for r in recs:
+            assert "factors" in r, r["name"]
+            acc = [1]
+            for f in r["factors"]:
+                assert f[-1] == 1
+                acc = pmul(acc, f)
+            assert acc == r["coeffs"], r["name"]

@@ -1,0 +1,103 @@
+"""End-to-end parity: rfr_factor / rfr_factor_batch / serving against the
+oracle's golden factorisations (bit-exact canonical factor lists)."""
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from gpu_util import golden  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2410_15880_b300 import Context
+    c = Context(device=0, timing=True)
+    yield c
+    c.close()
+
+
+def check_batch(ctx, recs):
+    res = ctx.factor_batch([r["coeffs"] for r in recs])
+    bad = [(r["name"], x.status, x.factors, r["factors"]) for r, x in zip(recs, res)
+           if not (x.ok and x.factors == r["factors"])]
+    assert not bad, bad[:3]
+    for r, x in zip(recs, res):
+        if "n" in r and r["n"] > 1:
+            assert x.diag["n"] == r["n"] and x.diag["r"] == r["r"], r["name"]
+    return res
+
+
+def test_single_degree24(ctx):
+    for r in golden("cfg1"):
+        x = ctx.factor(r["coeffs"])
+        assert x.ok and x.factors == r["factors"]
+
+
+def test_special_polynomials(ctx):
+    res = check_batch(ctx, golden("special"))
+    sd = [x for r, x in zip(golden("special"), res) if r["name"] == "swinnerton_dyer_f2"][0]
+    assert sd.diag["cand_pre"] >= 1 and sd.diag["verified"] == 0     # false candidates rejected
+
+
+def test_degree60_batch(ctx):
+    check_batch(ctx, golden("cfg2"))
+
+
+def test_serving_sample_batch(ctx):
+    check_batch(ctx, golden("cfg4_sample"))
+
+
+def test_degree100_batch(ctx):
+    res = check_batch(ctx, golden("cfg3"))
+    assert all(x.diag["half_sums"] > (1 << 24) for x in res)
+
+
+def test_one_launch_per_polynomial_equals_batch(ctx):
+    recs = golden("cfg2")[:8]
+    batch = ctx.factor_batch([r["coeffs"] for r in recs])
+    for r, b in zip(recs, batch):
+        a = ctx.factor(r["coeffs"])
+        assert a.factors == b.factors == r["factors"]
+
+
+def test_error_statuses(ctx):
+    from paper_2410_15880_b300._native import status_name
+    cases = {
+        "RFR_E_NOT_MONIC": [1, 2, 3],
+        "RFR_E_RANGE": [1 << 60, 1],
+        "RFR_E_NOT_SQUAREFREE": [2, -3, 0, 1],            # (x-1)^2 (x+2)
+    }
+    for want, p in cases.items():
+        assert status_name(ctx.factor(p).status) == want
+    assert ctx.factor([-7, 1]).factors == [[-7, 1]]      # degree 1
+    assert ctx.factor([1, 0, 0, 0, 1]).factors == [[1, 0, 0, 0, 1]]    # x^4+1 irreducible over Z
+
+
+def test_serving_alone_and_in_mix():
+    from paper_2410_15880_b300 import Context
+    recs = golden("cfg4_sample")
+    with Context(device=0, max_inflight=2, max_batch=16) as srv:
+        tickets = [srv.submit(r["coeffs"]) for r in recs]
+        out = [srv.wait(t, 120000) for t in tickets]
+        alone = srv.factor(recs[5]["coeffs"])
+    for r, x in zip(recs, out):
+        assert x.ok and x.factors == r["factors"], r["name"]
+    mixed = out[5]
+    assert alone.factors == mixed.factors
+    assert alone.diag["n"] == mixed.diag["n"] and alone.diag["window"] == mixed.diag["window"]
+
+
+def test_serving_cancel_and_poll():
+    from paper_2410_15880_b300 import Context
+    recs = golden("cfg2")[:20]
+    with Context(device=0, max_inflight=1, max_batch=1) as srv:
+        ts = [srv.submit(r["coeffs"]) for r in recs]
+        last = ts[-1]
+        st = srv.cancel(last)
+        assert st in (0, 1)                      # cancelled while queued, or already running
+        for t, r in zip(ts[:-1], recs[:-1]):
+            x = srv.wait(t, 120000)
+            assert x.factors == r["factors"]
+        x = srv.wait(last, 120000)
+        assert x.status in (0, -14)
+        assert srv.cancel(10 ** 9) == -1        # unknown ticket

@@ -1,0 +1,231 @@
+"""Stage-level parity of the CUDA path against the CPU oracle (through the C ABI).
+
+K-a roots, K-b weights, K-c enumerate, K-c/K-d/K-e match and K-f verify, each
+on seeded inputs, element by element where the result is unique."""
+import random
+
+import mpmath
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from gpu_util import coeff_tensor, golden, plans_numpy, to_u64, u64_tensor  # noqa: E402
+
+M64 = 1 << 64
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2410_15880_b300 as P
+    P.lib()
+    return P
+
+
+def circ(y):
+    y %= M64
+    return min(y, M64 - y)
+
+
+def small_set():
+    recs = golden("cfg1") + golden("special") + golden("cfg2")[:6] + golden("cfg4_sample")[:12]
+    return [r for r in recs if len(r["coeffs"]) > 2]
+
+
+# ---------------------------------------------------------------- K-a
+@pytest.mark.parametrize("mode", [0, 1])
+def test_roots_within_radius_and_residual(P, mode):
+    from oracle.roots import complex_roots
+    recs = small_set()
+    c, d = coeff_tensor([r["coeffs"] for r in recs])
+    roots, radius, status = P.stage_roots(c, d, mode)
+    torch.cuda.synchronize()
+    R, rad, st = roots.cpu().numpy(), radius.cpu().numpy(), status.cpu().numpy()
+    for i, r in enumerate(recs):
+        assert st[i] == 0, r["name"]
+        deg = len(r["coeffs"]) - 1
+        ref = complex_roots(r["coeffs"])
+        p = r["coeffs"]
+        for j in range(deg):
+            z = mpmath.mpc(mpmath.mpf(R[i, j, 0]) + R[i, j, 1], mpmath.mpf(R[i, j, 2]) + R[i, j, 3])
+            err = min(abs(z - w) for w in ref)
+            assert err <= rad[i, j], (r["name"], j, float(err), rad[i, j])      # inclusion radius holds
+            num = abs(mpmath.polyval([mpmath.mpf(x) for x in reversed(p)], z))
+            den = sum(abs(x) * abs(z) ** k for k, x in enumerate(p))
+            assert num / den <= 1e-10                                           # relative residual (FP64 bar)
+
+
+# ---------------------------------------------------------------- K-b
+def test_weights_against_oracle_rho(P):
+    from oracle.reduction import elements_from_roots
+    from oracle.roots import complex_roots
+    from oracle.sturm import real_root_count
+    recs = small_set()
+    c, d = coeff_tensor([r["coeffs"] for r in recs])
+    roots, radius, status = P.stage_roots(c, d)
+    plans = plans_numpy(P.stage_weights(c, d, roots, radius, status))
+    for i, r in enumerate(recs):
+        pl = plans[i]
+        assert pl["status"] == 0, r["name"]
+        els = elements_from_roots(complex_roots(r["coeffs"]), real_root_count(r["coeffs"]))
+        n = len(els)
+        assert (pl["n"], pl["r"]) == (n, r["r"]), r["name"]
+        assert pl["n_a"] == (n - 1) // 2 and pl["n_b"] == n - 1 - (n - 1) // 2
+        W = int(pl["window"])
+        for k, e in enumerate(els):
+            assert pl["kind"][k] == e.degree
+            ref = int(mpmath.nint(e.rho * M64)) % M64
+            assert circ(int(pl["w"][k]) - ref) <= W, (r["name"], k)
+            ref2 = int(mpmath.nint((e.t2 - mpmath.floor(e.t2)) * M64)) % M64
+            assert circ(int(pl["w2"][k]) - ref2) <= int(pl["window2"]), (r["name"], k)
+        # Vieta: all elements together sum to an integer
+        assert circ(sum(int(x) for x in pl["w"][:n])) <= W
+
+
+# ---------------------------------------------------------------- K-c plain
+@pytest.mark.parametrize("h", [0, 1, 3, 5, 6, 7, 11, 14])
+def test_enumerate_bit_exact(P, h):
+    from oracle.recombine import expand_values
+    from workloads import random_weights
+    w = [int(x) for x in random_weights(100 + h, max(h, 1))][:h]
+    keys = P.stage_enumerate(u64_tensor(w if h else [0]), h)
+    got = [int(x) for x in to_u64(keys)]
+    assert got == expand_values(w, M64)
+
+
+def test_enumerate_large_properties(P):
+    from oracle.recombine import value
+    from workloads import random_weights
+    h = 24
+    w = [int(x) for x in random_weights(7, h)]
+    keys = to_u64(P.stage_enumerate(u64_tensor(w), h))
+    # sum over all s of key(s) = 2^(h-1) * sum(w)  (mod 2^64)
+    assert int(keys.sum(dtype=np.uint64)) == (2 ** (h - 1) * sum(w)) % M64
+    rng = random.Random(3)
+    for s in [0, 1, (1 << h) - 1] + [rng.randrange(1 << h) for _ in range(200)]:
+        assert int(keys[s]) == value(s, w, M64)
+
+
+# ---------------------------------------------------------------- K-c/K-d/K-e match
+def _expected_pairs(wa, w2a, wb, w2b, W, W2):
+    from oracle.recombine import accept, band_pairs, expand_values
+    alpha, beta = expand_values(wa, M64), expand_values(wb, M64)
+    a2, b2 = expand_values(w2a, M64), expand_values(w2b, M64)
+    pairs = band_pairs(alpha, beta, M64, W)
+    return {(i, j) for (i, j) in pairs if accept((a2[i] + b2[j]) % M64, M64, W2)}
+
+
+def _run_match(P, wa, w2a, wb, w2b, W, W2, cap=1 << 16):
+    cand, ctr, _ = P.stage_match(u64_tensor(wa) if wa else u64_tensor([0])[:0],
+                                 u64_tensor(w2a) if wa else u64_tensor([0])[:0],
+                                 u64_tensor(wb) if wb else u64_tensor([0])[:0],
+                                 u64_tensor(w2b) if wb else u64_tensor([0])[:0], W, W2, cap)
+    torch.cuda.synchronize()
+    ctr = [int(x) for x in ctr.cpu().numpy().view(np.uint64)]
+    cnt = ctr[2]
+    got = [int(x) for x in to_u64(cand)[:min(cnt, cap)]]
+    na = len(wa)
+    return {(s & ((1 << na) - 1), s >> na) for s in got}, ctr, got
+
+
+@pytest.mark.parametrize("seed,na,nb", [(1, 0, 0), (2, 0, 1), (3, 1, 1), (4, 2, 3), (5, 4, 4),
+                                        (6, 5, 6), (7, 7, 8), (8, 9, 9), (9, 10, 11)])
+def test_match_bruteforce(P, seed, na, nb):
+    rng = random.Random(seed)
+    W = rng.choice([0, 3, 1 << 20, 1 << 52])
+    wa = [rng.randrange(M64) for _ in range(na)]
+    wb = [rng.randrange(M64) for _ in range(nb)]
+    if na and nb:                                   # plant an integral subset across the halves
+        wb[0] = (-(wa[0] + (wa[-1] if na > 1 else 0))) % M64
+    w2a = [rng.randrange(M64) for _ in range(na)]
+    w2b = [rng.randrange(M64) for _ in range(nb)]
+    W2 = 1 << 63                                    # Tr_2 filter off
+    got, ctr, raw = _run_match(P, wa, w2a, wb, w2b, W, W2)
+    exp = _expected_pairs(wa, w2a, wb, w2b, W, W2)
+    assert ctr[3] == 1                              # the empty pattern always matches
+    assert got == exp - {(0, 0)}
+    assert len(raw) == len(set(raw))                # every pair once
+    assert ctr[4] == 0
+
+
+def test_match_tr2_filter(P):
+    rng = random.Random(42)
+    na, nb = 8, 9
+    wa = [rng.randrange(M64) for _ in range(na)]
+    wb = [rng.randrange(M64) for _ in range(nb)]
+    W = 1 << 58                                    # wide Tr_1 window: many pairs
+    w2a = [rng.randrange(M64) for _ in range(na)]
+    w2b = [rng.randrange(M64) for _ in range(nb)]
+    W2 = 1 << 61
+    got, ctr, _ = _run_match(P, wa, w2a, wb, w2b, W, W2)
+    exp = _expected_pairs(wa, w2a, wb, w2b, W, W2)
+    assert got == exp - {(0, 0)} and len(got) > 0
+    assert ctr[2] == len(got) and ctr[1] >= ctr[2]
+
+
+def test_match_degenerate_all_zero(P):
+    # every weight 0 (e.g. all roots integers): every pattern is a candidate
+    na, nb = 4, 5
+    got, ctr, _ = _run_match(P, [0] * na, [0] * na, [0] * nb, [0] * nb, 5, 5)
+    assert got == {(i, j) for i in range(1 << na) for j in range(1 << nb)} - {(0, 0)}
+
+
+def test_match_candidate_cap(P):
+    na, nb = 4, 5
+    got, ctr, raw = _run_match(P, [0] * na, [0] * na, [0] * nb, [0] * nb, 5, 5, cap=10)
+    assert ctr[2] == (1 << 9) - 1 and len(raw) == 10
+
+
+@pytest.mark.parametrize("seed,na,nb", [(11, 14, 15), (12, 16, 16), (13, 17, 18)])
+def test_match_several_tiles_against_scan(P, seed, na, nb):
+    """Sizes that span many buckets and CTAs, vs RECOMBINE_A on the concatenation."""
+    from oracle.recombine import recombine_a
+    rng = random.Random(seed)
+    wa = [rng.randrange(M64) for _ in range(na)]
+    wb = [rng.randrange(M64) for _ in range(nb)]
+    # plant three integral subsets
+    wb[2] = (-(wa[0] + wa[5] + wb[7])) % M64
+    wa[9] = (-(wb[1] + wb[3])) % M64
+    W = 1 << 30
+    got, ctr, _ = _run_match(P, wa, [0] * na, wb, [0] * nb, W, 0)
+    scan = set(recombine_a(wa + wb + [0], M64, W)) - {0}
+    exp = {(s & ((1 << na) - 1), s >> na) for s in scan}
+    assert got == exp and len(exp) >= 2
+
+
+# ---------------------------------------------------------------- K-f verify
+def test_verify_true_and_false_patterns(P):
+    recs = [r for r in golden("cfg1") + golden("special") if len(r["factors"]) > 1 or r["name"].startswith("swinnerton")]
+    c, d = coeff_tensor([r["coeffs"] for r in recs])
+    roots, radius, status = P.stage_roots(c, d)
+    plans_t = P.stage_weights(c, d, roots, radius, status)
+    plans = plans_numpy(plans_t)
+    R = roots.cpu().numpy()
+    prob, lo, hi, expect_coeffs = [], [], [], []
+    for i, r in enumerate(recs):
+        pl = plans[i]
+        n = int(pl["n"])
+        for f in r["factors"]:
+            # elements whose root is a root of f
+            pat = 0
+            for k in range(n):
+                z = complex(R[i, pl["root0"][k], 0], R[i, pl["root0"][k], 2])
+                val = abs(np.polyval(list(reversed(f)), z))
+                scale = sum(abs(x) * abs(z) ** j for j, x in enumerate(f))
+                if val <= 1e-8 * scale:
+                    pat |= 1 << k
+            prob.append(i); lo.append(pat); hi.append(0); expect_coeffs.append(f)
+        if r["name"] == "swinnerton_dyer_f2":
+            # the pair {sqrt2+sqrt3, -sqrt2-sqrt3}: Tr_1 = 0 but not a factor (Section 2)
+            prob.append(i); lo.append(0b1001); hi.append(0); expect_coeffs.append(None)
+    pt = torch.tensor(prob, dtype=torch.int32, device="cuda")
+    res, co = P.stage_verify(c, d, roots, plans_t, pt, u64_tensor(lo), u64_tensor(hi), want_coeffs=True)
+    res = res.cpu().numpy()
+    co = co.cpu().numpy()
+    for j, f in enumerate(expect_coeffs):
+        if f is None:
+            assert res[j] == 0
+        else:
+            assert res[j] == 1, (j, f)
+            assert list(co[j, :len(f)]) == f
