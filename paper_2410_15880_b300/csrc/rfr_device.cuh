@@ -111,7 +111,10 @@ __device__ __forceinline__ double2 c_div(double2 a, double2 b) {
 // round(frac(x) * 2^64) mod 2^64 for a DD value x with |x| < 2^52.
 __device__ __forceinline__ uint64_t dd_frac_fixed64(dd x) {
     double fl = floor(x.hi);
-    dd f = two_sum(x.hi - fl, x.lo);           // x.hi - fl is exact; f in (-tiny, 1 + tiny)
+    // x.hi - fl is not exact when -1 < x.hi < 0 (it is x.hi + 1): keep its
+    // rounding error with TwoSum, then add x.lo.  f lies in (-tiny, 1 + tiny).
+    dd t = two_sum(x.hi, -fl);
+    dd f = two_sum(t.hi, t.lo + x.lo);
     double X = ldexp(f.hi, 64);                // exact scaling
     double Y = ldexp(f.lo, 64);
     double Xi = floor(X);
