@@ -1,0 +1,318 @@
+"""Benchmark of the RFR hot path on B300 (one JSON line on stdout).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--config cfg3|cfg2|cfg1|cfg5] [--count C] [--no-cpu-baseline]
+
+A step factors one batch of synthetic polynomials end to end (validate,
+roots, weights, enumerate + radix partition, match, verify, atoms).  The
+default workload is 32 polynomials of degree 100, coefficients uniform in
+[-100, 100], half products of random factors and half random (seed 3 + 1000
+* rank).  `value` is polynomials/s with the coefficients already in device
+memory (rfr_factor_batch_device); `e2e` is the same through rfr_factor_batch
+from host buffers.  Under torchrun each rank runs its own batch on its own GPU
+(weak scaling, no data-path collective); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "polynomials factored/sec at degree 100 (32-polynomial batch)"
+UNIT = "polys/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="cfg3", choices=["cfg1", "cfg2", "cfg3", "cfg5"])
+    ap.add_argument("--count", type=int, default=0, help="use only the first C polynomials")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--root-mode", type=int, default=0)
+    return ap.parse_args()
+
+
+def workload(cfg, rank, count):
+    import workloads as W
+    seeds = {"cfg1": 1, "cfg2": 2, "cfg3": 3, "cfg5": 5}
+    make = {"cfg1": W.config1, "cfg2": W.config2, "cfg3": W.config3, "cfg5": W.config5}[cfg]
+    insts = make(seeds[cfg] + 1000 * rank)
+    return insts[:count] if count else insts
+
+
+WORKLOAD_NAME = {
+    "cfg1": "degree-24 product (12+12, coeffs [-10,10]) + random degree-24",
+    "cfg2": "50 x degree 60, coeffs [-100,100], half products of 2-3 factors",
+    "cfg3": "32 x degree 100, coeffs [-100,100], half products (50+50 or 3 factors), half random",
+    "cfg5": "degree 120 = product of two random degree-60 factors, coeffs [-100,100]",
+}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
+def kernel_traffic(name, half_sums):
+    """DRAM bytes per launch for kernel `name` from its committed ncu summary
+    (profiles/<name>_*.md: 'dram_bytes_per_half_sum: X', 'source_sha256: H'),
+    scaled to the launch's half-sums; None if no summary or the kernel source
+    changed since the counters were taken."""
+    import glob
+    for f in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{name}_*.md"))):
+        txt = open(f).read()
+        m = re.search(r"dram_bytes_per_half_sum:\s*([0-9.eE+-]+)", txt)
+        h = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
+        src = os.path.join(ROOT, "paper_2410_15880_b300", "csrc", "k_match.cu")
+        if m and h and hashlib.sha256(open(src, "rb").read()).hexdigest() == h.group(1):
+            return float(m.group(1)) * half_sums
+    return None
+
+
+def cpu_oracle_sample(insts, budget_s=15.0, max_polys=8):
+    from oracle import factor as oracle_factor
+    t0 = time.perf_counter()
+    done = 0
+    for inst in insts[:max_polys]:
+        oracle_factor(inst.coeffs, construction=inst.factors)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done, dt
+
+
+def run_reference(a):
+    """The oracle as it stands, timed on host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    insts = workload(a.config, 0, a.count)
+    for i in range(a.warmup):
+        cpu_oracle_sample(insts[i % len(insts):], budget_s=0.0, max_polys=1)
+    t0 = time.perf_counter()
+    n = 0
+    for i in range(a.steps):
+        d, _ = cpu_oracle_sample(insts[(i % len(insts)):], budget_s=0.0, max_polys=1)
+        n += d
+    dt = time.perf_counter() - t0
+    v = n / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * dt / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME[a.config], "sample": "one polynomial per step"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{n} polynomials of the workload, one per step (CPU oracle: roots, Sturm, DDF irreducibility certificates)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_2410_15880_b300 import Context
+    insts = workload(a.config, rank, a.count)
+    B = len(insts)
+    arr = np.zeros((B, 129), dtype=np.int64)
+    for i, inst in enumerate(insts):
+        arr[i, :len(inst.coeffs)] = inst.coeffs
+    d_co = torch.from_numpy(arr).cuda()
+    d_dg = torch.tensor([inst.degree for inst in insts], dtype=torch.int32, device="cuda")
+    polys = [inst.coeffs for inst in insts]
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    with Context(device=local, timing=True, root_mode=a.root_mode) as ctx:
+        for _ in range(a.warmup):
+            res = ctx.factor_batch_device(d_co, d_dg)
+        # ---- timed region: device-resident inputs
+        clocks = Clocks(local)
+        clocks.start()
+        barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        per_step = []
+        for _ in range(a.steps):
+            res = ctx.factor_batch_device(d_co, d_dg)
+            per_step.append(res[0].diag)
+        ev1.record()
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop()
+        ms = ev0.elapsed_time(ev1)
+        if world > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        statuses = [r.status for r in res]
+        # ---- correctness of the last timed step (outside the timed region)
+        ok_golden = None
+        gpath = os.path.join(ROOT, "tests", "golden", f"{a.config}.json")
+        if rank == 0 and os.path.exists(gpath):
+            gold = json.load(open(gpath))[:B]
+            ok_golden = all(r.ok and r.factors == g["factors"] for r, g in zip(res, gold))
+        # ---- e2e: host buffers through rfr_factor_batch
+        for _ in range(2):
+            ctx.factor_batch(polys)
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        e2e_diag = None
+        for _ in range(a.steps):
+            r2 = ctx.factor_batch(polys)
+            e2e_diag = r2[0].diag
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        ms_e2e = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms_e2e], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        # ---- one launch per polynomial (same inputs, host buffers)
+        one_ms = None
+        if rank == 0:
+            torch.cuda.synchronize()
+            o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            o0.record()
+            singles = [ctx.factor(p) for p in polys]
+            o1.record()
+            torch.cuda.synchronize()
+            one_ms = o0.elapsed_time(o1)
+            single_ok = [s.factors for s in singles] == [r.factors for r in r2]
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    half_sums = sum(r.diag["half_sums"] for r in res)
+    polys_total = B * world * a.steps
+    value = polys_total / (ms / 1e3)
+    # dominant kernel: average launch durations from the library's CUDA events
+    join_us = statistics.mean(d["stage_us"][4] for d in per_step)
+    scat_us = statistics.mean(d["stage_us"][3] for d in per_step)
+    count_us = statistics.mean(d["stage_us"][2] for d in per_step)
+    roots_us = statistics.mean(d["stage_us"][0] for d in per_step)
+    peak, peak_kind = peaks()
+    kern = {"k_join": (join_us, 8.0 * half_sums), "k_scatter": (scat_us, 8.0 * half_sums)}
+    dom = max(kern, key=lambda k: kern[k][0])
+    dur_us, alg_bytes = kern[dom]
+    achieved = alg_bytes / (dur_us * 1e-6) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME[a.config], "polys_per_step": B,
+                   "half_sums_per_step": half_sums, "parallelism": f"replicas x{world}",
+                   "l2": "tables larger than L2 (no flush needed)", "root_mode": a.root_mode},
+        "half_sums_per_s": half_sums * world * a.steps / (ms / 1e3),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": kernel_traffic(dom, half_sums),
+                     "algorithmic_bytes": alg_bytes, "avg_launch_us": dur_us},
+        "stage_us_per_step": {"validate+roots": roots_us, "count+scans": count_us,
+                              "scatter": scat_us, "join": join_us,
+                              "device_total": statistics.mean(d["stage_us"][6] for d in per_step)},
+        "e2e": {"value": polys_total / (ms_e2e / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": int(e2e_diag["h2d_bytes"]), "d2h_bytes_per_step": int(e2e_diag["d2h_bytes"])},
+        "one_launch_per_polynomial": {"value": B / (one_ms / 1e3), "unit": UNIT, "same_factors": single_ok},
+        "gpu_launches": int(sum(d["launches"] for d in per_step)),
+        "clocks": clk,
+        "correct": {"statuses_ok": all(s == 0 for s in statuses), "matches_golden": ok_golden},
+    }
+    if not a.no_cpu_baseline:
+        n, dt = cpu_oracle_sample(workload(a.config, 0, a.count), budget_s=15.0)
+        line["cpu_baseline"] = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"first {n} polynomials of the workload ({dt:.1f} s): roots, Sturm, DDF certificates"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -80,7 +80,10 @@ typedef struct {
     double   eps_override;      /* > 0: integrality window eps (fraction of 1) replacing the derived one */
 } rfr_config;
 
-/* Per-polynomial diagnostics returned with each result. */
+/* Per-polynomial diagnostics returned with each result.  The stage times,
+ * copy bytes and launch count describe the whole batch the polynomial was
+ * factored in (batch_size polynomials); stage times are CUDA-event times on
+ * the batch's stream, filled when rfr_config.timing is set. */
 typedef struct {
     int      n, r, c;           /* n = r + c elements of Eq. 1: r real roots, c conjugate pairs */
     int      n_a, n_b;          /* half sizes of the meet-in-the-middle split (one element fixed out) */
@@ -92,7 +95,12 @@ typedef struct {
     uint64_t verified;          /* candidates proven to divide p                             */
     double   max_rel_residual;  /* max_i |p(z_i)| / sum_k |a_k||z_i|^k after the polish       */
     double   max_root_err;      /* largest inclusion radius                                  */
-    double   stage_us[8];       /* roots, weights, enumerate(count+scan+scatter), match, verify, atoms, host, total */
+    double   stage_us[8];       /* validate+roots, weights, enumerate count+scans, enumerate scatter,
+                                   match, verify+atoms, device total, host total (microseconds) */
+    uint64_t h2d_bytes;         /* bytes the batch copied host -> device                     */
+    uint64_t d2h_bytes;         /* bytes the batch copied device -> host                     */
+    uint32_t launches;          /* CUDA kernels the batch launched                           */
+    uint32_t batch_size;        /* polynomials in the batch                                  */
 } rfr_diag;
 
 /* A factorisation: n_factors monic irreducible factors in canonical order
@@ -142,6 +150,15 @@ int rfr_factor(rfr_ctx* ctx, const int64_t* coeffs, int degree, rfr_factors* out
  * that stopped the whole batch. */
 int rfr_factor_batch(rfr_ctx* ctx, int count, const int64_t* const* coeffs,
                      const int* degrees, rfr_factors* outs, int* statuses);
+
+/* As rfr_factor_batch, for inputs already in device memory:
+ * d_coeffs is int64 [count][RFR_MAX_DEGREE+1] (ascending, row i holds
+ * polynomial i, entries above its degree ignored) and d_degrees int32
+ * [count], both device pointers valid until the call returns.  Input
+ * checks run on the device.  Results are returned in host memory as for
+ * rfr_factor_batch. */
+int rfr_factor_batch_device(rfr_ctx* ctx, int count, const int64_t* d_coeffs,
+                            const int32_t* d_degrees, rfr_factors* outs, int* statuses);
 
 /* Serving API (continuous batching).  rfr_submit copies the input and
  * queues it; workers admit queued requests into batches as slots and device

@@ -27,6 +27,12 @@ extern "C" {
  * powers, entries above each problem's degree ignored. */
 #define RFR_LDC (RFR_MAX_DEGREE + 1)
 
+/* Status value of the validate and roots stages: square-free not proven
+ * modulo primes; the roots stage decides (disjoint inclusion discs prove
+ * distinct roots) and reports RFR_E_NOT_SQUAREFREE if it cannot separate
+ * them.  Never returned by the rfr.h calls. */
+#define RFR_SF_SUSPECT 2
+
 /* Per-polynomial plan written by the weights stage (one per problem).
  * Elements are the factors of Eq. 1 in canonical order: real roots
  * ascending, then conjugate pairs by (Re z, Im z) of the member with
@@ -52,12 +58,23 @@ typedef struct {
     uint8_t  root1[RFR_MAX_DEGREE];/* conjugate partner's root index (pairs only)       */
 } rfr_plan;
 
+/* K-v validate.  status[i] = RFR_OK, RFR_SF_SUSPECT, RFR_E_RANGE (degree
+ * outside [1,128] or |a_k| >= 2^53) or RFR_E_NOT_MONIC for the polynomial
+ * coeffs[i*RFR_LDC ..] of degree degrees[i].  Square-free is proven when
+ * gcd(p, p') is constant modulo 2^31-1 or 2^61-1 (Section 2 assumes
+ * square-free input). */
+int rfr_stage_validate(const int64_t* coeffs, const int32_t* degrees, int batch,
+                       int32_t* status, void* stream);
+
 /* K-a roots.  For problem i (degree degrees[i]) writes its roots to
  * roots[i*RFR_MAX_DEGREE*4 + 4*j + {0,1,2,3}] = (Re hi, Re lo, Im hi, Im lo)
  * as double-double values, the inclusion radius of root j to
  * radius[i*RFR_MAX_DEGREE + j] (a disc of that radius around the root
  * contains exactly one root of p when the discs are disjoint), and RFR_OK,
- * RFR_E_NO_CONVERGENCE or RFR_E_RANGE to status[i].
+ * RFR_E_NO_CONVERGENCE or RFR_E_RANGE to status[i].  status is in/out: on
+ * entry a negative value skips problem i (kept), RFR_SF_SUSPECT is carried
+ * through (and turns non-convergence into RFR_E_NOT_SQUAREFREE), anything
+ * else must be RFR_OK.
  * root_mode: RFR_ROOTS_FP64 or RFR_ROOTS_FP32_BULK.  Section 2, Eq. 1. */
 int rfr_stage_roots(const int64_t* coeffs, const int32_t* degrees, int batch,
                     int root_mode, double* roots, double* radius,

@@ -48,7 +48,8 @@ class Diag(C.Structure):
                 ("window", C.c_uint64), ("half_sums", C.c_uint64), ("cand_coarse", C.c_uint64),
                 ("cand_pre", C.c_uint64), ("cand_post", C.c_uint64), ("verified", C.c_uint64),
                 ("max_rel_residual", C.c_double), ("max_root_err", C.c_double),
-                ("stage_us", C.c_double * 8)]
+                ("stage_us", C.c_double * 8), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
+                ("launches", C.c_uint32), ("batch_size", C.c_uint32)]
 
 
 class Factors(C.Structure):
@@ -90,6 +91,8 @@ def lib():
         "rfr_set_allocator": (i32, [vp, ALLOC_FN, FREE_FN, vp]),
         "rfr_factor": (i32, [vp, i64p, i32, C.POINTER(Factors)]),
         "rfr_factor_batch": (i32, [vp, i32, C.POINTER(i64p), C.POINTER(C.c_int), C.POINTER(Factors), C.POINTER(C.c_int)]),
+        "rfr_factor_batch_device": (i32, [vp, i32, vp, vp, C.POINTER(Factors), C.POINTER(C.c_int)]),
+        "rfr_stage_validate": (i32, [vp, vp, i32, vp, vp]),
         "rfr_submit": (i32, [vp, i64p, i32, C.POINTER(u64)]),
         "rfr_poll": (i32, [vp, u64, C.POINTER(Factors)]),
         "rfr_wait": (i32, [vp, u64, i32, C.POINTER(Factors)]),
@@ -216,6 +219,20 @@ class Context:
             raise RFRError(rc, "rfr_factor_batch")
         return [_to_result(sts[i], outs[i]) for i in range(n)]
 
+    def factor_batch_device(self, coeffs, degrees) -> List[Result]:
+        """coeffs: int64 cuda tensor [count, 129] (ascending rows); degrees:
+        int32 cuda tensor [count].  Inputs stay in device memory."""
+        n = int(coeffs.shape[0])
+        outs = (Factors * n)()
+        sts = (C.c_int * n)()
+        rc = lib().rfr_factor_batch_device(self._h, n, C.c_void_p(coeffs.data_ptr()),
+                                           C.c_void_p(degrees.data_ptr()), outs, sts)
+        if rc != RFR_OK:
+            for i in range(n):
+                lib().rfr_factors_free(C.byref(outs[i]))
+            raise RFRError(rc, "rfr_factor_batch_device")
+        return [_to_result(sts[i], outs[i]) for i in range(n)]
+
     def submit(self, coeffs: Sequence[int]) -> int:
         t = C.c_uint64()
         st = lib().rfr_submit(self._h, _coeff_array(coeffs), len(coeffs) - 1, C.byref(t))
@@ -256,6 +273,15 @@ def _stream():
 def _check(st, what):
     if st != RFR_OK:
         raise RFRError(st, what)
+
+
+def stage_validate(coeffs, degrees):
+    """Device input checks; returns status int32 [B] (RFR_OK, RFR_SF_SUSPECT = 2, or an error)."""
+    import torch
+    B = coeffs.shape[0]
+    status = torch.zeros((B,), dtype=torch.int32, device=coeffs.device)
+    _check(lib().rfr_stage_validate(_ptr(coeffs), _ptr(degrees), B, _ptr(status), _stream()), "rfr_stage_validate")
+    return status
 
 
 def stage_roots(coeffs, degrees, root_mode: int = RFR_ROOTS_FP64):

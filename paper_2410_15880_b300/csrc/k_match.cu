@@ -9,17 +9,21 @@
 // with the circular reading (sums near 0 and near 2^64 both count).
 //
 // Layout and passes (per problem, all problems of a batch in each launch):
-//  * K-c + radix digit 1 (top d1 key bits, 4..8192 buckets):
-//      k_count   — Gray-code enumeration of every pattern, per-CTA bucket
-//                  histogram in shared memory;
+//  * Radix digit 1 (top d1 key bits, 4..8192 buckets), produced from sorted
+//    runs.  A half's h elements split into low bits 0..l-1 (l <= 16) and high
+//    bits l..h-1:
+//      k_ysort — list Y of the 2^l low-subset sums (low l key bits replaced by
+//                the low mask), sorted by a stable LSD radix sort (one CTA);
+//      k_runs<count>   — walks every run x + Y (one per high subset x);
+//                the keys of a run rise, so the 32 lanes of a step fall into
+//                a few buckets and one atomic per bucket group updates the
+//                per-CTA histogram;
 //      k_colscan / k_bscan — per-CTA offsets and bucket starts;
-//      k_scatter — the same enumeration again, each record written to its
-//                  bucket at a shared-memory cursor, so every CTA fills a
-//                  contiguous run of each bucket.
-//    Record (8 bytes): ((key << d1) & ~(2^h - 1)) | mask.  The top d1 key
-//    bits are implied by the bucket, so the record keeps key bits
-//    [63-d1 .. h-d1] and the pattern's mask; the truncation is below
-//    2^max(0, h-d1).
+//      k_runs<scatter> — the same walk, each bucket group reserving
+//                consecutive slots at the bucket's cursor and writing them.
+//    Record (8 bytes): ((key << d1) & ~(2^h - 1)) | mask, key = x + (y with
+//    its low l bits cleared).  The top d1 key bits are implied by the bucket;
+//    the coarse key is below the true sum by less than 2^l + 2^max(0, h-d1).
 //  * Radix digit 2 + K-e (k_join), one CTA per bucket: the bucket's table-a
 //    records are counting-sorted by the next 13 key bits into shared memory
 //    (chunks of 9216), then every table-b record of the bucket streams past
@@ -160,36 +164,275 @@ __global__ void __launch_bounds__(256) k_enum_plain(const uint64_t* __restrict__
     }
 }
 
-// ---------------------------------------------------------------- K-c + digit 1
-__global__ void __launch_bounds__(PART_THREADS) k_count(const HalfJob* __restrict__ hs, int nh) {
-    extern __shared__ uint32_t sh_hist[];
+// ---------------------------------------------------------------- K-d: sorted low list
+// One stable LSD pass over src[0..N) -> dst by the 8-bit digit at `shift`.
+// Warp w owns the contiguous input chunk w; ranks inside a warp come from
+// __match_any_sync, so equal digits keep their input order (stable).
+__device__ void lsd_pass(const uint64_t* src, uint64_t* dst, uint32_t N, int shift,
+                         uint32_t (*whist)[256], uint32_t* dbase, uint32_t* warp_sums) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t chunk = (N + 31) / 32;
+    const uint32_t b0 = min(N, (uint32_t)w * chunk), b1 = min(N, b0 + chunk);
+    for (int d = lane; d < 256; d += 32) whist[w][d] = 0u;
+    __syncwarp();
+    for (uint32_t base = b0; base < b1; base += 32) {
+        const uint32_t i = base + lane;
+        const bool valid = i < b1;
+        const uint64_t v = valid ? src[i] : 0ull;
+        const uint32_t d = valid ? (uint32_t)((v >> shift) & 255u) : 256u + lane;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (valid && lane == __ffs(peers) - 1) whist[w][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    uint32_t tot = 0;
+    if (threadIdx.x < 256)
+        for (int ww = 0; ww < 32; ++ww) {
+            const uint32_t c = whist[ww][threadIdx.x];
+            whist[ww][threadIdx.x] = tot;
+            tot += c;
+        }
+    uint32_t total;
+    const uint32_t ex = block_excl_scan(threadIdx.x < 256 ? tot : 0u, &total, warp_sums);
+    if (threadIdx.x < 256) dbase[threadIdx.x] = ex;
+    __syncthreads();
+    if (threadIdx.x < 256)
+        for (int ww = 0; ww < 32; ++ww) whist[ww][threadIdx.x] += dbase[threadIdx.x];
+    __syncthreads();
+    for (uint32_t base = b0; base < b1; base += 32) {
+        const uint32_t i = base + lane;
+        const bool valid = i < b1;
+        const uint64_t v = valid ? src[i] : 0ull;
+        const uint32_t d = valid ? (uint32_t)((v >> shift) & 255u) : 256u + lane;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid) dst[whist[w][d] + rank] = v;
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) whist[w][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+}
+
+// One CTA per half: Y[j] = (sum_{i < l, bit i of j} sw[i] with its low l bits
+// cleared) | j, for every j < 2^l, then sorted ascending by an LSD radix sort
+// over bits [l, 64) (the low l bits hold the mask and need no ordering).
+__global__ void __launch_bounds__(YSORT_THREADS) k_ysort(const HalfJob* __restrict__ hs, int nh) {
+    __shared__ uint64_t sw[32];
+    __shared__ uint32_t whist[32][256];
+    __shared__ uint32_t dbase[256];
+    __shared__ uint32_t warp_sums[32];
+    const HalfJob J = hs[blockIdx.x];
+    const int l = J.l;
+    const uint32_t N = 1u << l;
+    if (threadIdx.x < J.h) {
+        const uint64_t v = J.w[threadIdx.x];
+        sw[threadIdx.x] = J.neg ? 0ull - v : v;
+    }
+    __syncthreads();
+    const uint64_t lm = lowmask(l);
+    const int passes = N > 1 ? (64 - l + 7) / 8 : 0;
+    uint64_t* bufs[2] = {J.ylist, J.ytmp};
+    int cur = passes & 1;                       // after `passes` swaps the result is in ylist
+    uint64_t* out = bufs[cur];
+    enumerate_range(sw, 0, N, [&](uint64_t m, uint64_t key) { out[m] = (key & ~lm) | m; });
+    __syncthreads();
+    for (int p = 0; p < passes; ++p) {
+        lsd_pass(bufs[cur], bufs[cur ^ 1], N, l + 8 * p, whist, dbase, warp_sums);
+        cur ^= 1;
+    }
+}
+
+// Walk the runs x + Y (one per high subset x) of this CTA's share of the
+// half and, per bucket, count (COUNT) or write (SCATTER) its records.  In a
+// step of 32 elements the lanes are grouped by bucket (__match_any_sync) and
+// the group's leader adds the group size to the bucket's counter or reserves
+// that many consecutive slots at the bucket's cursor; the order of records
+// inside a bucket is irrelevant to the match.
+//
+// Range mode (at least 16 runs per CTA): the CTA sweeps the buckets in
+// ranges of 256.  Because Y is sorted, each run x + Y rotated to its smallest
+// key rises, so the records of a run in one bucket range are one contiguous
+// stretch; a per-run cursor remembers where the next range starts.  Only the
+// cursors of the current range are open, so every bucket's output sectors
+// are completed while still in L2.  Warps take runs round robin.
+// Piece mode (small halves): warps take pieces of up to 4096 consecutive
+// run elements and all buckets stay open (the tables fit in L2 anyway).
+constexpr int PIECE = 4096;
+constexpr int UNROLL = 4;
+constexpr int RANGE = 256;                    // buckets per sweep
+constexpr int MAX_RUNS_PER_CTA = 1024;
+// Piece mode only runs for halves with fewer than 16 runs (h < 20, so at most
+// 2^6 buckets); 64 KB covers it and range mode with room to spare.
+constexpr int RUNS_SMEM_MAX = 64 * 1024;
+
+struct RunCtx {
+    uint64_t lml, lmh, trunc, width, wc, hcap;
+    int d1, NB, sh, l, h, neg;
+};
+
+// Handle one element (already loaded) of run x: returns its bucket.
+template <bool SCATTER>
+__device__ __forceinline__ void emit(const HalfJob& J, const RunCtx& R, uint32_t* acc, uint32_t acc_base,
+                                     bool valid, uint64_t K, uint32_t k, uint64_t m, uint32_t lane_lt) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t peers = __match_any_sync(0xffffffffu, valid ? k : 0x80000000u + lane);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (valid && lane == leader) base = atomicAdd(&acc[k - acc_base], (uint32_t)__popc(peers));
+    if (SCATTER) {
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (valid) J.tab[base + __popc(peers & lane_lt)] = ((K << R.d1) & ~R.lmh) | m;
+    }
+    if (valid && R.neg) {
+        const uint64_t Kc = K & ~R.trunc;
+        const uint64_t off = Kc - ((uint64_t)k << R.sh);
+        const uint32_t kl = (k - 1u) & (uint32_t)(R.NB - 1), kh = (k + 1u) & (uint32_t)(R.NB - 1);
+        if (SCATTER) {
+            if (off < R.wc) {
+                const uint32_t hp = atomicAdd(&J.halo_cur[kl], 1u);
+                if (hp < R.hcap) { J.halo[2 * (size_t)hp] = Kc; J.halo[2 * (size_t)hp + 1] = m; }
+            }
+            if (R.width - off <= R.wc) {
+                const uint32_t hp = atomicAdd(&J.halo_cur[kh], 1u);
+                if (hp < R.hcap) { J.halo[2 * (size_t)hp] = Kc; J.halo[2 * (size_t)hp + 1] = m; }
+            }
+        } else {
+            if (off < R.wc) atomicAdd(&J.halo_cnt[kl], 1u);
+            if (R.width - off <= R.wc) atomicAdd(&J.halo_cnt[kh], 1u);
+        }
+    }
+}
+
+template <bool SCATTER>
+__global__ void __launch_bounds__(PART_THREADS) k_runs(const HalfJob* __restrict__ hs, int nh) {
+    extern __shared__ uint32_t dyn[];
     __shared__ uint64_t sw[32];
     const int j = find_last_le(nh, (int)blockIdx.x, [&](int i) { return hs[i].cta_base; });
     const HalfJob J = hs[j];
     const int c = blockIdx.x - J.cta_base;
-    const int d1 = J.d1, NB = 1 << d1, sh = 64 - d1;
-    for (int b = threadIdx.x; b < NB; b += blockDim.x) sh_hist[b] = 0u;
-    if (threadIdx.x < J.h) sw[threadIdx.x] = J.w[threadIdx.x];
-    __syncthreads();
-    const uint64_t per = (1ull << J.h) / (uint64_t)J.ctas;
-    const int tr = J.h > d1 ? J.h - d1 : 0;
-    const uint64_t trunc = lowmask(tr);
-    const uint64_t width = 1ull << sh, wc = J.wc;
-    const int neg = J.neg;
-    uint32_t* halo_cnt = J.halo_cnt;
-    enumerate_range(sw, per * (uint64_t)c, per, [&](uint64_t m, uint64_t key) {
-        const uint64_t K = neg ? (0ull - key) : key;
-        const uint32_t b = (uint32_t)(K >> sh);
-        atomicAdd(&sh_hist[b], 1u);
-        if (neg) {
-            const uint64_t off = (K & ~trunc) - ((uint64_t)b << sh);
-            if (off < wc) atomicAdd(&halo_cnt[(b - 1u) & (uint32_t)(NB - 1)], 1u);
-            if (width - off <= wc) atomicAdd(&halo_cnt[(b + 1u) & (uint32_t)(NB - 1)], 1u);
+    RunCtx R;
+    R.d1 = J.d1; R.NB = 1 << R.d1; R.sh = 64 - R.d1; R.l = J.l; R.h = J.h; R.neg = J.neg;
+    R.lml = lowmask(R.l); R.lmh = lowmask(R.h);
+    R.trunc = lowmask(R.h > R.d1 ? R.h - R.d1 : 0);
+    R.width = 1ull << R.sh; R.wc = J.wc; R.hcap = J.halo_cap;
+    if (threadIdx.x < R.h) {
+        const uint64_t v = J.w[threadIdx.x];
+        sw[threadIdx.x] = J.neg ? 0ull - v : v;
+    }
+    const int l = R.l, NB = R.NB;
+    const uint32_t N = 1u << l;
+    const uint64_t* __restrict__ Y = J.ylist;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int hx = R.h - l;
+    const bool range_mode = hx >= 4 && ((1 << hx) / J.ctas) >= 16;
+
+    if (!range_mode) {
+        uint32_t* acc = dyn;                  // all NB buckets
+        for (int b = threadIdx.x; b < NB; b += blockDim.x)
+            acc[b] = SCATTER ? J.bstart[b] + J.hist[(size_t)c * NB + b] : 0u;
+        __syncthreads();
+        const uint32_t piece = N < (uint32_t)PIECE ? N : (uint32_t)PIECE;
+        const uint32_t per_run = N / piece;
+        const uint64_t pieces = (1ull << R.h) / piece;
+        const uint64_t p0 = pieces * (uint64_t)c / (uint64_t)J.ctas, p1 = pieces * (uint64_t)(c + 1) / (uint64_t)J.ctas;
+        for (uint64_t pc = p0 + warp; pc < p1; pc += nwarps) {
+            const uint32_t xi = (uint32_t)(pc / per_run);
+            const uint32_t tbeg = (uint32_t)(pc % per_run) * piece;
+            uint64_t x = 0;
+            for (uint32_t t = xi; t; t &= t - 1) x += sw[l + __ffs(t) - 1];
+            const uint64_t xmask = (uint64_t)xi << l;
+            for (uint32_t t0 = tbeg; t0 < tbeg + piece; t0 += 32 * UNROLL) {
+                uint64_t yv[UNROLL];
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    const uint32_t t = t0 + 32 * u + lane;
+                    yv[u] = t < tbeg + piece ? Y[t] : 0ull;
+                }
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    const uint32_t t = t0 + 32 * u + lane;
+                    const uint64_t K = x + (yv[u] & ~R.lml);
+                    emit<SCATTER>(J, R, acc, 0u, t < tbeg + piece, K, (uint32_t)(K >> R.sh),
+                                  xmask | (yv[u] & R.lml), lt);
+                }
+            }
         }
-    });
+        if (!SCATTER) {
+            __syncthreads();
+            uint32_t* out = J.hist + (size_t)c * NB;
+            for (int b = threadIdx.x; b < NB; b += blockDim.x) out[b] = acc[b];
+        }
+        return;
+    }
+
+    // ---- range mode
+    const uint32_t G = (1u << hx) / (uint32_t)J.ctas;            // runs of this CTA (16..1024)
+    const uint32_t x0 = (uint32_t)c * G;
+    uint32_t* acc = dyn;                                         // [RANGE] cursors of the current range
+    uint32_t* curx = dyn + RANGE;                                // [G] next rotated index of each run
+    uint32_t* j0s = curx + MAX_RUNS_PER_CTA;                     // [G] rotation (index of the smallest key)
     __syncthreads();
-    uint32_t* out = J.hist + (size_t)c * NB;
-    for (int b = threadIdx.x; b < NB; b += blockDim.x) out[b] = sh_hist[b];
+    for (uint32_t g = threadIdx.x; g < G; g += blockDim.x) {
+        uint64_t x = 0;
+        for (uint32_t t = x0 + g; t; t &= t - 1) x += sw[l + __ffs(t) - 1];
+        const uint64_t T = 0ull - x;
+        uint32_t lo = 0, hi = N;                                 // first index with (Y & ~lml) >= 2^64 - x
+        if (x != 0) {
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if ((Y[mid] & ~R.lml) >= T) hi = mid; else lo = mid + 1;
+            }
+        }
+        j0s[g] = lo == N ? 0u : lo;
+        curx[g] = 0u;
+    }
+    const int nrange = NB > RANGE ? NB / RANGE : 1;
+    const int rw = NB > RANGE ? RANGE : NB;
+    for (int r = 0; r < nrange; ++r) {
+        const uint32_t k0 = (uint32_t)r * rw, kend = k0 + rw;
+        __syncthreads();
+        for (int b = threadIdx.x; b < rw; b += blockDim.x)
+            acc[b] = SCATTER ? J.bstart[k0 + b] + J.hist[(size_t)c * NB + k0 + b] : 0u;
+        __syncthreads();
+        for (uint32_t g = warp; g < G; g += nwarps) {
+            const uint32_t xi = x0 + g;
+            uint64_t x = 0;
+            for (uint32_t t = xi; t; t &= t - 1) x += sw[l + __ffs(t) - 1];
+            const uint64_t xmask = (uint64_t)xi << l;
+            const uint32_t j0 = j0s[g];
+            uint32_t t0 = curx[g];
+            bool done = t0 >= N;
+            while (!done) {
+                uint64_t yv[UNROLL];
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    const uint32_t t = t0 + 32 * u + lane;
+                    yv[u] = t < N ? Y[(j0 + t) & (N - 1)] : 0ull;
+                }
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    if (done) break;
+                    const uint32_t t = t0 + 32 * u + lane;
+                    const uint64_t K = x + (yv[u] & ~R.lml);
+                    const uint32_t k = (uint32_t)(K >> R.sh);
+                    const bool stop = t >= N || k >= kend;       // keys rise along the rotated run
+                    const uint32_t stops = __ballot_sync(0xffffffffu, stop);
+                    emit<SCATTER>(J, R, acc, k0, !stop, K, k, xmask | (yv[u] & R.lml), lt);
+                    if (stops) {
+                        done = true;
+                        t0 = t0 + 32 * u + (__ffs(stops) - 1);
+                    }
+                }
+                if (!done) t0 += 32 * UNROLL;
+            }
+            if (lane == 0) curx[g] = t0;
+        }
+        __syncthreads();
+        if (!SCATTER)
+            for (int b = threadIdx.x; b < rw; b += blockDim.x) J.hist[(size_t)c * NB + k0 + b] = acc[b];
+    }
 }
 
 __global__ void __launch_bounds__(256) k_colscan(const HalfJob* __restrict__ hs, int nh) {
@@ -220,45 +463,6 @@ __global__ void __launch_bounds__(1024) k_bscan(const HalfJob* __restrict__ hs, 
         for (int b = threadIdx.x; b < NB; b += blockDim.x) J.halo_cur[b] = J.halo_cnt[b];
         if (threadIdx.x == 0 && (uint64_t)J.halo_cnt[NB] > J.halo_cap) atomicExch(J.err, 1);
     }
-}
-
-__global__ void __launch_bounds__(PART_THREADS) k_scatter(const HalfJob* __restrict__ hs, int nh) {
-    extern __shared__ uint32_t cur[];
-    __shared__ uint64_t sw[32];
-    const int j = find_last_le(nh, (int)blockIdx.x, [&](int i) { return hs[i].cta_base; });
-    const HalfJob J = hs[j];
-    const int c = blockIdx.x - J.cta_base;
-    const int d1 = J.d1, NB = 1 << d1, sh = 64 - d1;
-    for (int b = threadIdx.x; b < NB; b += blockDim.x) cur[b] = J.bstart[b] + J.hist[(size_t)c * NB + b];
-    if (threadIdx.x < J.h) sw[threadIdx.x] = J.w[threadIdx.x];
-    __syncthreads();
-    const uint64_t per = (1ull << J.h) / (uint64_t)J.ctas;
-    const uint64_t lm = lowmask(J.h);
-    const int tr = J.h > d1 ? J.h - d1 : 0;
-    const uint64_t trunc = lowmask(tr);
-    const uint64_t width = 1ull << sh, wc = J.wc, hcap = J.halo_cap;
-    const int neg = J.neg;
-    uint64_t* tab = J.tab;
-    uint64_t* halo = J.halo;
-    uint32_t* halo_cur = J.halo_cur;
-    enumerate_range(sw, per * (uint64_t)c, per, [&](uint64_t m, uint64_t key) {
-        const uint64_t K = neg ? (0ull - key) : key;
-        const uint32_t b = (uint32_t)(K >> sh);
-        const uint32_t p = atomicAdd(&cur[b], 1u);
-        tab[p] = ((K << d1) & ~lm) | m;
-        if (neg) {
-            const uint64_t Kc = K & ~trunc;
-            const uint64_t off = Kc - ((uint64_t)b << sh);
-            if (off < wc) {
-                const uint32_t hp = atomicAdd(&halo_cur[(b - 1u) & (uint32_t)(NB - 1)], 1u);
-                if (hp < hcap) { halo[2 * (size_t)hp] = Kc; halo[2 * (size_t)hp + 1] = m; }
-            }
-            if (width - off <= wc) {
-                const uint32_t hp = atomicAdd(&halo_cur[(b + 1u) & (uint32_t)(NB - 1)], 1u);
-                if (hp < hcap) { halo[2 * (size_t)hp] = Kc; halo[2 * (size_t)hp + 1] = m; }
-            }
-        }
-    });
 }
 
 // ---------------------------------------------------------------- digit 2 + K-e
@@ -297,60 +501,77 @@ __global__ void __launch_bounds__(JOIN_THREADS, 2) k_join(const ProbJob* __restr
     const uint64_t* __restrict__ halo = P.B.halo;
     unsigned long long n_coarse = 0, n_pre = 0;
     __syncthreads();
+    constexpr int U = 4;                       // independent loads in flight per thread
+    const uint32_t stride = blockDim.x * U;
     for (uint32_t cs = a0; cs < a1; cs += JOIN_CAP) {
         const uint32_t m = min((uint32_t)JOIN_CAP, a1 - cs);
         for (int s = threadIdx.x; s < (1 << SUB_BITS); s += blockDim.x) off[s] = 0u;
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
-            const uint64_t r = tabA[cs + i];
-            const uint64_t dk = (r & ~la) >> d1;          // key offset inside the bucket
-            atomicAdd(&off[dk >> subsh], 1u);
+        for (uint32_t i0 = threadIdx.x; i0 < m; i0 += stride) {
+            uint64_t r[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) r[u] = i0 + u * blockDim.x < m ? tabA[cs + i0 + u * blockDim.x] : 0ull;
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (i0 + u * blockDim.x < m) atomicAdd(&off[((r[u] & ~la) >> d1) >> subsh], 1u);
         }
         __syncthreads();
         block_scan_array(off, 1 << SUB_BITS, false, warp_sums);
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
-            const uint64_t r = tabA[cs + i];
-            const uint64_t dk = (r & ~la) >> d1;
-            const uint32_t p = atomicAdd(&off[dk >> subsh], 1u);
-            As[p] = r;
+        for (uint32_t i0 = threadIdx.x; i0 < m; i0 += stride) {
+            uint64_t r[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) r[u] = i0 + u * blockDim.x < m ? tabA[cs + i0 + u * blockDim.x] : 0ull;
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (i0 + u * blockDim.x < m) As[atomicAdd(&off[((r[u] & ~la) >> d1) >> subsh], 1u)] = r[u];
         }
         __syncthreads();
-        for (uint32_t t = threadIdx.x; t < nbt; t += blockDim.x) {
-            uint64_t Kb, mb;
-            if (t < nbn) {
-                const uint64_t r = tabB[b0 + t];
-                Kb = lo_k | ((r & ~lb) >> d1);
-                mb = r & lb;
-            } else {
-                const size_t hi = 2 * (size_t)(h0 + (t - nbn));
-                Kb = halo[hi];
-                mb = halo[hi + 1];
+        for (uint32_t t0 = threadIdx.x; t0 < nbt; t0 += stride) {
+            uint64_t rb[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t t = t0 + u * blockDim.x;
+                rb[u] = t < nbn ? tabB[b0 + t] : 0ull;
             }
-            long long dlo = (long long)(Kb - Wc + 1ull - lo_k);
-            long long dhi = (long long)(Kb + Wc - 1ull - lo_k);
-            if (dhi < 0 || dlo >= width) continue;
-            if (dlo < 0) dlo = 0;
-            if (dhi > width - 1) dhi = width - 1;
-            const int s_lo = (int)(dlo >> subsh), s_hi = (int)(dhi >> subsh);
-            const uint32_t p0 = s_lo ? off[s_lo - 1] : 0u, p1 = off[s_hi];
-            for (uint32_t p = p0; p < p1; ++p) {
-                const uint64_t ra = As[p];
-                const uint64_t Ka = lo_k | ((ra & ~la) >> d1);
-                const long long diff = (long long)(Ka - Kb);
-                if (diff > -(long long)Wc && diff < (long long)Wc) {
-                    ++n_coarse;
-                    const uint64_t ma = ra & la;
-                    const uint64_t v = subset_sum(wa, ma) + subset_sum(wb, mb);
-                    if (circ_dist(v) <= W) {
-                        ++n_pre;
-                        const uint64_t t2 = subset_sum(w2a, ma) + subset_sum(w2b, mb);
-                        if (circ_dist(t2) <= W2) {
-                            if (ma == 0 && mb == 0) {
-                                P.ctr[3] = 1ull;
-                            } else {
-                                const unsigned long long idx = atomicAdd(&P.ctr[2], 1ull);
-                                if (idx < P.cap) P.cand[idx] = ma | (mb << n_a);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t t = t0 + u * blockDim.x;
+                if (t >= nbt) continue;
+                uint64_t Kb, mb;
+                if (t < nbn) {
+                    Kb = lo_k | ((rb[u] & ~lb) >> d1);
+                    mb = rb[u] & lb;
+                } else {
+                    const size_t hi = 2 * (size_t)(h0 + (t - nbn));
+                    Kb = halo[hi];
+                    mb = halo[hi + 1];
+                }
+                long long dlo = (long long)(Kb - Wc + 1ull - lo_k);
+                long long dhi = (long long)(Kb + Wc - 1ull - lo_k);
+                if (dhi < 0 || dlo >= width) continue;
+                if (dlo < 0) dlo = 0;
+                if (dhi > width - 1) dhi = width - 1;
+                const int s_lo = (int)(dlo >> subsh), s_hi = (int)(dhi >> subsh);
+                const uint32_t p0 = s_lo ? off[s_lo - 1] : 0u, p1 = off[s_hi];
+                for (uint32_t p = p0; p < p1; ++p) {
+                    const uint64_t ra = As[p];
+                    const uint64_t Ka = lo_k | ((ra & ~la) >> d1);
+                    const long long diff = (long long)(Ka - Kb);
+                    if (diff > -(long long)Wc && diff < (long long)Wc) {
+                        ++n_coarse;
+                        const uint64_t ma = ra & la;
+                        const uint64_t v = subset_sum(wa, ma) + subset_sum(wb, mb);
+                        if (circ_dist(v) <= W) {
+                            ++n_pre;
+                            const uint64_t t2 = subset_sum(w2a, ma) + subset_sum(w2b, mb);
+                            if (circ_dist(t2) <= W2) {
+                                if (ma == 0 && mb == 0) {
+                                    P.ctr[3] = 1ull;
+                                } else {
+                                    const unsigned long long idx = atomicAdd(&P.ctr[2], 1ull);
+                                    if (idx < P.cap) P.cand[idx] = ma | (mb << n_a);
+                                }
                             }
                         }
                     }
@@ -376,6 +597,8 @@ static uint64_t default_halo_cap(int n_b, int d1, uint64_t wc) {
 size_t match_bytes(const MatchGeom& g) {
     const size_t NB = (size_t)1 << g.d1;
     size_t b = 0;
+    b += 2 * align256(((size_t)1 << g.l_a) * 8);
+    b += 2 * align256(((size_t)1 << g.l_b) * 8);
     b += align256(((size_t)1 << g.n_a) * 8);
     b += align256(((size_t)1 << g.n_b) * 8);
     b += align256((size_t)g.ctas_a * NB * 4);
@@ -386,21 +609,38 @@ size_t match_bytes(const MatchGeom& g) {
     return b;
 }
 
+// CTAs of a half: range mode (16 .. 1024 runs per CTA) when it has at least
+// 16 runs, else at most one CTA per piece of up to 4096 run elements.
+static int clamp_ctas(int h, int l, int want) {
+    const int hx = h - l;
+    if (hx >= 4) {
+        int lo = hx > 10 ? 1 << (hx - 10) : 1, hi = 1 << (hx - 4);
+        int c = want < lo ? lo : (want > hi ? hi : want);
+        return c;
+    }
+    const int pieces = h > 12 ? 1 << (h - 12) : 1;
+    return want < pieces ? (want < 1 ? 1 : want) : pieces;
+}
+
 bool match_geometry(int n_a, int n_b, uint64_t W, int ctas_a, int ctas_b, MatchGeom* g) {
     if (n_a < 0 || n_b < n_a || n_b > 32) return false;
+    const int l_a = n_a < MAX_L ? n_a : MAX_L, l_b = n_b < MAX_L ? n_b : MAX_L;
     int d1 = n_a - 13;
     if (d1 < 2) d1 = 2;
     if (d1 > MAX_D1) d1 = MAX_D1;
     uint64_t wc = 0;
     for (; d1 >= 2; --d1) {
+        // coarse keys lose < 2^l (truncated low-list sums) + 2^tr (record truncation)
         const int tr = n_b > d1 ? n_b - d1 : 0;
-        wc = W + (1ull << tr);
+        wc = W + (1ull << l_b) + (1ull << tr);
         if (wc < W) continue;                                  // overflow
         if (wc < (1ull << (64 - d1)) / 4) break;
     }
     if (d1 < 2) return false;
     g->n_a = n_a; g->n_b = n_b; g->d1 = d1; g->wc = wc;
-    g->ctas_a = ctas_a; g->ctas_b = ctas_b;
+    g->l_a = l_a; g->l_b = l_b;
+    g->ctas_a = clamp_ctas(n_a, l_a, ctas_a);
+    g->ctas_b = clamp_ctas(n_b, l_b, ctas_b);
     g->hcap = default_halo_cap(n_b, d1, wc);
     g->bytes = match_bytes(*g);
     return true;
@@ -412,6 +652,11 @@ void match_layout(const MatchGeom& g, char* ws, ProbJob* pj) {
     auto take = [&](size_t bytes) { char* q = p; p += align256(bytes); return q; };
     HalfJob& A = pj->A;
     HalfJob& B = pj->B;
+    A.ylist = (uint64_t*)take(((size_t)1 << g.l_a) * 8);
+    A.ytmp = (uint64_t*)take(((size_t)1 << g.l_a) * 8);
+    B.ylist = (uint64_t*)take(((size_t)1 << g.l_b) * 8);
+    B.ytmp = (uint64_t*)take(((size_t)1 << g.l_b) * 8);
+    A.l = g.l_a; B.l = g.l_b;
     A.tab = (uint64_t*)take(((size_t)1 << g.n_a) * 8);
     B.tab = (uint64_t*)take(((size_t)1 << g.n_b) * 8);
     A.hist = (uint32_t*)take((size_t)g.ctas_a * NB * 4);
@@ -432,10 +677,15 @@ void match_layout(const MatchGeom& g, char* ws, ProbJob* pj) {
 }
 
 // Assign grid bases for a set of problems; fills halves[2*np].
-struct MatchGrid { int part_ctas, scan_ctas, join_ctas, nb_max; };
+struct MatchGrid { int part_ctas, scan_ctas, join_ctas, nb_max, nb_small; };
+
+static bool is_range_mode(const HalfJob& h) {
+    const int hx = h.h - h.l;
+    return hx >= 4 && ((1 << hx) / h.ctas) >= 16;
+}
 
 static MatchGrid assign_bases(ProbJob* jobs, int np, HalfJob* halves) {
-    MatchGrid g{0, 0, 0, 0};
+    MatchGrid g{0, 0, 0, 0, 0};
     for (int i = 0; i < np; ++i) {
         ProbJob& P = jobs[i];
         const int NB = 1 << P.d1;
@@ -445,6 +695,7 @@ static MatchGrid assign_bases(ProbJob* jobs, int np, HalfJob* halves) {
             g.part_ctas += hh[t]->ctas;
             hh[t]->scan_base = g.scan_ctas;
             g.scan_ctas += (NB + 255) / 256;
+            if (!is_range_mode(*hh[t]) && NB > g.nb_small) g.nb_small = NB;
             halves[2 * i + t] = *hh[t];
         }
         P.join_base = g.join_ctas;
@@ -460,9 +711,13 @@ static const size_t JOIN_SMEM = (size_t)JOIN_CAP * 8 + ((size_t)1 << SUB_BITS) *
 // Upload jobs (from host memory that stays valid until the copies finish:
 // pageable memory is staged before cudaMemcpyAsync returns) and launch.
 cudaError_t run_match(ProbJob* jobs, int np, ProbJob* dev_jobs, HalfJob* dev_halves,
-                      HalfJob* host_halves, cudaStream_t s, cudaEvent_t ev_mid) {
+                      HalfJob* host_halves, cudaStream_t s, cudaEvent_t ev_count, cudaEvent_t ev_scatter) {
     if (!g_attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_join, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)JOIN_SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_runs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RUNS_SMEM_MAX);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_runs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RUNS_SMEM_MAX);
         if (e != cudaSuccess) return e;
         g_attr_set = true;
     }
@@ -472,12 +727,16 @@ cudaError_t run_match(ProbJob* jobs, int np, ProbJob* dev_jobs, HalfJob* dev_hal
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(dev_jobs, jobs, sizeof(ProbJob) * np, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
-    const size_t psmem = (size_t)g.nb_max * 4;
-    k_count<<<g.part_ctas, PART_THREADS, psmem, s>>>(dev_halves, 2 * np);
+    size_t psmem = (size_t)(RANGE + 2 * MAX_RUNS_PER_CTA) * 4;
+    if ((size_t)g.nb_small * 4 > psmem) psmem = (size_t)g.nb_small * 4;
+    if (psmem > (size_t)RUNS_SMEM_MAX) return cudaErrorInvalidConfiguration;
+    k_ysort<<<2 * np, YSORT_THREADS, 0, s>>>(dev_halves, 2 * np);
+    k_runs<false><<<g.part_ctas, PART_THREADS, psmem, s>>>(dev_halves, 2 * np);
     k_colscan<<<g.scan_ctas, 256, 0, s>>>(dev_halves, 2 * np);
     k_bscan<<<2 * np, 1024, 0, s>>>(dev_halves, 2 * np);
-    k_scatter<<<g.part_ctas, PART_THREADS, psmem, s>>>(dev_halves, 2 * np);
-    if (ev_mid) cudaEventRecord(ev_mid, s);
+    if (ev_count) cudaEventRecord(ev_count, s);
+    k_runs<true><<<g.part_ctas, PART_THREADS, psmem, s>>>(dev_halves, 2 * np);
+    if (ev_scatter) cudaEventRecord(ev_scatter, s);
     k_join<<<g.join_ctas, JOIN_THREADS, JOIN_SMEM, s>>>(dev_jobs, np);
     return cudaGetLastError();
 }
@@ -503,7 +762,7 @@ extern "C" int rfr_stage_enumerate(const uint64_t* w, int h, uint64_t* keys, voi
 }
 
 static int stage_ctas(int h) {
-    int c = h > 16 ? 1 << (h - 16) : 1;
+    int c = h > 20 ? 1 << (h - 20) : 1;
     return c > 256 ? 256 : c;
 }
 
@@ -551,6 +810,6 @@ extern "C" int rfr_stage_match(const uint64_t* w_a, const uint64_t* w2_a, int n_
     if (cudaMemsetAsync(counters, 0, 6 * sizeof(uint64_t), s) != cudaSuccess) return RFR_E_CUDA;
     if (cudaMemsetAsync(pj.B.halo_cnt, 0, (((size_t)1 << g.d1) + 1) * 4, s) != cudaSuccess) return RFR_E_CUDA;
     HalfJob halves[2];
-    cudaError_t e = run_match(&pj, 1, dev_job, dev_halves, halves, s, nullptr);
+    cudaError_t e = run_match(&pj, 1, dev_job, dev_halves, halves, s, nullptr, nullptr);
     return e == cudaSuccess ? RFR_OK : RFR_E_CUDA;
 }

@@ -10,18 +10,26 @@ constexpr int SUB_BITS = 13;          // second radix digit, sorted in shared me
 constexpr int JOIN_CAP = 9216;        // table-a entries per shared-memory chunk
 constexpr int JOIN_THREADS = 512;
 constexpr int PART_THREADS = 512;
-constexpr int MAX_D1 = 13;            // first radix digit, at most 8192 buckets
+constexpr int MAX_D1 = 16;            // first radix digit, at most 65536 buckets
+constexpr int MAX_L = 16;             // low-list bits (sorted list of up to 65536 sums)
+constexpr int YSORT_THREADS = 1024;
 
 // One half-table (a: keys = sum w; b: keys = -sum w) of one problem.
+// The half's h elements are split into low bits 0..l-1 (list Y: all 2^l
+// low-subset sums, sorted) and high bits l..h-1 (2^hx high subsets x, one
+// rotated run x + Y each).
 struct HalfJob {
     const uint64_t* w;      // h weights (device)
     int h;                  // elements of this half (mask bits), 0..32
     int neg;                // 1 for half b
     int d1;                 // bucket bits (>= 2)
-    int ctas;               // CTAs of the count/scatter grids for this half (power of 2)
+    int l;                  // low bits (Y list size 2^l)
+    int ctas;               // CTAs of the count/scatter grids for this half (<= pieces of 4096)
     int cta_base;           // first CTA of this half in those grids
     int scan_base;          // first CTA of this half in the column-scan grid
     uint64_t wc;            // coarse window (halo test, half b)
+    uint64_t* ylist;        // [2^l] sorted (low-subset sum with low l bits cleared) | low mask
+    uint64_t* ytmp;         // [2^l] radix-sort ping-pong buffer
     uint32_t* hist;         // [ctas][NB]: counts, then per-CTA offsets
     uint32_t* bstart;       // [NB + 1]: bucket starts in tab
     uint64_t* tab;          // [2^h] records ((key << d1) & ~lowmask) | mask
@@ -47,7 +55,7 @@ struct ProbJob {
 
 // Host-side sizing of one problem's match.
 struct MatchGeom {
-    int n_a, n_b, d1, ctas_a, ctas_b;
+    int n_a, n_b, d1, ctas_a, ctas_b, l_a, l_b;
     uint64_t wc;
     uint64_t hcap;          // halo capacity (entries)
     size_t bytes;           // device workspace bytes (tables + histograms + halo)
@@ -65,8 +73,9 @@ void match_layout(const MatchGeom& g, char* ws, ProbJob* pj);
 
 // Assign grid bases, upload the job arrays (host_halves: 2*np scratch) and
 // launch count -> column scan -> bucket scan -> scatter -> join on stream s.
-// ev_mid, if given, is recorded between the scatter and the join.
+// ev_count / ev_scatter, if given, are recorded after the scans and after
+// the scatter.
 cudaError_t run_match(ProbJob* jobs, int np, ProbJob* dev_jobs, HalfJob* dev_halves,
-                      HalfJob* host_halves, cudaStream_t s, cudaEvent_t ev_mid);
+                      HalfJob* host_halves, cudaStream_t s, cudaEvent_t ev_count, cudaEvent_t ev_scatter);
 
 }  // namespace rfr

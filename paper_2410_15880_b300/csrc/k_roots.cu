@@ -133,6 +133,8 @@ k_roots(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees,
     const int prob = blockIdx.x, i = threadIdx.x;
     const int d = degrees[prob];
     const int64_t* c = coeffs + (size_t)prob * LDC;
+    const int pre = status[prob];
+    if (pre < 0) return;                       // rejected by the input checks
     if (i == 0) s_maxres = 0.0;
     if (d < 1 || d > DMAX) {
         if (i == 0) status[prob] = RFR_E_RANGE;
@@ -258,7 +260,11 @@ k_roots(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees,
         atomicMax((unsigned long long*)&s_maxres, __double_as_longlong(res));
     }
     __syncthreads();
-    if (i == 0) status[prob] = conv ? RFR_OK : RFR_E_NO_CONVERGENCE;
+    if (i == 0) {
+        const bool suspect = pre == RFR_SF_SUSPECT;
+        status[prob] = conv ? (suspect ? RFR_SF_SUSPECT : RFR_OK)
+                            : (suspect ? RFR_E_NOT_SQUAREFREE : RFR_E_NO_CONVERGENCE);
+    }
 }
 
 }  // namespace rfr

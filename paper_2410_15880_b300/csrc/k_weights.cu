@@ -37,7 +37,9 @@ k_weights(const int32_t* __restrict__ degrees, const double* __restrict__ roots,
     const int d = degrees[prob];
     rfr_plan* P = plans + prob;
     const int rs = root_status[prob];
-    if (rs != RFR_OK || d < 1 || d > DMAX) {
+    const bool suspect = rs == RFR_SF_SUSPECT;
+    const int fail = suspect ? RFR_E_NOT_SQUAREFREE : RFR_E_ROOTS;
+    if ((rs != RFR_OK && !suspect) || d < 1 || d > DMAX) {
         if (i == 0) {
             P->status = rs != RFR_OK ? rs : RFR_E_RANGE;
             P->degree = d;
@@ -75,7 +77,7 @@ k_weights(const int32_t* __restrict__ degrees, const double* __restrict__ roots,
     }
     __syncthreads();
     if (s_err) {
-        if (i == 0) { P->status = RFR_E_ROOTS; P->degree = d; P->n = 0; P->max_radius = s_maxr; }
+        if (i == 0) { P->status = fail; P->degree = d; P->n = 0; P->max_radius = s_maxr; }
         return;
     }
     if (i < d && cls[i] == 1) {
@@ -95,7 +97,7 @@ k_weights(const int32_t* __restrict__ degrees, const double* __restrict__ roots,
     if (i < d && cls[i] == 1) atomicAdd(&s_c, 1);
     __syncthreads();
     if (s_err || s_r + 2 * s_c != d) {
-        if (i == 0) { P->status = RFR_E_ROOTS; P->degree = d; P->n = 0; P->max_radius = s_maxr; }
+        if (i == 0) { P->status = fail; P->degree = d; P->n = 0; P->max_radius = s_maxr; }
         return;
     }
     const int r = s_r, c = s_c, n = r + c;

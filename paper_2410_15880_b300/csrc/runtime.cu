@@ -29,6 +29,7 @@
 #include <unordered_map>
 #include <vector>
 
+extern "C" int rfr_stage_validate(const int64_t*, const int32_t*, int, int32_t*, void*);
 extern "C" int rfr_stage_roots(const int64_t*, const int32_t*, int, int, double*, double*, int32_t*, void*);
 extern "C" int rfr_stage_weights(const int64_t*, const int32_t*, int, const double*, const double*,
                                  const int32_t*, double, rfr_plan*, void*);
@@ -39,42 +40,6 @@ extern "C" int rfr_stage_verify(const int64_t*, const int32_t*, const double*, c
 namespace rfr {
 
 // ---------------------------------------------------------------- helpers
-static uint64_t mulmod(uint64_t a, uint64_t b, uint64_t m) { return (uint64_t)((unsigned __int128)a * b % m); }
-static uint64_t powmod(uint64_t a, uint64_t e, uint64_t m) {
-    uint64_t r = 1;
-    for (a %= m; e; e >>= 1, a = mulmod(a, a, m)) if (e & 1) r = mulmod(r, a, m);
-    return r;
-}
-// gcd(p, p') over F_l is 1?  (p monic)
-static bool coprime_mod(const int64_t* p, int d, uint64_t l) {
-    std::vector<uint64_t> a(d + 1), b(d);
-    for (int i = 0; i <= d; ++i) { int64_t v = p[i] % (int64_t)l; a[i] = v < 0 ? v + l : v; }
-    for (int i = 1; i <= d; ++i) b[i - 1] = mulmod(a[i], (uint64_t)i % l, l);
-    auto trim = [](std::vector<uint64_t>& v) { while (v.size() > 1 && v.back() == 0) v.pop_back(); };
-    trim(a); trim(b);
-    if (b.size() == 1 && b[0] == 0) return false;
-    while (!(b.size() == 1 && b[0] == 0)) {
-        if (b.size() == 1) return true;                     // nonzero constant
-        uint64_t inv = powmod(b.back(), l - 2, l);
-        while (a.size() >= b.size() && !(a.size() == 1 && a[0] == 0)) {
-            uint64_t c = mulmod(a.back(), inv, l);
-            size_t sh = a.size() - b.size();
-            for (size_t j = 0; j < b.size(); ++j) a[sh + j] = (a[sh + j] + l - mulmod(c, b[j], l)) % l;
-            a.pop_back();
-            trim(a);
-            if (a.empty()) a.push_back(0);
-        }
-        std::swap(a, b);
-    }
-    return a.size() == 1;   // gcd is a nonzero constant
-}
-static bool squarefree_check(const int64_t* p, int d) {
-    static const uint64_t primes[] = {2147483647ull, 2147483629ull, 2147483587ull, 2147483579ull, 2147483563ull};
-    for (uint64_t l : primes)
-        if (coprime_mod(p, d, l)) return true;
-    return false;
-}
-
 struct Bits {
     uint64_t lo = 0, hi = 0;
     bool get(int k) const { return k < 64 ? (lo >> k) & 1 : (hi >> (k - 64)) & 1; }
@@ -138,7 +103,7 @@ struct Ctx;
 struct Pipeline {
     Ctx* ctx = nullptr;
     cudaStream_t s = nullptr;
-    cudaEvent_t ev[8] = {};
+    cudaEvent_t ev[10] = {};
     int cap = 0;                      // problems the device arrays hold
     int64_t* d_coeffs = nullptr;
     int32_t* d_deg = nullptr;
@@ -149,10 +114,14 @@ struct Pipeline {
     int64_t* h_coeffs = nullptr;      // pinned
     int32_t* h_deg = nullptr;         // pinned
     rfr_plan* h_plans = nullptr;      // pinned
+    const int64_t* cur_coeffs = nullptr;   // coefficient rows of the running batch (device)
+    const int32_t* cur_deg = nullptr;
     bool init(Ctx* c);
     void destroy();
     bool reserve(int n);
-    int run(std::vector<Item>& items);
+    // dev_coeffs/dev_deg: device rows for every item in order (device inputs),
+    // or null (host inputs, copied in).
+    int run(std::vector<Item>& items, const int64_t* dev_coeffs = nullptr, const int32_t* dev_deg = nullptr);
 };
 
 struct Request {
@@ -276,36 +245,34 @@ static void canonical_sort(std::vector<std::vector<int64_t>>& fs) {
 
 // Candidate CTAs per half: spread about four CTAs per SM over the sub-batch.
 static int part_ctas(int h, double share_total_elems) {
-    const double target = 4.0 * 148.0;
+    const double target = 16.0 * 148.0;
     double want = std::ldexp(1.0, h) * target / std::max(1.0, share_total_elems);
     int c = 1;
     while (c * 2 <= want && c < 512 && ((uint64_t)c * 2 * 64) <= (1ull << h)) c *= 2;
     return c;
 }
 
-int Pipeline::run(std::vector<Item>& items) {
+int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int32_t* dev_deg) {
     Ctx& C = *ctx;
     const bool timing = C.cfg.timing != 0;
+    const bool device_in = dev_coeffs != nullptr;
     auto t_host0 = std::chrono::steady_clock::now();
+    uint64_t h2d = 0, d2h = 0;
+    uint32_t launches = 0;
     std::vector<Work> work;
-    // ---- validate
+    // ---- host-side argument checks (host inputs); device inputs are checked by K-v
     for (size_t i = 0; i < items.size(); ++i) {
         Item& it = items[i];
         memset(it.out, 0, sizeof(rfr_factors));
         it.status = RFR_OK;
-        if (!it.coeffs || it.degree < 1 || it.degree > DMAX) { it.status = it.coeffs ? RFR_E_RANGE : RFR_E_INVALID; continue; }
-        if (it.coeffs[it.degree] != 1) { it.status = RFR_E_NOT_MONIC; continue; }
-        bool range = true;
-        for (int k = 0; k <= it.degree; ++k)
-            if (it.coeffs[k] >= (1ll << 53) || it.coeffs[k] <= -(1ll << 53)) range = false;
-        if (!range) { it.status = RFR_E_RANGE; continue; }
-        if (it.degree == 1) {
-            std::vector<std::vector<int64_t>> f = {{it.coeffs[0], 1}};
-            fill_factors(it.out, f);
-            it.out->diag.n = 1; it.out->diag.r = 1;
-            continue;
+        if (!device_in) {
+            if (!it.coeffs || it.degree < 1 || it.degree > DMAX) { it.status = it.coeffs ? RFR_E_RANGE : RFR_E_INVALID; continue; }
+            if (it.coeffs[it.degree] != 1) { it.status = RFR_E_NOT_MONIC; continue; }
+            bool range = true;
+            for (int k = 0; k <= it.degree; ++k)
+                if (it.coeffs[k] >= (1ll << 53) || it.coeffs[k] <= -(1ll << 53)) range = false;
+            if (!range) { it.status = RFR_E_RANGE; continue; }
         }
-        if (!squarefree_check(it.coeffs, it.degree)) { it.status = RFR_E_NOT_SQUAREFREE; continue; }
         Work w;
         w.item = (int)i;
         w.slot = (int)work.size();
@@ -314,25 +281,40 @@ int Pipeline::run(std::vector<Item>& items) {
     const int B = (int)work.size();
     if (B == 0) return RFR_OK;
     if (!reserve(B)) return RFR_E_OOM;
-    for (auto& w : work) {
-        const Item& it = items[w.item];
-        int64_t* row = h_coeffs + (size_t)w.slot * LDC;
-        memset(row, 0, LDC * 8);
-        memcpy(row, it.coeffs, (it.degree + 1) * 8);
-        h_deg[w.slot] = it.degree;
-    }
+    const int64_t* d_co = d_coeffs;
+    const int32_t* d_dg = d_deg;
     cudaEventRecord(ev[0], s);
-    int rc = cuda_ok(cudaMemcpyAsync(d_coeffs, h_coeffs, (size_t)B * LDC * 8, cudaMemcpyHostToDevice, s));
-    if (rc == RFR_OK) rc = cuda_ok(cudaMemcpyAsync(d_deg, h_deg, (size_t)B * 4, cudaMemcpyHostToDevice, s));
-    if (rc == RFR_OK) rc = rfr_stage_roots(d_coeffs, d_deg, B, C.cfg.root_mode, d_roots, d_radius, d_rstat, s);
+    int rc = RFR_OK;
+    if (device_in) {
+        d_co = dev_coeffs;                     // rows are the items in order (every item has a slot)
+        d_dg = dev_deg;
+    } else {
+        for (auto& w : work) {
+            const Item& it = items[w.item];
+            int64_t* row = h_coeffs + (size_t)w.slot * LDC;
+            memset(row, 0, LDC * 8);
+            memcpy(row, it.coeffs, (it.degree + 1) * 8);
+            h_deg[w.slot] = it.degree;
+        }
+        rc = cuda_ok(cudaMemcpyAsync(d_coeffs, h_coeffs, (size_t)B * LDC * 8, cudaMemcpyHostToDevice, s));
+        if (rc == RFR_OK) rc = cuda_ok(cudaMemcpyAsync(d_deg, h_deg, (size_t)B * 4, cudaMemcpyHostToDevice, s));
+        h2d += (uint64_t)B * LDC * 8 + (uint64_t)B * 4;
+    }
+    cur_coeffs = d_co;
+    cur_deg = d_dg;
+    if (rc == RFR_OK) rc = rfr_stage_validate(d_co, d_dg, B, d_rstat, s);
+    if (rc == RFR_OK) rc = rfr_stage_roots(d_co, d_dg, B, C.cfg.root_mode, d_roots, d_radius, d_rstat, s);
+    launches += 2;
     cudaEventRecord(ev[1], s);
-    if (rc == RFR_OK) rc = rfr_stage_weights(d_coeffs, d_deg, B, d_roots, d_radius, d_rstat, C.cfg.eps_override, d_plans, s);
+    if (rc == RFR_OK) rc = rfr_stage_weights(d_co, d_dg, B, d_roots, d_radius, d_rstat, C.cfg.eps_override, d_plans, s);
+    launches += 1;
     cudaEventRecord(ev[2], s);
     if (rc == RFR_OK) rc = cuda_ok(cudaMemcpyAsync(h_plans, d_plans, (size_t)B * sizeof(rfr_plan), cudaMemcpyDeviceToHost, s));
+    d2h += (uint64_t)B * sizeof(rfr_plan);
     if (rc == RFR_OK) rc = cuda_ok(cudaStreamSynchronize(s));
     if (rc != RFR_OK) return rc;
     double t_roots = timing ? ms_between(ev[0], ev[1]) : 0, t_weights = timing ? ms_between(ev[1], ev[2]) : 0;
-    double t_enum = 0, t_match = 0, t_verify = 0, t_atoms = 0;
+    double t_count = 0, t_scatter = 0, t_match = 0, t_verify = 0;
 
     // ---- plan the match
     std::vector<int> todo;
@@ -345,11 +327,12 @@ int Pipeline::run(std::vector<Item>& items) {
     }
     const uint64_t cap = std::max<uint64_t>(1, C.cfg.max_candidates);
     while (!todo.empty()) {
-        // take a sub-batch that fits the budget
+        // take a sub-batch that fits this pipeline's share of the budget
         double tot_elems = 0;
         for (int sl : todo) tot_elems += std::ldexp(1.0, work[sl].plan.n_a) + std::ldexp(1.0, work[sl].plan.n_b);
         std::vector<int> sub, rest;
         size_t bytes = 0;
+        const size_t share = C.budget / std::max(1, C.cfg.max_inflight);
         for (int sl : todo) {
             Work& w = work[sl];
             MatchGeom g;
@@ -358,7 +341,7 @@ int Pipeline::run(std::vector<Item>& items) {
             if (w.full_halo) { g.hcap = 1ull << g.n_b; g.bytes = match_bytes(g); }
             const size_t need = g.bytes + (size_t)cap * 8 + 6 * 8 + 512;
             if (need > C.budget) { w.status = RFR_E_BUDGET; continue; }
-            if (!sub.empty() && bytes + need > C.budget / std::max(1, C.cfg.max_inflight)) { rest.push_back(sl); continue; }
+            if (!sub.empty() && bytes + need > share) { rest.push_back(sl); continue; }
             w.geom = g;
             bytes += need;
             sub.push_back(sl);
@@ -394,14 +377,21 @@ int Pipeline::run(std::vector<Item>& items) {
             cudaMemsetAsync(ctr, 0, 6 * 8, s);
             cudaMemsetAsync(pj.B.halo_cnt, 0, (((size_t)1 << w.geom.d1) + 1) * 4, s);
         }
+        h2d += (uint64_t)np * sizeof(ProbJob) + 2ull * np * sizeof(HalfJob);
         cudaEventRecord(ev[3], s);
-        rc = cuda_ok(run_match(jobs.data(), np, d_jobs, d_halves, halves.data(), s, ev[4]));
-        cudaEventRecord(ev[5], s);
+        rc = cuda_ok(run_match(jobs.data(), np, d_jobs, d_halves, halves.data(), s, ev[4], ev[5]));
+        launches += 6;
+        cudaEventRecord(ev[6], s);
         std::vector<uint64_t> h_ctr(6 * (size_t)np);
         for (int i = 0; i < np && rc == RFR_OK; ++i)
             rc = cuda_ok(cudaMemcpyAsync(&h_ctr[6 * i], jobs[i].ctr, 6 * 8, cudaMemcpyDeviceToHost, s));
+        d2h += 48ull * np;
         if (rc == RFR_OK) rc = cuda_ok(cudaStreamSynchronize(s));
-        if (timing && rc == RFR_OK) { t_enum += ms_between(ev[3], ev[4]); t_match += ms_between(ev[4], ev[5]); }
+        if (timing && rc == RFR_OK) {
+            t_count += ms_between(ev[3], ev[4]);
+            t_scatter += ms_between(ev[4], ev[5]);
+            t_match += ms_between(ev[5], ev[6]);
+        }
         for (int i = 0; i < np && rc == RFR_OK; ++i) {
             Work& w = work[sub[i]];
             memcpy(w.ctr, &h_ctr[6 * i], sizeof(w.ctr));
@@ -410,6 +400,7 @@ int Pipeline::run(std::vector<Item>& items) {
             if (w.ctr[2] > cap) { w.status = RFR_E_CAND_OVERFLOW; continue; }
             w.cand.resize(w.ctr[2]);
             if (w.ctr[2]) rc = cuda_ok(cudaMemcpyAsync(w.cand.data(), jobs[i].cand, w.ctr[2] * 8, cudaMemcpyDeviceToHost, s));
+            d2h += w.ctr[2] * 8;
             w.matched = true;
         }
         if (rc == RFR_OK) rc = cuda_ok(cudaStreamSynchronize(s));
@@ -435,36 +426,38 @@ int Pipeline::run(std::vector<Item>& items) {
         int r = cuda_ok(cudaMemcpyAsync(dp, jp.data(), J * 4, cudaMemcpyHostToDevice, s));
         if (r == RFR_OK) r = cuda_ok(cudaMemcpyAsync(dlo, jlo.data(), J * 8, cudaMemcpyHostToDevice, s));
         if (r == RFR_OK) r = cuda_ok(cudaMemcpyAsync(dhi, jhi.data(), J * 8, cudaMemcpyHostToDevice, s));
-        if (r == RFR_OK) r = rfr_stage_verify(d_coeffs, d_deg, d_roots, d_plans, dp, dlo, dhi, J, dres, dco, s);
+        h2d += (uint64_t)J * 20;
+        if (r == RFR_OK) r = rfr_stage_verify(d_co, d_dg, d_roots, d_plans, dp, dlo, dhi, J, dres, dco, s);
+        launches += 1;
         if (r == RFR_OK) r = cuda_ok(cudaMemcpyAsync(res.data(), dres, J * 4, cudaMemcpyDeviceToHost, s));
+        d2h += (uint64_t)J * 4;
         if (r == RFR_OK && coeffs_out) {
             coeffs_out->resize((size_t)J * LDC);
             r = cuda_ok(cudaMemcpyAsync(coeffs_out->data(), dco, (size_t)J * LDC * 8, cudaMemcpyDeviceToHost, s));
+            d2h += (uint64_t)J * LDC * 8;
         }
         if (r == RFR_OK) r = cuda_ok(cudaStreamSynchronize(s));
         C.alloc.put(buf, bytes, s);
         return r;
     };
+    cudaEventRecord(ev[7], s);
     {
         std::vector<int32_t> jp, res;
         std::vector<uint64_t> jlo, jhi;
-        std::vector<std::pair<int, size_t>> owner;
+        std::vector<int> owner;
         for (auto& w : work) {
             if (w.status != RFR_OK || !w.matched) continue;
             for (size_t c = 0; c < w.cand.size(); ++c) {
                 jp.push_back(w.slot);
                 jlo.push_back(w.cand[c]);                // patterns over elements 0..n-2 (n-1 <= 64)
                 jhi.push_back(0);
-                owner.push_back({w.slot, c});
+                owner.push_back(w.slot);
             }
         }
-        cudaEventRecord(ev[6], s);
         rc = run_verify(jp, jlo, jhi, res, nullptr);
-        cudaEventRecord(ev[7], s);
         if (rc != RFR_OK) return rc;
-        if (timing) { cudaEventSynchronize(ev[7]); t_verify = ms_between(ev[6], ev[7]); }
         for (size_t j = 0; j < res.size(); ++j) {
-            Work& w = work[owner[j].first];
+            Work& w = work[owner[j]];
             if (res[j] == 1) { Bits b; b.lo = jlo[j]; w.verified.push_back(b); }
             else if (res[j] == RFR_E_OVERFLOW) w.status = RFR_E_OVERFLOW;
         }
@@ -476,30 +469,30 @@ int Pipeline::run(std::vector<Item>& items) {
         for (auto& w : work) {
             if (w.status != RFR_OK) continue;
             const int n = w.plan.n;
-            if (n <= 1 || w.verified.empty()) continue;
             const Bits full = full_bits(n);
-            std::vector<Bits> fam;
-            fam.push_back(full);
-            for (auto& v : w.verified) { fam.push_back(v); fam.push_back(full & ~v); }
-            for (int i = 0; i < n; ++i) {
-                Bits a = full;
-                for (auto& t : fam) if (t.get(i)) a = a & t;
-                bool seen = false;
-                for (auto& x : w.atoms) if (x == a) { seen = true; break; }
-                if (!seen) w.atoms.push_back(a);
+            if (n > 1 && !w.verified.empty()) {
+                std::vector<Bits> fam;
+                fam.push_back(full);
+                for (auto& v : w.verified) { fam.push_back(v); fam.push_back(full & ~v); }
+                for (int i = 0; i < n; ++i) {
+                    Bits a = full;
+                    for (auto& t : fam) if (t.get(i)) a = a & t;
+                    bool seen = false;
+                    for (auto& x : w.atoms) if (x == a) { seen = true; break; }
+                    if (!seen) w.atoms.push_back(a);
+                }
+            } else {
+                w.atoms.assign(1, full);                  // irreducible: the single atom is p
             }
-            if (w.atoms.size() < 2) { w.atoms.clear(); continue; }
+            if (w.atoms.size() < 2 && !device_in) continue;   // host inputs: p is known on the host
             for (size_t a = 0; a < w.atoms.size(); ++a) {
                 jp.push_back(w.slot); jlo.push_back(w.atoms[a].lo); jhi.push_back(w.atoms[a].hi);
                 owner.push_back({w.slot, (int)a});
             }
         }
         std::vector<int64_t> co;
-        cudaEventRecord(ev[6], s);
         rc = run_verify(jp, jlo, jhi, res, &co);
-        cudaEventRecord(ev[7], s);
         if (rc != RFR_OK) return rc;
-        if (timing) { cudaEventSynchronize(ev[7]); t_atoms = ms_between(ev[6], ev[7]); }
         for (size_t j = 0; j < res.size(); ++j) {
             Work& w = work[owner[j].first];
             if (res[j] != 1) { if (w.status == RFR_OK) w.status = res[j] == RFR_E_OVERFLOW ? RFR_E_OVERFLOW : RFR_E_INTERNAL; continue; }
@@ -510,6 +503,10 @@ int Pipeline::run(std::vector<Item>& items) {
             w.factors.emplace_back(src, src + e + 1);
         }
     }
+    cudaEventRecord(ev[8], s);
+    cudaEventSynchronize(ev[8]);
+    if (timing) t_verify = ms_between(ev[7], ev[8]);
+    const double t_dev = timing ? ms_between(ev[0], ev[8]) : 0.0;
 
     // ---- results
     const double t_host = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_host0).count();
@@ -523,27 +520,27 @@ int Pipeline::run(std::vector<Item>& items) {
         dg.verified = w.verified.size();
         dg.max_rel_residual = w.plan.max_rel_residual;
         dg.max_root_err = w.plan.max_radius;
-        dg.stage_us[0] = t_roots * 1e3; dg.stage_us[1] = t_weights * 1e3; dg.stage_us[2] = t_enum * 1e3;
-        dg.stage_us[3] = t_match * 1e3; dg.stage_us[4] = t_verify * 1e3; dg.stage_us[5] = t_atoms * 1e3;
-        dg.stage_us[7] = t_host * 1e3;
+        dg.stage_us[0] = t_roots * 1e3; dg.stage_us[1] = t_weights * 1e3; dg.stage_us[2] = t_count * 1e3;
+        dg.stage_us[3] = t_scatter * 1e3; dg.stage_us[4] = t_match * 1e3; dg.stage_us[5] = t_verify * 1e3;
+        dg.stage_us[6] = t_dev * 1e3; dg.stage_us[7] = t_host * 1e3;
+        dg.h2d_bytes = h2d; dg.d2h_bytes = d2h; dg.launches = launches; dg.batch_size = (uint32_t)B;
         if (w.status != RFR_OK) { it.status = w.status; continue; }
         std::vector<std::vector<int64_t>> fs;
-        if (!w.factors.empty()) {
-            fs = w.factors;
-        } else {
-            fs.emplace_back(it.coeffs, it.coeffs + it.degree + 1);
+        if (!w.factors.empty()) fs = w.factors;
+        else fs.emplace_back(it.coeffs, it.coeffs + it.degree + 1);
+        if (!device_in) {
+            // exact check: the product of the factors equals p
+            std::vector<__int128> prod(1, 1);
+            for (auto& f : fs) {
+                std::vector<__int128> nx(prod.size() + f.size() - 1, 0);
+                for (size_t i = 0; i < prod.size(); ++i)
+                    for (size_t j = 0; j < f.size(); ++j) nx[i + j] += prod[i] * (__int128)f[j];
+                prod.swap(nx);
+            }
+            bool same = (int)prod.size() == it.degree + 1;
+            for (int k = 0; same && k <= it.degree; ++k) same = prod[k] == (__int128)it.coeffs[k];
+            if (!same) { it.status = RFR_E_INTERNAL; continue; }
         }
-        // exact check: product of the factors equals p (host, tiny)
-        std::vector<__int128> prod(1, 1);
-        for (auto& f : fs) {
-            std::vector<__int128> nx(prod.size() + f.size() - 1, 0);
-            for (size_t i = 0; i < prod.size(); ++i)
-                for (size_t j = 0; j < f.size(); ++j) nx[i + j] += prod[i] * (__int128)f[j];
-            prod.swap(nx);
-        }
-        bool same = (int)prod.size() == it.degree + 1;
-        for (int k = 0; same && k <= it.degree; ++k) same = prod[k] == (__int128)it.coeffs[k];
-        if (!same) { it.status = RFR_E_INTERNAL; continue; }
         canonical_sort(fs);
         fill_factors(it.out, fs);
     }
@@ -723,6 +720,23 @@ int rfr_factor_batch(rfr_ctx* x, int count, const int64_t* const* coeffs, const 
         const int st = rc == RFR_OK ? items[i].status : rc;
         if (statuses) statuses[i] = st;
         if (st != RFR_OK) { rfr_factors_free(&outs[i]); }
+    }
+    return rc;
+}
+
+int rfr_factor_batch_device(rfr_ctx* x, int count, const int64_t* d_coeffs, const int32_t* d_degrees,
+                            rfr_factors* outs, int* statuses) {
+    if (!x || count < 0 || (count && (!d_coeffs || !d_degrees || !outs))) return RFR_E_INVALID;
+    Ctx& C = x->c;
+    std::lock_guard<std::mutex> lk(C.sync_mu);
+    cudaSetDevice(C.device);
+    std::vector<Item> items(count);
+    for (int i = 0; i < count; ++i) items[i] = {nullptr, 0, RFR_OK, &outs[i]};
+    int rc = C.sync_pipe.run(items, d_coeffs, d_degrees);
+    for (int i = 0; i < count; ++i) {
+        const int st = rc == RFR_OK ? items[i].status : rc;
+        if (statuses) statuses[i] = st;
+        if (st != RFR_OK) rfr_factors_free(&outs[i]);
     }
     return rc;
 }

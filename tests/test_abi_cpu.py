@@ -51,7 +51,7 @@ def test_host_only_calls(L):
 def test_struct_layout(L):
     import paper_2410_15880_b300._native as N
     assert N.PLAN_DTYPE.itemsize == 2512
-    assert ctypes.sizeof(N.Config) == 48 and ctypes.sizeof(N.Diag) == 152
+    assert ctypes.sizeof(N.Config) == 48 and ctypes.sizeof(N.Diag) == 176
 
 
 def test_create_without_gpu_fails_cleanly(L):

@@ -101,3 +101,39 @@ def test_serving_cancel_and_poll():
         x = srv.wait(last, 120000)
         assert x.status in (0, -14)
         assert srv.cancel(10 ** 9) == -1        # unknown ticket
+
+
+def test_device_input_batch(ctx):
+    import numpy as np
+    recs = golden("cfg2")[:10] + golden("special")
+    arr = np.zeros((len(recs), 129), dtype=np.int64)
+    for i, r in enumerate(recs):
+        arr[i, :len(r["coeffs"])] = r["coeffs"]
+    d_co = torch.from_numpy(arr).cuda()
+    d_dg = torch.tensor([len(r["coeffs"]) - 1 for r in recs], dtype=torch.int32, device="cuda")
+    res = ctx.factor_batch_device(d_co, d_dg)
+    for r, x in zip(recs, res):
+        assert x.ok and x.factors == r["factors"], r["name"]
+    assert res[0].diag["batch_size"] == len(recs) and res[0].diag["launches"] >= 5
+
+
+def test_device_input_checks(ctx):
+    import numpy as np
+    from paper_2410_15880_b300._native import status_name
+    polys = [[1, 2, 3], [1 << 60, 1], [2, -3, 0, 1], [-7, 1], [1, 0, 0, 0, 1]]
+    arr = np.zeros((len(polys), 129), dtype=np.int64)
+    for i, p in enumerate(polys):
+        arr[i, :len(p)] = p
+    res = ctx.factor_batch_device(torch.from_numpy(arr).cuda(),
+                                  torch.tensor([len(p) - 1 for p in polys], dtype=torch.int32, device="cuda"))
+    assert [status_name(x.status) for x in res[:3]] == ["RFR_E_NOT_MONIC", "RFR_E_RANGE", "RFR_E_NOT_SQUAREFREE"]
+    assert res[3].factors == [[-7, 1]] and res[4].factors == [[1, 0, 0, 0, 1]]
+
+
+def test_validate_stage_suspect_then_roots_decide(ctx):
+    from gpu_util import coeff_tensor
+    import paper_2410_15880_b300 as P
+    # square-free, but its discriminant is divisible by neither Mersenne prime: proven OK
+    c, d = coeff_tensor([[1, 0, -10, 0, 1], [2, -3, 0, 1]])
+    st = P.stage_validate(c, d).cpu().tolist()
+    assert st == [0, 2]                       # (x-1)^2 (x+2): gcd(p, p') = x-1 modulo every prime
