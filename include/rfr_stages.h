@@ -120,6 +120,26 @@ int rfr_stage_match(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
                     uint64_t* cand, uint64_t cap, uint64_t* counters,
                     void* stream);
 
+/* Match without any allocation (the paper has no counterpart; this is a
+ * service for callers that cannot allocate device memory, e.g. inside a host
+ * framework that owns all device memory, or a loop where a cudaMalloc that
+ * may synchronise the device is not allowed).  Same arguments and results as
+ * rfr_stage_match, minus the workspace: it uses a fixed array of
+ * RFR_NOALLOC_SCRATCH_BYTES in device memory that every GPU loading the
+ * library holds until the process exits.  Halves too large for it are
+ * rejected with RFR_E_BUDGET before anything runs (the limit is about
+ * n_a, n_b <= 18).  The array's device address is looked up on the first
+ * call made with a device current; make that first call before any stream
+ * capture.  All calls on a device share the array: calls that overlap on
+ * the GPU race and must be serialised by the caller.  The parts of the array
+ * that must start at zero are cleared by every call. */
+#define RFR_NOALLOC_SCRATCH_BYTES (16u << 20)
+int rfr_stage_match_noalloc(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
+                            const uint64_t* w_b, const uint64_t* w2_b, int n_b,
+                            uint64_t window, uint64_t window2,
+                            uint64_t* cand, uint64_t cap, uint64_t* counters,
+                            void* stream);
+
 /* K-f verify.  For job j: problem prob[j], element pattern
  * (pat_lo[j], pat_hi[j]) over that problem's n elements.  Builds the real
  * factor of Eq. 2 for the pattern or its complement (whichever has the

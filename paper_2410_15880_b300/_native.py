@@ -103,6 +103,7 @@ def lib():
         "rfr_stage_enumerate": (i32, [vp, i32, vp, vp]),
         "rfr_stage_match_workspace": (C.c_size_t, [i32, i32]),
         "rfr_stage_match": (i32, [vp, vp, i32, vp, vp, i32, u64, u64, vp, C.c_size_t, vp, u64, vp, vp]),
+        "rfr_stage_match_noalloc": (i32, [vp, vp, i32, vp, vp, i32, u64, u64, vp, u64, vp, vp]),
         "rfr_stage_verify": (i32, [vp, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
