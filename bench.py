@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--config", default="cfg3", choices=["cfg1", "cfg2", "cfg3", "cfg5"])
     ap.add_argument("--count", type=int, default=0, help="use only the first C polynomials")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--root-mode", type=int, default=0)
+    ap.add_argument("--root-mode", type=int, default=-1,
+                    help="0 = FP64 Aberth, 1 = FP32 bulk + FP64 (default: 1 for cfg3/cfg5, else 0)")
     return ap.parse_args()
 
 
@@ -180,6 +181,8 @@ def run_reference(a):
 
 def main():
     a = parse()
+    if a.root_mode < 0:
+        a.root_mode = 1 if a.config in ("cfg3", "cfg5") else 0
     if a.impl == "reference":
         return run_reference(a)
     import numpy as np
@@ -279,7 +282,7 @@ def main():
     count_us = statistics.mean(d["stage_us"][2] for d in per_step)
     roots_us = statistics.mean(d["stage_us"][0] for d in per_step)
     peak, peak_kind = peaks()
-    kern = {"k_join": (join_us, 8.0 * half_sums), "k_scatter": (scat_us, 8.0 * half_sums)}
+    kern = {"k_join": (join_us, 8.0 * half_sums), "k_runs": (scat_us, 8.0 * half_sums)}
     dom = max(kern, key=lambda k: kern[k][0])
     dur_us, alg_bytes = kern[dom]
     achieved = alg_bytes / (dur_us * 1e-6) / 1e9

@@ -119,6 +119,29 @@ __device__ void block_scan_array(uint32_t* a, int n, bool write_total, uint32_t*
     if (write_total && threadIdx.x == 0) a[n] = total;
 }
 
+// Shared-memory arrays scanned with one contiguous chunk per thread are
+// padded by one word every 32 (index s -> s + s/32): thread t's chunk then
+// starts in bank (17 t) mod 32 and a warp's accesses never collide.
+__device__ __forceinline__ int pad32(int s) { return s + (s >> 5); }
+
+// In-place exclusive scan of a padded shared array a[pad32(0 .. n)).
+__device__ void block_scan_padded(uint32_t* a, int n, uint32_t* warp_sums) {
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per;
+    uint32_t s = 0;
+    for (int i = 0; i < per; ++i)
+        if (b0 + i < n) s += a[pad32(b0 + i)];
+    uint32_t total;
+    uint32_t ex = block_excl_scan(s, &total, warp_sums);
+    for (int i = 0; i < per; ++i) {
+        if (b0 + i < n) {
+            const uint32_t v = a[pad32(b0 + i)];
+            a[pad32(b0 + i)] = ex;
+            ex += v;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- K-c plain
 // keys[s] for s < 2^h in pattern order.  Lanes own mask bits 0..5 (bit 0 is
 // the pair inside one 128-bit store), warps walk bits >= 6 in Gray order, so
@@ -304,6 +327,49 @@ __device__ __forceinline__ void emit(const HalfJob& J, const RunCtx& R, uint32_t
     }
 }
 
+// As emit, for a step whose valid lanes form a prefix (lanes below the first
+// set bit of `stops`) with non-decreasing buckets: groups are the maximal
+// stretches of equal buckets, found from the boundaries instead of a match.
+template <bool SCATTER>
+__device__ __forceinline__ void emit_sorted(const HalfJob& J, const RunCtx& R, uint32_t* acc, uint32_t acc_base,
+                                            bool valid, uint32_t stops, uint64_t K, uint32_t k, uint64_t m,
+                                            uint32_t lane_lt) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t pk = __shfl_up_sync(0xffffffffu, k, 1);
+    const bool head = valid && (lane == 0 || k != pk);
+    const uint32_t heads = __ballot_sync(0xffffffffu, head);
+    const uint32_t upto = heads & (lane_lt | (1u << lane));            // heads at or below this lane
+    const int leader = upto ? 31 - __clz(upto) : 0;
+    const uint32_t above = heads & ~(lane_lt | (1u << lane));
+    const int first_stop = stops ? __ffs(stops) - 1 : 32;
+    const int next_head = above ? __ffs(above) - 1 : 32;
+    const int gend = next_head < first_stop ? next_head : first_stop;
+    uint32_t base = 0;
+    if (head) base = atomicAdd(&acc[k - acc_base], (uint32_t)(gend - lane));
+    if (SCATTER) {
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (valid) J.tab[base + (uint32_t)(lane - leader)] = ((K << R.d1) & ~R.lmh) | m;
+    }
+    if (valid && R.neg) {
+        const uint64_t Kc = K & ~R.trunc;
+        const uint64_t off = Kc - ((uint64_t)k << R.sh);
+        const uint32_t kl = (k - 1u) & (uint32_t)(R.NB - 1), kh = (k + 1u) & (uint32_t)(R.NB - 1);
+        if (SCATTER) {
+            if (off < R.wc) {
+                const uint32_t hp = atomicAdd(&J.halo_cur[kl], 1u);
+                if (hp < R.hcap) { J.halo[2 * (size_t)hp] = Kc; J.halo[2 * (size_t)hp + 1] = m; }
+            }
+            if (R.width - off <= R.wc) {
+                const uint32_t hp = atomicAdd(&J.halo_cur[kh], 1u);
+                if (hp < R.hcap) { J.halo[2 * (size_t)hp] = Kc; J.halo[2 * (size_t)hp + 1] = m; }
+            }
+        } else {
+            if (off < R.wc) atomicAdd(&J.halo_cnt[kl], 1u);
+            if (R.width - off <= R.wc) atomicAdd(&J.halo_cnt[kh], 1u);
+        }
+    }
+}
+
 template <bool SCATTER>
 __global__ void __launch_bounds__(PART_THREADS) k_runs(const HalfJob* __restrict__ hs, int nh) {
     extern __shared__ uint32_t dyn[];
@@ -419,7 +485,7 @@ __global__ void __launch_bounds__(PART_THREADS) k_runs(const HalfJob* __restrict
                     const uint32_t k = (uint32_t)(K >> R.sh);
                     const bool stop = t >= N || k >= kend;       // keys rise along the rotated run
                     const uint32_t stops = __ballot_sync(0xffffffffu, stop);
-                    emit<SCATTER>(J, R, acc, k0, !stop, K, k, xmask | (yv[u] & R.lml), lt);
+                    emit_sorted<SCATTER>(J, R, acc, k0, !stop, stops, K, k, xmask | (yv[u] & R.lml), lt);
                     if (stops) {
                         done = true;
                         t0 = t0 + 32 * u + (__ffs(stops) - 1);
@@ -505,7 +571,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 2) k_join(const ProbJob* __restr
     const uint32_t stride = blockDim.x * U;
     for (uint32_t cs = a0; cs < a1; cs += JOIN_CAP) {
         const uint32_t m = min((uint32_t)JOIN_CAP, a1 - cs);
-        for (int s = threadIdx.x; s < (1 << SUB_BITS); s += blockDim.x) off[s] = 0u;
+        for (int s = threadIdx.x; s < pad32(1 << SUB_BITS); s += blockDim.x) off[s] = 0u;
         __syncthreads();
         for (uint32_t i0 = threadIdx.x; i0 < m; i0 += stride) {
             uint64_t r[U];
@@ -513,10 +579,10 @@ __global__ void __launch_bounds__(JOIN_THREADS, 2) k_join(const ProbJob* __restr
             for (int u = 0; u < U; ++u) r[u] = i0 + u * blockDim.x < m ? tabA[cs + i0 + u * blockDim.x] : 0ull;
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (i0 + u * blockDim.x < m) atomicAdd(&off[((r[u] & ~la) >> d1) >> subsh], 1u);
+                if (i0 + u * blockDim.x < m) atomicAdd(&off[pad32((int)(((r[u] & ~la) >> d1) >> subsh))], 1u);
         }
         __syncthreads();
-        block_scan_array(off, 1 << SUB_BITS, false, warp_sums);
+        block_scan_padded(off, 1 << SUB_BITS, warp_sums);
         __syncthreads();
         for (uint32_t i0 = threadIdx.x; i0 < m; i0 += stride) {
             uint64_t r[U];
@@ -524,7 +590,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 2) k_join(const ProbJob* __restr
             for (int u = 0; u < U; ++u) r[u] = i0 + u * blockDim.x < m ? tabA[cs + i0 + u * blockDim.x] : 0ull;
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (i0 + u * blockDim.x < m) As[atomicAdd(&off[((r[u] & ~la) >> d1) >> subsh], 1u)] = r[u];
+                if (i0 + u * blockDim.x < m) As[atomicAdd(&off[pad32((int)(((r[u] & ~la) >> d1) >> subsh))], 1u)] = r[u];
         }
         __syncthreads();
         for (uint32_t t0 = threadIdx.x; t0 < nbt; t0 += stride) {
@@ -553,7 +619,7 @@ __global__ void __launch_bounds__(JOIN_THREADS, 2) k_join(const ProbJob* __restr
                 if (dlo < 0) dlo = 0;
                 if (dhi > width - 1) dhi = width - 1;
                 const int s_lo = (int)(dlo >> subsh), s_hi = (int)(dhi >> subsh);
-                const uint32_t p0 = s_lo ? off[s_lo - 1] : 0u, p1 = off[s_hi];
+                const uint32_t p0 = s_lo ? off[pad32(s_lo - 1)] : 0u, p1 = off[pad32(s_hi)];
                 for (uint32_t p = p0; p < p1; ++p) {
                     const uint64_t ra = As[p];
                     const uint64_t Ka = lo_k | ((ra & ~la) >> d1);
@@ -706,7 +772,7 @@ static MatchGrid assign_bases(ProbJob* jobs, int np, HalfJob* halves) {
 }
 
 static bool g_attr_set = false;
-static const size_t JOIN_SMEM = (size_t)JOIN_CAP * 8 + ((size_t)1 << SUB_BITS) * 4;
+static const size_t JOIN_SMEM = (size_t)JOIN_CAP * 8 + ((size_t)1 << SUB_BITS) * 4 + ((size_t)1 << SUB_BITS) / 32 * 4;
 
 // Upload jobs (from host memory that stays valid until the copies finish:
 // pageable memory is staged before cudaMemcpyAsync returns) and launch.

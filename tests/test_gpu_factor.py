@@ -52,6 +52,13 @@ def test_degree100_batch(ctx):
     assert all(x.diag["half_sums"] > (1 << 24) for x in res)
 
 
+def test_degree100_batch_fp32_bulk_roots():
+    from paper_2410_15880_b300 import Context, RFR_ROOTS_FP32_BULK
+    with Context(device=0, root_mode=RFR_ROOTS_FP32_BULK) as c:
+        res = check_batch(c, golden("cfg3")[:16])
+    assert all(x.diag["max_root_err"] < 1e-20 for x in res)
+
+
 def test_one_launch_per_polynomial_equals_batch(ctx):
     recs = golden("cfg2")[:8]
     batch = ctx.factor_batch([r["coeffs"] for r in recs])
