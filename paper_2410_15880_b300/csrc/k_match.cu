@@ -122,7 +122,7 @@ __device__ void block_scan_array(uint32_t* a, int n, bool write_total, uint32_t*
 // Shared-memory arrays scanned with one contiguous chunk per thread are
 // padded by one word every 32 (index s -> s + s/32): thread t's chunk then
 // starts in bank (17 t) mod 32 and a warp's accesses never collide.
-__device__ __forceinline__ int pad32(int s) { return s + (s >> 5); }
+__host__ __device__ __forceinline__ int pad32(int s) { return s + (s >> 5); }
 
 // In-place exclusive scan of a padded shared array a[pad32(0 .. n)).
 __device__ void block_scan_padded(uint32_t* a, int n, uint32_t* warp_sums) {
@@ -650,6 +650,98 @@ __global__ void __launch_bounds__(JOIN_THREADS, 2) k_join(const ProbJob* __restr
     if (n_pre) atomicAdd(&P.ctr[1], n_pre);
 }
 
+// ---------------------------------------------------------------- fused small match
+// One CTA per problem with n_b <= 13: the 2^n_a table-a keys are enumerated
+// (Gray code) and counting-sorted by their top 13 bits into shared memory;
+// the 2^n_b table-b keys are enumerated on the fly and probe the circular
+// window directly.  Records are (key & ~(2^n_a - 1)) | mask, so the coarse
+// window is W + 2^n_a and every coarse hit is re-checked exactly.  No global
+// tables, one launch for all small problems of a batch.
+__global__ void __launch_bounds__(SMALL_THREADS, 2) k_small(const SmallJob* __restrict__ js, int np) {
+    extern __shared__ uint64_t smem[];
+    uint64_t* As = smem;                                       // 2^13 records
+    uint32_t* off = reinterpret_cast<uint32_t*>(As + (1 << SMALL_MAX_H));
+    __shared__ uint64_t wa[32], w2a[32], wb[32], w2b[32], nwb[32];
+    __shared__ uint32_t warp_sums[32];
+    const SmallJob& P = js[blockIdx.x];
+    const int n_a = P.n_a, n_b = P.n_b;
+    if (threadIdx.x < n_a) { wa[threadIdx.x] = P.w_a[threadIdx.x]; w2a[threadIdx.x] = P.w2_a[threadIdx.x]; }
+    if (threadIdx.x < n_b) {
+        wb[threadIdx.x] = P.w_b[threadIdx.x];
+        w2b[threadIdx.x] = P.w2_b[threadIdx.x];
+        nwb[threadIdx.x] = 0ull - P.w_b[threadIdx.x];
+    }
+    for (int s = threadIdx.x; s < pad32(1 << SUB_BITS); s += blockDim.x) off[s] = 0u;
+    __syncthreads();
+    const uint64_t la = lowmask(n_a), lb = lowmask(n_b);
+    const uint64_t Na = 1ull << n_a, Nb = 1ull << n_b;
+    const uint64_t W = P.W, W2 = P.W2, Wc = W + (1ull << n_a);
+    const int top = 64 - SUB_BITS;
+    enumerate_range(wa, 0, Na, [&](uint64_t m, uint64_t key) {
+        atomicAdd(&off[pad32((int)(key >> top))], 1u);
+    });
+    __syncthreads();
+    block_scan_padded(off, 1 << SUB_BITS, warp_sums);
+    __syncthreads();
+    enumerate_range(wa, 0, Na, [&](uint64_t m, uint64_t key) {
+        As[atomicAdd(&off[pad32((int)(key >> top))], 1u)] = (key & ~la) | m;
+    });
+    __syncthreads();
+    unsigned long long n_coarse = 0, n_pre = 0;
+    auto probe_range = [&](int s0, int s1, uint64_t Kb, uint64_t mb) {
+        const uint32_t p0 = s0 ? off[pad32(s0 - 1)] : 0u, p1 = off[pad32(s1)];
+        for (uint32_t p = p0; p < p1; ++p) {
+            const uint64_t ra = As[p];
+            const long long diff = (long long)((ra & ~la) - Kb);
+            if (diff > -(long long)Wc && diff < (long long)Wc) {
+                ++n_coarse;
+                const uint64_t ma = ra & la;
+                const uint64_t v = subset_sum(wa, ma) + subset_sum(wb, mb);
+                if (circ_dist(v) <= W) {
+                    ++n_pre;
+                    const uint64_t t2 = subset_sum(w2a, ma) + subset_sum(w2b, mb);
+                    if (circ_dist(t2) <= W2) {
+                        if (ma == 0 && mb == 0) {
+                            P.ctr[3] = 1ull;
+                        } else {
+                            const unsigned long long idx = atomicAdd(&P.ctr[2], 1ull);
+                            if (idx < P.cap) P.cand[idx] = ma | (mb << n_a);
+                        }
+                    }
+                }
+            }
+        }
+    };
+    enumerate_range(nwb, 0, Nb, [&](uint64_t mb, uint64_t Kb) {
+        const uint64_t lo = Kb - Wc + 1ull, hi = Kb + Wc - 1ull;
+        const int s_lo = (int)(lo >> top), s_hi = (int)(hi >> top);
+        if (lo <= hi) {
+            probe_range(s_lo, s_hi, Kb, mb);
+        } else {                                               // the window wraps past 2^64
+            probe_range(s_lo, (1 << SUB_BITS) - 1, Kb, mb);
+            probe_range(0, s_hi, Kb, mb);
+        }
+    });
+    if (n_coarse) atomicAdd(&P.ctr[0], n_coarse);
+    if (n_pre) atomicAdd(&P.ctr[1], n_pre);
+}
+
+static const size_t SMALL_SMEM = ((size_t)1 << SMALL_MAX_H) * 8 + (size_t)pad32(1 << SUB_BITS) * 4;
+static bool g_small_attr = false;
+
+cudaError_t run_small(const SmallJob* jobs, int np, SmallJob* dev_jobs, cudaStream_t s) {
+    if (np <= 0) return cudaSuccess;
+    if (!g_small_attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMALL_SMEM);
+        if (e != cudaSuccess) return e;
+        g_small_attr = true;
+    }
+    cudaError_t e = cudaMemcpyAsync(dev_jobs, jobs, sizeof(SmallJob) * np, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    k_small<<<np, SMALL_THREADS, SMALL_SMEM, s>>>(dev_jobs, np);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- host side
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -857,6 +949,16 @@ extern "C" int rfr_stage_match(const uint64_t* w_a, const uint64_t* w2_a, int n_
     if (n_a < 0 || n_b < n_a || n_b > 32 || !workspace || !counters || (!cand && cap)) return RFR_E_INVALID;
     if ((n_a && (!w_a || !w2_a)) || (n_b && (!w_b || !w2_b))) return RFR_E_INVALID;
     if (((uintptr_t)workspace) & 255) return RFR_E_INVALID;
+    if (n_b <= SMALL_MAX_H) {
+        if (window >= (1ull << 62)) return RFR_E_WINDOW;
+        SmallJob sj;
+        sj.w_a = w_a; sj.w2_a = w2_a; sj.w_b = w_b; sj.w2_b = w2_b;
+        sj.n_a = n_a; sj.n_b = n_b; sj.W = window; sj.W2 = window2;
+        sj.cand = cand; sj.cap = cap; sj.ctr = (unsigned long long*)counters;
+        cudaStream_t s = (cudaStream_t)stream;
+        if (cudaMemsetAsync(counters, 0, 6 * sizeof(uint64_t), s) != cudaSuccess) return RFR_E_CUDA;
+        return run_small(&sj, 1, (SmallJob*)workspace, s) == cudaSuccess ? RFR_OK : RFR_E_CUDA;
+    }
     MatchGeom g;
     if (!stage_geom(n_a, n_b, window, &g)) return RFR_E_WINDOW;
     if (g.bytes + 2048 > workspace_bytes) return RFR_E_INVALID;

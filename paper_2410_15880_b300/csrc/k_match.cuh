@@ -53,6 +53,20 @@ struct ProbJob {
     unsigned long long* ctr;    // [4]: coarse pairs, pairs within W, candidates (within W and W2, non-trivial), trivial seen
 };
 
+// One small problem (n_b <= SMALL_MAX_H) matched entirely in shared memory.
+constexpr int SMALL_MAX_H = 13;
+constexpr int SMALL_THREADS = 512;
+struct SmallJob {
+    const uint64_t* w_a;  const uint64_t* w2_a;
+    const uint64_t* w_b;  const uint64_t* w2_b;
+    int n_a, n_b;
+    uint64_t W, W2;
+    uint64_t* cand;
+    uint64_t cap;
+    unsigned long long* ctr;    // [6], as ProbJob
+};
+cudaError_t run_small(const SmallJob* jobs, int np, SmallJob* dev_jobs, cudaStream_t s);
+
 // Host-side sizing of one problem's match.
 struct MatchGeom {
     int n_a, n_b, d1, ctas_a, ctas_b, l_a, l_b;

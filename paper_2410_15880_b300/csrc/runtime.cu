@@ -326,6 +326,59 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
         todo.push_back(w.slot);
     }
     const uint64_t cap = std::max<uint64_t>(1, C.cfg.max_candidates);
+    // small problems: one fused shared-memory kernel for all of them
+    {
+        std::vector<int> small, big;
+        for (int sl : todo) (work[sl].plan.n_b <= SMALL_MAX_H && work[sl].plan.window < (1ull << 62) ? small : big).push_back(sl);
+        todo.swap(big);
+        if (!small.empty()) {
+            const int ns = (int)small.size();
+            const size_t per = (((size_t)cap * 8 + 255) & ~(size_t)255) + 256;
+            const size_t bytes = (size_t)ns * per + (((size_t)ns * sizeof(SmallJob)) + 255 & ~(size_t)255);
+            char* ws = (char*)C.alloc.get(bytes, s);
+            if (!ws) return RFR_E_OOM;
+            SmallJob* d_sj = (SmallJob*)ws;
+            char* p = ws + ((((size_t)ns * sizeof(SmallJob)) + 255) & ~(size_t)255);
+            std::vector<SmallJob> sj(ns);
+            std::vector<uint64_t*> ctrs(ns), cands(ns);
+            for (int i = 0; i < ns; ++i) {
+                Work& w = work[small[i]];
+                const rfr_plan* dp = d_plans + w.slot;
+                cands[i] = (uint64_t*)p; p += ((size_t)cap * 8 + 255) & ~(size_t)255;
+                ctrs[i] = (uint64_t*)p; p += 256;
+                sj[i].w_a = dp->w; sj[i].w2_a = dp->w2;
+                sj[i].w_b = dp->w + w.plan.n_a; sj[i].w2_b = dp->w2 + w.plan.n_a;
+                sj[i].n_a = w.plan.n_a; sj[i].n_b = w.plan.n_b;
+                sj[i].W = w.plan.window; sj[i].W2 = w.plan.window2;
+                sj[i].cand = cands[i]; sj[i].cap = cap; sj[i].ctr = (unsigned long long*)ctrs[i];
+                cudaMemsetAsync(ctrs[i], 0, 6 * 8, s);
+            }
+            h2d += (uint64_t)ns * sizeof(SmallJob);
+            cudaEventRecord(ev[5], s);
+            rc = cuda_ok(run_small(sj.data(), ns, d_sj, s));
+            launches += 1;
+            cudaEventRecord(ev[6], s);
+            std::vector<uint64_t> h_ctr(6 * (size_t)ns);
+            for (int i = 0; i < ns && rc == RFR_OK; ++i)
+                rc = cuda_ok(cudaMemcpyAsync(&h_ctr[6 * i], ctrs[i], 6 * 8, cudaMemcpyDeviceToHost, s));
+            d2h += 48ull * ns;
+            if (rc == RFR_OK) rc = cuda_ok(cudaStreamSynchronize(s));
+            if (timing && rc == RFR_OK) t_match += ms_between(ev[5], ev[6]);
+            for (int i = 0; i < ns && rc == RFR_OK; ++i) {
+                Work& w = work[small[i]];
+                memcpy(w.ctr, &h_ctr[6 * i], sizeof(w.ctr));
+                if (w.ctr[3] == 0) { w.status = RFR_E_INTERNAL; continue; }
+                if (w.ctr[2] > cap) { w.status = RFR_E_CAND_OVERFLOW; continue; }
+                w.cand.resize(w.ctr[2]);
+                if (w.ctr[2]) rc = cuda_ok(cudaMemcpyAsync(w.cand.data(), cands[i], w.ctr[2] * 8, cudaMemcpyDeviceToHost, s));
+                d2h += w.ctr[2] * 8;
+                w.matched = true;
+            }
+            if (rc == RFR_OK) rc = cuda_ok(cudaStreamSynchronize(s));
+            C.alloc.put(ws, bytes, s);
+            if (rc != RFR_OK) return rc;
+        }
+    }
     while (!todo.empty()) {
         // take a sub-batch that fits this pipeline's share of the budget
         double tot_elems = 0;
