@@ -110,15 +110,29 @@ size_t rfr_stage_match_workspace(int n_a, int n_b);
  * dist(y) = min(y, 2^64 - y) (Eq. 9 / Eq. 19 made circular), to
  * cand[0 .. min(count, cap)).  counters (device, uint64 [6]) receive
  * {coarse pairs, pairs within W, pairs also within W2 (= count), trivial
- * pattern seen (1/0), halo overflow (1/0), 0}.  w_a/w2_a hold n_a weights, w_b/w2_b n_b; 0 <= n_a,
+ * pattern seen (1/0), layout overflow (1/0), 0}.  w_a/w2_a hold n_a weights, w_b/w2_b n_b; 0 <= n_a,
  * n_b <= 32.  workspace: rfr_stage_match_workspace(n_a, n_b) bytes,
- * 256-byte aligned.  Section 3.3 (RECOMBINE_C's result set). */
+ * 256-byte aligned.  Section 3.3 (RECOMBINE_C's result set).
+ * Tables of half b with n_b <= 13 are matched in one shared-memory kernel.
+ * Larger ones use per-bucket regions with 25 % slack over the mean count
+ * (no count pass); if keys cluster so that a region or a halo list fills up,
+ * counters[4] is set to 1 and the candidates are incomplete: the caller then
+ * runs rfr_stage_match_exact, which sizes every bucket with a count pass. */
 int rfr_stage_match(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
                     const uint64_t* w_b, const uint64_t* w2_b, int n_b,
                     uint64_t window, uint64_t window2,
                     void* workspace, size_t workspace_bytes,
                     uint64_t* cand, uint64_t cap, uint64_t* counters,
                     void* stream);
+
+/* As rfr_stage_match, with bucket regions sized exactly by a count pass over
+ * both halves (never overflows; one more enumeration pass). */
+int rfr_stage_match_exact(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
+                          const uint64_t* w_b, const uint64_t* w2_b, int n_b,
+                          uint64_t window, uint64_t window2,
+                          void* workspace, size_t workspace_bytes,
+                          uint64_t* cand, uint64_t cap, uint64_t* counters,
+                          void* stream);
 
 /* Match without any allocation (the paper has no counterpart; this is a
  * service for callers that cannot allocate device memory, e.g. inside a host

@@ -294,6 +294,31 @@ struct RunCtx {
     int d1, NB, sh, l, h, neg;
 };
 
+// Record r at position p of bucket k (exact layout: p is already absolute).
+__device__ __forceinline__ void store_record(const HalfJob& J, uint32_t k, uint32_t p, uint64_t r) {
+    if (J.opt_cap) {
+        if (p < J.opt_cap) J.tab[(size_t)k * J.opt_cap + p] = r;
+        else atomicExch(J.err, 1);                         // region full: redo with the exact layout
+    } else {
+        J.tab[p] = r;
+    }
+}
+
+__device__ __forceinline__ void store_halo(const HalfJob& J, const RunCtx& R, uint32_t k, uint64_t Kc, uint64_t m) {
+    size_t slot;
+    if (J.opt_cap) {
+        const uint32_t hp = atomicAdd(&J.hcount[k], 1u);
+        if (hp >= J.opt_hcap) { atomicExch(J.err, 1); return; }
+        slot = (size_t)k * J.opt_hcap + hp;
+    } else {
+        const uint32_t hp = atomicAdd(&J.halo_cur[k], 1u);
+        if (hp >= R.hcap) return;                           // counted: k_bscan already flagged it
+        slot = hp;
+    }
+    J.halo[2 * slot] = Kc;
+    J.halo[2 * slot + 1] = m;
+}
+
 // Handle one element (already loaded) of run x: returns its bucket.
 template <bool SCATTER>
 __device__ __forceinline__ void emit(const HalfJob& J, const RunCtx& R, uint32_t* acc, uint32_t acc_base,
@@ -302,24 +327,20 @@ __device__ __forceinline__ void emit(const HalfJob& J, const RunCtx& R, uint32_t
     const uint32_t peers = __match_any_sync(0xffffffffu, valid ? k : 0x80000000u + lane);
     const int leader = __ffs(peers) - 1;
     uint32_t base = 0;
-    if (valid && lane == leader) base = atomicAdd(&acc[k - acc_base], (uint32_t)__popc(peers));
+    if (valid && lane == leader)
+        base = J.opt_cap ? atomicAdd(&J.bcount[k], (uint32_t)__popc(peers))
+                         : atomicAdd(&acc[k - acc_base], (uint32_t)__popc(peers));
     if (SCATTER) {
         base = __shfl_sync(0xffffffffu, base, leader);
-        if (valid) J.tab[base + __popc(peers & lane_lt)] = ((K << R.d1) & ~R.lmh) | m;
+        if (valid) store_record(J, k, base + __popc(peers & lane_lt), ((K << R.d1) & ~R.lmh) | m);
     }
     if (valid && R.neg) {
         const uint64_t Kc = K & ~R.trunc;
         const uint64_t off = Kc - ((uint64_t)k << R.sh);
         const uint32_t kl = (k - 1u) & (uint32_t)(R.NB - 1), kh = (k + 1u) & (uint32_t)(R.NB - 1);
         if (SCATTER) {
-            if (off < R.wc) {
-                const uint32_t hp = atomicAdd(&J.halo_cur[kl], 1u);
-                if (hp < R.hcap) { J.halo[2 * (size_t)hp] = Kc; J.halo[2 * (size_t)hp + 1] = m; }
-            }
-            if (R.width - off <= R.wc) {
-                const uint32_t hp = atomicAdd(&J.halo_cur[kh], 1u);
-                if (hp < R.hcap) { J.halo[2 * (size_t)hp] = Kc; J.halo[2 * (size_t)hp + 1] = m; }
-            }
+            if (off < R.wc) store_halo(J, R, kl, Kc, m);
+            if (R.width - off <= R.wc) store_halo(J, R, kh, Kc, m);
         } else {
             if (off < R.wc) atomicAdd(&J.halo_cnt[kl], 1u);
             if (R.width - off <= R.wc) atomicAdd(&J.halo_cnt[kh], 1u);
@@ -345,24 +366,20 @@ __device__ __forceinline__ void emit_sorted(const HalfJob& J, const RunCtx& R, u
     const int next_head = above ? __ffs(above) - 1 : 32;
     const int gend = next_head < first_stop ? next_head : first_stop;
     uint32_t base = 0;
-    if (head) base = atomicAdd(&acc[k - acc_base], (uint32_t)(gend - lane));
+    if (head)
+        base = J.opt_cap ? atomicAdd(&J.bcount[k], (uint32_t)(gend - lane))
+                         : atomicAdd(&acc[k - acc_base], (uint32_t)(gend - lane));
     if (SCATTER) {
         base = __shfl_sync(0xffffffffu, base, leader);
-        if (valid) J.tab[base + (uint32_t)(lane - leader)] = ((K << R.d1) & ~R.lmh) | m;
+        if (valid) store_record(J, k, base + (uint32_t)(lane - leader), ((K << R.d1) & ~R.lmh) | m);
     }
     if (valid && R.neg) {
         const uint64_t Kc = K & ~R.trunc;
         const uint64_t off = Kc - ((uint64_t)k << R.sh);
         const uint32_t kl = (k - 1u) & (uint32_t)(R.NB - 1), kh = (k + 1u) & (uint32_t)(R.NB - 1);
         if (SCATTER) {
-            if (off < R.wc) {
-                const uint32_t hp = atomicAdd(&J.halo_cur[kl], 1u);
-                if (hp < R.hcap) { J.halo[2 * (size_t)hp] = Kc; J.halo[2 * (size_t)hp + 1] = m; }
-            }
-            if (R.width - off <= R.wc) {
-                const uint32_t hp = atomicAdd(&J.halo_cur[kh], 1u);
-                if (hp < R.hcap) { J.halo[2 * (size_t)hp] = Kc; J.halo[2 * (size_t)hp + 1] = m; }
-            }
+            if (off < R.wc) store_halo(J, R, kl, Kc, m);
+            if (R.width - off <= R.wc) store_halo(J, R, kh, Kc, m);
         } else {
             if (off < R.wc) atomicAdd(&J.halo_cnt[kl], 1u);
             if (R.width - off <= R.wc) atomicAdd(&J.halo_cnt[kh], 1u);
@@ -397,7 +414,7 @@ __global__ void __launch_bounds__(PART_THREADS) k_runs(const HalfJob* __restrict
     if (!range_mode) {
         uint32_t* acc = dyn;                  // all NB buckets
         for (int b = threadIdx.x; b < NB; b += blockDim.x)
-            acc[b] = SCATTER ? J.bstart[b] + J.hist[(size_t)c * NB + b] : 0u;
+            acc[b] = (SCATTER && !J.opt_cap) ? J.bstart[b] + J.hist[(size_t)c * NB + b] : 0u;
         __syncthreads();
         const uint32_t piece = N < (uint32_t)PIECE ? N : (uint32_t)PIECE;
         const uint32_t per_run = N / piece;
@@ -460,7 +477,7 @@ __global__ void __launch_bounds__(PART_THREADS) k_runs(const HalfJob* __restrict
         const uint32_t k0 = (uint32_t)r * rw, kend = k0 + rw;
         __syncthreads();
         for (int b = threadIdx.x; b < rw; b += blockDim.x)
-            acc[b] = SCATTER ? J.bstart[k0 + b] + J.hist[(size_t)c * NB + k0 + b] : 0u;
+            acc[b] = (SCATTER && !J.opt_cap) ? J.bstart[k0 + b] + J.hist[(size_t)c * NB + k0 + b] : 0u;
         __syncthreads();
         for (uint32_t g = warp; g < G; g += nwarps) {
             const uint32_t xi = x0 + g;
@@ -555,12 +572,19 @@ __global__ void __launch_bounds__(JOIN_THREADS, 2) k_join(const ProbJob* __restr
     const uint64_t lo_k = (uint64_t)k << sh;
     const long long width = (long long)(1ull << sh);
     const uint64_t la = lowmask(n_a), lb = lowmask(n_b);
-    const uint32_t a0 = P.A.bstart[k], a1 = P.A.bstart[k + 1];
-    const uint32_t b0 = P.B.bstart[k], b1 = P.B.bstart[k + 1];
-    const uint64_t hcap = P.B.halo_cap;
-    const uint32_t h0 = (uint32_t)min((uint64_t)P.B.halo_cnt[k], hcap);
-    const uint32_t h1 = (uint32_t)min((uint64_t)P.B.halo_cnt[k + 1], hcap);
-    const uint32_t nbn = b1 - b0, nbt = nbn + (h1 - h0);
+    uint64_t a0, a1, b0, b1, h0, h1;
+    if (P.A.opt_cap) {
+        a0 = (uint64_t)k * P.A.opt_cap; a1 = a0 + min(P.A.bcount[k], P.A.opt_cap);
+        b0 = (uint64_t)k * P.B.opt_cap; b1 = b0 + min(P.B.bcount[k], P.B.opt_cap);
+        h0 = (uint64_t)k * P.B.opt_hcap; h1 = h0 + min(P.B.hcount[k], P.B.opt_hcap);
+    } else {
+        const uint64_t hcap = P.B.halo_cap;
+        a0 = P.A.bstart[k]; a1 = P.A.bstart[k + 1];
+        b0 = P.B.bstart[k]; b1 = P.B.bstart[k + 1];
+        h0 = min((uint64_t)P.B.halo_cnt[k], hcap);
+        h1 = min((uint64_t)P.B.halo_cnt[k + 1], hcap);
+    }
+    const uint32_t nbn = (uint32_t)(b1 - b0), nbt = nbn + (uint32_t)(h1 - h0);
     const uint64_t Wc = P.Wc, W = P.W, W2 = P.W2;
     const uint64_t* __restrict__ tabA = P.A.tab;
     const uint64_t* __restrict__ tabB = P.B.tab;
@@ -569,17 +593,18 @@ __global__ void __launch_bounds__(JOIN_THREADS, 2) k_join(const ProbJob* __restr
     __syncthreads();
     constexpr int U = 4;                       // independent loads in flight per thread
     const uint32_t stride = blockDim.x * U;
-    for (uint32_t cs = a0; cs < a1; cs += JOIN_CAP) {
-        const uint32_t m = min((uint32_t)JOIN_CAP, a1 - cs);
+    for (uint64_t cs = a0; cs < a1; cs += JOIN_CAP) {
+        const uint32_t m = (uint32_t)min((uint64_t)JOIN_CAP, a1 - cs);
         for (int s = threadIdx.x; s < pad32(1 << SUB_BITS); s += blockDim.x) off[s] = 0u;
         __syncthreads();
+        // digit 2 = the top 13 bits of the record (key bits below the bucket's d1 bits)
         for (uint32_t i0 = threadIdx.x; i0 < m; i0 += stride) {
             uint64_t r[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) r[u] = i0 + u * blockDim.x < m ? tabA[cs + i0 + u * blockDim.x] : 0ull;
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (i0 + u * blockDim.x < m) atomicAdd(&off[pad32((int)(((r[u] & ~la) >> d1) >> subsh))], 1u);
+                if (i0 + u * blockDim.x < m) atomicAdd(&off[pad32((int)(r[u] >> (64 - SUB_BITS)))], 1u);
         }
         __syncthreads();
         block_scan_padded(off, 1 << SUB_BITS, warp_sums);
@@ -590,10 +615,30 @@ __global__ void __launch_bounds__(JOIN_THREADS, 2) k_join(const ProbJob* __restr
             for (int u = 0; u < U; ++u) r[u] = i0 + u * blockDim.x < m ? tabA[cs + i0 + u * blockDim.x] : 0ull;
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (i0 + u * blockDim.x < m) As[atomicAdd(&off[pad32((int)(((r[u] & ~la) >> d1) >> subsh))], 1u)] = r[u];
+                if (i0 + u * blockDim.x < m) As[atomicAdd(&off[pad32((int)(r[u] >> (64 - SUB_BITS)))], 1u)] = r[u];
         }
         __syncthreads();
-        for (uint32_t t0 = threadIdx.x; t0 < nbt; t0 += stride) {
+        // Records of one bucket hold (key << d1) with their low bits cleared,
+        // so |Ka - Kb| < Wc is |ra - rb| < Wc << d1 on the masked records.
+        const uint64_t Wd = Wc << d1;
+        auto hit = [&](uint64_t ra, uint64_t mb) {
+            ++n_coarse;
+            const uint64_t ma = ra & la;
+            const uint64_t v = subset_sum(wa, ma) + subset_sum(wb, mb);
+            if (circ_dist(v) <= W) {
+                ++n_pre;
+                const uint64_t t2 = subset_sum(w2a, ma) + subset_sum(w2b, mb);
+                if (circ_dist(t2) <= W2) {
+                    if (ma == 0 && mb == 0) {
+                        P.ctr[3] = 1ull;
+                    } else {
+                        const unsigned long long idx = atomicAdd(&P.ctr[2], 1ull);
+                        if (idx < P.cap) P.cand[idx] = ma | (mb << n_a);
+                    }
+                }
+            }
+        };
+        for (uint32_t t0 = threadIdx.x; t0 < nbn; t0 += stride) {
             uint64_t rb[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -602,46 +647,35 @@ __global__ void __launch_bounds__(JOIN_THREADS, 2) k_join(const ProbJob* __restr
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const uint32_t t = t0 + u * blockDim.x;
-                if (t >= nbt) continue;
-                uint64_t Kb, mb;
-                if (t < nbn) {
-                    Kb = lo_k | ((rb[u] & ~lb) >> d1);
-                    mb = rb[u] & lb;
-                } else {
-                    const size_t hi = 2 * (size_t)(h0 + (t - nbn));
-                    Kb = halo[hi];
-                    mb = halo[hi + 1];
-                }
-                long long dlo = (long long)(Kb - Wc + 1ull - lo_k);
-                long long dhi = (long long)(Kb + Wc - 1ull - lo_k);
-                if (dhi < 0 || dlo >= width) continue;
-                if (dlo < 0) dlo = 0;
-                if (dhi > width - 1) dhi = width - 1;
-                const int s_lo = (int)(dlo >> subsh), s_hi = (int)(dhi >> subsh);
+                if (t0 + u * blockDim.x >= nbn) continue;
+                const uint64_t rkb = rb[u] & ~lb, mb = rb[u] & lb;
+                const uint64_t lo = rkb > Wd - 1 ? rkb - (Wd - 1) : 0ull;
+                const uint64_t hi = rkb < ~0ull - (Wd - 1) ? rkb + (Wd - 1) : ~0ull;
+                const int s_lo = (int)(lo >> (64 - SUB_BITS)), s_hi = (int)(hi >> (64 - SUB_BITS));
                 const uint32_t p0 = s_lo ? off[pad32(s_lo - 1)] : 0u, p1 = off[pad32(s_hi)];
                 for (uint32_t p = p0; p < p1; ++p) {
                     const uint64_t ra = As[p];
-                    const uint64_t Ka = lo_k | ((ra & ~la) >> d1);
-                    const long long diff = (long long)(Ka - Kb);
-                    if (diff > -(long long)Wc && diff < (long long)Wc) {
-                        ++n_coarse;
-                        const uint64_t ma = ra & la;
-                        const uint64_t v = subset_sum(wa, ma) + subset_sum(wb, mb);
-                        if (circ_dist(v) <= W) {
-                            ++n_pre;
-                            const uint64_t t2 = subset_sum(w2a, ma) + subset_sum(w2b, mb);
-                            if (circ_dist(t2) <= W2) {
-                                if (ma == 0 && mb == 0) {
-                                    P.ctr[3] = 1ull;
-                                } else {
-                                    const unsigned long long idx = atomicAdd(&P.ctr[2], 1ull);
-                                    if (idx < P.cap) P.cand[idx] = ma | (mb << n_a);
-                                }
-                            }
-                        }
-                    }
+                    const long long diff = (long long)((ra & ~la) - rkb);
+                    if (diff > -(long long)Wd && diff < (long long)Wd) hit(ra, mb);
                 }
+            }
+        }
+        // halo records (from the neighbouring buckets): full coarse keys
+        for (uint32_t t = nbn + threadIdx.x; t < nbt; t += blockDim.x) {
+            const size_t hi2 = 2 * (size_t)(h0 + (t - nbn));
+            const uint64_t Kb = halo[hi2], mb = halo[hi2 + 1];
+            long long dlo = (long long)(Kb - Wc + 1ull - lo_k);
+            long long dhi = (long long)(Kb + Wc - 1ull - lo_k);
+            if (dhi < 0 || dlo >= width) continue;
+            if (dlo < 0) dlo = 0;
+            if (dhi > width - 1) dhi = width - 1;
+            const int s_lo = (int)(dlo >> subsh), s_hi = (int)(dhi >> subsh);
+            const uint32_t p0 = s_lo ? off[pad32(s_lo - 1)] : 0u, p1 = off[pad32(s_hi)];
+            for (uint32_t p = p0; p < p1; ++p) {
+                const uint64_t ra = As[p];
+                const uint64_t Ka = lo_k | ((ra & ~la) >> d1);
+                const long long diff = (long long)(Ka - Kb);
+                if (diff > -(long long)Wc && diff < (long long)Wc) hit(ra, mb);
             }
         }
         __syncthreads();
@@ -757,6 +791,11 @@ size_t match_bytes(const MatchGeom& g) {
     size_t b = 0;
     b += 2 * align256(((size_t)1 << g.l_a) * 8);
     b += 2 * align256(((size_t)1 << g.l_b) * 8);
+    if (g.optimistic) {
+        b += align256(NB * g.cap_a * 8) + align256(NB * g.cap_b * 8);
+        b += align256(NB * 4) * 3 + align256(NB * g.hcap_per * 16);
+        return b;
+    }
     b += align256(((size_t)1 << g.n_a) * 8);
     b += align256(((size_t)1 << g.n_b) * 8);
     b += align256((size_t)g.ctas_a * NB * 4);
@@ -780,7 +819,7 @@ static int clamp_ctas(int h, int l, int want) {
     return want < pieces ? (want < 1 ? 1 : want) : pieces;
 }
 
-bool match_geometry(int n_a, int n_b, uint64_t W, int ctas_a, int ctas_b, MatchGeom* g) {
+bool match_geometry(int n_a, int n_b, uint64_t W, int ctas_a, int ctas_b, MatchGeom* g, bool optimistic) {
     if (n_a < 0 || n_b < n_a || n_b > 32) return false;
     const int l_a = n_a < MAX_L ? n_a : MAX_L, l_b = n_b < MAX_L ? n_b : MAX_L;
     int d1 = n_a - 13;
@@ -800,6 +839,15 @@ bool match_geometry(int n_a, int n_b, uint64_t W, int ctas_a, int ctas_b, MatchG
     g->ctas_a = clamp_ctas(n_a, l_a, ctas_a);
     g->ctas_b = clamp_ctas(n_b, l_b, ctas_b);
     g->hcap = default_halo_cap(n_b, d1, wc);
+    // optimistic layout: 25 % + 64 slack per bucket over the mean count (keys of
+    // random polynomials spread evenly; clustered keys overflow and are redone
+    // with the exact layout)
+    g->optimistic = optimistic && d1 >= 2;
+    const uint64_t ea = (1ull << n_a) >> d1, eb = (1ull << n_b) >> d1;
+    g->cap_a = (uint32_t)((ea + ea / 4 + 64 + 3) & ~3ull);
+    g->cap_b = (uint32_t)((eb + eb / 4 + 64 + 3) & ~3ull);
+    const double halo_mean = 2.0 * (double)wc / (double)(1ull << (64 - d1)) * (double)eb;
+    g->hcap_per = (uint32_t)(8.0 + 4.0 * halo_mean);
     g->bytes = match_bytes(*g);
     return true;
 }
@@ -815,6 +863,29 @@ void match_layout(const MatchGeom& g, char* ws, ProbJob* pj) {
     B.ylist = (uint64_t*)take(((size_t)1 << g.l_b) * 8);
     B.ytmp = (uint64_t*)take(((size_t)1 << g.l_b) * 8);
     A.l = g.l_a; B.l = g.l_b;
+    A.h = g.n_a; B.h = g.n_b;
+    A.neg = 0; B.neg = 1;
+    A.d1 = B.d1 = g.d1;
+    A.ctas = g.ctas_a; B.ctas = g.ctas_b;
+    A.wc = B.wc = g.wc;
+    pj->n_a = g.n_a; pj->n_b = g.n_b; pj->d1 = g.d1; pj->Wc = g.wc;
+    A.halo_cnt = nullptr; A.halo_cur = nullptr; A.halo = nullptr; A.halo_cap = 0;
+    A.hcount = nullptr; A.opt_hcap = 0;
+    if (g.optimistic) {
+        A.opt_cap = g.cap_a; B.opt_cap = g.cap_b; B.opt_hcap = g.hcap_per;
+        A.tab = (uint64_t*)take(NB * g.cap_a * 8);
+        B.tab = (uint64_t*)take(NB * g.cap_b * 8);
+        A.bcount = (uint32_t*)take(NB * 4);
+        B.bcount = (uint32_t*)take(NB * 4);
+        B.hcount = (uint32_t*)take(NB * 4);
+        B.halo = (uint64_t*)take(NB * g.hcap_per * 16);
+        B.halo_cap = 0;
+        A.hist = B.hist = nullptr; A.bstart = B.bstart = nullptr;
+        B.halo_cnt = nullptr; B.halo_cur = nullptr;
+        return;
+    }
+    A.opt_cap = B.opt_cap = 0; B.opt_hcap = 0;
+    A.bcount = B.bcount = nullptr; B.hcount = nullptr;
     A.tab = (uint64_t*)take(((size_t)1 << g.n_a) * 8);
     B.tab = (uint64_t*)take(((size_t)1 << g.n_b) * 8);
     A.hist = (uint32_t*)take((size_t)g.ctas_a * NB * 4);
@@ -825,13 +896,6 @@ void match_layout(const MatchGeom& g, char* ws, ProbJob* pj) {
     B.halo_cur = (uint32_t*)take(NB * 4);
     B.halo_cap = g.hcap;
     B.halo = (uint64_t*)take((size_t)g.hcap * 16);
-    A.halo_cnt = nullptr; A.halo_cur = nullptr; A.halo = nullptr; A.halo_cap = 0;
-    A.h = g.n_a; B.h = g.n_b;
-    A.neg = 0; B.neg = 1;
-    A.d1 = B.d1 = g.d1;
-    A.ctas = g.ctas_a; B.ctas = g.ctas_b;
-    A.wc = B.wc = g.wc;
-    pj->n_a = g.n_a; pj->n_b = g.n_b; pj->d1 = g.d1; pj->Wc = g.wc;
 }
 
 // Assign grid bases for a set of problems; fills halves[2*np].
@@ -889,9 +953,11 @@ cudaError_t run_match(ProbJob* jobs, int np, ProbJob* dev_jobs, HalfJob* dev_hal
     if ((size_t)g.nb_small * 4 > psmem) psmem = (size_t)g.nb_small * 4;
     if (psmem > (size_t)RUNS_SMEM_MAX) return cudaErrorInvalidConfiguration;
     k_ysort<<<2 * np, YSORT_THREADS, 0, s>>>(dev_halves, 2 * np);
-    k_runs<false><<<g.part_ctas, PART_THREADS, psmem, s>>>(dev_halves, 2 * np);
-    k_colscan<<<g.scan_ctas, 256, 0, s>>>(dev_halves, 2 * np);
-    k_bscan<<<2 * np, 1024, 0, s>>>(dev_halves, 2 * np);
+    if (!jobs[0].A.opt_cap) {
+        k_runs<false><<<g.part_ctas, PART_THREADS, psmem, s>>>(dev_halves, 2 * np);
+        k_colscan<<<g.scan_ctas, 256, 0, s>>>(dev_halves, 2 * np);
+        k_bscan<<<2 * np, 1024, 0, s>>>(dev_halves, 2 * np);
+    }
     if (ev_count) cudaEventRecord(ev_count, s);
     k_runs<true><<<g.part_ctas, PART_THREADS, psmem, s>>>(dev_halves, 2 * np);
     if (ev_scatter) cudaEventRecord(ev_scatter, s);
@@ -926,26 +992,27 @@ static int stage_ctas(int h) {
 
 // Stage workspace: job structs, then one problem's buffers with a halo large
 // enough for every record of table b (so no window can overflow it).
-static bool stage_geom(int n_a, int n_b, uint64_t W, MatchGeom* g) {
-    if (!match_geometry(n_a, n_b, W, stage_ctas(n_a), stage_ctas(n_b), g)) return false;
+static bool stage_geom(int n_a, int n_b, uint64_t W, MatchGeom* g, bool optimistic) {
+    if (!match_geometry(n_a, n_b, W, stage_ctas(n_a), stage_ctas(n_b), g, optimistic)) return false;
     g->hcap = 1ull << n_b;
     g->bytes = match_bytes(*g);
     return true;
 }
 
 extern "C" size_t rfr_stage_match_workspace(int n_a, int n_b) {
-    MatchGeom g;
-    if (!stage_geom(n_a, n_b, 0, &g)) return 0;
+    MatchGeom g, go;
+    if (!stage_geom(n_a, n_b, 0, &g, false)) return 0;
+    if (stage_geom(n_a, n_b, 0, &go, true) && go.bytes > g.bytes) g.bytes = go.bytes;
     // the bucket count only shrinks for wider windows; budget for d1 = MAX_D1 histograms
     const size_t hist_extra = ((size_t)stage_ctas(n_a) + stage_ctas(n_b)) * ((size_t)1 << MAX_D1) * 4 + 8 * 4096;
     return g.bytes + hist_extra + 2048;
 }
 
-extern "C" int rfr_stage_match(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
-                               const uint64_t* w_b, const uint64_t* w2_b, int n_b,
-                               uint64_t window, uint64_t window2,
-                               void* workspace, size_t workspace_bytes,
-                               uint64_t* cand, uint64_t cap, uint64_t* counters, void* stream) {
+static int stage_match(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
+                       const uint64_t* w_b, const uint64_t* w2_b, int n_b,
+                       uint64_t window, uint64_t window2,
+                       void* workspace, size_t workspace_bytes,
+                       uint64_t* cand, uint64_t cap, uint64_t* counters, void* stream, bool optimistic) {
     if (n_a < 0 || n_b < n_a || n_b > 32 || !workspace || !counters || (!cand && cap)) return RFR_E_INVALID;
     if ((n_a && (!w_a || !w2_a)) || (n_b && (!w_b || !w2_b))) return RFR_E_INVALID;
     if (((uintptr_t)workspace) & 255) return RFR_E_INVALID;
@@ -960,7 +1027,7 @@ extern "C" int rfr_stage_match(const uint64_t* w_a, const uint64_t* w2_a, int n_
         return run_small(&sj, 1, (SmallJob*)workspace, s) == cudaSuccess ? RFR_OK : RFR_E_CUDA;
     }
     MatchGeom g;
-    if (!stage_geom(n_a, n_b, window, &g)) return RFR_E_WINDOW;
+    if (!stage_geom(n_a, n_b, window, &g, optimistic)) return RFR_E_WINDOW;
     if (g.bytes + 2048 > workspace_bytes) return RFR_E_INVALID;
     char* base = (char*)workspace;
     ProbJob* dev_job = (ProbJob*)base;
@@ -976,8 +1043,28 @@ extern "C" int rfr_stage_match(const uint64_t* w_a, const uint64_t* w2_a, int n_
     pj.ctr = (unsigned long long*)counters;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(counters, 0, 6 * sizeof(uint64_t), s) != cudaSuccess) return RFR_E_CUDA;
-    if (cudaMemsetAsync(pj.B.halo_cnt, 0, (((size_t)1 << g.d1) + 1) * 4, s) != cudaSuccess) return RFR_E_CUDA;
+    if (cudaMemsetAsync(g.optimistic ? (void*)pj.A.bcount : (void*)pj.B.halo_cnt, 0,
+                        (g.optimistic ? 3 * (((((size_t)1 << g.d1) * 4) + 255) & ~(size_t)255)
+                                      : (((size_t)1 << g.d1) + 1) * 4), s) != cudaSuccess) return RFR_E_CUDA;
     HalfJob halves[2];
     cudaError_t e = run_match(&pj, 1, dev_job, dev_halves, halves, s, nullptr, nullptr);
     return e == cudaSuccess ? RFR_OK : RFR_E_CUDA;
+}
+
+extern "C" int rfr_stage_match(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
+                               const uint64_t* w_b, const uint64_t* w2_b, int n_b,
+                               uint64_t window, uint64_t window2,
+                               void* workspace, size_t workspace_bytes,
+                               uint64_t* cand, uint64_t cap, uint64_t* counters, void* stream) {
+    return stage_match(w_a, w2_a, n_a, w_b, w2_b, n_b, window, window2, workspace, workspace_bytes,
+                       cand, cap, counters, stream, true);
+}
+
+extern "C" int rfr_stage_match_exact(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
+                                     const uint64_t* w_b, const uint64_t* w2_b, int n_b,
+                                     uint64_t window, uint64_t window2,
+                                     void* workspace, size_t workspace_bytes,
+                                     uint64_t* cand, uint64_t cap, uint64_t* counters, void* stream) {
+    return stage_match(w_a, w2_a, n_a, w_b, w2_b, n_b, window, window2, workspace, workspace_bytes,
+                       cand, cap, counters, stream, false);
 }

@@ -37,7 +37,13 @@ struct HalfJob {
     uint32_t* halo_cur;     // [NB]     (half b): halo write cursors
     uint64_t* halo;         // [halo_cap][2] (half b): (coarse key, mask)
     uint64_t halo_cap;
-    int* err;               // set to 1 on halo overflow
+    int* err;               // set to 1 on halo or bucket overflow
+    // optimistic layout (no count pass): bucket k owns tab[k*opt_cap ..) and
+    // halo[k*opt_hcap ..); bcount / hcount are the final cursors (= counts)
+    uint32_t opt_cap;       // 0: exact layout from the count pass
+    uint32_t opt_hcap;
+    uint32_t* bcount;       // [NB]
+    uint32_t* hcount;       // [NB] (half b)
 };
 
 // One problem's match.
@@ -70,6 +76,9 @@ cudaError_t run_small(const SmallJob* jobs, int np, SmallJob* dev_jobs, cudaStre
 // Host-side sizing of one problem's match.
 struct MatchGeom {
     int n_a, n_b, d1, ctas_a, ctas_b, l_a, l_b;
+    bool optimistic;        // per-bucket slack regions instead of a count pass
+    uint32_t cap_a, cap_b;  // optimistic bucket capacities (records)
+    uint32_t hcap_per;      // optimistic halo slots per bucket
     uint64_t wc;
     uint64_t hcap;          // halo capacity (entries)
     size_t bytes;           // device workspace bytes (tables + histograms + halo)
@@ -77,7 +86,8 @@ struct MatchGeom {
 
 // Choose bucket bits and coarse window; returns false if the window is too
 // wide for any bucket layout.
-bool match_geometry(int n_a, int n_b, uint64_t W, int ctas_a, int ctas_b, MatchGeom* g);
+bool match_geometry(int n_a, int n_b, uint64_t W, int ctas_a, int ctas_b, MatchGeom* g,
+                    bool optimistic = true);
 
 // Bytes of one problem's buffers for geometry g (uses g.hcap).
 size_t match_bytes(const MatchGeom& g);
@@ -89,6 +99,9 @@ void match_layout(const MatchGeom& g, char* ws, ProbJob* pj);
 // launch count -> column scan -> bucket scan -> scatter -> join on stream s.
 // ev_count / ev_scatter, if given, are recorded after the scans and after
 // the scatter.
+// All problems of one call use the same layout (all optimistic or all exact);
+// the optimistic cursors (bcount, hcount) and the exact halo counts must be
+// zeroed by the caller.
 cudaError_t run_match(ProbJob* jobs, int np, ProbJob* dev_jobs, HalfJob* dev_halves,
                       HalfJob* host_halves, cudaStream_t s, cudaEvent_t ev_count, cudaEvent_t ev_scatter);
 

@@ -386,11 +386,14 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
         std::vector<int> sub, rest;
         size_t bytes = 0;
         const size_t share = C.budget / std::max(1, C.cfg.max_inflight);
+        // one layout per sub-batch: optimistic first, exact for problems that overflowed it
+        const bool exact_round = work[todo[0]].full_halo;
         for (int sl : todo) {
             Work& w = work[sl];
+            if (w.full_halo != exact_round) { rest.push_back(sl); continue; }
             MatchGeom g;
             if (!match_geometry(w.plan.n_a, w.plan.n_b, w.plan.window, part_ctas(w.plan.n_a, tot_elems),
-                                part_ctas(w.plan.n_b, tot_elems), &g)) { w.status = RFR_E_WINDOW; continue; }
+                                part_ctas(w.plan.n_b, tot_elems), &g, !w.full_halo)) { w.status = RFR_E_WINDOW; continue; }
             if (w.full_halo) { g.hcap = 1ull << g.n_b; g.bytes = match_bytes(g); }
             const size_t need = g.bytes + (size_t)cap * 8 + 6 * 8 + 512;
             if (need > C.budget) { w.status = RFR_E_BUDGET; continue; }
@@ -428,12 +431,15 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
             pj.ctr = (unsigned long long*)ctr;
             pj.A.err = pj.B.err = (int*)(ctr + 4);
             cudaMemsetAsync(ctr, 0, 6 * 8, s);
-            cudaMemsetAsync(pj.B.halo_cnt, 0, (((size_t)1 << w.geom.d1) + 1) * 4, s);
+            if (w.geom.optimistic)
+                cudaMemsetAsync(pj.A.bcount, 0, 3 * (((((size_t)1 << w.geom.d1) * 4) + 255) & ~(size_t)255), s);
+            else
+                cudaMemsetAsync(pj.B.halo_cnt, 0, (((size_t)1 << w.geom.d1) + 1) * 4, s);
         }
         h2d += (uint64_t)np * sizeof(ProbJob) + 2ull * np * sizeof(HalfJob);
         cudaEventRecord(ev[3], s);
         rc = cuda_ok(run_match(jobs.data(), np, d_jobs, d_halves, halves.data(), s, ev[4], ev[5]));
-        launches += 6;
+        launches += exact_round ? 6 : 3;
         cudaEventRecord(ev[6], s);
         std::vector<uint64_t> h_ctr(6 * (size_t)np);
         for (int i = 0; i < np && rc == RFR_OK; ++i)

@@ -120,11 +120,11 @@ def _expected_pairs(wa, w2a, wb, w2b, W, W2):
     return {(i, j) for (i, j) in pairs if accept((a2[i] + b2[j]) % M64, M64, W2)}
 
 
-def _run_match(P, wa, w2a, wb, w2b, W, W2, cap=1 << 16):
+def _run_match(P, wa, w2a, wb, w2b, W, W2, cap=1 << 16, exact=False):
     cand, ctr, _ = P.stage_match(u64_tensor(wa) if wa else u64_tensor([0])[:0],
                                  u64_tensor(w2a) if wa else u64_tensor([0])[:0],
                                  u64_tensor(wb) if wb else u64_tensor([0])[:0],
-                                 u64_tensor(w2b) if wb else u64_tensor([0])[:0], W, W2, cap)
+                                 u64_tensor(w2b) if wb else u64_tensor([0])[:0], W, W2, cap, exact=exact)
     torch.cuda.synchronize()
     ctr = [int(x) for x in ctr.cpu().numpy().view(np.uint64)]
     cnt = ctr[2]
@@ -181,9 +181,11 @@ def test_match_candidate_cap(P):
     assert ctr[2] == (1 << 9) - 1 and len(raw) == 10
 
 
+@pytest.mark.parametrize("exact", [False, True])
 @pytest.mark.parametrize("seed,na,nb", [(11, 14, 15), (12, 16, 16), (13, 17, 18)])
-def test_match_several_tiles_against_scan(P, seed, na, nb):
-    """Sizes that span many buckets and CTAs, vs RECOMBINE_A on the concatenation."""
+def test_match_several_tiles_against_scan(P, seed, na, nb, exact):
+    """Sizes that span many buckets and CTAs, vs RECOMBINE_A on the concatenation,
+    with the slack-region layout and with the exact (count pass) layout."""
     from oracle.recombine import recombine_a
     rng = random.Random(seed)
     wa = [rng.randrange(M64) for _ in range(na)]
@@ -192,7 +194,8 @@ def test_match_several_tiles_against_scan(P, seed, na, nb):
     wb[2] = (-(wa[0] + wa[5] + wb[7])) % M64
     wa[9] = (-(wb[1] + wb[3])) % M64
     W = 1 << 30
-    got, ctr, _ = _run_match(P, wa, [0] * na, wb, [0] * nb, W, 0)
+    got, ctr, _ = _run_match(P, wa, [0] * na, wb, [0] * nb, W, 0, exact=exact)
+    assert ctr[4] == 0
     scan = set(recombine_a(wa + wb + [0], M64, W)) - {0}
     exp = {(s & ((1 << na) - 1), s >> na) for s in scan}
     assert got == exp and len(exp) >= 2
@@ -233,3 +236,21 @@ def test_verify_true_and_false_patterns(P):
         else:
             assert res[j] == 1, (j, f)
             assert list(co[j, :len(f)]) == f
+
+
+def test_match_clustered_keys_overflow_then_exact(P):
+    """Weights below 2^40 put every key in one bucket: the slack layout must
+    report the overflow, and the exact layout must give the scan's answer."""
+    from oracle.recombine import recombine_a
+    rng = random.Random(77)
+    na, nb = 14, 15
+    wa = [rng.randrange(1 << 40) for _ in range(na)]
+    wb = [rng.randrange(1 << 40) for _ in range(nb)]
+    wa[0] = 0                                           # {a0} sums to an integer
+    W = 1 << 20
+    _, ctr, _ = _run_match(P, wa, [0] * na, wb, [0] * nb, W, 0)
+    assert ctr[4] == 1
+    got, ctr2, _ = _run_match(P, wa, [0] * na, wb, [0] * nb, W, 0, exact=True)
+    assert ctr2[4] == 0
+    scan = set(recombine_a(wa + wb + [0], M64, W)) - {0}
+    assert got == {(s & ((1 << na) - 1), s >> na) for s in scan} and (1, 0) in got
