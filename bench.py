@@ -216,6 +216,19 @@ def cpu_oracle_sample(insts, budget_s=15.0, max_polys=8):
     return done, dt
 
 
+def max_over_ranks(value: float, world: int) -> float:
+    """Max of a per-rank time over all ranks (the slowest replica sets the
+    step time).  Uses a CUDA tensor under NCCL, a CPU tensor under gloo."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(a):
     """The oracle as it stands, timed on host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -289,11 +302,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
         clk = clocks.stop()
-        ms = ev0.elapsed_time(ev1)
-        if world > 1:
-            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ev0.elapsed_time(ev1), world)
         statuses = [r.status for r in res]
         # ---- correctness of the last timed step (outside the timed region)
         ok_golden = None
@@ -315,11 +324,7 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         barrier()
-        ms_e2e = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms_e2e], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e2e = float(t.item())
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1), world)
         # ---- one launch per polynomial (same inputs, host buffers)
         one_ms = None
         if rank == 0:

@@ -283,7 +283,8 @@ __global__ void __launch_bounds__(YSORT_THREADS) k_ysort(const HalfJob* __restri
 // run elements and all buckets stay open (the tables fit in L2 anyway).
 constexpr int PIECE = 4096;
 constexpr int UNROLL = 4;
-constexpr int RANGE = 256;                    // buckets per sweep
+constexpr int RANGE = 256;                    // buckets per sweep (at least)
+constexpr int RANGE_MAX = 4096;               // buckets per sweep when buckets are many
 constexpr int MAX_RUNS_PER_CTA = 1024;
 // Piece mode only runs for halves with fewer than 16 runs (h < 20, so at most
 // 2^6 buckets); 64 KB covers it and range mode with room to spare.
@@ -317,6 +318,22 @@ __device__ __forceinline__ void store_halo(const HalfJob& J, const RunCtx& R, ui
     }
     J.halo[2 * slot] = Kc;
     J.halo[2 * slot + 1] = m;
+}
+
+// Copy (SCATTER) or count a table-b record into the halo of the neighbouring
+// bucket when its coarse window reaches across the bucket edge.
+template <bool SCATTER>
+__device__ __forceinline__ void halo_check(const HalfJob& J, const RunCtx& R, uint64_t K, uint32_t k, uint64_t m) {
+    const uint64_t Kc = K & ~R.trunc;
+    const uint64_t off = Kc - ((uint64_t)k << R.sh);
+    const uint32_t kl = (k - 1u) & (uint32_t)(R.NB - 1), kh = (k + 1u) & (uint32_t)(R.NB - 1);
+    if (SCATTER) {
+        if (off < R.wc) store_halo(J, R, kl, Kc, m);
+        if (R.width - off <= R.wc) store_halo(J, R, kh, Kc, m);
+    } else {
+        if (off < R.wc) atomicAdd(&J.halo_cnt[kl], 1u);
+        if (R.width - off <= R.wc) atomicAdd(&J.halo_cnt[kh], 1u);
+    }
 }
 
 // Handle one element (already loaded) of run x: returns its bucket.
@@ -388,7 +405,7 @@ __device__ __forceinline__ void emit_sorted(const HalfJob& J, const RunCtx& R, u
 }
 
 template <bool SCATTER>
-__global__ void __launch_bounds__(PART_THREADS) k_runs(const HalfJob* __restrict__ hs, int nh) {
+__global__ void __launch_bounds__(PART_THREADS, 2) k_runs(const HalfJob* __restrict__ hs, int nh) {
     extern __shared__ uint32_t dyn[];
     __shared__ uint64_t sw[32];
     const int j = find_last_le(nh, (int)blockIdx.x, [&](int i) { return hs[i].cta_base; });
@@ -453,8 +470,8 @@ __global__ void __launch_bounds__(PART_THREADS) k_runs(const HalfJob* __restrict
     // ---- range mode
     const uint32_t G = (1u << hx) / (uint32_t)J.ctas;            // runs of this CTA (16..1024)
     const uint32_t x0 = (uint32_t)c * G;
-    uint32_t* acc = dyn;                                         // [RANGE] cursors of the current range
-    uint32_t* curx = dyn + RANGE;                                // [G] next rotated index of each run
+    uint32_t* acc = dyn;                                         // [rw] cursors of the current range
+    uint32_t* curx = dyn + RANGE_MAX;                            // [G] next rotated index of each run
     uint32_t* j0s = curx + MAX_RUNS_PER_CTA;                     // [G] rotation (index of the smallest key)
     __syncthreads();
     for (uint32_t g = threadIdx.x; g < G; g += blockDim.x) {
@@ -471,8 +488,11 @@ __global__ void __launch_bounds__(PART_THREADS) k_runs(const HalfJob* __restrict
         j0s[g] = lo == N ? 0u : lo;
         curx[g] = 0u;
     }
-    const int nrange = NB > RANGE ? NB / RANGE : 1;
-    const int rw = NB > RANGE ? RANGE : NB;
+    // sweep width: at least RANGE buckets and about 256 records of each run per sweep
+    int rw = RANGE;
+    while (rw < RANGE_MAX && (int)(((uint64_t)rw << l) >> R.d1) < 256) rw <<= 1;
+    if (rw > NB) rw = NB;
+    const int nrange = NB / rw;
     for (int r = 0; r < nrange; ++r) {
         const uint32_t k0 = (uint32_t)r * rw, kend = k0 + rw;
         __syncthreads();
@@ -488,27 +508,63 @@ __global__ void __launch_bounds__(PART_THREADS) k_runs(const HalfJob* __restrict
             uint32_t t0 = curx[g];
             bool done = t0 >= N;
             while (!done) {
-                uint64_t yv[UNROLL];
+                // 1. load UNROLL steps, compute keys, buckets and stop lanes
+                uint64_t Kv[UNROLL], mv[UNROLL];
+                uint32_t kv[UNROLL], stv[UNROLL];
 #pragma unroll
                 for (int u = 0; u < UNROLL; ++u) {
                     const uint32_t t = t0 + 32 * u + lane;
-                    yv[u] = t < N ? Y[(j0 + t) & (N - 1)] : 0ull;
+                    const uint64_t y = t < N ? Y[(j0 + t) & (N - 1)] : 0ull;
+                    Kv[u] = x + (y & ~R.lml);
+                    mv[u] = xmask | (y & R.lml);
+                    kv[u] = (uint32_t)(Kv[u] >> R.sh);
                 }
+                int nsteps = UNROLL;
 #pragma unroll
                 for (int u = 0; u < UNROLL; ++u) {
-                    if (done) break;
                     const uint32_t t = t0 + 32 * u + lane;
-                    const uint64_t K = x + (yv[u] & ~R.lml);
-                    const uint32_t k = (uint32_t)(K >> R.sh);
-                    const bool stop = t >= N || k >= kend;       // keys rise along the rotated run
-                    const uint32_t stops = __ballot_sync(0xffffffffu, stop);
-                    emit_sorted<SCATTER>(J, R, acc, k0, !stop, stops, K, k, xmask | (yv[u] & R.lml), lt);
-                    if (stops) {
-                        done = true;
-                        t0 = t0 + 32 * u + (__ffs(stops) - 1);
+                    stv[u] = __ballot_sync(0xffffffffu, t >= N || kv[u] >= kend);   // keys rise along the run
+                    if (stv[u] && nsteps == UNROLL) nsteps = u + 1;
+                }
+                // 2. one reservation per bucket group, all steps' atomics in flight together
+                uint32_t bv[UNROLL];
+                int lv[UNROLL];
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    bv[u] = 0; lv[u] = 0;
+                    if (u >= nsteps) continue;
+                    const int first_stop = stv[u] ? __ffs(stv[u]) - 1 : 32;
+                    const bool valid = lane < first_stop;
+                    const uint32_t pk = __shfl_up_sync(0xffffffffu, kv[u], 1);
+                    const bool head = valid && (lane == 0 || kv[u] != pk);
+                    const uint32_t heads = __ballot_sync(0xffffffffu, head);
+                    const uint32_t upto = heads & (lt | (1u << lane));
+                    lv[u] = upto ? 31 - __clz(upto) : 0;
+                    const uint32_t above = heads & ~(lt | (1u << lane));
+                    const int next_head = above ? __ffs(above) - 1 : 32;
+                    const int gend = next_head < first_stop ? next_head : first_stop;
+                    if (head)
+                        bv[u] = J.opt_cap ? atomicAdd(&J.bcount[kv[u]], (uint32_t)(gend - lane))
+                                          : atomicAdd(&acc[kv[u] - k0], (uint32_t)(gend - lane));
+                }
+                // 3. positions, records, halo
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    if (u >= nsteps) continue;
+                    const int first_stop = stv[u] ? __ffs(stv[u]) - 1 : 32;
+                    const bool valid = lane < first_stop;
+                    if (SCATTER) {
+                        const uint32_t base = __shfl_sync(0xffffffffu, bv[u], lv[u]);
+                        if (valid) store_record(J, kv[u], base + (uint32_t)(lane - lv[u]), ((Kv[u] << R.d1) & ~R.lmh) | mv[u]);
                     }
+                    if (valid && R.neg) halo_check<SCATTER>(J, R, Kv[u], kv[u], mv[u]);
                 }
-                if (!done) t0 += 32 * UNROLL;
+                if (stv[nsteps - 1]) {
+                    done = true;
+                    t0 = t0 + 32 * (nsteps - 1) + (__ffs(stv[nsteps - 1]) - 1);
+                } else {
+                    t0 += 32 * UNROLL;
+                }
             }
             if (lane == 0) curx[g] = t0;
         }
@@ -949,7 +1005,7 @@ cudaError_t run_match(ProbJob* jobs, int np, ProbJob* dev_jobs, HalfJob* dev_hal
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(dev_jobs, jobs, sizeof(ProbJob) * np, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
-    size_t psmem = (size_t)(RANGE + 2 * MAX_RUNS_PER_CTA) * 4;
+    size_t psmem = (size_t)(RANGE_MAX + 2 * MAX_RUNS_PER_CTA) * 4;
     if ((size_t)g.nb_small * 4 > psmem) psmem = (size_t)g.nb_small * 4;
     if (psmem > (size_t)RUNS_SMEM_MAX) return cudaErrorInvalidConfiguration;
     k_ysort<<<2 * np, YSORT_THREADS, 0, s>>>(dev_halves, 2 * np);

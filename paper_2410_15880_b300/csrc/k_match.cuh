@@ -10,7 +10,7 @@ constexpr int SUB_BITS = 13;          // second radix digit, sorted in shared me
 constexpr int JOIN_CAP = 9216;        // table-a entries per shared-memory chunk
 constexpr int JOIN_THREADS = 512;
 constexpr int PART_THREADS = 512;
-constexpr int MAX_D1 = 16;            // first radix digit, at most 65536 buckets
+constexpr int MAX_D1 = 18;            // first radix digit, at most 262144 buckets
 constexpr int MAX_L = 16;             // low-list bits (sorted list of up to 65536 sums)
 constexpr int YSORT_THREADS = 1024;
 

@@ -59,6 +59,11 @@ def test_degree100_batch_fp32_bulk_roots():
     assert all(x.diag["max_root_err"] < 1e-20 for x in res)
 
 
+def test_degree120_product(ctx):
+    res = check_batch(ctx, golden("cfg5"))
+    assert res[0].diag["n_b"] >= 30 and res[0].diag["half_sums"] > (1 << 31)
+
+
 def test_one_launch_per_polynomial_equals_batch(ctx):
     recs = golden("cfg2")[:8]
     batch = ctx.factor_batch([r["coeffs"] for r in recs])
