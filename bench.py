@@ -284,7 +284,7 @@ def main():
         if world > 1:
             dist.barrier()
 
-    with Context(device=local, timing=True, root_mode=a.root_mode) as ctx:
+    with Context(device=local, timing=True, root_mode=a.root_mode, autotune=True) as ctx:
         for _ in range(a.warmup):
             res = ctx.factor_batch_device(d_co, d_dg)
         # ---- timed region: device-resident inputs
@@ -360,7 +360,8 @@ def main():
         "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME[a.config], "polys_per_step": B,
                    "half_sums_per_step": half_sums, "parallelism": f"replicas x{world}",
-                   "l2": "tables larger than L2 (no flush needed)", "root_mode": a.root_mode},
+                   "l2": "tables larger than L2 (no flush needed)", "root_mode": a.root_mode,
+                   "autotune": "layouts tuned per (n_a, n_b) during warm-up"},
         "half_sums_per_s": half_sums * world * a.steps / (ms / 1e3),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,

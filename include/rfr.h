@@ -78,6 +78,12 @@ typedef struct {
     int      timing;            /* 1: record CUDA events per stage into rfr_diag.stage_us   */
     uint64_t max_candidates;    /* per polynomial cap on candidate patterns (after the Tr_1/Tr_2 windows) */
     double   eps_override;      /* > 0: integrality window eps (fraction of 1) replacing the derived one */
+    int      use_graphs;        /* 1: replay the batch prologue (copy in, validate, roots, weights,
+                                   plans out) as a captured CUDA graph per batch size */
+    int      autotune;          /* 1: time candidate layouts (low-list bits, bucket digit, CTAs per
+                                   SM) on the first problem of each (n_a, n_b) class and keep the best */
+    const char* tune_cache_path;/* NULL, or a text file that stores tuned layouts across runs (read at
+                                   create, appended when a class is tuned); the string is copied */
 } rfr_config;
 
 /* Per-polynomial diagnostics returned with each result.  The stage times,
@@ -122,7 +128,8 @@ typedef void* (*rfr_alloc_fn)(size_t bytes, void* user, void* stream);
 typedef void  (*rfr_free_fn)(void* ptr, size_t bytes, void* user, void* stream);
 
 /* Fill *cfg with defaults: device 0, budget 0 (auto), max_inflight 2,
- * max_batch 64, FP64 roots, timing off, 1<<16 candidates, no override.
+ * max_batch 64, FP64 roots, timing off, 1<<16 candidates, no override,
+ * graphs on, autotune off, no tune cache file.
  * Returns RFR_E_INVALID if cfg is NULL. */
 int rfr_config_default(rfr_config* cfg);
 

@@ -875,10 +875,14 @@ static int clamp_ctas(int h, int l, int want) {
     return want < pieces ? (want < 1 ? 1 : want) : pieces;
 }
 
-bool match_geometry(int n_a, int n_b, uint64_t W, int ctas_a, int ctas_b, MatchGeom* g, bool optimistic) {
+bool match_geometry(int n_a, int n_b, uint64_t W, int ctas_a, int ctas_b, MatchGeom* g, bool optimistic,
+                    const TuneParams* tp) {
     if (n_a < 0 || n_b < n_a || n_b > 32) return false;
-    const int l_a = n_a < MAX_L ? n_a : MAX_L, l_b = n_b < MAX_L ? n_b : MAX_L;
-    int d1 = n_a - 13;
+    const TuneParams dflt;
+    if (!tp) tp = &dflt;
+    const int lm = tp->l_max < 10 ? 10 : (tp->l_max > 18 ? 18 : tp->l_max);
+    const int l_a = n_a < lm ? n_a : lm, l_b = n_b < lm ? n_b : lm;
+    int d1 = n_a - tp->d1_off;
     if (d1 < 2) d1 = 2;
     if (d1 > MAX_D1) d1 = MAX_D1;
     uint64_t wc = 0;

@@ -11,7 +11,6 @@ constexpr int JOIN_CAP = 9216;        // table-a entries per shared-memory chunk
 constexpr int JOIN_THREADS = 512;
 constexpr int PART_THREADS = 512;
 constexpr int MAX_D1 = 18;            // first radix digit, at most 262144 buckets
-constexpr int MAX_L = 16;             // low-list bits (sorted list of up to 65536 sums)
 constexpr int YSORT_THREADS = 1024;
 
 // One half-table (a: keys = sum w; b: keys = -sum w) of one problem.
@@ -84,10 +83,17 @@ struct MatchGeom {
     size_t bytes;           // device workspace bytes (tables + histograms + halo)
 };
 
+// Layout knobs chosen by the autotuner (defaults: 16, 13, 16).
+struct TuneParams {
+    int l_max = 16;          // low-list bits (sorted list Y of up to 2^l_max sums)
+    int d1_off = 13;         // bucket bits d1 = n_a - d1_off (mean table-a bucket 2^d1_off)
+    int cta_per_sm = 16;     // scatter CTAs per SM over a sub-batch
+};
+
 // Choose bucket bits and coarse window; returns false if the window is too
 // wide for any bucket layout.
 bool match_geometry(int n_a, int n_b, uint64_t W, int ctas_a, int ctas_b, MatchGeom* g,
-                    bool optimistic = true);
+                    bool optimistic = true, const TuneParams* tp = nullptr);
 
 // Bytes of one problem's buffers for geometry g (uses g.hcap).
 size_t match_bytes(const MatchGeom& g);

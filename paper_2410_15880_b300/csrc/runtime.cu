@@ -23,7 +23,11 @@
 #include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <fstream>
+#include <map>
 #include <memory>
+#include <sstream>
+#include <string>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -116,6 +120,15 @@ struct Pipeline {
     rfr_plan* h_plans = nullptr;      // pinned
     const int64_t* cur_coeffs = nullptr;   // coefficient rows of the running batch (device)
     const int32_t* cur_deg = nullptr;
+    // captured prologue graphs (copy in, validate, roots, weights, plans out) per batch shape
+    struct PrologueGraph { int B; int mode; double eps; cudaGraphExec_t exec; };
+    std::vector<PrologueGraph> graphs;
+    void drop_graphs() {
+        for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+        graphs.clear();
+    }
+    int issue_prologue(int B, const int64_t* d_co, const int32_t* d_dg, bool copy_in,
+                       uint64_t& h2d, uint64_t& d2h, uint32_t& launches);
     bool init(Ctx* c);
     void destroy();
     bool reserve(int n);
@@ -153,6 +166,10 @@ struct Ctx {
     int running_batches = 0;
     std::vector<std::thread> workers;
     std::vector<std::unique_ptr<Pipeline>> worker_pipes;
+    // autotuned layouts per (n_a, n_b)
+    std::mutex tune_mu;
+    std::map<std::pair<int, int>, TuneParams> tuned;
+    std::string tune_path, device_name;
 
     // Reserve `bytes` of the device budget; waits while other batches hold it.
     bool reserve(size_t bytes) {
@@ -181,6 +198,7 @@ bool Pipeline::init(Ctx* c) {
 
 void Pipeline::destroy() {
     if (s) cudaStreamSynchronize(s);
+    drop_graphs();
     auto put = [&](void* p) { if (p) ctx->alloc.put(p, 0, s); };
     put(d_coeffs); put(d_deg); put(d_roots); put(d_radius); put(d_rstat); put(d_plans);
     if (s) cudaStreamSynchronize(s);
@@ -196,6 +214,7 @@ bool Pipeline::reserve(int n) {
     if (n <= cap) return true;
     int nc = std::max(n, std::max(16, cap * 2));
     cudaStreamSynchronize(s);
+    drop_graphs();                      // they name the buffers freed below
     auto put = [&](void* p) { if (p) ctx->alloc.put(p, 0, s); };
     put(d_coeffs); put(d_deg); put(d_roots); put(d_radius); put(d_rstat); put(d_plans);
     if (h_coeffs) cudaFreeHost(h_coeffs);
@@ -244,12 +263,110 @@ static void canonical_sort(std::vector<std::vector<int64_t>>& fs) {
 }
 
 // Candidate CTAs per half: spread about four CTAs per SM over the sub-batch.
-static int part_ctas(int h, double share_total_elems) {
-    const double target = 16.0 * 148.0;
+static int part_ctas(int h, double share_total_elems, int cta_per_sm = 16) {
+    const double target = (double)cta_per_sm * 148.0;
     double want = std::ldexp(1.0, h) * target / std::max(1.0, share_total_elems);
     int c = 1;
     while (c * 2 <= want && c < 512 && ((uint64_t)c * 2 * 64) <= (1ull << h)) c *= 2;
     return c;
+}
+
+int Pipeline::issue_prologue(int B, const int64_t* d_co, const int32_t* d_dg, bool copy_in,
+                             uint64_t& h2d, uint64_t& d2h, uint32_t& launches) {
+    Ctx& C = *ctx;
+    cudaEventRecord(ev[0], s);
+    int rc = RFR_OK;
+    if (copy_in) {
+        rc = cuda_ok(cudaMemcpyAsync(d_coeffs, h_coeffs, (size_t)B * LDC * 8, cudaMemcpyHostToDevice, s));
+        if (rc == RFR_OK) rc = cuda_ok(cudaMemcpyAsync(d_deg, h_deg, (size_t)B * 4, cudaMemcpyHostToDevice, s));
+        h2d += (uint64_t)B * LDC * 8 + (uint64_t)B * 4;
+    }
+    if (rc == RFR_OK) rc = rfr_stage_validate(d_co, d_dg, B, d_rstat, s);
+    if (rc == RFR_OK) rc = rfr_stage_roots(d_co, d_dg, B, C.cfg.root_mode, d_roots, d_radius, d_rstat, s);
+    launches += 2;
+    cudaEventRecord(ev[1], s);
+    if (rc == RFR_OK) rc = rfr_stage_weights(d_co, d_dg, B, d_roots, d_radius, d_rstat, C.cfg.eps_override, d_plans, s);
+    launches += 1;
+    cudaEventRecord(ev[2], s);
+    if (rc == RFR_OK) rc = cuda_ok(cudaMemcpyAsync(h_plans, d_plans, (size_t)B * sizeof(rfr_plan), cudaMemcpyDeviceToHost, s));
+    d2h += (uint64_t)B * sizeof(rfr_plan);
+    return rc;
+}
+
+// Time one problem's match with layout knobs tp (one warm-up and one timed
+// run); returns milliseconds, or a negative value if the layout does not fit.
+static double time_layout(Ctx& C, cudaStream_t s, const rfr_plan& plan, const rfr_plan* dplan,
+                          const TuneParams& tp, cudaEvent_t e0, cudaEvent_t e1) {
+    MatchGeom g;
+    const double elems = std::ldexp(1.0, plan.n_a) + std::ldexp(1.0, plan.n_b);
+    auto ctas = [&](int h) {
+        double want = std::ldexp(1.0, h) * tp.cta_per_sm * 148.0 / elems;
+        int c = 1;
+        while (c * 2 <= want && c < 512) c *= 2;
+        return c;
+    };
+    if (!match_geometry(plan.n_a, plan.n_b, plan.window, ctas(plan.n_a), ctas(plan.n_b), &g, true, &tp)) return -1.0;
+    const size_t bytes = g.bytes + 4096 + 256 + 2048;
+    if (bytes > C.budget / 2) return -1.0;
+    char* ws = (char*)C.alloc.get(bytes, s);
+    if (!ws) return -1.0;
+    double best = -1.0;
+    for (int rep = 0; rep < 2; ++rep) {
+        ProbJob pj;
+        memset(&pj, 0, sizeof(pj));
+        match_layout(g, ws + 2048, &pj);
+        uint64_t* ctr = (uint64_t*)(ws + 2048 + g.bytes);
+        uint64_t* cand = ctr + 32;
+        pj.A.w = dplan->w; pj.B.w = dplan->w + plan.n_a;
+        pj.w_a = dplan->w; pj.w2_a = dplan->w2; pj.w_b = dplan->w + plan.n_a; pj.w2_b = dplan->w2 + plan.n_a;
+        pj.W = plan.window; pj.W2 = plan.window2;
+        pj.cand = cand; pj.cap = 256; pj.ctr = (unsigned long long*)ctr;
+        pj.A.err = pj.B.err = (int*)(ctr + 4);
+        cudaMemsetAsync(ctr, 0, 64, s);
+        cudaMemsetAsync(pj.A.bcount, 0, 3 * (((((size_t)1 << g.d1) * 4) + 255) & ~(size_t)255), s);
+        HalfJob halves[2];
+        cudaEventRecord(e0, s);
+        if (run_match(&pj, 1, (ProbJob*)ws, (HalfJob*)(ws + 1024), halves, s, nullptr, nullptr) != cudaSuccess) break;
+        cudaEventRecord(e1, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) break;
+        best = ms_between(e0, e1);
+    }
+    C.alloc.put(ws, bytes, s);
+    cudaGetLastError();
+    return best;
+}
+
+// Coordinate search over the layout knobs for one (n_a, n_b) class.
+static TuneParams tune_class(Ctx& C, cudaStream_t s, const rfr_plan& plan, const rfr_plan* dplan,
+                             cudaEvent_t e0, cudaEvent_t e1) {
+    TuneParams best;
+    double tbest = time_layout(C, s, plan, dplan, best, e0, e1);
+    if (tbest < 0) return best;
+    const int lvals[] = {15, 17}, dvals[] = {12}, cvals[] = {8, 32};
+    for (int v : lvals) { TuneParams t = best; t.l_max = v; double m = time_layout(C, s, plan, dplan, t, e0, e1); if (m > 0 && m < tbest) { tbest = m; best = t; } }
+    for (int v : dvals) { TuneParams t = best; t.d1_off = v; double m = time_layout(C, s, plan, dplan, t, e0, e1); if (m > 0 && m < tbest) { tbest = m; best = t; } }
+    for (int v : cvals) { TuneParams t = best; t.cta_per_sm = v; double m = time_layout(C, s, plan, dplan, t, e0, e1); if (m > 0 && m < tbest) { tbest = m; best = t; } }
+    return best;
+}
+
+static void tune_cache_load(Ctx& C) {
+    if (C.tune_path.empty()) return;
+    std::ifstream f(C.tune_path);
+    std::string line;
+    while (std::getline(f, line)) {
+        std::istringstream is(line);
+        std::string dev;
+        int na, nb;
+        TuneParams t;
+        if (std::getline(is, dev, '\t') && dev == C.device_name && (is >> na >> nb >> t.l_max >> t.d1_off >> t.cta_per_sm))
+            C.tuned[{na, nb}] = t;
+    }
+}
+
+static void tune_cache_store(Ctx& C, int na, int nb, const TuneParams& t) {
+    if (C.tune_path.empty()) return;
+    std::ofstream f(C.tune_path, std::ios::app);
+    f << C.device_name << '\t' << na << ' ' << nb << ' ' << t.l_max << ' ' << t.d1_off << ' ' << t.cta_per_sm << '\n';
 }
 
 int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int32_t* dev_deg) {
@@ -283,7 +400,6 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
     if (!reserve(B)) return RFR_E_OOM;
     const int64_t* d_co = d_coeffs;
     const int32_t* d_dg = d_deg;
-    cudaEventRecord(ev[0], s);
     int rc = RFR_OK;
     if (device_in) {
         d_co = dev_coeffs;                     // rows are the items in order (every item has a slot)
@@ -296,21 +412,36 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
             memcpy(row, it.coeffs, (it.degree + 1) * 8);
             h_deg[w.slot] = it.degree;
         }
-        rc = cuda_ok(cudaMemcpyAsync(d_coeffs, h_coeffs, (size_t)B * LDC * 8, cudaMemcpyHostToDevice, s));
-        if (rc == RFR_OK) rc = cuda_ok(cudaMemcpyAsync(d_deg, h_deg, (size_t)B * 4, cudaMemcpyHostToDevice, s));
-        h2d += (uint64_t)B * LDC * 8 + (uint64_t)B * 4;
     }
     cur_coeffs = d_co;
     cur_deg = d_dg;
-    if (rc == RFR_OK) rc = rfr_stage_validate(d_co, d_dg, B, d_rstat, s);
-    if (rc == RFR_OK) rc = rfr_stage_roots(d_co, d_dg, B, C.cfg.root_mode, d_roots, d_radius, d_rstat, s);
-    launches += 2;
-    cudaEventRecord(ev[1], s);
-    if (rc == RFR_OK) rc = rfr_stage_weights(d_co, d_dg, B, d_roots, d_radius, d_rstat, C.cfg.eps_override, d_plans, s);
-    launches += 1;
-    cudaEventRecord(ev[2], s);
-    if (rc == RFR_OK) rc = cuda_ok(cudaMemcpyAsync(h_plans, d_plans, (size_t)B * sizeof(rfr_plan), cudaMemcpyDeviceToHost, s));
-    d2h += (uint64_t)B * sizeof(rfr_plan);
+    if (!device_in && C.cfg.use_graphs) {
+        // the prologue's shape depends only on B and the root settings: replay a captured graph
+        cudaGraphExec_t exec = nullptr;
+        for (auto& g : graphs)
+            if (g.B == B && g.mode == C.cfg.root_mode && g.eps == C.cfg.eps_override) exec = g.exec;
+        if (!exec) {
+            uint64_t h0 = 0, d0 = 0;
+            uint32_t l0 = 0;
+            cudaGraph_t graph = nullptr;
+            rc = cuda_ok(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            if (rc == RFR_OK) {
+                const int rc2 = issue_prologue(B, d_co, d_dg, true, h0, d0, l0);
+                rc = cuda_ok(cudaStreamEndCapture(s, &graph));
+                if (rc == RFR_OK) rc = rc2;
+            }
+            if (rc == RFR_OK) rc = cuda_ok(cudaGraphInstantiate(&exec, graph, 0));
+            if (graph) cudaGraphDestroy(graph);
+            if (rc != RFR_OK) { cudaGetLastError(); return rc; }
+            graphs.push_back({B, C.cfg.root_mode, C.cfg.eps_override, exec});
+        }
+        h2d += (uint64_t)B * LDC * 8 + (uint64_t)B * 4;
+        d2h += (uint64_t)B * sizeof(rfr_plan);
+        launches += 3;
+        rc = cuda_ok(cudaGraphLaunch(exec, s));
+    } else {
+        rc = issue_prologue(B, d_co, d_dg, !device_in, h2d, d2h, launches);
+    }
     if (rc == RFR_OK) rc = cuda_ok(cudaStreamSynchronize(s));
     if (rc != RFR_OK) return rc;
     double t_roots = timing ? ms_between(ev[0], ev[1]) : 0, t_weights = timing ? ms_between(ev[1], ev[2]) : 0;
@@ -379,6 +510,23 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
             if (rc != RFR_OK) return rc;
         }
     }
+    if (C.cfg.autotune) {
+        for (int sl : todo) {
+            Work& w = work[sl];
+            const std::pair<int, int> key{w.plan.n_a, w.plan.n_b};
+            bool have;
+            { std::lock_guard<std::mutex> lk(C.tune_mu); have = C.tuned.count(key) > 0; }
+            if (have) continue;
+            const TuneParams t = tune_class(C, s, w.plan, d_plans + w.slot, ev[8], ev[9]);
+            std::lock_guard<std::mutex> lk(C.tune_mu);
+            if (!C.tuned.count(key)) { C.tuned[key] = t; tune_cache_store(C, key.first, key.second, t); }
+        }
+    }
+    auto params_for = [&](const Work& w) {
+        std::lock_guard<std::mutex> lk(C.tune_mu);
+        auto it = C.tuned.find({w.plan.n_a, w.plan.n_b});
+        return it == C.tuned.end() ? TuneParams() : it->second;
+    };
     while (!todo.empty()) {
         // take a sub-batch that fits this pipeline's share of the budget
         double tot_elems = 0;
@@ -392,8 +540,9 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
             Work& w = work[sl];
             if (w.full_halo != exact_round) { rest.push_back(sl); continue; }
             MatchGeom g;
-            if (!match_geometry(w.plan.n_a, w.plan.n_b, w.plan.window, part_ctas(w.plan.n_a, tot_elems),
-                                part_ctas(w.plan.n_b, tot_elems), &g, !w.full_halo)) { w.status = RFR_E_WINDOW; continue; }
+            const TuneParams tp = params_for(w);
+            if (!match_geometry(w.plan.n_a, w.plan.n_b, w.plan.window, part_ctas(w.plan.n_a, tot_elems, tp.cta_per_sm),
+                                part_ctas(w.plan.n_b, tot_elems, tp.cta_per_sm), &g, !w.full_halo, &tp)) { w.status = RFR_E_WINDOW; continue; }
             if (w.full_halo) { g.hcap = 1ull << g.n_b; g.bytes = match_bytes(g); }
             const size_t need = g.bytes + (size_t)cap * 8 + 6 * 8 + 512;
             if (need > C.budget) { w.status = RFR_E_BUDGET; continue; }
@@ -685,6 +834,9 @@ int rfr_config_default(rfr_config* cfg) {
     cfg->timing = 0;
     cfg->max_candidates = 1ull << 16;
     cfg->eps_override = 0.0;
+    cfg->use_graphs = 1;
+    cfg->autotune = 0;
+    cfg->tune_cache_path = nullptr;
     return RFR_OK;
 }
 
@@ -706,6 +858,13 @@ int rfr_create(const rfr_config* cfg_in, rfr_ctx** out) {
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     C.budget = cfg.mem_budget_bytes ? cfg.mem_budget_bytes : (size_t)(fr * 0.85);
+    {
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, cfg.device) == cudaSuccess) C.device_name = prop.name;
+        if (cfg.tune_cache_path) C.tune_path = cfg.tune_cache_path;
+        C.cfg.tune_cache_path = nullptr;        // the caller's string is not kept
+        tune_cache_load(C);
+    }
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, cfg.device) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;
@@ -759,6 +918,7 @@ int rfr_set_allocator(rfr_ctx* x, rfr_alloc_fn a, rfr_free_fn f, void* user) {
         if (P.h_plans) cudaFreeHost(P.h_plans);
         P.h_coeffs = nullptr; P.h_deg = nullptr; P.h_plans = nullptr;
         P.cap = 0;
+        P.drop_graphs();
     };
     reset(C.sync_pipe);
     for (auto& p : C.worker_pipes) reset(*p);

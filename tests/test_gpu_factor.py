@@ -149,3 +149,16 @@ def test_validate_stage_suspect_then_roots_decide(ctx):
     c, d = coeff_tensor([[1, 0, -10, 0, 1], [2, -3, 0, 1]])
     st = P.stage_validate(c, d).cpu().tolist()
     assert st == [0, 2]                       # (x-1)^2 (x+2): gcd(p, p') = x-1 modulo every prime
+
+
+def test_autotune_and_graphs_do_not_change_results(tmp_path):
+    from paper_2410_15880_b300 import Context
+    recs = golden("cfg2")[:12] + golden("cfg3")[:4]
+    cache = str(tmp_path / "tune.txt")
+    with Context(device=0, autotune=True, tune_cache_path=cache) as c:
+        check_batch(c, recs)
+        check_batch(c, recs)                       # second pass uses the cache and the captured graph
+    lines = open(cache).read().strip().splitlines()
+    assert len(lines) >= 2 and all(len(l.split("\t")[1].split()) == 5 for l in lines)
+    with Context(device=0, use_graphs=False, tune_cache_path=cache) as c:
+        check_batch(c, recs)
