@@ -45,8 +45,8 @@ def parse():
                     help="requests of the serving stream (0 = skip the serving leg)")
     ap.add_argument("--serving-load", type=float, default=0.8,
                     help="Poisson arrival rate as a fraction of the measured closed-loop capacity")
-    ap.add_argument("--root-mode", type=int, default=-1,
-                    help="0 = FP64 Aberth, 1 = FP32 bulk + FP64 (default: 1 for cfg3/cfg5, else 0)")
+    ap.add_argument("--root-mode", type=int, default=1,
+                    help="0 = FP64 Aberth, 1 = FP32 bulk + FP64 (default)")
     return ap.parse_args()
 
 
@@ -257,8 +257,6 @@ def run_reference(a):
 
 def main():
     a = parse()
-    if a.root_mode < 0:
-        a.root_mode = 1 if a.config in ("cfg3", "cfg5") else 0
     if a.impl == "reference":
         return run_reference(a)
     import numpy as np

@@ -128,7 +128,7 @@ typedef void* (*rfr_alloc_fn)(size_t bytes, void* user, void* stream);
 typedef void  (*rfr_free_fn)(void* ptr, size_t bytes, void* user, void* stream);
 
 /* Fill *cfg with defaults: device 0, budget 0 (auto), max_inflight 2,
- * max_batch 64, FP64 roots, timing off, 1<<16 candidates, no override,
+ * max_batch 64, FP32-bulk roots, timing off, 1<<16 candidates, no override,
  * graphs on, autotune off, no tune cache file.
  * Returns RFR_E_INVALID if cfg is NULL. */
 int rfr_config_default(rfr_config* cfg);

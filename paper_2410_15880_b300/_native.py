@@ -153,7 +153,7 @@ class Context:
     """A library context (rfr_create).  Thread-safe; use as a context manager."""
 
     def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_inflight: int = 2,
-                 max_batch: int = 64, root_mode: int = RFR_ROOTS_FP64, timing: bool = False,
+                 max_batch: int = 64, root_mode: int = RFR_ROOTS_FP32_BULK, timing: bool = False,
                  max_candidates: int = 1 << 16, eps_override: float = 0.0, use_graphs: bool = True,
                  autotune: bool = False, tune_cache_path: Optional[str] = None):
         L = lib()

@@ -1,6 +1,9 @@
 // k_roots.cu — K-a: batched root finder (the "black box" of Section 2).
 //
-// One CTA per polynomial, one thread per root (d <= 128).
+// Three kernels: k_aberth (one CTA per polynomial, one thread per root,
+// d <= 128) for steps 1-2; k_polish and k_radius (one warp per 32 roots,
+// spread over the whole GPU, because the double-double work is FP64-bound and
+// independent per root) for steps 3 and 4.
 //  1. Starting points from the Newton polygon of p (upper convex hull of
 //     (k, log|a_k|)): for each hull edge of width m, m points on a circle
 //     whose radius is the edge's geometric-mean root modulus (Bini 1996).
@@ -12,7 +15,7 @@
 //     A root stops moving when its correction is below 4 ulp or |p(z_i)| is
 //     below the rounding-error bound of its evaluation.  In FP32-bulk mode
 //     the same iteration runs in FP32 first and FP64 finishes it.
-//  3. Two Newton steps with p evaluated in double-double arithmetic (the
+//  3. One Newton step with p evaluated in double-double arithmetic (the
 //     correction itself in FP64), so each root is kept as a DD value.
 //  4. Inclusion radius: r_i = d |p(z_i)| / prod_{j != i} |z_i - z_j|, with
 //     |p(z_i)| enlarged by the DD evaluation's error bound.  When the discs
@@ -126,24 +129,23 @@ __device__ cdd eval_dd(const double* a, int d, cdd Z, bool reversed) {
     return P;
 }
 
+// Kernel 1: Aberth iterations, one CTA per polynomial.  Writes the FP64
+// approximations to roots[.., 0] / roots[.., 2] and the convergence status.
 __global__ void __launch_bounds__(DMAX)
-k_roots(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees,
-        int root_mode, double* __restrict__ roots, double* __restrict__ radius,
-        int32_t* __restrict__ status) {
+k_aberth(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees,
+         int root_mode, double* __restrict__ roots, int32_t* __restrict__ status) {
     __shared__ double a[DMAX + 1];
     __shared__ float af[DMAX + 1];
     __shared__ cx<double> z[DMAX];
     __shared__ cx<float> zf[DMAX];
     __shared__ int hull[DMAX + 2];
     __shared__ int nhull, kmin, s_flag;
-    __shared__ double s_maxres;
 
     const int prob = blockIdx.x, i = threadIdx.x;
     const int d = degrees[prob];
     const int64_t* c = coeffs + (size_t)prob * LDC;
     const int pre = status[prob];
     if (pre < 0) return;                       // rejected by the input checks
-    if (i == 0) s_maxres = 0.0;
     if (d < 1 || d > DMAX) {
         if (i == 0) status[prob] = RFR_E_RANGE;
         return;
@@ -196,19 +198,53 @@ k_roots(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees,
     } else {
         conv = aberth<double>(a, d, z, 600, &s_flag);
     }
+    if (i < d) {
+        double* out = roots + ((size_t)prob * DMAX + i) * 4;
+        out[0] = z[i].x; out[1] = 0.0; out[2] = z[i].y; out[3] = 0.0;
+    }
+    if (i == 0) {
+        const bool suspect = pre == RFR_SF_SUSPECT;
+        status[prob] = conv ? (suspect ? RFR_SF_SUSPECT : RFR_OK)
+                            : (suspect ? RFR_E_NOT_SQUAREFREE : RFR_E_NO_CONVERGENCE);
+    }
+}
 
-    // Double-double Newton polish.
-    cdd Z = cdd_make(0.0, 0.0);
-    if (i < d) Z = cdd_make(z[i].x, z[i].y);
-    for (int it = 0; it < 2 && i < d; ++it) {
+// One warp per 32 roots of one polynomial: blockIdx.x = problem * 4 + chunk.
+constexpr int CHUNKS = DMAX / 32;
+struct RootSlot { int prob, d, i, chunk; };
+__device__ __forceinline__ bool root_slot(const int32_t* degrees, const int32_t* status, RootSlot* r) {
+    r->prob = blockIdx.x / CHUNKS;
+    r->chunk = blockIdx.x % CHUNKS;
+    r->d = degrees[r->prob];
+    r->i = r->chunk * 32 + threadIdx.x;
+    const int st = status[r->prob];
+    return (st == RFR_OK || st == RFR_SF_SUSPECT) && r->d >= 1 && r->d <= DMAX;
+}
+
+// Kernel 2: one Newton step per root with p evaluated in double-double (the
+// correction itself in FP64), so each root becomes a DD value.
+__global__ void __launch_bounds__(32)
+k_polish(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees,
+         const int32_t* __restrict__ status, double* __restrict__ roots) {
+    __shared__ double a[DMAX + 1];
+    RootSlot R;
+    if (!root_slot(degrees, status, &R)) return;
+    const int d = R.d, i = R.i;
+    if (R.chunk * 32 >= d) return;
+    const int64_t* c = coeffs + (size_t)R.prob * LDC;
+    for (int k = threadIdx.x; k <= d; k += 32) a[k] = (double)c[k];
+    __syncwarp();
+    if (i >= d) return;
+    double* out = roots + ((size_t)R.prob * DMAX + i) * 4;
+    cdd Z = cdd_make(out[0], out[2]);
+    // one Newton step from the FP64 Aberth root (error ~1e-16 |z|) squares the
+    // error; the inclusion radius computed afterwards certifies what it reached
+    for (int it = 0; it < 1; ++it) {
         cx<double> zh = cxm<double>(Z.re.hi, Z.im.hi);
         bool rev = cabsv(zh) > 1.0;
-        bool noise;
-        cx<double> Nf = newton_ratio<double>(a, d, zh, &noise);   // FP64 fallback for the derivative part
         cx<double> N;
         if (!rev) {
             cdd P = eval_dd(a, d, Z, false);
-            // p'(z) in FP64
             cx<double> p = cxm<double>(a[d], 0), dp = cxm<double>(0, 0);
             for (int k = d - 1; k >= 0; --k) { dp = dp * zh + p; p = p * zh + cxm<double>(a[k], 0); }
             N = cdivv(cxm<double>(P.re.hi, P.im.hi), dp);
@@ -221,62 +257,69 @@ k_roots(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees,
             cx<double> Ph = cxm<double>(P.re.hi, P.im.hi);
             N = cdivv(zh * Ph, cscale(Ph, (double)d) - wh * dP);
         }
-        if (!(cabsv(N) < 1e300)) N = Nf;
+        if (!(cabsv(N) < 1e300)) {                              // degenerate: plain FP64 Newton ratio
+            bool noise;
+            N = newton_ratio<double>(a, d, zh, &noise);
+        }
         Z.re = dd_add_d(Z.re, -N.x);
         Z.im = dd_add_d(Z.im, -N.y);
     }
-    __syncthreads();
-    if (i < d) z[i] = cxm<double>(Z.re.hi, Z.im.hi);
-    __syncthreads();
+    out[0] = Z.re.hi; out[1] = Z.re.lo; out[2] = Z.im.hi; out[3] = Z.im.lo;
+}
 
-    // Inclusion radius.
-    if (i < d) {
-        cx<double> zh = z[i];
-        double az = cabsv(zh);
-        bool rev = az > 1.0;
-        double lp, res;
-        if (!rev) {
-            cdd P = eval_dd(a, d, Z, false);
-            double mag = 0.0;
-            for (int k = d; k >= 0; --k) mag = mag * az + fabs(a[k]);
-            double pv = hypot(P.re.hi, P.im.hi);
-            double err = (double)(2 * d + 8) * 0x1p-100 * mag;
-            lp = log2(pv + err);
-            res = pv / mag;
-        } else {
-            cdd W = cdd_inv(Z);
-            cdd P = eval_dd(a, d, W, true);
-            double aw = 1.0 / az, mag = 0.0;
-            for (int k = 0; k <= d; ++k) mag = mag * aw + fabs(a[k]);
-            double pv = hypot(P.re.hi, P.im.hi);
-            double err = (double)(2 * d + 8) * 0x1p-100 * mag;
-            lp = (double)d * log2(az) + log2(pv + err);
-            res = pv / mag;
-        }
-        // log2 of prod_{j != i} |z_i - z_j| in FP32 (d <= 128 terms, each with
-        // relative error ~1e-7: the sum is within 2e-5 of the exact value,
-        // far inside the 1.01 safety factor below)
-        float lprodf = 0.f;
-        bool coincide = false;
-        for (int j = 0; j < d; ++j) {
-            if (j == i) continue;
-            const float dist = (float)cabsv(zh - z[j]);
-            if (!(dist > 0.f)) coincide = true; else lprodf += log2f(dist);
-        }
-        const double lprod = (double)lprodf;
-        double r = coincide ? INFINITY : exp2(log2((double)d) + lp - lprod) * 1.01 + 0x1p-96 * az;
-        if (d == 1) r = 0x1p-96 * az + 0x1p-100;
-        double* out = roots + ((size_t)prob * DMAX + i) * 4;
-        out[0] = Z.re.hi; out[1] = Z.re.lo; out[2] = Z.im.hi; out[3] = Z.im.lo;
-        radius[(size_t)prob * DMAX + i] = r;
-        atomicMax((unsigned long long*)&s_maxres, __double_as_longlong(res));
+// Kernel 3: inclusion radius r_i = d |p(z_i)| / prod_{j != i} |z_i - z_j| with
+// |p(z_i)| from a double-double evaluation plus its error bound.
+__global__ void __launch_bounds__(32)
+k_radius(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees,
+         const int32_t* __restrict__ status, const double* __restrict__ roots,
+         double* __restrict__ radius) {
+    __shared__ double a[DMAX + 1];
+    __shared__ cx<double> z[DMAX];
+    RootSlot R;
+    if (!root_slot(degrees, status, &R)) return;
+    const int d = R.d, i = R.i;
+    if (R.chunk * 32 >= d) return;
+    const int64_t* c = coeffs + (size_t)R.prob * LDC;
+    const double* Rt = roots + (size_t)R.prob * DMAX * 4;
+    for (int k = threadIdx.x; k <= d; k += 32) a[k] = (double)c[k];
+    for (int k = threadIdx.x; k < d; k += 32) z[k] = cxm<double>(Rt[4 * k], Rt[4 * k + 2]);
+    __syncwarp();
+    if (i >= d) return;
+    const cdd Z = {{Rt[4 * i], Rt[4 * i + 1]}, {Rt[4 * i + 2], Rt[4 * i + 3]}};
+    const cx<double> zh = z[i];
+    const double az = cabsv(zh);
+    const bool rev = az > 1.0;
+    double lp;
+    if (!rev) {
+        cdd P = eval_dd(a, d, Z, false);
+        double mag = 0.0;
+        for (int k = d; k >= 0; --k) mag = mag * az + fabs(a[k]);
+        double pv = hypot(P.re.hi, P.im.hi);
+        double err = (double)(2 * d + 8) * 0x1p-100 * mag;
+        lp = log2(pv + err);
+    } else {
+        cdd W = cdd_inv(Z);
+        cdd P = eval_dd(a, d, W, true);
+        double aw = 1.0 / az, mag = 0.0;
+        for (int k = 0; k <= d; ++k) mag = mag * aw + fabs(a[k]);
+        double pv = hypot(P.re.hi, P.im.hi);
+        double err = (double)(2 * d + 8) * 0x1p-100 * mag;
+        lp = (double)d * log2(az) + log2(pv + err);
     }
-    __syncthreads();
-    if (i == 0) {
-        const bool suspect = pre == RFR_SF_SUSPECT;
-        status[prob] = conv ? (suspect ? RFR_SF_SUSPECT : RFR_OK)
-                            : (suspect ? RFR_E_NOT_SQUAREFREE : RFR_E_NO_CONVERGENCE);
+    // log2 of prod_{j != i} |z_i - z_j| in FP32 (d <= 128 terms, each with
+    // relative error ~1e-7: the sum is within 2e-5 of the exact value,
+    // far inside the 1.01 safety factor below)
+    float lprodf = 0.f;
+    bool coincide = false;
+    for (int j = 0; j < d; ++j) {
+        if (j == i) continue;
+        const float dist = (float)cabsv(zh - z[j]);
+        if (!(dist > 0.f)) coincide = true; else lprodf += log2f(dist);
     }
+    const double lprod = (double)lprodf;
+    double r = coincide ? INFINITY : exp2(log2((double)d) + lp - lprod) * 1.01 + 0x1p-96 * az;
+    if (d == 1) r = 0x1p-96 * az + 0x1p-100;
+    radius[(size_t)R.prob * DMAX + i] = r;
 }
 
 }  // namespace rfr
@@ -288,6 +331,9 @@ extern "C" int rfr_stage_roots(const int64_t* coeffs, const int32_t* degrees, in
                                int32_t* status, void* stream) {
     if (batch < 0 || !coeffs || !degrees || !roots || !radius || !status) return RFR_E_INVALID;
     if (batch == 0) return RFR_OK;
-    k_roots<<<batch, DMAX, 0, (cudaStream_t)stream>>>(coeffs, degrees, root_mode, roots, radius, status);
+    cudaStream_t s = (cudaStream_t)stream;
+    k_aberth<<<batch, DMAX, 0, s>>>(coeffs, degrees, root_mode, roots, status);
+    k_polish<<<batch * CHUNKS, 32, 0, s>>>(coeffs, degrees, status, roots);
+    k_radius<<<batch * CHUNKS, 32, 0, s>>>(coeffs, degrees, status, roots, radius);
     return cudaGetLastError() == cudaSuccess ? RFR_OK : RFR_E_CUDA;
 }

@@ -25,14 +25,14 @@
 namespace rfr {
 
 __global__ void __launch_bounds__(DMAX)
-k_weights(const int32_t* __restrict__ degrees, const double* __restrict__ roots,
+k_weights(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees, const double* __restrict__ roots,
           const double* __restrict__ radius, const int32_t* __restrict__ root_status,
           double eps_override, rfr_plan* __restrict__ plans) {
     __shared__ double zx[DMAX], zy[DMAX], rr[DMAX];
     __shared__ int cls[DMAX];        // 0 real, 1 upper, 2 lower
     __shared__ int partner[DMAX], taken[DMAX];
     __shared__ int s_err, s_r, s_c;
-    __shared__ double s_e1, s_e2, s_maxr;
+    __shared__ double s_e1, s_e2, s_maxr, s_res;
     const int prob = blockIdx.x, i = threadIdx.x;
     const int d = degrees[prob];
     rfr_plan* P = plans + prob;
@@ -55,7 +55,35 @@ k_weights(const int32_t* __restrict__ degrees, const double* __restrict__ roots,
         taken[i] = 0;
         partner[i] = -1;
     }
-    if (i == 0) { s_err = 0; s_r = 0; s_c = 0; s_e1 = 0.0; s_e2 = 0.0; s_maxr = 0.0; }
+    if (i == 0) { s_err = 0; s_r = 0; s_c = 0; s_e1 = 0.0; s_e2 = 0.0; s_maxr = 0.0; s_res = 0.0; }
+    __syncthreads();
+    if (i < d) {
+        // FP64 relative residual |p(z)| / sum |a_k| |z|^k of the root's FP64 part
+        // (reversed polynomial at 1/z when |z| > 1, where the ratio is the same)
+        const int64_t* c = coeffs + (size_t)prob * LDC;
+        const double az = hypot(zx[i], zy[i]);
+        double pr, pi, mag;
+        if (az <= 1.0) {
+            pr = (double)c[d]; pi = 0.0; mag = fabs(pr);
+            for (int k = d - 1; k >= 0; --k) {
+                const double t = pr * zx[i] - pi * zy[i] + (double)c[k];
+                pi = pr * zy[i] + pi * zx[i];
+                pr = t;
+                mag = mag * az + fabs((double)c[k]);
+            }
+        } else {
+            const double wx = zx[i] / (az * az), wy = -zy[i] / (az * az), aw = 1.0 / az;
+            pr = (double)c[0]; pi = 0.0; mag = fabs(pr);
+            for (int k = 1; k <= d; ++k) {
+                const double t = pr * wx - pi * wy + (double)c[k];
+                pi = pr * wy + pi * wx;
+                pr = t;
+                mag = mag * aw + fabs((double)c[k]);
+            }
+        }
+        const double res = hypot(pr, pi) / mag;
+        atomicMax((unsigned long long*)&s_res, __double_as_longlong(isfinite(res) ? res : 1e308));
+    }
     __syncthreads();
 
     if (i < d) {
@@ -161,6 +189,7 @@ k_weights(const int32_t* __restrict__ degrees, const double* __restrict__ roots,
         P->window = W;
         P->window2 = W2;
         P->max_radius = s_maxr;
+        P->max_rel_residual = s_res;
         P->sum_err1 = s_e1;
         P->sum_err2 = s_e2;
     }
@@ -174,9 +203,8 @@ extern "C" int rfr_stage_weights(const int64_t* coeffs, const int32_t* degrees, 
                                  const double* roots, const double* radius,
                                  const int32_t* root_status, double eps_override,
                                  rfr_plan* plans, void* stream) {
-    (void)coeffs;
-    if (batch < 0 || !degrees || !roots || !radius || !root_status || !plans) return RFR_E_INVALID;
+    if (batch < 0 || !coeffs || !degrees || !roots || !radius || !root_status || !plans) return RFR_E_INVALID;
     if (batch == 0) return RFR_OK;
-    k_weights<<<batch, DMAX, 0, (cudaStream_t)stream>>>(degrees, roots, radius, root_status, eps_override, plans);
+    k_weights<<<batch, DMAX, 0, (cudaStream_t)stream>>>(coeffs, degrees, roots, radius, root_status, eps_override, plans);
     return cudaGetLastError() == cudaSuccess ? RFR_OK : RFR_E_CUDA;
 }

@@ -293,43 +293,57 @@ int Pipeline::issue_prologue(int B, const int64_t* d_co, const int32_t* d_dg, bo
     return rc;
 }
 
-// Time one problem's match with layout knobs tp (one warm-up and one timed
-// run); returns milliseconds, or a negative value if the layout does not fit.
+// Time one problem's match with layout knobs tp: the problem is matched as
+// `copies` identical problems in one launch sequence, so that the CTA counts
+// and the concurrency resemble a real sub-batch; one warm-up, one timed run.
+// Returns milliseconds per problem, or a negative value if it does not fit.
 static double time_layout(Ctx& C, cudaStream_t s, const rfr_plan& plan, const rfr_plan* dplan,
                           const TuneParams& tp, cudaEvent_t e0, cudaEvent_t e1) {
-    MatchGeom g;
     const double elems = std::ldexp(1.0, plan.n_a) + std::ldexp(1.0, plan.n_b);
-    auto ctas = [&](int h) {
-        double want = std::ldexp(1.0, h) * tp.cta_per_sm * 148.0 / elems;
-        int c = 1;
-        while (c * 2 <= want && c < 512) c *= 2;
-        return c;
-    };
-    if (!match_geometry(plan.n_a, plan.n_b, plan.window, ctas(plan.n_a), ctas(plan.n_b), &g, true, &tp)) return -1.0;
-    const size_t bytes = g.bytes + 4096 + 256 + 2048;
-    if (bytes > C.budget / 2) return -1.0;
+    MatchGeom g;
+    int copies = 8;
+    for (; copies >= 1; copies /= 2) {
+        auto ctas = [&](int h) {
+            double want = std::ldexp(1.0, h) * tp.cta_per_sm * 148.0 / (elems * copies);
+            int c = 1;
+            while (c * 2 <= want && c < 512) c *= 2;
+            return c;
+        };
+        if (!match_geometry(plan.n_a, plan.n_b, plan.window, ctas(plan.n_a), ctas(plan.n_b), &g, true, &tp)) return -1.0;
+        if ((g.bytes + 4096) * (size_t)copies + 4096 <= C.budget / 2) break;
+    }
+    if (copies < 1) return -1.0;
+    const size_t per = ((g.bytes + 255) & ~(size_t)255) + 4096;
+    const size_t head = (((size_t)copies * sizeof(ProbJob) + 255) & ~(size_t)255) + (((size_t)2 * copies * sizeof(HalfJob) + 255) & ~(size_t)255);
+    const size_t bytes = head + per * copies;
     char* ws = (char*)C.alloc.get(bytes, s);
     if (!ws) return -1.0;
     double best = -1.0;
+    std::vector<ProbJob> jobs(copies);
+    std::vector<HalfJob> halves(2 * copies);
+    ProbJob* d_jobs = (ProbJob*)ws;
+    HalfJob* d_halves = (HalfJob*)(ws + (((size_t)copies * sizeof(ProbJob) + 255) & ~(size_t)255));
     for (int rep = 0; rep < 2; ++rep) {
-        ProbJob pj;
-        memset(&pj, 0, sizeof(pj));
-        match_layout(g, ws + 2048, &pj);
-        uint64_t* ctr = (uint64_t*)(ws + 2048 + g.bytes);
-        uint64_t* cand = ctr + 32;
-        pj.A.w = dplan->w; pj.B.w = dplan->w + plan.n_a;
-        pj.w_a = dplan->w; pj.w2_a = dplan->w2; pj.w_b = dplan->w + plan.n_a; pj.w2_b = dplan->w2 + plan.n_a;
-        pj.W = plan.window; pj.W2 = plan.window2;
-        pj.cand = cand; pj.cap = 256; pj.ctr = (unsigned long long*)ctr;
-        pj.A.err = pj.B.err = (int*)(ctr + 4);
-        cudaMemsetAsync(ctr, 0, 64, s);
-        cudaMemsetAsync(pj.A.bcount, 0, 3 * (((((size_t)1 << g.d1) * 4) + 255) & ~(size_t)255), s);
-        HalfJob halves[2];
+        for (int c = 0; c < copies; ++c) {
+            char* base = ws + head + per * c;
+            ProbJob& pj = jobs[c];
+            memset(&pj, 0, sizeof(pj));
+            match_layout(g, base, &pj);
+            uint64_t* ctr = (uint64_t*)(base + ((g.bytes + 255) & ~(size_t)255));
+            uint64_t* cand = ctr + 32;
+            pj.A.w = dplan->w; pj.B.w = dplan->w + plan.n_a;
+            pj.w_a = dplan->w; pj.w2_a = dplan->w2; pj.w_b = dplan->w + plan.n_a; pj.w2_b = dplan->w2 + plan.n_a;
+            pj.W = plan.window; pj.W2 = plan.window2;
+            pj.cand = cand; pj.cap = 256; pj.ctr = (unsigned long long*)ctr;
+            pj.A.err = pj.B.err = (int*)(ctr + 4);
+            cudaMemsetAsync(ctr, 0, 64, s);
+            cudaMemsetAsync(pj.A.bcount, 0, 3 * (((((size_t)1 << g.d1) * 4) + 255) & ~(size_t)255), s);
+        }
         cudaEventRecord(e0, s);
-        if (run_match(&pj, 1, (ProbJob*)ws, (HalfJob*)(ws + 1024), halves, s, nullptr, nullptr) != cudaSuccess) break;
+        if (run_match(jobs.data(), copies, d_jobs, d_halves, halves.data(), s, nullptr, nullptr) != cudaSuccess) break;
         cudaEventRecord(e1, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) break;
-        best = ms_between(e0, e1);
+        best = ms_between(e0, e1) / copies;
     }
     C.alloc.put(ws, bytes, s);
     cudaGetLastError();
@@ -830,7 +844,7 @@ int rfr_config_default(rfr_config* cfg) {
     cfg->mem_budget_bytes = 0;
     cfg->max_inflight = 2;
     cfg->max_batch = 64;
-    cfg->root_mode = RFR_ROOTS_FP64;
+    cfg->root_mode = RFR_ROOTS_FP32_BULK;
     cfg->timing = 0;
     cfg->max_candidates = 1ull << 16;
     cfg->eps_override = 0.0;

@@ -41,7 +41,7 @@ def test_host_only_calls(L):
     assert L.rfr_strerror(12345) == b"unknown status"
     cfg = N.Config()
     assert L.rfr_config_default(ctypes.byref(cfg)) == 0
-    assert cfg.max_inflight == 2 and cfg.max_candidates == 1 << 16 and cfg.root_mode == 0
+    assert cfg.max_inflight == 2 and cfg.max_candidates == 1 << 16 and cfg.root_mode == 1
     assert cfg.use_graphs == 1 and cfg.autotune == 0 and not cfg.tune_cache_path
     assert L.rfr_config_default(None) == -1
     assert L.rfr_destroy(None) == 0

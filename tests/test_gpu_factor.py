@@ -24,6 +24,8 @@ def check_batch(ctx, recs):
     for r, x in zip(recs, res):
         if "n" in r and r["n"] > 1:
             assert x.diag["n"] == r["n"] and x.diag["r"] == r["r"], r["name"]
+        if len(r["coeffs"]) > 2:
+            assert 0.0 < x.diag["max_rel_residual"] <= 1e-10, (r["name"], x.diag["max_rel_residual"])
     return res
 
 
@@ -52,10 +54,10 @@ def test_degree100_batch(ctx):
     assert all(x.diag["half_sums"] > (1 << 24) for x in res)
 
 
-def test_degree100_batch_fp32_bulk_roots():
-    from paper_2410_15880_b300 import Context, RFR_ROOTS_FP32_BULK
-    with Context(device=0, root_mode=RFR_ROOTS_FP32_BULK) as c:
-        res = check_batch(c, golden("cfg3")[:16])
+def test_degree100_batch_fp64_roots():
+    from paper_2410_15880_b300 import Context, RFR_ROOTS_FP64
+    with Context(device=0, root_mode=RFR_ROOTS_FP64) as c:
+        res = check_batch(c, golden("cfg3")[:16] + golden("cfg2")[:8])
     assert all(x.diag["max_root_err"] < 1e-20 for x in res)
 
 
