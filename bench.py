@@ -47,6 +47,8 @@ def parse():
                     help="Poisson arrival rate as a fraction of the measured closed-loop capacity")
     ap.add_argument("--root-mode", type=int, default=1,
                     help="0 = FP64 Aberth, 1 = FP32 bulk + FP64 (default)")
+    ap.add_argument("--no-autotune", action="store_true", help="use the default match layout")
+    ap.add_argument("--tune-cache", default="", help="file that stores tuned match layouts")
     return ap.parse_args()
 
 
@@ -282,7 +284,8 @@ def main():
         if world > 1:
             dist.barrier()
 
-    with Context(device=local, timing=True, root_mode=a.root_mode, autotune=True) as ctx:
+    with Context(device=local, timing=True, root_mode=a.root_mode, autotune=not a.no_autotune,
+                 tune_cache_path=a.tune_cache) as ctx:
         for _ in range(a.warmup):
             res = ctx.factor_batch_device(d_co, d_dg)
         # ---- timed region: device-resident inputs
@@ -359,7 +362,7 @@ def main():
         "config": {"workload": WORKLOAD_NAME[a.config], "polys_per_step": B,
                    "half_sums_per_step": half_sums, "parallelism": f"replicas x{world}",
                    "l2": "tables larger than L2 (no flush needed)", "root_mode": a.root_mode,
-                   "autotune": "layouts tuned per (n_a, n_b) during warm-up"},
+                   "autotune": ("off" if a.no_autotune else "layouts tuned per (n_a, n_b) during warm-up")},
         "half_sums_per_s": half_sums * world * a.steps / (ms / 1e3),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,

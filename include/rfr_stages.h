@@ -134,6 +134,22 @@ int rfr_stage_match_exact(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
                           uint64_t* cand, uint64_t cap, uint64_t* counters,
                           void* stream);
 
+/* As rfr_stage_match, always with the fused match that keeps no key tables
+ * in device memory: sorted lists of the halves' low-subset sums are built
+ * by merging, and each CTA generates a range of half a's keys into a
+ * shared-memory table and looks half b's keys of that range up in it.
+ * rfr_stage_match uses it by itself for n_a >= 18.  Returns RFR_E_WINDOW if
+ * a half has more than 31 elements or the window is too wide for it (about
+ * W >= 2^(59 - max(n_a - 13, 2))); counters[4] = 1 when one key range holds
+ * more than 16384 keys of half a (clustered keys: use
+ * rfr_stage_match_exact).  Section 3.3. */
+int rfr_stage_match_fused(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
+                          const uint64_t* w_b, const uint64_t* w2_b, int n_b,
+                          uint64_t window, uint64_t window2,
+                          void* workspace, size_t workspace_bytes,
+                          uint64_t* cand, uint64_t cap, uint64_t* counters,
+                          void* stream);
+
 /* Match without any allocation (the paper has no counterpart; this is a
  * service for callers that cannot allocate device memory, e.g. inside a host
  * framework that owns all device memory, or a loop where a cudaMalloc that

@@ -98,3 +98,48 @@ def band_pairs(alpha_vals, beta_vals, M: int, window: int):
     reported, not only the first per i."""
     return {(i, j) for i, a in enumerate(alpha_vals) for j, b in enumerate(beta_vals)
             if accept((a + b) % M, M, window)}
+
+
+def _signed64(x: int) -> int:
+    x %= 1 << 64
+    return x - (1 << 64) if x >= (1 << 63) else x
+
+
+def expand_values_u64(w):
+    """EXPAND (Section 3.3) before its sort, modulo 2^64, as a uint64 array in
+    pattern order: entry s is the sum of w[i] over the set bits i of s.
+    (Sums are formed on the int64 view: two's-complement addition is
+    addition modulo 2^64.)"""
+    vals = np.zeros(1, dtype=np.int64)
+    for x in w:
+        vals = np.concatenate([vals, vals + _signed64(int(x))])
+    return vals.view(np.uint64)
+
+
+def band_pairs_sorted(w_a, w_b, window: int):
+    """The pair set of band_pairs for M = 2^64 and halves too large to pair
+    by brute force: every (i, j) whose value alpha_i + beta_j (sums of the
+    half-a weights over the bits of i and of the half-b weights over the bits
+    of j) is accepted.  The meet in the middle of Section 3.3 written with a
+    library sort: beta is sorted once and, for every alpha_i, the betas in
+    the circular window [-alpha_i - window, -alpha_i + window] are found by
+    binary search."""
+    alpha = expand_values_u64(w_a)
+    beta = expand_values_u64(w_b)
+    if window >= (1 << 63):
+        return {(i, j) for i in range(len(alpha)) for j in range(len(beta))}
+    order = np.argsort(beta, kind="stable")
+    sb = beta[order]
+    neg = -alpha.view(np.int64)                           # -alpha_i modulo 2^64
+    lo = (neg - _signed64(window)).view(np.uint64)
+    hi = (neg + _signed64(window)).view(np.uint64)
+    out = set()
+    wrap = lo > hi                                        # the window runs over 2^64 -> 0
+    a0 = np.searchsorted(sb, lo, side="left")
+    a1 = np.searchsorted(sb, hi, side="right")
+    for i in np.nonzero(~wrap & (a1 > a0))[0]:
+        out.update((int(i), int(j)) for j in order[a0[i]:a1[i]])
+    for i in np.nonzero(wrap)[0]:                         # [lo, 2^64) and [0, hi]
+        out.update((int(i), int(j)) for j in order[:a1[i]])
+        out.update((int(i), int(j)) for j in order[a0[i]:])
+    return out

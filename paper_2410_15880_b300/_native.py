@@ -106,6 +106,7 @@ def lib():
         "rfr_stage_match": (i32, [vp, vp, i32, vp, vp, i32, u64, u64, vp, C.c_size_t, vp, u64, vp, vp]),
         "rfr_stage_match_noalloc": (i32, [vp, vp, i32, vp, vp, i32, u64, u64, vp, u64, vp, vp]),
         "rfr_stage_match_exact": (i32, [vp, vp, i32, vp, vp, i32, u64, u64, vp, C.c_size_t, vp, u64, vp, vp]),
+        "rfr_stage_match_fused": (i32, [vp, vp, i32, vp, vp, i32, u64, u64, vp, C.c_size_t, vp, u64, vp, vp]),
         "rfr_stage_verify": (i32, [vp, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -325,10 +326,12 @@ def match_workspace_bytes(n_a: int, n_b: int) -> int:
     return int(lib().rfr_stage_match_workspace(n_a, n_b))
 
 
-def stage_match(w_a, w2_a, w_b, w2_b, window: int, window2: int, cap: int, exact: bool = False):
+def stage_match(w_a, w2_a, w_b, w2_b, window: int, window2: int, cap: int, exact: bool = False,
+                fused: bool = False):
     """Weights as int64 cuda tensors (uint64 bits).  Returns (cand int64 [cap],
     counters int64 [6], workspace).  exact=True uses rfr_stage_match_exact
-    (count-pass layout) instead of the slack-region layout."""
+    (tables with the count-pass layout); fused=True uses rfr_stage_match_fused
+    (no tables, any size it fits); otherwise rfr_stage_match chooses."""
     import torch
     n_a, n_b = int(w_a.numel()), int(w_b.numel())
     dev = w_b.device
@@ -338,7 +341,8 @@ def stage_match(w_a, w2_a, w_b, w2_b, window: int, window2: int, cap: int, exact
     aligned = (base + 255) & ~255
     cand = torch.zeros((max(cap, 1),), dtype=torch.int64, device=dev)
     ctr = torch.zeros((6,), dtype=torch.int64, device=dev)
-    fn = lib().rfr_stage_match_exact if exact else lib().rfr_stage_match
+    fn = (lib().rfr_stage_match_exact if exact else
+          lib().rfr_stage_match_fused if fused else lib().rfr_stage_match)
     _check(fn(_ptr(w_a) if n_a else None, _ptr(w2_a) if n_a else None, n_a,
                                  _ptr(w_b) if n_b else None, _ptr(w2_b) if n_b else None, n_b,
                                  int(window), int(window2), C.c_void_p(aligned), ws_bytes,

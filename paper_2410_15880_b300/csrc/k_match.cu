@@ -36,6 +36,7 @@
 #include "rfr_device.cuh"
 #include "k_match.cuh"
 #include <cstring>
+#include <vector>
 
 namespace rfr {
 
@@ -843,6 +844,7 @@ static uint64_t default_halo_cap(int n_b, int d1, uint64_t wc) {
 }
 
 size_t match_bytes(const MatchGeom& g) {
+    if (g.fused) return mitm_half_bytes(g.l_a) + mitm_half_bytes(g.l_b);
     const size_t NB = (size_t)1 << g.d1;
     size_t b = 0;
     b += 2 * align256(((size_t)1 << g.l_a) * 8);
@@ -876,8 +878,14 @@ static int clamp_ctas(int h, int l, int want) {
 }
 
 bool match_geometry(int n_a, int n_b, uint64_t W, int ctas_a, int ctas_b, MatchGeom* g, bool optimistic,
-                    const TuneParams* tp) {
+                    const TuneParams* tp, int fuse) {
     if (n_a < 0 || n_b < n_a || n_b > 32) return false;
+    if (optimistic && (fuse == FUSE_ALWAYS || (fuse == FUSE_AUTO && n_a >= FUSED_MIN_NA))) {
+        if (mitm_geometry(n_a, n_b, W, g)) return true;
+        if (fuse == FUSE_ALWAYS) return false;
+    }
+    g->fused = false;
+    g->nbl = g->slab = g->wf = 0;
     const TuneParams dflt;
     if (!tp) tp = &dflt;
     const int lm = tp->l_max < 10 ? 10 : (tp->l_max > 18 ? 18 : tp->l_max);
@@ -918,6 +926,25 @@ void match_layout(const MatchGeom& g, char* ws, ProbJob* pj) {
     auto take = [&](size_t bytes) { char* q = p; p += align256(bytes); return q; };
     HalfJob& A = pj->A;
     HalfJob& B = pj->B;
+    pj->fused = g.fused ? 1 : 0;
+    pj->nbl = g.nbl; pj->slab = g.slab; pj->wf = g.wf;
+    A.kb1 = B.kb1 = nullptr; A.mb0 = A.mb1 = B.mb0 = B.mb1 = nullptr;
+    if (g.fused) {
+        mitm_layout_half(g.l_a, p, &A);
+        mitm_layout_half(g.l_b, p, &B);
+        A.l = g.l_a; B.l = g.l_b;
+        A.h = g.n_a; B.h = g.n_b;
+        A.neg = 0; B.neg = 1;
+        A.d1 = B.d1 = g.d1;
+        A.ctas = B.ctas = 0;
+        A.wc = B.wc = g.wc;
+        pj->n_a = g.n_a; pj->n_b = g.n_b; pj->d1 = g.d1; pj->Wc = g.wc;
+        A.hist = B.hist = nullptr; A.bstart = B.bstart = nullptr; A.tab = B.tab = nullptr;
+        A.halo_cnt = B.halo_cnt = nullptr; A.halo_cur = B.halo_cur = nullptr; A.halo = B.halo = nullptr;
+        A.halo_cap = B.halo_cap = 0; A.opt_cap = B.opt_cap = 0; A.opt_hcap = B.opt_hcap = 0;
+        A.bcount = B.bcount = nullptr; A.hcount = B.hcount = nullptr;
+        return;
+    }
     A.ylist = (uint64_t*)take(((size_t)1 << g.l_a) * 8);
     A.ytmp = (uint64_t*)take(((size_t)1 << g.l_a) * 8);
     B.ylist = (uint64_t*)take(((size_t)1 << g.l_b) * 8);
@@ -993,7 +1020,8 @@ static const size_t JOIN_SMEM = (size_t)JOIN_CAP * 8 + ((size_t)1 << SUB_BITS) *
 // Upload jobs (from host memory that stays valid until the copies finish:
 // pageable memory is staged before cudaMemcpyAsync returns) and launch.
 cudaError_t run_match(ProbJob* jobs, int np, ProbJob* dev_jobs, HalfJob* dev_halves,
-                      HalfJob* host_halves, cudaStream_t s, cudaEvent_t ev_count, cudaEvent_t ev_scatter) {
+                      HalfJob* host_halves, cudaStream_t s, cudaEvent_t ev_count, cudaEvent_t ev_scatter,
+                      int* launches) {
     if (!g_attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_join, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)JOIN_SMEM);
         if (e == cudaSuccess)
@@ -1003,26 +1031,51 @@ cudaError_t run_match(ProbJob* jobs, int np, ProbJob* dev_jobs, HalfJob* dev_hal
         if (e != cudaSuccess) return e;
         g_attr_set = true;
     }
-    MatchGrid g = assign_bases(jobs, np, host_halves);
-    cudaError_t e;
-    e = cudaMemcpyAsync(dev_halves, host_halves, sizeof(HalfJob) * 2 * np, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(dev_jobs, jobs, sizeof(ProbJob) * np, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return e;
-    size_t psmem = (size_t)(RANGE_MAX + 2 * MAX_RUNS_PER_CTA) * 4;
-    if ((size_t)g.nb_small * 4 > psmem) psmem = (size_t)g.nb_small * 4;
-    if (psmem > (size_t)RUNS_SMEM_MAX) return cudaErrorInvalidConfiguration;
-    k_ysort<<<2 * np, YSORT_THREADS, 0, s>>>(dev_halves, 2 * np);
-    if (!jobs[0].A.opt_cap) {
-        k_runs<false><<<g.part_ctas, PART_THREADS, psmem, s>>>(dev_halves, 2 * np);
-        k_colscan<<<g.scan_ctas, 256, 0, s>>>(dev_halves, 2 * np);
-        k_bscan<<<2 * np, 1024, 0, s>>>(dev_halves, 2 * np);
+    // table problems first (compacted to the front of a copy), fused ones after
+    std::vector<ProbJob> T;
+    std::vector<const ProbJob*> F;
+    for (int i = 0; i < np; ++i) {
+        if (jobs[i].fused) F.push_back(&jobs[i]);
+        else T.push_back(jobs[i]);
     }
-    if (ev_count) cudaEventRecord(ev_count, s);
-    k_runs<true><<<g.part_ctas, PART_THREADS, psmem, s>>>(dev_halves, 2 * np);
-    if (ev_scatter) cudaEventRecord(ev_scatter, s);
-    k_join<<<g.join_ctas, JOIN_THREADS, JOIN_SMEM, s>>>(dev_jobs, np);
-    return cudaGetLastError();
+    const int nT = (int)T.size(), nF = (int)F.size();
+    int nl = 0;
+    cudaError_t e = cudaSuccess;
+    if (nT) {
+        MatchGrid g = assign_bases(T.data(), nT, host_halves);
+        e = cudaMemcpyAsync(dev_halves, host_halves, sizeof(HalfJob) * 2 * nT, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(dev_jobs, T.data(), sizeof(ProbJob) * nT, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+        size_t psmem = (size_t)(RANGE_MAX + 2 * MAX_RUNS_PER_CTA) * 4;
+        if ((size_t)g.nb_small * 4 > psmem) psmem = (size_t)g.nb_small * 4;
+        if (psmem > (size_t)RUNS_SMEM_MAX) return cudaErrorInvalidConfiguration;
+        k_ysort<<<2 * nT, YSORT_THREADS, 0, s>>>(dev_halves, 2 * nT);
+        ++nl;
+        if (!T[0].A.opt_cap) {
+            k_runs<false><<<g.part_ctas, PART_THREADS, psmem, s>>>(dev_halves, 2 * nT);
+            k_colscan<<<g.scan_ctas, 256, 0, s>>>(dev_halves, 2 * nT);
+            k_bscan<<<2 * nT, 1024, 0, s>>>(dev_halves, 2 * nT);
+            nl += 3;
+        }
+        if (ev_count) cudaEventRecord(ev_count, s);
+        k_runs<true><<<g.part_ctas, PART_THREADS, psmem, s>>>(dev_halves, 2 * nT);
+        if (ev_scatter) cudaEventRecord(ev_scatter, s);
+        k_join<<<g.join_ctas, JOIN_THREADS, JOIN_SMEM, s>>>(dev_jobs, nT);
+        nl += 2;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (nF) {
+        e = run_mitm(F.data(), nF, dev_jobs + nT, dev_halves + 2 * nT, s, nT ? nullptr : ev_count);
+        if (!nT && ev_scatter) cudaEventRecord(ev_scatter, s);
+        nl += mitm_launches(F.data(), nF);
+    } else if (!nT) {
+        if (ev_count) cudaEventRecord(ev_count, s);
+        if (ev_scatter) cudaEventRecord(ev_scatter, s);
+    }
+    if (launches) *launches = nl;
+    return e;
 }
 
 }  // namespace rfr
@@ -1052,17 +1105,18 @@ static int stage_ctas(int h) {
 
 // Stage workspace: job structs, then one problem's buffers with a halo large
 // enough for every record of table b (so no window can overflow it).
-static bool stage_geom(int n_a, int n_b, uint64_t W, MatchGeom* g, bool optimistic) {
-    if (!match_geometry(n_a, n_b, W, stage_ctas(n_a), stage_ctas(n_b), g, optimistic)) return false;
+static bool stage_geom(int n_a, int n_b, uint64_t W, MatchGeom* g, bool optimistic, int fuse = FUSE_AUTO) {
+    if (!match_geometry(n_a, n_b, W, stage_ctas(n_a), stage_ctas(n_b), g, optimistic, nullptr, fuse)) return false;
     g->hcap = 1ull << n_b;
     g->bytes = match_bytes(*g);
     return true;
 }
 
 extern "C" size_t rfr_stage_match_workspace(int n_a, int n_b) {
-    MatchGeom g, go;
+    MatchGeom g, go, gf;
     if (!stage_geom(n_a, n_b, 0, &g, false)) return 0;
     if (stage_geom(n_a, n_b, 0, &go, true) && go.bytes > g.bytes) g.bytes = go.bytes;
+    if (stage_geom(n_a, n_b, 0, &gf, true, FUSE_ALWAYS) && gf.bytes > g.bytes) g.bytes = gf.bytes;
     // the bucket count only shrinks for wider windows; budget for d1 = MAX_D1 histograms
     const size_t hist_extra = ((size_t)stage_ctas(n_a) + stage_ctas(n_b)) * ((size_t)1 << MAX_D1) * 4 + 8 * 4096;
     return g.bytes + hist_extra + 2048;
@@ -1072,11 +1126,12 @@ static int stage_match(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
                        const uint64_t* w_b, const uint64_t* w2_b, int n_b,
                        uint64_t window, uint64_t window2,
                        void* workspace, size_t workspace_bytes,
-                       uint64_t* cand, uint64_t cap, uint64_t* counters, void* stream, bool optimistic) {
+                       uint64_t* cand, uint64_t cap, uint64_t* counters, void* stream, bool optimistic,
+                       int fuse = FUSE_AUTO) {
     if (n_a < 0 || n_b < n_a || n_b > 32 || !workspace || !counters || (!cand && cap)) return RFR_E_INVALID;
     if ((n_a && (!w_a || !w2_a)) || (n_b && (!w_b || !w2_b))) return RFR_E_INVALID;
     if (((uintptr_t)workspace) & 255) return RFR_E_INVALID;
-    if (n_b <= SMALL_MAX_H) {
+    if (n_b <= SMALL_MAX_H && fuse != FUSE_ALWAYS) {
         if (window >= (1ull << 62)) return RFR_E_WINDOW;
         SmallJob sj;
         sj.w_a = w_a; sj.w2_a = w2_a; sj.w_b = w_b; sj.w2_b = w2_b;
@@ -1087,7 +1142,7 @@ static int stage_match(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
         return run_small(&sj, 1, (SmallJob*)workspace, s) == cudaSuccess ? RFR_OK : RFR_E_CUDA;
     }
     MatchGeom g;
-    if (!stage_geom(n_a, n_b, window, &g, optimistic)) return RFR_E_WINDOW;
+    if (!stage_geom(n_a, n_b, window, &g, optimistic, fuse)) return RFR_E_WINDOW;
     if (g.bytes + 2048 > workspace_bytes) return RFR_E_INVALID;
     char* base = (char*)workspace;
     ProbJob* dev_job = (ProbJob*)base;
@@ -1103,7 +1158,8 @@ static int stage_match(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
     pj.ctr = (unsigned long long*)counters;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(counters, 0, 6 * sizeof(uint64_t), s) != cudaSuccess) return RFR_E_CUDA;
-    if (cudaMemsetAsync(g.optimistic ? (void*)pj.A.bcount : (void*)pj.B.halo_cnt, 0,
+    if (!g.fused &&
+        cudaMemsetAsync(g.optimistic ? (void*)pj.A.bcount : (void*)pj.B.halo_cnt, 0,
                         (g.optimistic ? 3 * (((((size_t)1 << g.d1) * 4) + 255) & ~(size_t)255)
                                       : (((size_t)1 << g.d1) + 1) * 4), s) != cudaSuccess) return RFR_E_CUDA;
     HalfJob halves[2];
@@ -1127,4 +1183,13 @@ extern "C" int rfr_stage_match_exact(const uint64_t* w_a, const uint64_t* w2_a, 
                                      uint64_t* cand, uint64_t cap, uint64_t* counters, void* stream) {
     return stage_match(w_a, w2_a, n_a, w_b, w2_b, n_b, window, window2, workspace, workspace_bytes,
                        cand, cap, counters, stream, false);
+}
+
+extern "C" int rfr_stage_match_fused(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
+                                     const uint64_t* w_b, const uint64_t* w2_b, int n_b,
+                                     uint64_t window, uint64_t window2,
+                                     void* workspace, size_t workspace_bytes,
+                                     uint64_t* cand, uint64_t cap, uint64_t* counters, void* stream) {
+    return stage_match(w_a, w2_a, n_a, w_b, w2_b, n_b, window, window2, workspace, workspace_bytes,
+                       cand, cap, counters, stream, true, FUSE_ALWAYS);
 }

@@ -43,6 +43,10 @@ struct HalfJob {
     uint32_t opt_hcap;
     uint32_t* bcount;       // [NB]
     uint32_t* hcount;       // [NB] (half b)
+    // fused match (k_mitm): list-building buffers; ytmp is the first key buffer
+    uint64_t* kb1;          // [2^(l-1)] second key buffer (l > 12)
+    uint32_t* mb0;          // [2^(l-1)] mask buffers
+    uint32_t* mb1;
 };
 
 // One problem's match.
@@ -56,6 +60,8 @@ struct ProbJob {
     uint64_t* cand;
     uint64_t cap;
     unsigned long long* ctr;    // [4]: coarse pairs, pairs within W, candidates (within W and W2, non-trivial), trivial seen
+    int fused;              // 1: matched by k_mitm (no tables)
+    int nbl, slab, wf;      // k_mitm: bins per unit (log2), units per CTA, fingerprint window
 };
 
 // One small problem (n_b <= SMALL_MAX_H) matched entirely in shared memory.
@@ -81,6 +87,8 @@ struct MatchGeom {
     uint64_t wc;
     uint64_t hcap;          // halo capacity (entries)
     size_t bytes;           // device workspace bytes (tables + histograms + halo)
+    bool fused;             // k_mitm: sorted lists only, units of 2^(64-d1) keys
+    int nbl, slab, wf;
 };
 
 // Layout knobs chosen by the autotuner (defaults: 16, 13, 16).
@@ -90,10 +98,27 @@ struct TuneParams {
     int cta_per_sm = 16;     // scatter CTAs per SM over a sub-batch
 };
 
+// Which match a problem gets: tables in device memory, or the fused match
+// (k_mitm) for halves of at least FUSED_MIN_NA elements, or only the fused one.
+enum { FUSE_NEVER = 0, FUSE_AUTO = 1, FUSE_ALWAYS = 2 };
+constexpr int FUSED_MIN_NA = 18;
+
 // Choose bucket bits and coarse window; returns false if the window is too
-// wide for any bucket layout.
+// wide for any bucket layout.  optimistic = false always gives the table
+// match with the exact (count-pass) layout.
 bool match_geometry(int n_a, int n_b, uint64_t W, int ctas_a, int ctas_b, MatchGeom* g,
-                    bool optimistic = true, const TuneParams* tp = nullptr);
+                    bool optimistic = true, const TuneParams* tp = nullptr, int fuse = FUSE_AUTO);
+
+// Geometry of the fused match; false if the halves or the window do not fit it.
+bool mitm_geometry(int n_a, int n_b, uint64_t W, MatchGeom* g);
+size_t mitm_half_bytes(int l);
+void mitm_layout_half(int l, char*& p, HalfJob* h);
+// Build the sorted lists and run k_mitm for the fused problems F[0..nF);
+// dev_mjobs / dev_yjobs hold nF ProbJob / 2*nF HalfJob slots of device memory.
+// ev_lists (if given) is recorded after the sorted lists are built.
+cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev_yjobs, cudaStream_t s,
+                     cudaEvent_t ev_lists = nullptr);
+int mitm_launches(const ProbJob* const* F, int nF);
 
 // Bytes of one problem's buffers for geometry g (uses g.hcap).
 size_t match_bytes(const MatchGeom& g);
@@ -108,7 +133,10 @@ void match_layout(const MatchGeom& g, char* ws, ProbJob* pj);
 // All problems of one call use the same layout (all optimistic or all exact);
 // the optimistic cursors (bcount, hcount) and the exact halo counts must be
 // zeroed by the caller.
+// Fused problems (ProbJob::fused) may be mixed in; they run k_mitm after the
+// table problems' join.  *launches (if given) receives the kernel count.
 cudaError_t run_match(ProbJob* jobs, int np, ProbJob* dev_jobs, HalfJob* dev_halves,
-                      HalfJob* host_halves, cudaStream_t s, cudaEvent_t ev_count, cudaEvent_t ev_scatter);
+                      HalfJob* host_halves, cudaStream_t s, cudaEvent_t ev_count, cudaEvent_t ev_scatter,
+                      int* launches = nullptr);
 
 }  // namespace rfr

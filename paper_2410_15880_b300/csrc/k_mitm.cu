@@ -1,0 +1,585 @@
+// k_mitm.cu — fused meet-in-the-middle match (K-c + K-d + K-e of Section 3.3
+// for large halves, with no key tables in device memory).
+//
+// Each half's h elements are split into low elements 0..l-1 and high
+// elements l..h-1.  The sorted list Y of all 2^l low-subset sums is built
+// once per half by merging (k_ybuild_smem, k_ymerge: the sorted list of a
+// set plus one element is the merge of the list and its copy shifted by the
+// element's weight).  Every high subset x gives one sorted run x + Y
+// (rotated to start at its smallest key), so a half is 2^(h-l) sorted runs.
+//
+// The key space [0, 2^64) is cut into 2^d1 units of width U.  One CTA walks a
+// slab of consecutive units and keeps one cursor per run; per unit it
+//   1. reads, from every run of half a, the stretch of keys inside the unit
+//      and appends them, as 16-bit fingerprints of their position in the
+//      unit plus their pattern masks, to a shared-memory table with one
+//      linked list per bin, marking each key's cell in an occupancy bitmap;
+//   2. reads, from every run of half b, the stretch of keys within Wc of the
+//      unit, [lo - Wc, hi + Wc) (circularly), tests the one or two bitmap
+//      cells its window touches and, for the few keys whose cells are
+//      occupied, walks the lists of the bins around it (queued per warp and
+//      walked 32 at a time, so that lanes do not wait on each other).
+// A pair (a, b) with |K_a - K_b| < Wc (keys of half b are negated sums, so
+// K_a - K_b is the pattern's Tr_1 value) is met exactly once, in the unit
+// holding K_a.  Fingerprint hits are re-checked exactly against the Tr_1
+// window W (Eq. 9 / Eq. 19, circular) and the Tr_2 window W2, as in the table
+// join, so the candidate set is the same as RECOMBINE_C's.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include <cuda_runtime.h>
+#include "k_match.cuh"
+#include "rfr_device.cuh"
+
+namespace rfr {
+namespace {
+
+constexpr int YS_LOG = 12;                                     // list levels built in shared memory
+constexpr int YS_THREADS = 1024;
+constexpr size_t YS_SMEM = ((size_t)2 << YS_LOG) * (8 + 4);    // two (key, mask) buffers of 2^12
+constexpr int YM_THREADS = 256;
+constexpr int YM_PER = 16;                                     // merge outputs per thread
+
+constexpr int MT_THREADS = 1024;
+constexpr int MT_ACAP = 12288;                                 // table-a keys of one unit (mean 8192)
+constexpr int MT_WSLOTS = 320;                                 // private table slots per warp (mean 256) ...
+constexpr int MT_POOL = MT_ACAP - 32 * MT_WSLOTS;              // ... and a shared pool for warps that fill theirs
+constexpr int MT_NBL = 13;                                     // at most 2^13 bins per unit
+constexpr int MT_RUNS = 1024;                                  // runs per half
+constexpr int MT_BM_LOG = 18;                                  // occupancy bitmap: about 2^18 cells per unit
+constexpr int MT_BMW = (1 << (MT_BM_LOG - 5)) + 2;             // + margin cells on both sides
+constexpr int MT_QCAP = 64;                                    // deferred lookups per warp
+constexpr int GL = 8;                                          // lanes walking one run together
+constexpr uint32_t MT_NIL = 0xffffffffu;
+constexpr size_t MT_SMEM = (size_t)MT_ACAP * (4 + 2 + 2) + ((size_t)4 << MT_NBL) + (size_t)MT_BMW * 4 +
+                           (size_t)MT_RUNS * (8 + 4 + 4) * 2 + (size_t)(MT_THREADS / 32) * MT_QCAP * 8;
+
+__device__ __forceinline__ uint64_t mt_lowmask(int h) { return h ? (~0ull >> (64 - h)) : 0ull; }
+__device__ __forceinline__ int mt_pad(int i) { return i + (i >> 5); }
+
+__device__ __forceinline__ uint32_t lower_bound_keys(const uint64_t* K, uint32_t n, uint64_t v) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (K[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Outputs d0 .. d1-1 of the merge of the sorted keys K[0..n) with the sorted
+// sequence B[t] = K[(r + t) mod n] + w (K shifted by w, rotated to its
+// smallest element; equal keys take K first).  n is a power of two.
+template <class Out>
+__device__ __forceinline__ void merge_range(const uint64_t* __restrict__ K, const uint32_t* __restrict__ M,
+                                            uint32_t n, uint32_t r, uint64_t w, uint32_t bit,
+                                            uint32_t d0, uint32_t d1, Out out) {
+    const uint32_t nm = n - 1;
+    uint32_t lo = d0 > n ? d0 - n : 0, hi = d0 < n ? d0 : n;
+    while (lo < hi) {                                          // merge path: A's share of the first d0
+        const uint32_t mid = (lo + hi) >> 1;
+        if (K[mid] <= K[(r + d0 - mid - 1) & nm] + w) lo = mid + 1; else hi = mid;
+    }
+    uint32_t a = lo, b = d0 - lo;
+    for (uint32_t d = d0; d < d1; ++d) {
+        const uint64_t ka = a < n ? K[a] : 0ull;
+        const uint64_t kb = b < n ? K[(r + b) & nm] + w : 0ull;
+        if (b >= n || (a < n && ka <= kb)) { out(d, ka, M[a]); ++a; }
+        else { out(d, kb, M[(r + b) & nm] | bit); ++b; }
+    }
+}
+
+struct YJob {
+    const uint64_t* w;          // the half's weights (elements 0..l-1 used)
+    int l, neg;                 // list bits; keys are negated sums for half b
+    uint64_t* kb[2];            // [2^(l-1)] exact sums, ping-pong (l > YS_LOG only)
+    uint32_t* mb[2];            // [2^(l-1)] their masks
+    uint64_t* ylist;            // [2^l] result: (sum & ~(2^l - 1)) | mask, ascending by sum
+};
+
+// Levels 0 .. min(l, 12) - 1 of one half's list in shared memory.
+__global__ void __launch_bounds__(YS_THREADS) k_ybuild_smem(const YJob* __restrict__ js) {
+    extern __shared__ __align__(16) uint64_t ys_sm[];
+    uint64_t* Kb[2] = {ys_sm, ys_sm + (1 << YS_LOG)};
+    uint32_t* M0 = reinterpret_cast<uint32_t*>(ys_sm + (2 << YS_LOG));
+    uint32_t* Mb[2] = {M0, M0 + (1 << YS_LOG)};
+    const YJob J = js[blockIdx.x];
+    const int s = J.l < YS_LOG ? J.l : YS_LOG;
+    if (threadIdx.x == 0) { Kb[0][0] = 0ull; Mb[0][0] = 0u; }
+    __syncthreads();
+    for (int i = 0; i < s; ++i) {
+        const uint32_t n = 1u << i;
+        const uint64_t w = J.neg ? 0ull - J.w[i] : J.w[i];
+        const uint64_t* K = Kb[i & 1];
+        const uint32_t* M = Mb[i & 1];
+        uint64_t* KO = Kb[(i + 1) & 1];
+        uint32_t* MO = Mb[(i + 1) & 1];
+        const uint32_t r = lower_bound_keys(K, n, 0ull - w);   // first key that wraps when w is added
+        const uint32_t tot = 2 * n, per = (tot + blockDim.x - 1) / blockDim.x;
+        const uint32_t d0 = min(tot, threadIdx.x * per), d1 = min(tot, d0 + per);
+        if (d0 < d1)
+            merge_range(K, M, n, r, w, 1u << i, d0, d1, [&](uint32_t d, uint64_t k, uint32_t m) { KO[d] = k; MO[d] = m; });
+        __syncthreads();
+    }
+    const uint64_t* K = Kb[s & 1];
+    const uint32_t* M = Mb[s & 1];
+    const uint32_t ns = 1u << s;
+    if (s == J.l) {
+        const uint64_t lm = mt_lowmask(J.l);
+        for (uint32_t j = threadIdx.x; j < ns; j += blockDim.x) J.ylist[j] = (K[j] & ~lm) | M[j];
+    } else {
+        for (uint32_t j = threadIdx.x; j < ns; j += blockDim.x) { J.kb[0][j] = K[j]; J.mb[0][j] = M[j]; }
+    }
+}
+
+// Level i >= 12 (2^i sums -> 2^(i+1)) for every half with l > i; cpl CTAs per
+// half, YM_PER outputs per thread.  The last level writes the packed list.
+__global__ void __launch_bounds__(YM_THREADS) k_ymerge(const YJob* __restrict__ js, int i, int cpl) {
+    __shared__ uint32_t s_r;
+    const YJob& J = js[blockIdx.x / cpl];
+    const int c = blockIdx.x % cpl;
+    const uint32_t n = 1u << i;
+    const int p = (i - YS_LOG) & 1;
+    const uint64_t* K = J.kb[p];
+    const uint32_t* M = J.mb[p];
+    const uint64_t w = J.neg ? 0ull - J.w[i] : J.w[i];
+    if (threadIdx.x == 0) s_r = lower_bound_keys(K, n, 0ull - w);
+    __syncthreads();
+    const uint32_t r = s_r;
+    const uint32_t per_cta = 2 * n / (uint32_t)cpl;
+    const uint32_t d0 = (uint32_t)c * per_cta + threadIdx.x * YM_PER, d1 = d0 + YM_PER;
+    if (i == J.l - 1) {
+        const uint64_t lm = mt_lowmask(J.l);
+        uint64_t* Y = J.ylist;
+        merge_range(K, M, n, r, w, 1u << i, d0, d1, [&](uint32_t d, uint64_t k, uint32_t m) { Y[d] = (k & ~lm) | m; });
+    } else {
+        uint64_t* KO = J.kb[p ^ 1];
+        uint32_t* MO = J.mb[p ^ 1];
+        merge_range(K, M, n, r, w, 1u << i, d0, d1, [&](uint32_t d, uint64_t k, uint32_t m) { KO[d] = k; MO[d] = m; });
+    }
+}
+
+struct MitmJob {
+    const uint64_t* ya;  const uint64_t* yb;                 // sorted low lists
+    const uint64_t* w_a; const uint64_t* w2_a;
+    const uint64_t* w_b; const uint64_t* w2_b;
+    int n_a, n_b, l_a, l_b;
+    int d1, nbl, slab, wf;                                    // units, bins per unit, units per CTA, fingerprint window
+    int cta_base, pad0;
+    uint64_t W, W2, Wc;
+    uint64_t* cand;
+    uint64_t cap;
+    unsigned long long* ctr;
+    int* err;
+};
+
+__device__ __forceinline__ uint64_t mask_sum(const uint64_t* w, uint32_t m) {
+    uint64_t s = 0;
+    for (; m; m &= m - 1) s += w[__ffs(m) - 1];
+    return s;
+}
+
+// First rotated index t in [0, N] of run (x, j0) with key >= v (keys rise along t).
+__device__ __forceinline__ uint32_t run_lower_bound(const uint64_t* Y, uint32_t j0, uint32_t N, uint64_t x,
+                                                    uint64_t keep, uint64_t v) {
+    uint32_t lo = 0, hi = N;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (x + (Y[(j0 + mid) & (N - 1)] & keep) < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// First index j of the (unrotated) list with (Y[j] & keep) >= v.
+__device__ __forceinline__ uint32_t list_lower_bound(const uint64_t* Y, uint32_t N, uint64_t keep, uint64_t v) {
+    uint32_t lo = 0, hi = N;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((Y[mid] & keep) < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restrict__ js, int np) {
+    extern __shared__ __align__(16) unsigned char mt_sm[];
+    uint32_t* msk = reinterpret_cast<uint32_t*>(mt_sm);                // [ACAP] table-a masks
+    uint32_t* head = msk + MT_ACAP;                                     // [bins] first key of each bin (list)
+    uint32_t* bm = head + (1 << MT_NBL);                                // [BMW] cells holding a table-a key
+    uint64_t* xa = reinterpret_cast<uint64_t*>(bm + MT_BMW);            // run offsets, half a
+    uint64_t* xb = xa + MT_RUNS;                                        // run offsets, half b
+    uint2* queue = reinterpret_cast<uint2*>(xb + MT_RUNS);              // [warps][QCAP] deferred lookups
+    uint32_t* j0a = reinterpret_cast<uint32_t*>(queue + (MT_THREADS / 32) * MT_QCAP);
+    uint32_t* ta = j0a + MT_RUNS;
+    uint32_t* j0b = ta + MT_RUNS;
+    uint32_t* tb = j0b + MT_RUNS;
+    uint16_t* fpr = reinterpret_cast<uint16_t*>(tb + MT_RUNS);          // [ACAP] table-a fingerprints
+    uint16_t* nxt = fpr + MT_ACAP;                                      // [ACAP] next key of the same bin
+    __shared__ uint64_t wa[32], w2a[32], wb[32], w2b[32];
+    __shared__ uint32_t s_count;
+
+    int jl = 0, jh = np - 1;                                            // last job with cta_base <= blockIdx.x
+    while (jl < jh) {
+        const int mid = (jl + jh + 1) >> 1;
+        if (js[mid].cta_base <= (int)blockIdx.x) jl = mid; else jh = mid - 1;
+    }
+    const MitmJob& P = js[jl];
+    const int c = blockIdx.x - P.cta_base;
+    const int n_a = P.n_a, n_b = P.n_b, la = P.l_a, lb = P.l_b;
+    const uint32_t Na = 1u << la, Nb = 1u << lb;
+    const int RA = 1 << (n_a - la), RB = 1 << (n_b - lb);
+    const uint64_t keepa = ~mt_lowmask(la), keepb = ~mt_lowmask(lb);
+    const int d1 = P.d1, su = 64 - d1, nbl = P.nbl, bsh = su - nbl, fsh = bsh - 16;
+    const uint32_t NB = 1u << d1;
+    const uint64_t U = 1ull << su;
+    const uint64_t Wc = P.Wc, W = P.W, W2 = P.W2;
+    const int wf = P.wf;
+    const int nbins = 1 << nbl;
+    // cells of 2^rsh fingerprint positions, wider than 2 wf, shifted by one cell so
+    // that the windows of keys just outside the unit stay at cell >= 0
+    int rsh = nbl + 16 > MT_BM_LOG ? nbl + 16 - MT_BM_LOG : 0;
+    while ((1 << rsh) <= 2 * wf + 1) ++rsh;
+    const int coff = 1 << rsh;
+    const int nbmw = (((1 << (nbl + 16)) >> rsh) + 3 + 31) >> 5;
+    const uint64_t* __restrict__ Ya = P.ya;
+    const uint64_t* __restrict__ Yb = P.yb;
+    const uint32_t k0 = (uint32_t)c * (uint32_t)P.slab, k1 = k0 + (uint32_t)P.slab;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int gi = lane / GL, gl = lane % GL, gsh = gi * GL;          // run group of this lane
+    const int gid = warp * (32 / GL) + gi, NG = (int)blockDim.x / GL;
+    const uint32_t gbits = (1u << GL) - 1u;
+    const uint32_t lma = Na - 1u, lmb = Nb - 1u;                      // low-list masks (l <= 21)
+    uint2* wq = queue + warp * MT_QCAP;
+
+    if (threadIdx.x < n_a) { wa[threadIdx.x] = P.w_a[threadIdx.x]; w2a[threadIdx.x] = P.w2_a[threadIdx.x]; }
+    if (threadIdx.x < n_b) { wb[threadIdx.x] = P.w_b[threadIdx.x]; w2b[threadIdx.x] = P.w2_b[threadIdx.x]; }
+    __syncthreads();
+    // run state: offset x, rotation j0 (index of the smallest key), cursor at the slab's first unit
+    for (int g = threadIdx.x; g < RA; g += blockDim.x) {
+        uint64_t x = 0;
+        for (uint32_t t = (uint32_t)g; t; t &= t - 1) x += wa[la + __ffs(t) - 1];
+        const uint32_t j0 = list_lower_bound(Ya, Na, keepa, 0ull - x) & (Na - 1);
+        xa[g] = x; j0a[g] = j0;
+        ta[g] = k0 ? run_lower_bound(Ya, j0, Na, x, keepa, (uint64_t)k0 << su) : 0u;
+    }
+    for (int g = threadIdx.x; g < RB; g += blockDim.x) {
+        uint64_t x = 0;
+        for (uint32_t t = (uint32_t)g; t; t &= t - 1) x -= wb[lb + __ffs(t) - 1];
+        const uint32_t j0 = list_lower_bound(Yb, Nb, keepb, 0ull - x) & (Nb - 1);
+        xb[g] = x; j0b[g] = j0;
+        tb[g] = k0 ? run_lower_bound(Yb, j0, Nb, x, keepb, ((uint64_t)k0 << su) - Wc) : 0u;
+    }
+
+    unsigned long long n_coarse = 0, n_pre = 0;
+    auto hit = [&](uint32_t ma, uint32_t mb) {
+        ++n_coarse;
+        const uint64_t v = mask_sum(wa, ma) + mask_sum(wb, mb);
+        if (circ_dist(v) <= W) {
+            ++n_pre;
+            const uint64_t t2 = mask_sum(w2a, ma) + mask_sum(w2b, mb);
+            if (circ_dist(t2) <= W2) {
+                if (ma == 0 && mb == 0) {
+                    P.ctr[3] = 1ull;
+                } else {
+                    const unsigned long long idx = atomicAdd(&P.ctr[2], 1ull);
+                    if (idx < P.cap) P.cand[idx] = (uint64_t)ma | ((uint64_t)mb << n_a);
+                }
+            }
+        }
+    };
+    // Does a cell within wf of fingerprint position pb (-wf <= pb < 2^(nbl+16) + wf) hold a key?
+    auto maybe = [&](int pb) -> bool {
+        const uint32_t q0 = (uint32_t)(pb + coff - wf) >> rsh, q1 = (uint32_t)(pb + coff + wf) >> rsh;
+        const uint32_t w0 = bm[q0 >> 5];
+        const uint32_t w1 = (q1 >> 5) == (q0 >> 5) ? w0 : bm[q1 >> 5];
+        return (((w0 >> (q0 & 31)) | (w1 >> (q1 & 31))) & 1u) != 0u;
+    };
+    // The table-a keys of the bins around pb: fingerprints within wf are re-checked exactly.
+    auto scan_bins = [&](int pb, uint32_t mb) {
+        const int plo = pb - wf < 0 ? 0 : pb - wf;
+        const int phi = pb + wf > (nbins << 16) - 1 ? (nbins << 16) - 1 : pb + wf;
+        for (int bin = plo >> 16; bin <= (phi >> 16); ++bin)
+            for (uint32_t e = head[bin]; e != MT_NIL; e = nxt[e] == 0xffffu ? MT_NIL : nxt[e]) {
+                const int d = ((bin << 16) | (int)fpr[e]) - pb;
+                if (d >= -wf && d <= wf) hit(msk[e], mb);
+            }
+    };
+    // Warp-uniform: queue the lanes whose lookup may hit; scan 32 queued lookups at a time.
+    uint32_t qn = 0;
+    auto enqueue = [&](bool need, int pb, uint32_t mb) {
+        const uint32_t qb = __ballot_sync(0xffffffffu, need);
+        if (!qb) return;
+        if (need) wq[qn + __popc(qb & lt)] = make_uint2((uint32_t)pb, mb);
+        qn += __popc(qb);
+        if (qn >= 32) {
+            __syncwarp();
+            const uint2 e = wq[lane];
+            const uint2 e2 = lane + 32 < (int)qn ? wq[lane + 32] : make_uint2(0u, 0u);
+            __syncwarp();
+            if (lane + 32 < (int)qn) wq[lane] = e2;
+            qn -= 32;
+            scan_bins((int)e.x, e.y);
+        }
+    };
+    auto drain = [&]() {
+        if (!qn) return;
+        __syncwarp();
+        if (lane < (int)qn) {
+            const uint2 e = wq[lane];
+            scan_bins((int)e.x, e.y);
+        }
+        qn = 0;
+        __syncwarp();
+    };
+    // one run of half b, from rotated index t while key - base < span (no cursor update)
+    auto walk_b = [&](int g, uint32_t t, uint64_t base, uint64_t span, uint64_t lo) {
+        const uint64_t xbb = xb[g] - base, lob = lo - base;
+        const uint32_t j0 = j0b[g];
+        for (;;) {
+            const uint32_t idx = t + lane;
+            const uint64_t y = idx < Nb ? Yb[(j0 + idx) & (Nb - 1)] : 0ull;
+            const uint64_t rk = xbb + (y & keepb);
+            const bool in = idx < Nb && rk < span;
+            const int pb = (int)((long long)(rk - lob) >> fsh);
+            enqueue(in && maybe(pb), pb, ((uint32_t)g << lb) | (uint32_t)(y & ~keepb));
+            const uint32_t cnt = __popc(__ballot_sync(0xffffffffu, in));
+            t += cnt;
+            if (cnt < 32) break;
+        }
+    };
+
+    for (uint32_t k = k0; k < k1; ++k) {
+        const uint64_t lo = (uint64_t)k << su;
+        for (int b = threadIdx.x; b < nbins; b += blockDim.x) head[b] = MT_NIL;
+        for (int b = threadIdx.x; b < nbmw; b += blockDim.x) bm[b] = 0u;
+        if (threadIdx.x == 0) s_count = 0u;
+        __syncthreads();
+        // ---- table a: every key of the unit.  Groups of GL lanes walk one run each
+        // (GL consecutive keys per step); a group whose run leaves the unit takes the
+        // next run from a CTA-wide pool.  One slot reservation per warp step.
+        // Group j of GL lanes walks runs j, j + NG, ... (NG groups per CTA), GL consecutive
+        // keys per step with three steps of loads in flight; the warp steps until its
+        // groups' runs leave the unit.
+        {
+            uint32_t wused = 0;                                          // warp-uniform
+            for (int run = gid; run - gi < RA; run += NG) {
+                bool act = run < RA;
+                uint64_t xl = 0, y0 = 0, y1 = 0, y2 = 0, y3 = 0;
+                uint32_t jj = 0, t = 0;
+                if (act) {
+                    xl = xa[run] - lo; jj = j0a[run]; t = ta[run];
+                    const uint64_t* Yr = Ya;
+                    y0 = t + gl < Na ? Yr[(jj + t + gl) & (Na - 1)] : 0ull;
+                    y1 = t + GL + gl < Na ? Yr[(jj + t + GL + gl) & (Na - 1)] : 0ull;
+                    y2 = t + 2 * GL + gl < Na ? Yr[(jj + t + 2 * GL + gl) & (Na - 1)] : 0ull;
+                    y3 = t + 3 * GL + gl < Na ? Yr[(jj + t + 3 * GL + gl) & (Na - 1)] : 0ull;
+                }
+                while (__any_sync(0xffffffffu, act)) {
+                    const uint64_t y = y0;
+                    const uint64_t rel = xl + (y & ~(uint64_t)lma);
+                    const bool in = act && t + gl < Na && rel < U;
+                    const uint32_t bal = __ballot_sync(0xffffffffu, in);
+                    const uint32_t cnt = __popc((bal >> gsh) & gbits);
+                    const uint32_t tot = __popc(bal);
+                    uint32_t slot;
+                    if (wused + tot <= (uint32_t)MT_WSLOTS) {            // the warp's own slots
+                        slot = (uint32_t)warp * MT_WSLOTS + wused + __popc(bal & lt);
+                        wused += tot;
+                    } else {                                              // the shared pool
+                        uint32_t pbase = 0;
+                        if (lane == 0) pbase = atomicAdd(&s_count, tot);
+                        pbase = __shfl_sync(0xffffffffu, pbase, 0) + __popc(bal & lt);
+                        slot = pbase < (uint32_t)MT_POOL ? 32u * MT_WSLOTS + pbase : (uint32_t)MT_ACAP;
+                    }
+                    if (in && slot < (uint32_t)MT_ACAP) {
+                        const uint32_t pv = (uint32_t)(rel >> fsh);
+                        fpr[slot] = (uint16_t)pv;
+                        msk[slot] = ((uint32_t)run << la) | ((uint32_t)y & lma);
+                        nxt[slot] = (uint16_t)atomicExch(&head[pv >> 16], slot);
+                        const uint32_t q = (pv + (uint32_t)coff) >> rsh;
+                        atomicOr(&bm[q >> 5], 1u << (q & 31));
+                    }
+                    t += cnt;
+                    act = act && cnt == (uint32_t)GL;
+                    y0 = y1; y1 = y2; y2 = y3;
+                    const uint32_t i3 = t + 3 * GL + gl;
+                    y3 = act && i3 < Na ? Ya[(jj + i3) & (Na - 1)] : 0ull;
+                }
+                if (gl == 0 && run < RA) ta[run] = t;
+            }
+        }
+        __syncthreads();
+        if (s_count > (uint32_t)MT_POOL) {                             // clustered keys: redo with tables
+            if (threadIdx.x == 0) atomicExch(P.err, 1);
+            return;
+        }
+        // ---- half b: keys in [lo - Wc, hi + Wc), each looked up in the table
+        const uint64_t base = k ? lo - Wc : 0ull;
+        const uint64_t span = (k == NB - 1) ? 0ull - base : lo + U + Wc - base;
+        const uint64_t nxtb = k ? U : U - Wc;                             // next unit's base - base
+        const uint64_t lob = lo - base;                                   // key - lo = (key - base) - lob
+        for (int run = gid; run - gi < RB; run += NG) {
+            bool act = run < RB;
+            bool fnd = !act;
+            uint64_t xbb = 0, y0 = 0, y1 = 0, y2 = 0, y3 = 0;
+            uint32_t jj = 0, t = 0, nt = 0;
+            if (act) {
+                xbb = xb[run] - base; jj = j0b[run]; t = tb[run]; nt = t;
+                y0 = t + gl < Nb ? Yb[(jj + t + gl) & (Nb - 1)] : 0ull;
+                y1 = t + GL + gl < Nb ? Yb[(jj + t + GL + gl) & (Nb - 1)] : 0ull;
+                y2 = t + 2 * GL + gl < Nb ? Yb[(jj + t + 2 * GL + gl) & (Nb - 1)] : 0ull;
+                y3 = t + 3 * GL + gl < Nb ? Yb[(jj + t + 3 * GL + gl) & (Nb - 1)] : 0ull;
+            }
+            while (__any_sync(0xffffffffu, act)) {
+                const uint64_t y = y0;
+                const bool valid = act && t + gl < Nb;
+                const uint64_t rk = xbb + (y & ~(uint64_t)lmb);
+                const bool in = valid && rk < span;
+                const int pb = (int)((long long)(rk - lob) >> fsh);
+                enqueue(in && maybe(pb), pb, ((uint32_t)run << lb) | ((uint32_t)y & lmb));
+                const uint32_t cnt = __popc((__ballot_sync(0xffffffffu, in) >> gsh) & gbits);
+                const uint32_t cn = __popc((__ballot_sync(0xffffffffu, valid && rk < nxtb) >> gsh) & gbits);
+                if (!fnd) { nt += cn; fnd = cn < (uint32_t)GL; }
+                t += cnt;
+                act = act && cnt == (uint32_t)GL;
+                y0 = y1; y1 = y2; y2 = y3;
+                const uint32_t i3 = t + 3 * GL + gl;
+                y3 = act && i3 < Nb ? Yb[(jj + i3) & (Nb - 1)] : 0ull;
+            }
+            if (gl == 0 && run < RB) tb[run] = nt;
+        }
+        // circular wrap: unit 0 also meets keys of b in [2^64 - Wc, 2^64), the last unit keys in [0, Wc)
+        if (k == 0)
+            for (int g = warp; g < RB; g += nwarps) {
+                const uint32_t s0 = run_lower_bound(Yb, j0b[g], Nb, xb[g], keepb, 0ull - Wc);
+                walk_b(g, s0, 0ull - Wc, Wc, lo);
+            }
+        if (k == NB - 1)
+            for (int g = warp; g < RB; g += nwarps) walk_b(g, 0u, 0ull, Wc, lo);
+        drain();
+        __syncthreads();
+    }
+    if (n_coarse) atomicAdd(&P.ctr[0], n_coarse);
+    if (n_pre) atomicAdd(&P.ctr[1], n_pre);
+}
+
+bool g_mitm_attr = false;
+
+}  // namespace
+
+bool mitm_geometry(int n_a, int n_b, uint64_t W, MatchGeom* g) {
+    if (n_a < 2 || n_b < n_a || n_b > 31) return false;
+    auto lsplit = [](int h) { return h <= 10 ? h : (h - 7 < 10 ? 10 : (h - 7 > 21 ? 21 : h - 7)); };
+    const int la = lsplit(n_a), lb = lsplit(n_b);
+    if ((1 << (n_a - la)) > MT_RUNS || (1 << (n_b - lb)) > MT_RUNS) return false;
+    int d1 = n_a - 13;
+    if (d1 < 2) d1 = 2;
+    const int su = 64 - d1;
+    const uint64_t wc = W + (1ull << la) + (1ull << lb) + 2;
+    if (wc < W) return false;
+    // a key's window must touch at most two bins: bin width 2^(su - nbl) > 2 Wc
+    int nbl = MT_NBL;
+    while (nbl >= 4 && !(wc < (1ull << (su - nbl - 1)))) --nbl;
+    if (nbl < 4) return false;
+    const int fsh = su - nbl - 16;
+    const uint32_t NB = 1u << d1;
+    uint32_t slab = NB / 256;
+    if (slab < 1) slab = 1;
+    if (slab > 64) slab = 64;
+    memset(g, 0, sizeof(*g));
+    g->fused = true;
+    g->optimistic = true;
+    g->n_a = n_a; g->n_b = n_b; g->d1 = d1; g->wc = wc;
+    g->l_a = la; g->l_b = lb;
+    g->nbl = nbl; g->slab = (int)slab;
+    g->wf = (int)((wc >> fsh) + 1);
+    g->bytes = match_bytes(*g);
+    return true;
+}
+
+size_t mitm_half_bytes(int l) {
+    auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t b = a256((size_t)8 << l);
+    if (l > YS_LOG) b += 2 * a256((size_t)8 << (l - 1)) + 2 * a256((size_t)4 << (l - 1));
+    return b;
+}
+
+void mitm_layout_half(int l, char*& p, HalfJob* h) {
+    auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~(size_t)255; return q; };
+    h->ylist = (uint64_t*)take((size_t)8 << l);
+    h->ytmp = h->kb1 = nullptr;
+    h->mb0 = h->mb1 = nullptr;
+    if (l > YS_LOG) {
+        h->ytmp = (uint64_t*)take((size_t)8 << (l - 1));
+        h->kb1 = (uint64_t*)take((size_t)8 << (l - 1));
+        h->mb0 = (uint32_t*)take((size_t)4 << (l - 1));
+        h->mb1 = (uint32_t*)take((size_t)4 << (l - 1));
+    }
+}
+
+int mitm_launches(const ProbJob* const* F, int nF) {
+    int maxl = 0;
+    for (int i = 0; i < nF; ++i) maxl = std::max(maxl, std::max(F[i]->A.l, F[i]->B.l));
+    return nF ? 2 + std::max(0, maxl - YS_LOG) : 0;
+}
+
+cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev_yjobs, cudaStream_t s,
+                     cudaEvent_t ev_lists) {
+    static_assert(sizeof(MitmJob) <= sizeof(ProbJob), "MitmJob must fit a ProbJob slot");
+    static_assert(sizeof(YJob) <= sizeof(HalfJob), "YJob must fit a HalfJob slot");
+    if (nF <= 0) return cudaSuccess;
+    cudaError_t e;
+    if (!g_mitm_attr) {
+        e = cudaFuncSetAttribute(k_ybuild_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)YS_SMEM);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mitm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MT_SMEM);
+        if (e != cudaSuccess) return e;
+        g_mitm_attr = true;
+    }
+    std::vector<YJob> yj;
+    yj.reserve(2 * (size_t)nF);
+    for (int i = 0; i < nF; ++i) {
+        const HalfJob* hh[2] = {&F[i]->A, &F[i]->B};
+        for (const HalfJob* h : hh) {
+            YJob y;
+            y.w = h->w; y.l = h->l; y.neg = h->neg;
+            y.kb[0] = h->ytmp; y.kb[1] = h->kb1;
+            y.mb[0] = h->mb0; y.mb[1] = h->mb1;
+            y.ylist = h->ylist;
+            yj.push_back(y);
+        }
+    }
+    std::stable_sort(yj.begin(), yj.end(), [](const YJob& a, const YJob& b) { return a.l > b.l; });
+    YJob* d_yj = (YJob*)dev_yjobs;
+    e = cudaMemcpyAsync(d_yj, yj.data(), sizeof(YJob) * yj.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    k_ybuild_smem<<<(int)yj.size(), YS_THREADS, YS_SMEM, s>>>(d_yj);
+    for (int i = YS_LOG; i < yj[0].l; ++i) {
+        int nh = 0;
+        while (nh < (int)yj.size() && yj[nh].l > i) ++nh;
+        const int cpl = 1 << (i + 1 - YS_LOG);
+        k_ymerge<<<nh * cpl, YM_THREADS, 0, s>>>(d_yj, i, cpl);
+    }
+    if (ev_lists) cudaEventRecord(ev_lists, s);
+    std::vector<MitmJob> mj(nF);
+    int ctas = 0;
+    for (int i = 0; i < nF; ++i) {
+        const ProbJob& P = *F[i];
+        MitmJob& m = mj[i];
+        memset(&m, 0, sizeof(m));
+        m.ya = P.A.ylist; m.yb = P.B.ylist;
+        m.w_a = P.w_a; m.w2_a = P.w2_a; m.w_b = P.w_b; m.w2_b = P.w2_b;
+        m.n_a = P.n_a; m.n_b = P.n_b; m.l_a = P.A.l; m.l_b = P.B.l;
+        m.d1 = P.d1; m.nbl = P.nbl; m.slab = P.slab; m.wf = P.wf;
+        m.cta_base = ctas;
+        m.W = P.W; m.W2 = P.W2; m.Wc = P.Wc;
+        m.cand = P.cand; m.cap = P.cap; m.ctr = P.ctr; m.err = P.A.err;
+        ctas += (1 << P.d1) / P.slab;
+    }
+    MitmJob* d_mj = (MitmJob*)dev_mjobs;
+    e = cudaMemcpyAsync(d_mj, mj.data(), sizeof(MitmJob) * nF, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    k_mitm<<<ctas, MT_THREADS, MT_SMEM, s>>>(d_mj, nF);
+    return cudaGetLastError();
+}
+
+}  // namespace rfr

@@ -337,7 +337,7 @@ static double time_layout(Ctx& C, cudaStream_t s, const rfr_plan& plan, const rf
             pj.cand = cand; pj.cap = 256; pj.ctr = (unsigned long long*)ctr;
             pj.A.err = pj.B.err = (int*)(ctr + 4);
             cudaMemsetAsync(ctr, 0, 64, s);
-            cudaMemsetAsync(pj.A.bcount, 0, 3 * (((((size_t)1 << g.d1) * 4) + 255) & ~(size_t)255), s);
+            if (!g.fused) cudaMemsetAsync(pj.A.bcount, 0, 3 * (((((size_t)1 << g.d1) * 4) + 255) & ~(size_t)255), s);
         }
         cudaEventRecord(e0, s);
         if (run_match(jobs.data(), copies, d_jobs, d_halves, halves.data(), s, nullptr, nullptr) != cudaSuccess) break;
@@ -354,6 +354,8 @@ static double time_layout(Ctx& C, cudaStream_t s, const rfr_plan& plan, const rf
 static TuneParams tune_class(Ctx& C, cudaStream_t s, const rfr_plan& plan, const rfr_plan* dplan,
                              cudaEvent_t e0, cudaEvent_t e1) {
     TuneParams best;
+    MatchGeom g0;
+    if (match_geometry(plan.n_a, plan.n_b, plan.window, 1, 1, &g0, true) && g0.fused) return best;   // no table knobs
     double tbest = time_layout(C, s, plan, dplan, best, e0, e1);
     if (tbest < 0) return best;
     const int lvals[] = {15, 17}, dvals[] = {12}, cvals[] = {8, 32};
@@ -594,15 +596,18 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
             pj.ctr = (unsigned long long*)ctr;
             pj.A.err = pj.B.err = (int*)(ctr + 4);
             cudaMemsetAsync(ctr, 0, 6 * 8, s);
-            if (w.geom.optimistic)
+            if (w.geom.fused)
+                ;                                       // k_mitm keeps no tables
+            else if (w.geom.optimistic)
                 cudaMemsetAsync(pj.A.bcount, 0, 3 * (((((size_t)1 << w.geom.d1) * 4) + 255) & ~(size_t)255), s);
             else
                 cudaMemsetAsync(pj.B.halo_cnt, 0, (((size_t)1 << w.geom.d1) + 1) * 4, s);
         }
         h2d += (uint64_t)np * sizeof(ProbJob) + 2ull * np * sizeof(HalfJob);
         cudaEventRecord(ev[3], s);
-        rc = cuda_ok(run_match(jobs.data(), np, d_jobs, d_halves, halves.data(), s, ev[4], ev[5]));
-        launches += exact_round ? 6 : 3;
+        int nl = 0;
+        rc = cuda_ok(run_match(jobs.data(), np, d_jobs, d_halves, halves.data(), s, ev[4], ev[5], &nl));
+        launches += (uint32_t)nl;
         cudaEventRecord(ev[6], s);
         std::vector<uint64_t> h_ctr(6 * (size_t)np);
         for (int i = 0; i < np && rc == RFR_OK; ++i)

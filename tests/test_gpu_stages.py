@@ -120,11 +120,12 @@ def _expected_pairs(wa, w2a, wb, w2b, W, W2):
     return {(i, j) for (i, j) in pairs if accept((a2[i] + b2[j]) % M64, M64, W2)}
 
 
-def _run_match(P, wa, w2a, wb, w2b, W, W2, cap=1 << 16, exact=False):
+def _run_match(P, wa, w2a, wb, w2b, W, W2, cap=1 << 16, exact=False, fused=False):
     cand, ctr, _ = P.stage_match(u64_tensor(wa) if wa else u64_tensor([0])[:0],
                                  u64_tensor(w2a) if wa else u64_tensor([0])[:0],
                                  u64_tensor(wb) if wb else u64_tensor([0])[:0],
-                                 u64_tensor(w2b) if wb else u64_tensor([0])[:0], W, W2, cap, exact=exact)
+                                 u64_tensor(w2b) if wb else u64_tensor([0])[:0], W, W2, cap, exact=exact,
+                                 fused=fused)
     torch.cuda.synchronize()
     ctr = [int(x) for x in ctr.cpu().numpy().view(np.uint64)]
     cnt = ctr[2]
@@ -133,9 +134,12 @@ def _run_match(P, wa, w2a, wb, w2b, W, W2, cap=1 << 16, exact=False):
     return {(s & ((1 << na) - 1), s >> na) for s in got}, ctr, got
 
 
+@pytest.mark.parametrize("fused", [False, True])
 @pytest.mark.parametrize("seed,na,nb", [(1, 0, 0), (2, 0, 1), (3, 1, 1), (4, 2, 3), (5, 4, 4),
                                         (6, 5, 6), (7, 7, 8), (8, 9, 9), (9, 10, 11)])
-def test_match_bruteforce(P, seed, na, nb):
+def test_match_bruteforce(P, seed, na, nb, fused):
+    if fused and na < 2:
+        pytest.skip("the fused match needs two elements per half")
     rng = random.Random(seed)
     W = rng.choice([0, 3, 1 << 20, 1 << 52])
     wa = [rng.randrange(M64) for _ in range(na)]
@@ -145,7 +149,7 @@ def test_match_bruteforce(P, seed, na, nb):
     w2a = [rng.randrange(M64) for _ in range(na)]
     w2b = [rng.randrange(M64) for _ in range(nb)]
     W2 = 1 << 63                                    # Tr_2 filter off
-    got, ctr, raw = _run_match(P, wa, w2a, wb, w2b, W, W2)
+    got, ctr, raw = _run_match(P, wa, w2a, wb, w2b, W, W2, fused=fused)
     exp = _expected_pairs(wa, w2a, wb, w2b, W, W2)
     assert ctr[3] == 1                              # the empty pattern always matches
     assert got == exp - {(0, 0)}
@@ -181,11 +185,13 @@ def test_match_candidate_cap(P):
     assert ctr[2] == (1 << 9) - 1 and len(raw) == 10
 
 
-@pytest.mark.parametrize("exact", [False, True])
+@pytest.mark.parametrize("layout", ["slack", "exact", "fused"])
 @pytest.mark.parametrize("seed,na,nb", [(11, 14, 15), (12, 16, 16), (13, 17, 18)])
-def test_match_several_tiles_against_scan(P, seed, na, nb, exact):
+def test_match_several_tiles_against_scan(P, seed, na, nb, layout):
     """Sizes that span many buckets and CTAs, vs RECOMBINE_A on the concatenation,
-    with the slack-region layout and with the exact (count pass) layout."""
+    with the slack-region layout, the exact (count pass) layout and the fused
+    match (many key units, several runs per half)."""
+    exact, fused = layout == "exact", layout == "fused"
     from oracle.recombine import recombine_a
     rng = random.Random(seed)
     wa = [rng.randrange(M64) for _ in range(na)]
@@ -194,7 +200,7 @@ def test_match_several_tiles_against_scan(P, seed, na, nb, exact):
     wb[2] = (-(wa[0] + wa[5] + wb[7])) % M64
     wa[9] = (-(wb[1] + wb[3])) % M64
     W = 1 << 30
-    got, ctr, _ = _run_match(P, wa, [0] * na, wb, [0] * nb, W, 0, exact=exact)
+    got, ctr, _ = _run_match(P, wa, [0] * na, wb, [0] * nb, W, 0, exact=exact, fused=fused)
     assert ctr[4] == 0
     scan = set(recombine_a(wa + wb + [0], M64, W)) - {0}
     exp = {(s & ((1 << na) - 1), s >> na) for s in scan}
@@ -249,6 +255,63 @@ def test_match_clustered_keys_overflow_then_exact(P):
     wa[0] = 0                                           # {a0} sums to an integer
     W = 1 << 20
     _, ctr, _ = _run_match(P, wa, [0] * na, wb, [0] * nb, W, 0)
+    assert ctr[4] == 1
+    got, ctr2, _ = _run_match(P, wa, [0] * na, wb, [0] * nb, W, 0, exact=True)
+    assert ctr2[4] == 0
+    scan = set(recombine_a(wa + wb + [0], M64, W)) - {0}
+    assert got == {(s & ((1 << na) - 1), s >> na) for s in scan} and (1, 0) in got
+
+
+# ---------------------------------------------------------------- fused match at large sizes
+@pytest.mark.parametrize("seed,na,nb,logW,tr2", [(31, 20, 21, 30, False), (32, 22, 22, 38, True),
+                                               (33, 23, 24, 30, False)])
+def test_match_fused_large_against_sorted_mitm(P, seed, na, nb, logW, tr2):
+    """The fused match (sorted lists built by merging, key units in shared
+    memory) at sizes with 2^7 runs per half and up to 2^10 key units, vs the
+    sorted-list meet in the middle of the oracle.  Planted weights put pairs
+    across the circular wrap in both directions and across the unit boundary
+    at 2^63; three integral subsets are planted too."""
+    from oracle.recombine import accept, band_pairs_sorted, expand_values_u64
+    rng = random.Random(seed)
+    wa = [rng.randrange(M64) for _ in range(na)]
+    wb = [rng.randrange(M64) for _ in range(nb)]
+    wa[0], wb[0] = M64 - 3, M64 - 2                   # K_a = 2^64 - 3 meets K_b = 2 (over the wrap)
+    wa[1], wb[1] = 3, 2                               # K_a = 3 meets K_b = 2^64 - 2
+    wa[2], wb[2] = (1 << 63) - 1, (1 << 63) - 1       # K_a just below 2^63, K_b just above
+    wb[5] = (-(wa[4] + wa[7] + wb[9])) % M64
+    wa[11] = (-(wb[12] + wb[13])) % M64
+    W = 1 << logW
+    if tr2:
+        w2a = [rng.randrange(M64) for _ in range(na)]
+        w2b = [rng.randrange(M64) for _ in range(nb)]
+        W2 = 1 << 62
+    else:
+        w2a, w2b, W2 = [0] * na, [0] * nb, 0
+    got, ctr, raw = _run_match(P, wa, w2a, wb, w2b, W, W2, cap=1 << 20, fused=True)
+    pairs = band_pairs_sorted(wa, wb, W)
+    if tr2:
+        a2, b2 = expand_values_u64(w2a), expand_values_u64(w2b)
+        pairs = {(i, j) for (i, j) in pairs if accept(int(a2[i] + b2[j]), M64, W2)}
+    assert ctr[4] == 0 and ctr[3] == 1
+    assert got == pairs - {(0, 0)}
+    assert len(raw) == len(set(raw)) and ctr[2] == len(raw)
+    assert ctr[1] >= ctr[2] and ctr[0] >= ctr[1]
+    if not tr2:                                       # planted pairs (Tr_2 may reject them otherwise)
+        for pl in [(1, 1), (2, 2), (4, 4), (1 | 2, 1 | 2)]:
+            assert pl in got
+
+
+def test_match_fused_clustered_keys_overflow(P):
+    """2^15 keys of half a in one key unit overflow the fused table: the
+    counters say so and the table match with the exact layout gives the scan."""
+    from oracle.recombine import recombine_a
+    rng = random.Random(78)
+    na, nb = 15, 15
+    wa = [rng.randrange(1 << 40) for _ in range(na)]
+    wb = [rng.randrange(1 << 40) for _ in range(nb)]
+    wa[0] = 0
+    W = 1 << 20
+    _, ctr, _ = _run_match(P, wa, [0] * na, wb, [0] * nb, W, 0, fused=True)
     assert ctr[4] == 1
     got, ctr2, _ = _run_match(P, wa, [0] * na, wb, [0] * nb, W, 0, exact=True)
     assert ctr2[4] == 0

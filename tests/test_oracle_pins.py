@@ -153,6 +153,28 @@ def test_band_pairs_equals_scan_on_concatenation():
         assert scan == mitm
 
 
+def test_band_pairs_sorted_equals_brute_force():
+    # The sorted-list meet in the middle gives the brute-force pair set for
+    # M = 2^64, with windows that run over 2^64 -> 0, zero weights (many equal
+    # values) and the empty window.
+    from oracle.recombine import band_pairs_sorted
+    rng = random.Random(17)
+    M = 1 << 64
+    for trial in range(30):
+        na, nb = rng.randint(0, 6), rng.randint(0, 6)
+        if trial % 5 == 0:
+            wa = [rng.randrange(8) for _ in range(na)]
+            wb = [(-rng.randrange(8)) % M for _ in range(nb)]
+        else:
+            wa = [rng.randrange(M) for _ in range(na)]
+            wb = [rng.randrange(M) for _ in range(nb)]
+        if na and nb and trial % 3 == 0:
+            wb[0] = (M - wa[0] + rng.randrange(-3, 4)) % M          # a pair straddling 0
+        W = rng.choice([0, 2, 1 << 40, 1 << 62])
+        brute = band_pairs(expand_values(wa, M), expand_values(wb, M), M, W)
+        assert band_pairs_sorted(wa, wb, W) == brute
+
+
 def test_recombine_vectorised_equals_loop():
     rng = random.Random(21)
     M = 1 << 62
