@@ -101,8 +101,9 @@ typedef struct {
     uint64_t verified;          /* candidates proven to divide p                             */
     double   max_rel_residual;  /* max_i |p(z_i)| / sum_k |a_k||z_i|^k after the polish       */
     double   max_root_err;      /* largest inclusion radius                                  */
-    double   stage_us[8];       /* validate+roots, weights, enumerate count+scans, enumerate scatter,
-                                   match, verify+atoms, device total, host total (microseconds) */
+    double   stage_us[8];       /* validate+roots, weights, sorted lists (+ count pass and scans of
+                                   the table match), table scatter, match (table join and/or
+                                   the fused match), verify+atoms, device total, host total (us) */
     uint64_t h2d_bytes;         /* bytes the batch copied host -> device                     */
     uint64_t d2h_bytes;         /* bytes the batch copied device -> host                     */
     uint32_t launches;          /* CUDA kernels the batch launched                           */

@@ -1067,8 +1067,8 @@ cudaError_t run_match(ProbJob* jobs, int np, ProbJob* dev_jobs, HalfJob* dev_hal
         if (e != cudaSuccess) return e;
     }
     if (nF) {
-        e = run_mitm(F.data(), nF, dev_jobs + nT, dev_halves + 2 * nT, s, nT ? nullptr : ev_count);
-        if (!nT && ev_scatter) cudaEventRecord(ev_scatter, s);
+        e = run_mitm(F.data(), nF, dev_jobs + nT, dev_halves + 2 * nT, s, nT ? nullptr : ev_count,
+                     nT ? nullptr : ev_scatter);
         nl += mitm_launches(F.data(), nF);
     } else if (!nT) {
         if (ev_count) cudaEventRecord(ev_count, s);

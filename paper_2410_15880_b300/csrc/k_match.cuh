@@ -115,9 +115,9 @@ size_t mitm_half_bytes(int l);
 void mitm_layout_half(int l, char*& p, HalfJob* h);
 // Build the sorted lists and run k_mitm for the fused problems F[0..nF);
 // dev_mjobs / dev_yjobs hold nF ProbJob / 2*nF HalfJob slots of device memory.
-// ev_lists (if given) is recorded after the sorted lists are built.
+// ev_lists and ev_lists2 (if given) are recorded after the sorted lists are built.
 cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev_yjobs, cudaStream_t s,
-                     cudaEvent_t ev_lists = nullptr);
+                     cudaEvent_t ev_lists = nullptr, cudaEvent_t ev_lists2 = nullptr);
 int mitm_launches(const ProbJob* const* F, int nF);
 
 // Bytes of one problem's buffers for geometry g (uses g.hcap).
@@ -134,7 +134,9 @@ void match_layout(const MatchGeom& g, char* ws, ProbJob* pj);
 // the optimistic cursors (bcount, hcount) and the exact halo counts must be
 // zeroed by the caller.
 // Fused problems (ProbJob::fused) may be mixed in; they run k_mitm after the
-// table problems' join.  *launches (if given) receives the kernel count.
+// table problems' join (with only fused problems, ev_count and ev_scatter are
+// both recorded after their sorted lists are built).  *launches (if given)
+// receives the kernel count.
 cudaError_t run_match(ProbJob* jobs, int np, ProbJob* dev_jobs, HalfJob* dev_halves,
                       HalfJob* host_halves, cudaStream_t s, cudaEvent_t ev_count, cudaEvent_t ev_scatter,
                       int* launches = nullptr);

@@ -43,8 +43,7 @@ constexpr int YM_PER = 16;                                     // merge outputs 
 
 constexpr int MT_THREADS = 1024;
 constexpr int MT_ACAP = 12288;                                 // table-a keys of one unit (mean 8192)
-constexpr int MT_WSLOTS = 320;                                 // private table slots per warp (mean 256) ...
-constexpr int MT_POOL = MT_ACAP - 32 * MT_WSLOTS;              // ... and a shared pool for warps that fill theirs
+constexpr int MT_POOL = MT_ACAP / 8;                           // shared slots for warps that fill their own
 constexpr int MT_NBL = 13;                                     // at most 2^13 bins per unit
 constexpr int MT_RUNS = 1024;                                  // runs per half
 constexpr int MT_BM_LOG = 18;                                  // occupancy bitmap: about 2^18 cells per unit
@@ -249,6 +248,9 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
     const int gid = warp * (32 / GL) + gi, NG = (int)blockDim.x / GL;
     const uint32_t gbits = (1u << GL) - 1u;
     const uint32_t lma = Na - 1u, lmb = Nb - 1u;                      // low-list masks (l <= 21)
+    // table slots: the warps holding runs of half a share all but MT_POOL slots equally
+    const int nwa = (RA + (32 / GL) - 1) / (32 / GL) < nwarps ? (RA + (32 / GL) - 1) / (32 / GL) : nwarps;
+    const uint32_t wslots = (uint32_t)((MT_ACAP - MT_POOL) / nwa);
     uint2* wq = queue + warp * MT_QCAP;
 
     if (threadIdx.x < n_a) { wa[threadIdx.x] = P.w_a[threadIdx.x]; w2a[threadIdx.x] = P.w2_a[threadIdx.x]; }
@@ -287,12 +289,11 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
             }
         }
     };
-    // Does a cell within wf of fingerprint position pb (-wf <= pb < 2^(nbl+16) + wf) hold a key?
+    // Does the cell of fingerprint position pb (-wf <= pb < 2^(nbl+16) + wf) hold a
+    // table-a key within wf?  (Each key marks every cell its window touches.)
     auto maybe = [&](int pb) -> bool {
-        const uint32_t q0 = (uint32_t)(pb + coff - wf) >> rsh, q1 = (uint32_t)(pb + coff + wf) >> rsh;
-        const uint32_t w0 = bm[q0 >> 5];
-        const uint32_t w1 = (q1 >> 5) == (q0 >> 5) ? w0 : bm[q1 >> 5];
-        return (((w0 >> (q0 & 31)) | (w1 >> (q1 & 31))) & 1u) != 0u;
+        const uint32_t q = (uint32_t)(pb + coff) >> rsh;
+        return ((bm[q >> 5] >> (q & 31)) & 1u) != 0u;
     };
     // The table-a keys of the bins around pb: fingerprints within wf are re-checked exactly.
     auto scan_bins = [&](int pb, uint32_t mb) {
@@ -382,22 +383,23 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
                     const uint32_t cnt = __popc((bal >> gsh) & gbits);
                     const uint32_t tot = __popc(bal);
                     uint32_t slot;
-                    if (wused + tot <= (uint32_t)MT_WSLOTS) {            // the warp's own slots
-                        slot = (uint32_t)warp * MT_WSLOTS + wused + __popc(bal & lt);
+                    if (wused + tot <= wslots) {                          // the warp's own slots
+                        slot = MT_POOL + (uint32_t)warp * wslots + wused + __popc(bal & lt);
                         wused += tot;
                     } else {                                              // the shared pool
                         uint32_t pbase = 0;
                         if (lane == 0) pbase = atomicAdd(&s_count, tot);
                         pbase = __shfl_sync(0xffffffffu, pbase, 0) + __popc(bal & lt);
-                        slot = pbase < (uint32_t)MT_POOL ? 32u * MT_WSLOTS + pbase : (uint32_t)MT_ACAP;
+                        slot = pbase < (uint32_t)MT_POOL ? pbase : (uint32_t)MT_ACAP;
                     }
                     if (in && slot < (uint32_t)MT_ACAP) {
                         const uint32_t pv = (uint32_t)(rel >> fsh);
                         fpr[slot] = (uint16_t)pv;
                         msk[slot] = ((uint32_t)run << la) | ((uint32_t)y & lma);
                         nxt[slot] = (uint16_t)atomicExch(&head[pv >> 16], slot);
-                        const uint32_t q = (pv + (uint32_t)coff) >> rsh;
-                        atomicOr(&bm[q >> 5], 1u << (q & 31));
+                        const uint32_t q0 = (pv + (uint32_t)(coff - wf)) >> rsh, q1 = (pv + (uint32_t)(coff + wf)) >> rsh;
+                        atomicOr(&bm[q0 >> 5], 1u << (q0 & 31));
+                        if (q1 != q0) atomicOr(&bm[q1 >> 5], 1u << (q1 & 31));
                     }
                     t += cnt;
                     act = act && cnt == (uint32_t)GL;
@@ -524,7 +526,7 @@ int mitm_launches(const ProbJob* const* F, int nF) {
 }
 
 cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev_yjobs, cudaStream_t s,
-                     cudaEvent_t ev_lists) {
+                     cudaEvent_t ev_lists, cudaEvent_t ev_lists2) {
     static_assert(sizeof(MitmJob) <= sizeof(ProbJob), "MitmJob must fit a ProbJob slot");
     static_assert(sizeof(YJob) <= sizeof(HalfJob), "YJob must fit a HalfJob slot");
     if (nF <= 0) return cudaSuccess;
@@ -560,6 +562,7 @@ cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev
         k_ymerge<<<nh * cpl, YM_THREADS, 0, s>>>(d_yj, i, cpl);
     }
     if (ev_lists) cudaEventRecord(ev_lists, s);
+    if (ev_lists2) cudaEventRecord(ev_lists2, s);
     std::vector<MitmJob> mj(nF);
     int ctas = 0;
     for (int i = 0; i < nF; ++i) {
