@@ -47,7 +47,7 @@ constexpr int MT_POOL = MT_ACAP / 8;                           // shared slots f
 constexpr int MT_NBL = 13;                                     // at most 2^13 bins per unit
 constexpr int MT_RUNS = 1024;                                  // runs per half
 constexpr int MT_BM_LOG = 18;                                  // occupancy bitmap: about 2^18 cells per unit
-constexpr int MT_BMW = (1 << (MT_BM_LOG - 5)) + 2;             // + margin cells on both sides
+constexpr int MT_BMW = (1 << (MT_BM_LOG - 5)) + 4;             // + margin cells on both sides (16-byte multiple)
 constexpr int MT_QCAP = 64;                                    // deferred lookups per warp
 constexpr int GL = 8;                                          // lanes walking one run together
 constexpr uint32_t MT_NIL = 0xffffffffu;
@@ -55,7 +55,6 @@ constexpr size_t MT_SMEM = (size_t)MT_ACAP * (4 + 2 + 2) + ((size_t)4 << MT_NBL)
                            (size_t)MT_RUNS * (8 + 4 + 4) * 2 + (size_t)(MT_THREADS / 32) * MT_QCAP * 8;
 
 __device__ __forceinline__ uint64_t mt_lowmask(int h) { return h ? (~0ull >> (64 - h)) : 0ull; }
-__device__ __forceinline__ int mt_pad(int i) { return i + (i >> 5); }
 
 __device__ __forceinline__ uint32_t lower_bound_keys(const uint64_t* K, uint32_t n, uint64_t v) {
     uint32_t lo = 0, hi = n;
@@ -351,32 +350,29 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
 
     for (uint32_t k = k0; k < k1; ++k) {
         const uint64_t lo = (uint64_t)k << su;
-        for (int b = threadIdx.x; b < nbins; b += blockDim.x) head[b] = MT_NIL;
-        for (int b = threadIdx.x; b < nbmw; b += blockDim.x) bm[b] = 0u;
+        {   // reset the table heads and the bitmap with 16-byte stores
+            uint4* h4 = reinterpret_cast<uint4*>(head);
+            for (int b = threadIdx.x; b < (nbins >> 2); b += blockDim.x) h4[b] = make_uint4(MT_NIL, MT_NIL, MT_NIL, MT_NIL);
+            uint4* b4 = reinterpret_cast<uint4*>(bm);
+            for (int b = threadIdx.x; b < ((nbmw + 3) >> 2); b += blockDim.x) b4[b] = make_uint4(0u, 0u, 0u, 0u);
+        }
         if (threadIdx.x == 0) s_count = 0u;
         __syncthreads();
         // ---- table a: every key of the unit.  Groups of GL lanes walk one run each
-        // (GL consecutive keys per step); a group whose run leaves the unit takes the
-        // next run from a CTA-wide pool.  One slot reservation per warp step.
-        // Group j of GL lanes walks runs j, j + NG, ... (NG groups per CTA), GL consecutive
-        // keys per step with three steps of loads in flight; the warp steps until its
-        // groups' runs leave the unit.
+        // (GL consecutive keys per step, a ring of four chunks in flight); the warp
+        // steps until its groups' runs leave the unit.
         {
             uint32_t wused = 0;                                          // warp-uniform
             for (int run = gid; run - gi < RA; run += NG) {
                 bool act = run < RA;
-                uint64_t xl = 0, y0 = 0, y1 = 0, y2 = 0, y3 = 0;
-                uint32_t jj = 0, t = 0;
-                if (act) {
-                    xl = xa[run] - lo; jj = j0a[run]; t = ta[run];
-                    const uint64_t* Yr = Ya;
-                    y0 = t + gl < Na ? Yr[(jj + t + gl) & (Na - 1)] : 0ull;
-                    y1 = t + GL + gl < Na ? Yr[(jj + t + GL + gl) & (Na - 1)] : 0ull;
-                    y2 = t + 2 * GL + gl < Na ? Yr[(jj + t + 2 * GL + gl) & (Na - 1)] : 0ull;
-                    y3 = t + 3 * GL + gl < Na ? Yr[(jj + t + 3 * GL + gl) & (Na - 1)] : 0ull;
-                }
-                while (__any_sync(0xffffffffu, act)) {
-                    const uint64_t y = y0;
+                const int rr = act ? run : 0;
+                const uint64_t xl = xa[rr] - lo;
+                const uint32_t jj = j0a[rr];
+                uint32_t t = act ? ta[rr] : 0u;
+                // chunks are read unconditionally: the index is taken modulo Na
+                uint64_t y0 = Ya[(jj + t + gl) & lma], y1 = Ya[(jj + t + GL + gl) & lma];
+                uint64_t y2 = Ya[(jj + t + 2 * GL + gl) & lma], y3 = Ya[(jj + t + 3 * GL + gl) & lma];
+                auto step = [&](uint64_t& y) {
                     const uint64_t rel = xl + (y & ~(uint64_t)lma);
                     const bool in = act && t + gl < Na && rel < U;
                     const uint32_t bal = __ballot_sync(0xffffffffu, in);
@@ -403,9 +399,17 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
                     }
                     t += cnt;
                     act = act && cnt == (uint32_t)GL;
-                    y0 = y1; y1 = y2; y2 = y3;
-                    const uint32_t i3 = t + 3 * GL + gl;
-                    y3 = act && i3 < Na ? Ya[(jj + i3) & (Na - 1)] : 0ull;
+                    y = Ya[(jj + t + 3 * GL + gl) & lma];                 // the chunk four ahead
+                };
+                for (;;) {
+                    if (!__any_sync(0xffffffffu, act)) break;
+                    step(y0);
+                    if (!__any_sync(0xffffffffu, act)) break;
+                    step(y1);
+                    if (!__any_sync(0xffffffffu, act)) break;
+                    step(y2);
+                    if (!__any_sync(0xffffffffu, act)) break;
+                    step(y3);
                 }
                 if (gl == 0 && run < RA) ta[run] = t;
             }
@@ -422,33 +426,47 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
         const uint64_t lob = lo - base;                                   // key - lo = (key - base) - lob
         for (int run = gid; run - gi < RB; run += NG) {
             bool act = run < RB;
-            bool fnd = !act;
-            uint64_t xbb = 0, y0 = 0, y1 = 0, y2 = 0, y3 = 0;
-            uint32_t jj = 0, t = 0, nt = 0;
-            if (act) {
-                xbb = xb[run] - base; jj = j0b[run]; t = tb[run]; nt = t;
-                y0 = t + gl < Nb ? Yb[(jj + t + gl) & (Nb - 1)] : 0ull;
-                y1 = t + GL + gl < Nb ? Yb[(jj + t + GL + gl) & (Nb - 1)] : 0ull;
-                y2 = t + 2 * GL + gl < Nb ? Yb[(jj + t + 2 * GL + gl) & (Nb - 1)] : 0ull;
-                y3 = t + 3 * GL + gl < Nb ? Yb[(jj + t + 3 * GL + gl) & (Nb - 1)] : 0ull;
-            }
-            while (__any_sync(0xffffffffu, act)) {
-                const uint64_t y = y0;
-                const bool valid = act && t + gl < Nb;
+            const int rr = act ? run : 0;
+            const uint64_t xbb = xb[rr] - base;
+            const uint32_t jj = j0b[rr];
+            const uint32_t t0 = act ? tb[rr] : 0u;
+            uint32_t t = t0;
+            uint64_t y0 = Yb[(jj + t + gl) & lmb], y1 = Yb[(jj + t + GL + gl) & lmb];
+            uint64_t y2 = Yb[(jj + t + 2 * GL + gl) & lmb], y3 = Yb[(jj + t + 3 * GL + gl) & lmb];
+            auto step = [&](uint64_t& y) {
                 const uint64_t rk = xbb + (y & ~(uint64_t)lmb);
-                const bool in = valid && rk < span;
+                const bool in = act && t + gl < Nb && rk < span;
                 const int pb = (int)((long long)(rk - lob) >> fsh);
                 enqueue(in && maybe(pb), pb, ((uint32_t)run << lb) | ((uint32_t)y & lmb));
                 const uint32_t cnt = __popc((__ballot_sync(0xffffffffu, in) >> gsh) & gbits);
-                const uint32_t cn = __popc((__ballot_sync(0xffffffffu, valid && rk < nxtb) >> gsh) & gbits);
-                if (!fnd) { nt += cn; fnd = cn < (uint32_t)GL; }
                 t += cnt;
                 act = act && cnt == (uint32_t)GL;
-                y0 = y1; y1 = y2; y2 = y3;
-                const uint32_t i3 = t + 3 * GL + gl;
-                y3 = act && i3 < Nb ? Yb[(jj + i3) & (Nb - 1)] : 0ull;
+                y = Yb[(jj + t + 3 * GL + gl) & lmb];
+            };
+            for (;;) {
+                if (!__any_sync(0xffffffffu, act)) break;
+                step(y0);
+                if (!__any_sync(0xffffffffu, act)) break;
+                step(y1);
+                if (!__any_sync(0xffffffffu, act)) break;
+                step(y2);
+                if (!__any_sync(0xffffffffu, act)) break;
+                step(y3);
             }
-            if (gl == 0 && run < RB) tb[run] = nt;
+            // next unit's start: the first key >= its lo - Wc, i.e. with key - base >= nxtb;
+            // those keys close the stretch [t0, t), so look back from its end
+            if (gl == 0 && run < RB) {
+                uint32_t nt = t;
+                if (t > t0 && xbb + (Yb[(jj + t - 1) & lmb] & ~(uint64_t)lmb) >= nxtb) {
+                    uint32_t lo_i = t0, hi_i = t - 1;                    // keys in the band: search
+                    while (lo_i < hi_i) {
+                        const uint32_t mid = (lo_i + hi_i) >> 1;
+                        if (xbb + (Yb[(jj + mid) & lmb] & ~(uint64_t)lmb) < nxtb) lo_i = mid + 1; else hi_i = mid;
+                    }
+                    nt = lo_i;
+                }
+                tb[run] = nt;
+            }
         }
         // circular wrap: unit 0 also meets keys of b in [2^64 - Wc, 2^64), the last unit keys in [0, Wc)
         if (k == 0)
