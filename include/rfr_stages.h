@@ -110,7 +110,8 @@ size_t rfr_stage_match_workspace(int n_a, int n_b);
  * dist(y) = min(y, 2^64 - y) (Eq. 9 / Eq. 19 made circular), to
  * cand[0 .. min(count, cap)).  counters (device, uint64 [6]) receive
  * {coarse pairs, pairs within W, pairs also within W2 (= count), trivial
- * pattern seen (1/0), layout overflow (1/0), 0}.  w_a/w2_a hold n_a weights, w_b/w2_b n_b; 0 <= n_a,
+ * pattern seen (1/0), layout overflow (1/0), fingerprint hits of the fused
+ * match (0 for the other matches)}.  w_a/w2_a hold n_a weights, w_b/w2_b n_b; 0 <= n_a,
  * n_b <= 32.  workspace: rfr_stage_match_workspace(n_a, n_b) bytes,
  * 256-byte aligned.  Section 3.3 (RECOMBINE_C's result set).
  * Tables of half b with n_b <= 13 are matched in one shared-memory kernel.
@@ -141,8 +142,10 @@ int rfr_stage_match_exact(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
  * rfr_stage_match uses it by itself for n_a >= 18.  Returns RFR_E_WINDOW if
  * a half has more than 31 elements or the window is too wide for it (about
  * W >= 2^(59 - max(n_a - 13, 2))); counters[4] = 1 when one key range holds
- * more than 16384 keys of half a (clustered keys: use
- * rfr_stage_match_exact).  Section 3.3. */
+ * more than 12288 keys of half a (clustered keys), or when the workspace has
+ * no room for all fingerprint hits (very wide windows; every hit takes 8
+ * bytes beyond rfr_stage_match_workspace, which has room for 2^20): use
+ * rfr_stage_match_exact, or pass more workspace.  Section 3.3. */
 int rfr_stage_match_fused(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
                           const uint64_t* w_b, const uint64_t* w2_b, int n_b,
                           uint64_t window, uint64_t window2,

@@ -844,7 +844,7 @@ static uint64_t default_halo_cap(int n_b, int d1, uint64_t wc) {
 }
 
 size_t match_bytes(const MatchGeom& g) {
-    if (g.fused) return mitm_half_bytes(g.l_a) + mitm_half_bytes(g.l_b);
+    if (g.fused) return mitm_half_bytes(g.l_a) + mitm_half_bytes(g.l_b) + align256(mitm_hit_cap(g) * 8);
     const size_t NB = (size_t)1 << g.d1;
     size_t b = 0;
     b += 2 * align256(((size_t)1 << g.l_a) * 8);
@@ -928,10 +928,13 @@ void match_layout(const MatchGeom& g, char* ws, ProbJob* pj) {
     HalfJob& B = pj->B;
     pj->fused = g.fused ? 1 : 0;
     pj->nbl = g.nbl; pj->slab = g.slab; pj->wf = g.wf;
-    A.kb1 = B.kb1 = nullptr; A.mb0 = A.mb1 = B.mb0 = B.mb1 = nullptr;
+    A.kb1 = B.kb1 = nullptr;
+    pj->hits = nullptr; pj->hcap = 0;
     if (g.fused) {
         mitm_layout_half(g.l_a, p, &A);
         mitm_layout_half(g.l_b, p, &B);
+        pj->hcap = mitm_hit_cap(g);
+        pj->hits = (uint64_t*)take(pj->hcap * 8);
         A.l = g.l_a; B.l = g.l_b;
         A.h = g.n_a; B.h = g.n_b;
         A.neg = 0; B.neg = 1;
@@ -1116,7 +1119,13 @@ extern "C" size_t rfr_stage_match_workspace(int n_a, int n_b) {
     MatchGeom g, go, gf;
     if (!stage_geom(n_a, n_b, 0, &g, false)) return 0;
     if (stage_geom(n_a, n_b, 0, &go, true) && go.bytes > g.bytes) g.bytes = go.bytes;
-    if (stage_geom(n_a, n_b, 0, &gf, true, FUSE_ALWAYS) && gf.bytes > g.bytes) g.bytes = gf.bytes;
+    if (stage_geom(n_a, n_b, 0, &gf, true, FUSE_ALWAYS)) {
+        // room for the fused match's fingerprint hits: up to 2^20 pairs (more hits, at
+        // very wide windows, report counters[4] unless the caller passes more workspace)
+        const int e = n_a + n_b < 20 ? n_a + n_b : 20;
+        const size_t fb = gf.bytes + ((size_t)8 << e);
+        if (fb > g.bytes) g.bytes = fb;
+    }
     // the bucket count only shrinks for wider windows; budget for d1 = MAX_D1 histograms
     const size_t hist_extra = ((size_t)stage_ctas(n_a) + stage_ctas(n_b)) * ((size_t)1 << MAX_D1) * 4 + 8 * 4096;
     return g.bytes + hist_extra + 2048;
@@ -1143,13 +1152,19 @@ static int stage_match(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
     }
     MatchGeom g;
     if (!stage_geom(n_a, n_b, window, &g, optimistic, fuse)) return RFR_E_WINDOW;
-    if (g.bytes + 2048 > workspace_bytes) return RFR_E_INVALID;
+    const size_t need = g.fused ? g.bytes - align256(mitm_hit_cap(g) * 8) + 8 : g.bytes;   // fused: hits may be fewer
+    if (need + 2048 > workspace_bytes) return RFR_E_INVALID;
     char* base = (char*)workspace;
     ProbJob* dev_job = (ProbJob*)base;
     HalfJob* dev_halves = (HalfJob*)(base + 1024);
     ProbJob pj;
     memset(&pj, 0, sizeof(pj));
     match_layout(g, base + 2048, &pj);
+    if (g.fused) {                         // hits: whatever the workspace holds beyond the lists
+        const size_t used = 2048 + (g.bytes - align256(pj.hcap * 8));
+        const uint64_t room = workspace_bytes > used ? (uint64_t)((workspace_bytes - used) / 8) : 0;
+        if (room < pj.hcap) pj.hcap = room;
+    }
     pj.A.err = pj.B.err = (int*)(counters + 4);
     pj.A.w = w_a; pj.B.w = w_b;
     pj.w_a = w_a; pj.w2_a = w2_a; pj.w_b = w_b; pj.w2_b = w2_b;

@@ -43,10 +43,8 @@ struct HalfJob {
     uint32_t opt_hcap;
     uint32_t* bcount;       // [NB]
     uint32_t* hcount;       // [NB] (half b)
-    // fused match (k_mitm): list-building buffers; ytmp is the first key buffer
-    uint64_t* kb1;          // [2^(l-1)] second key buffer (l > 12)
-    uint32_t* mb0;          // [2^(l-1)] mask buffers
-    uint32_t* mb1;
+    // fused match (k_mitm): list-building buffers; ytmp is the first one
+    uint64_t* kb1;          // [2^(l-1)] second buffer (l > 12)
 };
 
 // One problem's match.
@@ -62,6 +60,8 @@ struct ProbJob {
     unsigned long long* ctr;    // [4]: coarse pairs, pairs within W, candidates (within W and W2, non-trivial), trivial seen
     int fused;              // 1: matched by k_mitm (no tables)
     int nbl, slab, wf;      // k_mitm: bins per unit (log2), units per CTA, fingerprint window
+    uint64_t* hits;         // k_mitm: fingerprint hits awaiting the exact check (count in ctr[5])
+    uint64_t hcap;
 };
 
 // One small problem (n_b <= SMALL_MAX_H) matched entirely in shared memory.
@@ -112,6 +112,7 @@ bool match_geometry(int n_a, int n_b, uint64_t W, int ctas_a, int ctas_b, MatchG
 // Geometry of the fused match; false if the halves or the window do not fit it.
 bool mitm_geometry(int n_a, int n_b, uint64_t W, MatchGeom* g);
 size_t mitm_half_bytes(int l);
+uint64_t mitm_hit_cap(const MatchGeom& g);
 void mitm_layout_half(int l, char*& p, HalfJob* h);
 // Build the sorted lists and run k_mitm for the fused problems F[0..nF);
 // dev_mjobs / dev_yjobs hold nF ProbJob / 2*nF HalfJob slots of device memory.

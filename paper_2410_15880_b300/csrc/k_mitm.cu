@@ -5,7 +5,8 @@
 // elements l..h-1.  The sorted list Y of all 2^l low-subset sums is built
 // once per half by merging (k_ybuild_smem, k_ymerge: the sorted list of a
 // set plus one element is the merge of the list and its copy shifted by the
-// element's weight).  Every high subset x gives one sorted run x + Y
+// element's weight).  The low weights are rounded to multiples of 2^l for
+// the list, so an entry is its sum's high bits with the subset's mask below.  Every high subset x gives one sorted run x + Y
 // (rotated to start at its smallest key), so a half is 2^(h-l) sorted runs.
 //
 // The key space [0, 2^64) is cut into 2^d1 units of width U.  One CTA walks a
@@ -37,7 +38,7 @@ namespace {
 
 constexpr int YS_LOG = 12;                                     // list levels built in shared memory
 constexpr int YS_THREADS = 1024;
-constexpr size_t YS_SMEM = ((size_t)2 << YS_LOG) * (8 + 4);    // two (key, mask) buffers of 2^12
+constexpr size_t YS_SMEM = ((size_t)2 << YS_LOG) * 8;          // two buffers of 2^12 entries
 constexpr int YM_THREADS = 256;
 constexpr int YM_PER = 16;                                     // merge outputs per thread
 
@@ -65,73 +66,70 @@ __device__ __forceinline__ uint32_t lower_bound_keys(const uint64_t* K, uint32_t
     return lo;
 }
 
-// Outputs d0 .. d1-1 of the merge of the sorted keys K[0..n) with the sorted
-// sequence B[t] = K[(r + t) mod n] + w (K shifted by w, rotated to its
-// smallest element; equal keys take K first).  n is a power of two.
+// Outputs d0 .. d1-1 of the merge of the sorted entries K[0..n) with the sorted
+// sequence B[t] = K[(r + t) mod n] + c (K shifted by c, rotated to its smallest
+// element; equal entries take K first).  n is a power of two.
 template <class Out>
-__device__ __forceinline__ void merge_range(const uint64_t* __restrict__ K, const uint32_t* __restrict__ M,
-                                            uint32_t n, uint32_t r, uint64_t w, uint32_t bit,
+__device__ __forceinline__ void merge_range(const uint64_t* __restrict__ K, uint32_t n, uint32_t r, uint64_t c,
                                             uint32_t d0, uint32_t d1, Out out) {
     const uint32_t nm = n - 1;
     uint32_t lo = d0 > n ? d0 - n : 0, hi = d0 < n ? d0 : n;
-    while (lo < hi) {                                          // merge path: A's share of the first d0
+    while (lo < hi) {                                          // merge path: K's share of the first d0
         const uint32_t mid = (lo + hi) >> 1;
-        if (K[mid] <= K[(r + d0 - mid - 1) & nm] + w) lo = mid + 1; else hi = mid;
+        if (K[mid] <= K[(r + d0 - mid - 1) & nm] + c) lo = mid + 1; else hi = mid;
     }
     uint32_t a = lo, b = d0 - lo;
     for (uint32_t d = d0; d < d1; ++d) {
         const uint64_t ka = a < n ? K[a] : 0ull;
-        const uint64_t kb = b < n ? K[(r + b) & nm] + w : 0ull;
-        if (b >= n || (a < n && ka <= kb)) { out(d, ka, M[a]); ++a; }
-        else { out(d, kb, M[(r + b) & nm] | bit); ++b; }
+        const uint64_t kb = b < n ? K[(r + b) & nm] + c : 0ull;
+        if (b >= n || (a < n && ka <= kb)) { out(d, ka); ++a; }
+        else { out(d, kb); ++b; }
     }
+}
+
+// List entries are (S & ~(2^l - 1)) | mask, where S is the sum over the mask of
+// the low weights rounded to multiples of 2^l (so |S - exact sum| <= l * 2^(l-1)).
+// Adding element i to every entry is adding the constant c_i = round(w_i) + 2^i:
+// the mask bits never carry into S.
+__device__ __forceinline__ uint64_t list_step(const uint64_t* w, int neg, int i, int l) {
+    const uint64_t wi = neg ? 0ull - w[i] : w[i];
+    const uint64_t half = l ? 1ull << (l - 1) : 0ull;
+    return ((wi + half) & ~mt_lowmask(l)) + (1ull << i);
 }
 
 struct YJob {
     const uint64_t* w;          // the half's weights (elements 0..l-1 used)
     int l, neg;                 // list bits; keys are negated sums for half b
-    uint64_t* kb[2];            // [2^(l-1)] exact sums, ping-pong (l > YS_LOG only)
-    uint32_t* mb[2];            // [2^(l-1)] their masks
-    uint64_t* ylist;            // [2^l] result: (sum & ~(2^l - 1)) | mask, ascending by sum
+    uint64_t* kb[2];            // [2^(l-1)] intermediate levels, ping-pong (l > YS_LOG only)
+    uint64_t* ylist;            // [2^l] result, ascending
 };
 
 // Levels 0 .. min(l, 12) - 1 of one half's list in shared memory.
 __global__ void __launch_bounds__(YS_THREADS) k_ybuild_smem(const YJob* __restrict__ js) {
     extern __shared__ __align__(16) uint64_t ys_sm[];
     uint64_t* Kb[2] = {ys_sm, ys_sm + (1 << YS_LOG)};
-    uint32_t* M0 = reinterpret_cast<uint32_t*>(ys_sm + (2 << YS_LOG));
-    uint32_t* Mb[2] = {M0, M0 + (1 << YS_LOG)};
     const YJob J = js[blockIdx.x];
     const int s = J.l < YS_LOG ? J.l : YS_LOG;
-    if (threadIdx.x == 0) { Kb[0][0] = 0ull; Mb[0][0] = 0u; }
+    if (threadIdx.x == 0) Kb[0][0] = 0ull;
     __syncthreads();
     for (int i = 0; i < s; ++i) {
         const uint32_t n = 1u << i;
-        const uint64_t w = J.neg ? 0ull - J.w[i] : J.w[i];
+        const uint64_t c = list_step(J.w, J.neg, i, J.l);
         const uint64_t* K = Kb[i & 1];
-        const uint32_t* M = Mb[i & 1];
         uint64_t* KO = Kb[(i + 1) & 1];
-        uint32_t* MO = Mb[(i + 1) & 1];
-        const uint32_t r = lower_bound_keys(K, n, 0ull - w);   // first key that wraps when w is added
+        const uint32_t r = lower_bound_keys(K, n, 0ull - c);   // first entry that wraps when c is added
         const uint32_t tot = 2 * n, per = (tot + blockDim.x - 1) / blockDim.x;
         const uint32_t d0 = min(tot, threadIdx.x * per), d1 = min(tot, d0 + per);
-        if (d0 < d1)
-            merge_range(K, M, n, r, w, 1u << i, d0, d1, [&](uint32_t d, uint64_t k, uint32_t m) { KO[d] = k; MO[d] = m; });
+        if (d0 < d1) merge_range(K, n, r, c, d0, d1, [&](uint32_t d, uint64_t k) { KO[d] = k; });
         __syncthreads();
     }
     const uint64_t* K = Kb[s & 1];
-    const uint32_t* M = Mb[s & 1];
-    const uint32_t ns = 1u << s;
-    if (s == J.l) {
-        const uint64_t lm = mt_lowmask(J.l);
-        for (uint32_t j = threadIdx.x; j < ns; j += blockDim.x) J.ylist[j] = (K[j] & ~lm) | M[j];
-    } else {
-        for (uint32_t j = threadIdx.x; j < ns; j += blockDim.x) { J.kb[0][j] = K[j]; J.mb[0][j] = M[j]; }
-    }
+    uint64_t* out = s == J.l ? J.ylist : J.kb[0];
+    for (uint32_t j = threadIdx.x; j < (1u << s); j += blockDim.x) out[j] = K[j];
 }
 
-// Level i >= 12 (2^i sums -> 2^(i+1)) for every half with l > i; cpl CTAs per
-// half, YM_PER outputs per thread.  The last level writes the packed list.
+// Level i >= 12 (2^i entries -> 2^(i+1)) for every half with l > i; cpl CTAs per
+// half, YM_PER outputs per thread.  The last level writes the list itself.
 __global__ void __launch_bounds__(YM_THREADS) k_ymerge(const YJob* __restrict__ js, int i, int cpl) {
     __shared__ uint32_t s_r;
     const YJob& J = js[blockIdx.x / cpl];
@@ -139,22 +137,14 @@ __global__ void __launch_bounds__(YM_THREADS) k_ymerge(const YJob* __restrict__ 
     const uint32_t n = 1u << i;
     const int p = (i - YS_LOG) & 1;
     const uint64_t* K = J.kb[p];
-    const uint32_t* M = J.mb[p];
-    const uint64_t w = J.neg ? 0ull - J.w[i] : J.w[i];
-    if (threadIdx.x == 0) s_r = lower_bound_keys(K, n, 0ull - w);
+    const uint64_t cs = list_step(J.w, J.neg, i, J.l);
+    if (threadIdx.x == 0) s_r = lower_bound_keys(K, n, 0ull - cs);
     __syncthreads();
     const uint32_t r = s_r;
     const uint32_t per_cta = 2 * n / (uint32_t)cpl;
     const uint32_t d0 = (uint32_t)c * per_cta + threadIdx.x * YM_PER, d1 = d0 + YM_PER;
-    if (i == J.l - 1) {
-        const uint64_t lm = mt_lowmask(J.l);
-        uint64_t* Y = J.ylist;
-        merge_range(K, M, n, r, w, 1u << i, d0, d1, [&](uint32_t d, uint64_t k, uint32_t m) { Y[d] = (k & ~lm) | m; });
-    } else {
-        uint64_t* KO = J.kb[p ^ 1];
-        uint32_t* MO = J.mb[p ^ 1];
-        merge_range(K, M, n, r, w, 1u << i, d0, d1, [&](uint32_t d, uint64_t k, uint32_t m) { KO[d] = k; MO[d] = m; });
-    }
+    uint64_t* KO = i == J.l - 1 ? J.ylist : J.kb[p ^ 1];
+    merge_range(K, n, r, cs, d0, d1, [&](uint32_t d, uint64_t k) { KO[d] = k; });
 }
 
 struct MitmJob {
@@ -169,6 +159,9 @@ struct MitmJob {
     uint64_t cap;
     unsigned long long* ctr;
     int* err;
+    uint64_t* hits;                                           // fingerprint hits: ma | mb << 32
+    unsigned long long* nhits;
+    uint64_t hcap;
 };
 
 __device__ __forceinline__ uint64_t mask_sum(const uint64_t* w, uint32_t m) {
@@ -271,22 +264,11 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
         tb[g] = k0 ? run_lower_bound(Yb, j0, Nb, x, keepb, ((uint64_t)k0 << su) - Wc) : 0u;
     }
 
-    unsigned long long n_coarse = 0, n_pre = 0;
+    // a fingerprint hit: the pair is re-checked exactly by k_mitm_check
     auto hit = [&](uint32_t ma, uint32_t mb) {
-        ++n_coarse;
-        const uint64_t v = mask_sum(wa, ma) + mask_sum(wb, mb);
-        if (circ_dist(v) <= W) {
-            ++n_pre;
-            const uint64_t t2 = mask_sum(w2a, ma) + mask_sum(w2b, mb);
-            if (circ_dist(t2) <= W2) {
-                if (ma == 0 && mb == 0) {
-                    P.ctr[3] = 1ull;
-                } else {
-                    const unsigned long long idx = atomicAdd(&P.ctr[2], 1ull);
-                    if (idx < P.cap) P.cand[idx] = (uint64_t)ma | ((uint64_t)mb << n_a);
-                }
-            }
-        }
+        const unsigned long long idx = atomicAdd(P.nhits, 1ull);
+        if (idx < P.hcap) P.hits[idx] = (uint64_t)ma | ((uint64_t)mb << 32);
+        else atomicExch(P.err, 1);                                   // more hits than room: redo with tables
     };
     // Does the cell of fingerprint position pb (-wf <= pb < 2^(nbl+16) + wf) hold a
     // table-a key within wf?  (Each key marks every cell its window touches.)
@@ -298,11 +280,14 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
     auto scan_bins = [&](int pb, uint32_t mb) {
         const int plo = pb - wf < 0 ? 0 : pb - wf;
         const int phi = pb + wf > (nbins << 16) - 1 ? (nbins << 16) - 1 : pb + wf;
-        for (int bin = plo >> 16; bin <= (phi >> 16); ++bin)
-            for (uint32_t e = head[bin]; e != MT_NIL; e = nxt[e] == 0xffffu ? MT_NIL : nxt[e]) {
+        for (int bin = plo >> 16; bin <= (phi >> 16); ++bin) {
+            uint32_t e = head[bin];
+            for (int steps = 0; e < (uint32_t)MT_ACAP && steps < MT_ACAP; ++steps) {   // lists end in NIL; bounded anyway
                 const int d = ((bin << 16) | (int)fpr[e]) - pb;
                 if (d >= -wf && d <= wf) hit(msk[e], mb);
+                e = nxt[e] == 0xffffu ? MT_NIL : nxt[e];
             }
+        }
     };
     // Warp-uniform: queue the lanes whose lookup may hit; scan 32 queued lookups at a time.
     uint32_t qn = 0;
@@ -479,8 +464,39 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
         drain();
         __syncthreads();
     }
-    if (n_coarse) atomicAdd(&P.ctr[0], n_coarse);
+}
+
+// Exact re-check of the fingerprint hits of problem blockIdx.x / cpl: Tr_1 within
+// W (Eq. 9 / Eq. 19, circular), then Tr_2 within W2, from the two pattern masks.
+__global__ void __launch_bounds__(256) k_mitm_check(const MitmJob* __restrict__ js, int cpl) {
+    __shared__ uint64_t wa[32], w2a[32], wb[32], w2b[32];
+    const MitmJob& P = js[blockIdx.x / cpl];
+    const int c = blockIdx.x % cpl;
+    if (threadIdx.x < P.n_a) { wa[threadIdx.x] = P.w_a[threadIdx.x]; w2a[threadIdx.x] = P.w2_a[threadIdx.x]; }
+    if (threadIdx.x < P.n_b) { wb[threadIdx.x] = P.w_b[threadIdx.x]; w2b[threadIdx.x] = P.w2_b[threadIdx.x]; }
+    __syncthreads();
+    unsigned long long nh = *P.nhits;
+    if (nh > P.hcap) nh = P.hcap;
+    unsigned long long n_pre = 0;
+    for (unsigned long long i = (unsigned long long)c * blockDim.x + threadIdx.x; i < nh; i += (unsigned long long)cpl * blockDim.x) {
+        const uint64_t h = P.hits[i];
+        const uint32_t ma = (uint32_t)h, mb = (uint32_t)(h >> 32);
+        const uint64_t v = mask_sum(wa, ma) + mask_sum(wb, mb);
+        if (circ_dist(v) <= P.W) {
+            ++n_pre;
+            const uint64_t t2 = mask_sum(w2a, ma) + mask_sum(w2b, mb);
+            if (circ_dist(t2) <= P.W2) {
+                if (ma == 0 && mb == 0) {
+                    P.ctr[3] = 1ull;
+                } else {
+                    const unsigned long long idx = atomicAdd(&P.ctr[2], 1ull);
+                    if (idx < P.cap) P.cand[idx] = (uint64_t)ma | ((uint64_t)mb << P.n_a);
+                }
+            }
+        }
+    }
     if (n_pre) atomicAdd(&P.ctr[1], n_pre);
+    if (c == 0 && threadIdx.x == 0) atomicAdd(&P.ctr[0], nh);
 }
 
 bool g_mitm_attr = false;
@@ -495,7 +511,8 @@ bool mitm_geometry(int n_a, int n_b, uint64_t W, MatchGeom* g) {
     int d1 = n_a - 13;
     if (d1 < 2) d1 = 2;
     const int su = 64 - d1;
-    const uint64_t wc = W + (1ull << la) + (1ull << lb) + 2;
+    // keys in the lists carry the rounding of the low weights: <= l * 2^(l-1) per half
+    const uint64_t wc = W + (uint64_t)la * (1ull << (la > 0 ? la - 1 : 0)) + (uint64_t)lb * (1ull << (lb > 0 ? lb - 1 : 0)) + 2;
     if (wc < W) return false;
     // a key's window must touch at most two bins: bin width 2^(su - nbl) > 2 Wc
     int nbl = MT_NBL;
@@ -517,10 +534,20 @@ bool mitm_geometry(int n_a, int n_b, uint64_t W, MatchGeom* g) {
     return true;
 }
 
+// Fingerprint hits of one problem: pairs with |K_a - K_b| below (wf + 1) 2^fsh,
+// expected 2^(n_a + n_b) (2 wf + 3) 2^fsh / 2^64; room for 4x that + 2^16.
+uint64_t mitm_hit_cap(const MatchGeom& g) {
+    const int fsh = (64 - g.d1) - g.nbl - 16;
+    const double e = std::ldexp((double)(2 * g.wf + 3), g.n_a + g.n_b + fsh - 64);
+    const double all = std::ldexp(1.0, g.n_a + g.n_b);
+    const double cap = std::min(all, 4.0 * e + 65536.0);
+    return (uint64_t)cap + 1;
+}
+
 size_t mitm_half_bytes(int l) {
     auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t b = a256((size_t)8 << l);
-    if (l > YS_LOG) b += 2 * a256((size_t)8 << (l - 1)) + 2 * a256((size_t)4 << (l - 1));
+    if (l > YS_LOG) b += 2 * a256((size_t)8 << (l - 1));
     return b;
 }
 
@@ -528,19 +555,16 @@ void mitm_layout_half(int l, char*& p, HalfJob* h) {
     auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~(size_t)255; return q; };
     h->ylist = (uint64_t*)take((size_t)8 << l);
     h->ytmp = h->kb1 = nullptr;
-    h->mb0 = h->mb1 = nullptr;
     if (l > YS_LOG) {
         h->ytmp = (uint64_t*)take((size_t)8 << (l - 1));
         h->kb1 = (uint64_t*)take((size_t)8 << (l - 1));
-        h->mb0 = (uint32_t*)take((size_t)4 << (l - 1));
-        h->mb1 = (uint32_t*)take((size_t)4 << (l - 1));
     }
 }
 
 int mitm_launches(const ProbJob* const* F, int nF) {
     int maxl = 0;
     for (int i = 0; i < nF; ++i) maxl = std::max(maxl, std::max(F[i]->A.l, F[i]->B.l));
-    return nF ? 2 + std::max(0, maxl - YS_LOG) : 0;
+    return nF ? 3 + std::max(0, maxl - YS_LOG) : 0;
 }
 
 cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev_yjobs, cudaStream_t s,
@@ -563,7 +587,6 @@ cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev
             YJob y;
             y.w = h->w; y.l = h->l; y.neg = h->neg;
             y.kb[0] = h->ytmp; y.kb[1] = h->kb1;
-            y.mb[0] = h->mb0; y.mb[1] = h->mb1;
             y.ylist = h->ylist;
             yj.push_back(y);
         }
@@ -594,12 +617,14 @@ cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev
         m.cta_base = ctas;
         m.W = P.W; m.W2 = P.W2; m.Wc = P.Wc;
         m.cand = P.cand; m.cap = P.cap; m.ctr = P.ctr; m.err = P.A.err;
+        m.hits = P.hits; m.nhits = P.ctr + 5; m.hcap = P.hcap;          // counters[5]: fingerprint hits
         ctas += (1 << P.d1) / P.slab;
     }
     MitmJob* d_mj = (MitmJob*)dev_mjobs;
     e = cudaMemcpyAsync(d_mj, mj.data(), sizeof(MitmJob) * nF, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
     k_mitm<<<ctas, MT_THREADS, MT_SMEM, s>>>(d_mj, nF);
+    k_mitm_check<<<nF * 64, 256, 0, s>>>(d_mj, 64);
     return cudaGetLastError();
 }
 
