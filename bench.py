@@ -43,8 +43,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=2000,
                     help="requests of the serving stream (0 = skip the serving leg)")
-    ap.add_argument("--serving-load", type=float, default=0.8,
-                    help="Poisson arrival rate as a fraction of the measured closed-loop capacity")
+    ap.add_argument("--serving-loads", default="0.5,0.8",
+                    help="Poisson arrival rates as fractions of the measured closed-loop capacity")
     ap.add_argument("--root-mode", type=int, default=1,
                     help="0 = FP64 Aberth, 1 = FP32 bulk + FP64 (default)")
     ap.add_argument("--no-autotune", action="store_true", help="use the default match layout")
@@ -168,10 +168,11 @@ def kernel_traffic(name, half_sums):
     return None
 
 
-def serving_leg(device, n_requests, load, max_inflight=3, max_batch=64):
+def serving_leg(device, n_requests, loads, max_inflight=3, max_batch=64):
     """Serving stream (degrees uniform in [20,100], coefficients in [-1000,1000],
-    30 % products): closed-loop capacity first, then Poisson arrivals at
-    `load` x capacity through rfr_submit / rfr_wait; latency = completion -
+    30 % products): closed-loop capacity first (every request submitted at
+    once, so batches are full), then for each load in `loads` Poisson arrivals
+    at load x capacity through rfr_submit / rfr_wait; latency = completion -
     arrival on the host clock."""
     import workloads as W
     from paper_2410_15880_b300 import Context
@@ -180,6 +181,9 @@ def serving_leg(device, n_requests, load, max_inflight=3, max_batch=64):
     gpath = os.path.join(ROOT, "tests", "golden", "cfg4_sample.json")
     if os.path.exists(gpath):
         gold = {g["index"]: g["factors"] for g in json.load(open(gpath))}
+    out = {"requests": len(reqs), "max_inflight": max_inflight, "max_batch": max_batch,
+           "workload": "degrees uniform [20,100], coeffs [-1000,1000], 30% products, Poisson arrivals",
+           "loads": []}
     with Context(device=device, max_inflight=max_inflight, max_batch=max_batch) as srv:
         # warm-up
         for t in [srv.submit(r.coeffs) for r in reqs[:64]]:
@@ -189,42 +193,45 @@ def serving_leg(device, n_requests, load, max_inflight=3, max_batch=64):
         for t in tickets:
             srv.wait(t)
         cap = len(reqs) / (time.perf_counter() - t0)
-        rate = load * cap
-        # open loop: arrivals of the workload rescaled to `rate`
-        scale = reqs[-1].arrival_s / (len(reqs) / rate)
-        arrivals = [r.arrival_s / scale for r in reqs]
-        done_at = [0.0] * len(reqs)
-        results = [None] * len(reqs)
-        tick = [0] * len(reqs)
-        ready = threading.Semaphore(0)
+        out["capacity_polys_per_s"] = cap
+        ok, golden_ok = True, True
+        for load in loads:
+            rate = load * cap
+            # open loop: arrivals of the workload rescaled to `rate`
+            scale = reqs[-1].arrival_s / (len(reqs) / rate)
+            arrivals = [r.arrival_s / scale for r in reqs]
+            done_at = [0.0] * len(reqs)
+            results = [None] * len(reqs)
+            tick = [0] * len(reqs)
+            ready = threading.Semaphore(0)
 
-        def waiter():
-            for i in range(len(reqs)):
-                ready.acquire()
-                results[i] = srv.wait(tick[i])
-                done_at[i] = time.perf_counter()
+            def waiter():
+                for i in range(len(reqs)):
+                    ready.acquire()
+                    results[i] = srv.wait(tick[i])
+                    done_at[i] = time.perf_counter()
 
-        th = threading.Thread(target=waiter)
-        th.start()
-        start = time.perf_counter()
-        for i, r in enumerate(reqs):
-            now = time.perf_counter() - start
-            if arrivals[i] > now:
-                time.sleep(arrivals[i] - now)
-            tick[i] = srv.submit(r.coeffs)
-            ready.release()
-        th.join()
-        makespan = max(done_at) - start
-    lat = sorted((done_at[i] - start - arrivals[i]) * 1e3 for i in range(len(reqs)))
-    q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))]
-    ok = all(x is not None and x.ok for x in results)
-    golden_ok = all(results[i].factors == f for i, f in gold.items() if i < len(results))
-    return {"requests": len(reqs), "load": load, "capacity_polys_per_s": cap, "rate_per_s": rate,
-            "p50_ms": q(0.50), "p99_ms": q(0.99), "max_ms": lat[-1],
-            "throughput_polys_per_s": len(reqs) / makespan, "all_ok": ok,
-            "golden_checked": sum(1 for i in gold if i < len(results)), "golden_ok": golden_ok,
-            "workload": "degrees uniform [20,100], coeffs [-1000,1000], 30% products, Poisson arrivals",
-            "max_inflight": max_inflight, "max_batch": max_batch}
+            th = threading.Thread(target=waiter)
+            th.start()
+            start = time.perf_counter()
+            for i, r in enumerate(reqs):
+                now = time.perf_counter() - start
+                if arrivals[i] > now:
+                    time.sleep(arrivals[i] - now)
+                tick[i] = srv.submit(r.coeffs)
+                ready.release()
+            th.join()
+            makespan = max(done_at) - start
+            lat = sorted((done_at[i] - start - arrivals[i]) * 1e3 for i in range(len(reqs)))
+            q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))]
+            ok = ok and all(x is not None and x.ok for x in results)
+            golden_ok = golden_ok and all(results[i].factors == f for i, f in gold.items() if i < len(results))
+            out["loads"].append({"load": load, "rate_per_s": rate, "p50_ms": q(0.50), "p99_ms": q(0.99),
+                                 "max_ms": lat[-1], "throughput_polys_per_s": len(reqs) / makespan})
+    out["all_ok"] = ok
+    out["golden_checked"] = sum(1 for i in gold if i < len(reqs))
+    out["golden_ok"] = golden_ok
+    return out
 
 
 def cpu_oracle_sample(insts, budget_s=15.0, max_polys=8):
@@ -418,7 +425,7 @@ def main():
         "correct": {"statuses_ok": all(s == 0 for s in statuses), "matches_golden": ok_golden},
     }
     if a.serving_requests > 0 and world == 1:
-        line["serving"] = serving_leg(local, a.serving_requests, a.serving_load)
+        line["serving"] = serving_leg(local, a.serving_requests, [float(x) for x in a.serving_loads.split(",")])
     if not a.no_cpu_baseline:
         n, dt = cpu_oracle_sample(workload(a.config, 0, a.count), budget_s=15.0)
         line["cpu_baseline"] = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -240,9 +240,10 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
     const int gid = warp * (32 / GL) + gi, NG = (int)blockDim.x / GL;
     const uint32_t gbits = (1u << GL) - 1u;
     const uint32_t lma = Na - 1u, lmb = Nb - 1u;                      // low-list masks (l <= 21)
-    // table slots: the warps holding runs of half a share all but MT_POOL slots equally
-    const int nwa = (RA + (32 / GL) - 1) / (32 / GL) < nwarps ? (RA + (32 / GL) - 1) / (32 / GL) : nwarps;
-    const uint32_t wslots = (uint32_t)((MT_ACAP - MT_POOL) / nwa);
+    // table slots: the groups holding a run of half a (RA <= groups, one run each)
+    // share all but MT_POOL slots equally
+    const int gact = RA < (int)blockDim.x / GL ? RA : (int)blockDim.x / GL;
+    const uint32_t gslots = (uint32_t)((MT_ACAP - MT_POOL) / gact);
     uint2* wq = queue + warp * MT_QCAP;
 
     if (threadIdx.x < n_a) { wa[threadIdx.x] = P.w_a[threadIdx.x]; w2a[threadIdx.x] = P.w2_a[threadIdx.x]; }
@@ -291,10 +292,10 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
     };
     // Warp-uniform: queue the lanes whose lookup may hit; scan 32 queued lookups at a time.
     uint32_t qn = 0;
-    auto enqueue = [&](bool need, int pb, uint32_t mb) {
+    auto enqueue = [&](bool need, int pb, uint32_t run_b, uint32_t ylow) {
         const uint32_t qb = __ballot_sync(0xffffffffu, need);
         if (!qb) return;
-        if (need) wq[qn + __popc(qb & lt)] = make_uint2((uint32_t)pb, mb);
+        if (need) wq[qn + __popc(qb & lt)] = make_uint2((uint32_t)pb, (run_b << lb) | (ylow & lmb));
         qn += __popc(qb);
         if (qn >= 32) {
             __syncwarp();
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
             const uint64_t rk = xbb + (y & keepb);
             const bool in = idx < Nb && rk < span;
             const int pb = (int)((long long)(rk - lob) >> fsh);
-            enqueue(in && maybe(pb), pb, ((uint32_t)g << lb) | (uint32_t)(y & ~keepb));
+            enqueue(in && maybe(pb), pb, (uint32_t)g, (uint32_t)y);
             const uint32_t cnt = __popc(__ballot_sync(0xffffffffu, in));
             t += cnt;
             if (cnt < 32) break;
@@ -347,13 +348,15 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
         // (GL consecutive keys per step, a ring of four chunks in flight); the warp
         // steps until its groups' runs leave the unit.
         {
-            uint32_t wused = 0;                                          // warp-uniform
             for (int run = gid; run - gi < RA; run += NG) {
                 bool act = run < RA;
                 const int rr = act ? run : 0;
                 const uint64_t xl = xa[rr] - lo;
                 const uint32_t jj = j0a[rr];
                 uint32_t t = act ? ta[rr] : 0u;
+                const uint32_t tfirst = t;
+                // this group's slots: gslots from gbase; keys beyond them go to the shared pool
+                const uint32_t gbase = MT_POOL + (uint32_t)(act ? gid : 0) * gslots;
                 // chunks are read unconditionally: the index is taken modulo Na
                 uint64_t y0 = Ya[(jj + t + gl) & lma], y1 = Ya[(jj + t + GL + gl) & lma];
                 uint64_t y2 = Ya[(jj + t + 2 * GL + gl) & lma], y3 = Ya[(jj + t + 3 * GL + gl) & lma];
@@ -362,16 +365,14 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
                     const bool in = act && t + gl < Na && rel < U;
                     const uint32_t bal = __ballot_sync(0xffffffffu, in);
                     const uint32_t cnt = __popc((bal >> gsh) & gbits);
-                    const uint32_t tot = __popc(bal);
-                    uint32_t slot;
-                    if (wused + tot <= wslots) {                          // the warp's own slots
-                        slot = MT_POOL + (uint32_t)warp * wslots + wused + __popc(bal & lt);
-                        wused += tot;
-                    } else {                                              // the shared pool
+                    const uint32_t off = t - tfirst + gl;                  // this key's place in the run's stretch
+                    uint32_t slot = gbase + off;
+                    const uint32_t spill = __ballot_sync(0xffffffffu, in && off >= gslots);
+                    if (spill) {                                          // rare: the run overran its slots
                         uint32_t pbase = 0;
-                        if (lane == 0) pbase = atomicAdd(&s_count, tot);
-                        pbase = __shfl_sync(0xffffffffu, pbase, 0) + __popc(bal & lt);
-                        slot = pbase < (uint32_t)MT_POOL ? pbase : (uint32_t)MT_ACAP;
+                        if (lane == 0) pbase = atomicAdd(&s_count, (uint32_t)__popc(spill));
+                        pbase = __shfl_sync(0xffffffffu, pbase, 0) + __popc(spill & lt);
+                        if (in && off >= gslots) slot = pbase < (uint32_t)MT_POOL ? pbase : (uint32_t)MT_ACAP;
                     }
                     if (in && slot < (uint32_t)MT_ACAP) {
                         const uint32_t pv = (uint32_t)(rel >> fsh);
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
                 const uint64_t rk = xbb + (y & ~(uint64_t)lmb);
                 const bool in = act && t + gl < Nb && rk < span;
                 const int pb = (int)((long long)(rk - lob) >> fsh);
-                enqueue(in && maybe(pb), pb, ((uint32_t)run << lb) | ((uint32_t)y & lmb));
+                enqueue(in && maybe(pb), pb, (uint32_t)run, (uint32_t)y);
                 const uint32_t cnt = __popc((__ballot_sync(0xffffffffu, in) >> gsh) & gbits);
                 t += cnt;
                 act = act && cnt == (uint32_t)GL;
