@@ -45,9 +45,9 @@ constexpr int YM_PER = 16;                                     // merge outputs 
 constexpr int MT_THREADS = 1024;
 constexpr int MT_ACAP = 12288;                                 // table-a keys of one unit (mean 8192)
 constexpr int MT_POOL = MT_ACAP / 8;                           // shared slots for warps that fill their own
-constexpr int MT_NBL = 13;                                     // at most 2^13 bins per unit
+constexpr int MT_NBL = 12;                                     // at most 2^12 bins per unit
 constexpr int MT_RUNS = 1024;                                  // runs per half
-constexpr int MT_BM_LOG = 18;                                  // occupancy bitmap: about 2^18 cells per unit
+constexpr int MT_BM_LOG = 19;                                  // occupancy bitmap: about 2^19 cells per unit
 constexpr int MT_BMW = (1 << (MT_BM_LOG - 5)) + 4;             // + margin cells on both sides (16-byte multiple)
 constexpr int MT_QCAP = 64;                                    // deferred lookups per warp
 constexpr int GL = 8;                                          // lanes walking one run together

@@ -1,9 +1,8 @@
 // k_roots.cu — K-a: batched root finder (the "black box" of Section 2).
 //
 // Three kernels: k_aberth (one CTA per polynomial, one thread per root,
-// d <= 128) for steps 1-2; k_polish and k_radius (one warp per 32 roots,
-// spread over the whole GPU, because the double-double work is FP64-bound and
-// independent per root) for steps 3 and 4.
+// d <= 128) for steps 1-2; k_polish and k_radius (one warp per root, the
+// polynomial split over its lanes, spread over the whole GPU) for steps 3 and 4.
 //  1. Starting points from the Newton polygon of p (upper convex hull of
 //     (k, log|a_k|)): for each hull edge of width m, m points on a circle
 //     whose radius is the edge's geometric-mean root modulus (Bini 1996).
@@ -117,18 +116,6 @@ __device__ bool aberth(const T* a, int d, cx<T>* z, int max_iter, int* s_flag) {
     return false;
 }
 
-// p(Z) in double-double (|z| <= 1) or P(W), W = 1/Z (|z| > 1).
-__device__ cdd eval_dd(const double* a, int d, cdd Z, bool reversed) {
-    if (!reversed) {
-        cdd P = cdd_make(a[d], 0.0);
-        for (int k = d - 1; k >= 0; --k) P = cdd_add_d(cdd_mul(P, Z), a[k]);
-        return P;
-    }
-    cdd P = cdd_make(a[0], 0.0);
-    for (int k = 1; k <= d; ++k) P = cdd_add_d(cdd_mul(P, Z), a[k]);
-    return P;
-}
-
 // Kernel 1: Aberth iterations, one CTA per polynomial.  Writes the FP64
 // approximations to roots[.., 0] / roots[.., 2] and the convergence status.
 __global__ void __launch_bounds__(DMAX)
@@ -153,7 +140,11 @@ k_aberth(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees
     for (int k = i; k <= d; k += blockDim.x) { a[k] = (double)c[k]; af[k] = (float)c[k]; }
     __syncthreads();
 
-    // Newton polygon: upper hull of (k, log2|a_k|) over a_k != 0.
+    // Newton polygon: upper hull of (k, log2|a_k|) over a_k != 0.  The starting
+    // points only steer the iteration, so the logs are taken once, in FP32.
+    __shared__ float la[DMAX + 1];
+    for (int k = i; k <= d; k += blockDim.x) la[k] = a[k] != 0.0 ? log2f(fabsf(af[k])) : 0.f;
+    __syncthreads();
     if (i == 0) {
         int km = 0;
         while (km < d && a[km] == 0.0) ++km;
@@ -161,12 +152,11 @@ k_aberth(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees
         int h = 0;
         for (int k = km; k <= d; ++k) {
             if (a[k] == 0.0) continue;
-            double yk = log2(fabs(a[k]));
+            const float yk = la[k];
             while (h >= 2) {
-                int o = hull[h - 2], p = hull[h - 1];
-                double yo = log2(fabs(a[o])), yp = log2(fabs(a[p]));
-                double cr = (double)(p - o) * (yk - yo) - (yp - yo) * (double)(k - o);
-                if (cr >= 0.0) --h; else break;
+                const int o = hull[h - 2], q = hull[h - 1];
+                const float cr = (float)(q - o) * (yk - la[o]) - (la[q] - la[o]) * (float)(k - o);
+                if (cr >= 0.f) --h; else break;
             }
             hull[h++] = k;
         }
@@ -178,11 +168,11 @@ k_aberth(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees
         if (i >= kmin) {
             int e = 0;
             while (e + 1 < nhull - 1 && hull[e + 1] <= i) ++e;
-            int k0 = hull[e], k1 = hull[e + 1], m = k1 - k0, j = i - k0;
-            double u = exp2((log2(fabs(a[k0])) - log2(fabs(a[k1]))) / (double)m);
-            double s, co;
-            sincospi(2.0 * ((double)j + 0.25) / (double)m + 0.22 * (double)e + 0.13, &s, &co);
-            z0 = cxm<double>(u * co, u * s);
+            const int k0 = hull[e], k1 = hull[e + 1], m = k1 - k0, j = i - k0;
+            const float u = exp2f((la[k0] - la[k1]) / (float)m);
+            float sn, cs;
+            sincospif(2.f * ((float)j + 0.25f) / (float)m + 0.22f * (float)e + 0.13f, &sn, &cs);
+            z0 = cxm<double>((double)(u * cs), (double)(u * sn));
         }
         z[i] = z0;
         zf[i] = cxm<float>((float)z0.x, (float)z0.y);
@@ -209,117 +199,191 @@ k_aberth(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees
     }
 }
 
-// One warp per 32 roots of one polynomial: blockIdx.x = problem * 4 + chunk.
-constexpr int CHUNKS = DMAX / 32;
-struct RootSlot { int prob, d, i, chunk; };
-__device__ __forceinline__ bool root_slot(const int32_t* degrees, const int32_t* status, RootSlot* r) {
-    r->prob = blockIdx.x / CHUNKS;
-    r->chunk = blockIdx.x % CHUNKS;
+// Steps 3 and 4 take SL = 4 lanes per root, RPC roots of one polynomial per
+// CTA: blockIdx.x = problem * (DMAX / RPC) + chunk.  A polynomial is evaluated
+// by a split Horner scheme: lane l of a root sums the B = ceil((d+1)/SL)
+// coefficients k in [lB, lB + B) as q_l(z) = sum a_k z^(k - lB) (Horner), and
+// a shuffle tree forms p(z) = sum_l z^(lB) q_l(z) with the powers z^(sB),
+// s = 1, 2.  The chain is about d / 4 steps and the total work stays about d
+// steps per root (the FP64 rate of the part, not latency, is the limit).
+constexpr int SL = 4;                         // lanes per root
+constexpr int RPC = 32;                       // roots per CTA (RPC * SL threads)
+constexpr int RCHUNKS = DMAX / RPC;
+struct RootWarp { int prob, d, i, lane; };
+__device__ __forceinline__ bool root_warp(const int32_t* degrees, const int32_t* status, RootWarp* r) {
+    r->prob = blockIdx.x / RCHUNKS;
     r->d = degrees[r->prob];
-    r->i = r->chunk * 32 + threadIdx.x;
+    r->lane = threadIdx.x % SL;
+    r->i = (blockIdx.x % RCHUNKS) * RPC + (int)threadIdx.x / SL;
     const int st = status[r->prob];
-    return (st == RFR_OK || st == RFR_SF_SUSPECT) && r->d >= 1 && r->d <= DMAX;
+    return (st == RFR_OK || st == RFR_SF_SUSPECT) && r->d >= 1 && r->d <= DMAX &&
+           (blockIdx.x % RCHUNKS) * RPC < r->d;
+}
+
+__device__ __forceinline__ cdd shfl_down_cdd(cdd v, int s) {
+    v.re.hi = __shfl_down_sync(0xffffffffu, v.re.hi, s, SL);
+    v.re.lo = __shfl_down_sync(0xffffffffu, v.re.lo, s, SL);
+    v.im.hi = __shfl_down_sync(0xffffffffu, v.im.hi, s, SL);
+    v.im.lo = __shfl_down_sync(0xffffffffu, v.im.lo, s, SL);
+    return v;
+}
+
+// sum_{k=0}^{n} c(k) Z^k in double-double, split over the root's SL lanes; its
+// lane 0 returns it.
+template <class Coef>
+__device__ cdd warp_poly_dd(int n, cdd Z, Coef c) {
+    const int lane = threadIdx.x % SL, B = (n + SL) / SL, k0 = lane * B;
+    const int k1 = k0 + B - 1 < n ? k0 + B - 1 : n;
+    cdd q = cdd_make(0.0, 0.0);
+    if (k0 <= n) {
+        q = cdd_make(c(k1), 0.0);
+        for (int k = k1 - 1; k >= k0; --k) q = cdd_add_d(cdd_mul(q, Z), c(k));
+    }
+    cdd zp = Z;
+    for (int t = 1; t < B; ++t) zp = cdd_mul(zp, Z);
+    for (int s = 1; s < SL; s <<= 1) {
+        const cdd o = shfl_down_cdd(q, s);
+        if ((lane & (2 * s - 1)) == 0) q = cdd_add(q, cdd_mul(zp, o));
+        zp = cdd_mul(zp, zp);
+    }
+    return q;
+}
+
+// The same in FP64 complex arithmetic.
+template <class Coef>
+__device__ cx<double> warp_poly_c(int n, cx<double> z, Coef c) {
+    const int lane = threadIdx.x % SL, B = (n + SL) / SL, k0 = lane * B;
+    const int k1 = k0 + B - 1 < n ? k0 + B - 1 : n;
+    cx<double> q = cxm<double>(0.0, 0.0);
+    if (k0 <= n) {
+        q = cxm<double>(c(k1), 0.0);
+        for (int k = k1 - 1; k >= k0; --k) q = q * z + cxm<double>(c(k), 0.0);
+    }
+    cx<double> zp = z;
+    for (int t = 1; t < B; ++t) zp = zp * z;
+    for (int s = 1; s < SL; s <<= 1) {
+        cx<double> o;
+        o.x = __shfl_down_sync(0xffffffffu, q.x, s, SL);
+        o.y = __shfl_down_sync(0xffffffffu, q.y, s, SL);
+        if ((lane & (2 * s - 1)) == 0) q = q + zp * o;
+        zp = zp * zp;
+    }
+    return q;
+}
+
+// sum_{k=0}^{n} c(k) r^k for real r >= 0, split the same way.
+template <class Coef>
+__device__ double warp_poly_r(int n, double r, Coef c) {
+    const int lane = threadIdx.x % SL, B = (n + SL) / SL, k0 = lane * B;
+    const int k1 = k0 + B - 1 < n ? k0 + B - 1 : n;
+    double q = 0.0;
+    if (k0 <= n) {
+        q = c(k1);
+        for (int k = k1 - 1; k >= k0; --k) q = q * r + c(k);
+    }
+    double rp = r;
+    for (int t = 1; t < B; ++t) rp *= r;
+    for (int s = 1; s < SL; s <<= 1) {
+        const double o = __shfl_down_sync(0xffffffffu, q, s, SL);
+        if ((lane & (2 * s - 1)) == 0) q += rp * o;
+        rp *= rp;
+    }
+    return q;
 }
 
 // Kernel 2: one Newton step per root with p evaluated in double-double (the
 // correction itself in FP64), so each root becomes a DD value.
-__global__ void __launch_bounds__(32)
+__global__ void __launch_bounds__(RPC * SL)
 k_polish(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees,
          const int32_t* __restrict__ status, double* __restrict__ roots) {
     __shared__ double a[DMAX + 1];
-    RootSlot R;
-    if (!root_slot(degrees, status, &R)) return;
+    RootWarp R;
+    if (!root_warp(degrees, status, &R)) return;              // uniform over the CTA
     const int d = R.d, i = R.i;
-    if (R.chunk * 32 >= d) return;
     const int64_t* c = coeffs + (size_t)R.prob * LDC;
-    for (int k = threadIdx.x; k <= d; k += 32) a[k] = (double)c[k];
-    __syncwarp();
-    if (i >= d) return;
-    double* out = roots + ((size_t)R.prob * DMAX + i) * 4;
+    for (int k = threadIdx.x; k <= d; k += blockDim.x) a[k] = (double)c[k];
+    __syncthreads();
+    // lanes of roots past the degree compute on the last root and write nothing
+    // (every lane of the warp takes part in the shuffles)
+    const bool live = i < d;
+    double* out = roots + ((size_t)R.prob * DMAX + (live ? i : d - 1)) * 4;
     cdd Z = cdd_make(out[0], out[2]);
     // one Newton step from the FP64 Aberth root (error ~1e-16 |z|) squares the
     // error; the inclusion radius computed afterwards certifies what it reached
-    for (int it = 0; it < 1; ++it) {
-        cx<double> zh = cxm<double>(Z.re.hi, Z.im.hi);
-        bool rev = cabsv(zh) > 1.0;
-        cx<double> N;
-        if (!rev) {
-            cdd P = eval_dd(a, d, Z, false);
-            cx<double> p = cxm<double>(a[d], 0), dp = cxm<double>(0, 0);
-            for (int k = d - 1; k >= 0; --k) { dp = dp * zh + p; p = p * zh + cxm<double>(a[k], 0); }
-            N = cdivv(cxm<double>(P.re.hi, P.im.hi), dp);
-        } else {
-            cdd W = cdd_inv(Z);
-            cdd P = eval_dd(a, d, W, true);
-            cx<double> wh = cxm<double>(W.re.hi, W.im.hi);
-            cx<double> Pp = cxm<double>(a[0], 0), dP = cxm<double>(0, 0);
-            for (int k = 1; k <= d; ++k) { dP = dP * wh + Pp; Pp = Pp * wh + cxm<double>(a[k], 0); }
-            cx<double> Ph = cxm<double>(P.re.hi, P.im.hi);
-            N = cdivv(zh * Ph, cscale(Ph, (double)d) - wh * dP);
-        }
+    const cx<double> zh = cxm<double>(Z.re.hi, Z.im.hi);
+    const bool rev = cabsv(zh) > 1.0;
+    // |z| > 1: P(w) = w^d p(1/w) = sum_m a_{d-m} w^m at w = 1/z.  The evaluation
+    // is the same call either way (the lanes of a warp hold different roots).
+    const cdd X = rev ? cdd_inv(Z) : Z;
+    const cx<double> xh = cxm<double>(X.re.hi, X.im.hi);
+    const cdd P = warp_poly_dd(d, X, [&](int k) { return a[rev ? d - k : k]; });
+    const cx<double> dP = warp_poly_c(d - 1, xh, [&](int m) { return (double)(m + 1) * a[rev ? d - m - 1 : m + 1]; });
+    const cx<double> Ph = cxm<double>(P.re.hi, P.im.hi);
+    cx<double> N = rev ? cdivv(zh * Ph, cscale(Ph, (double)d) - xh * dP) : cdivv(Ph, dP);
+    if (R.lane == 0 && live) {
         if (!(cabsv(N) < 1e300)) {                              // degenerate: plain FP64 Newton ratio
             bool noise;
             N = newton_ratio<double>(a, d, zh, &noise);
         }
         Z.re = dd_add_d(Z.re, -N.x);
         Z.im = dd_add_d(Z.im, -N.y);
+        out[0] = Z.re.hi; out[1] = Z.re.lo; out[2] = Z.im.hi; out[3] = Z.im.lo;
     }
-    out[0] = Z.re.hi; out[1] = Z.re.lo; out[2] = Z.im.hi; out[3] = Z.im.lo;
 }
 
 // Kernel 3: inclusion radius r_i = d |p(z_i)| / prod_{j != i} |z_i - z_j| with
 // |p(z_i)| from a double-double evaluation plus its error bound.
-__global__ void __launch_bounds__(32)
+__global__ void __launch_bounds__(RPC * SL)
 k_radius(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees,
          const int32_t* __restrict__ status, const double* __restrict__ roots,
          double* __restrict__ radius) {
     __shared__ double a[DMAX + 1];
     __shared__ cx<double> z[DMAX];
-    RootSlot R;
-    if (!root_slot(degrees, status, &R)) return;
+    RootWarp R;
+    if (!root_warp(degrees, status, &R)) return;              // uniform over the CTA
     const int d = R.d, i = R.i;
-    if (R.chunk * 32 >= d) return;
     const int64_t* c = coeffs + (size_t)R.prob * LDC;
     const double* Rt = roots + (size_t)R.prob * DMAX * 4;
-    for (int k = threadIdx.x; k <= d; k += 32) a[k] = (double)c[k];
-    for (int k = threadIdx.x; k < d; k += 32) z[k] = cxm<double>(Rt[4 * k], Rt[4 * k + 2]);
-    __syncwarp();
-    if (i >= d) return;
-    const cdd Z = {{Rt[4 * i], Rt[4 * i + 1]}, {Rt[4 * i + 2], Rt[4 * i + 3]}};
-    const cx<double> zh = z[i];
+    for (int k = threadIdx.x; k <= d; k += blockDim.x) a[k] = (double)c[k];
+    for (int k = threadIdx.x; k < d; k += blockDim.x) z[k] = cxm<double>(Rt[4 * k], Rt[4 * k + 2]);
+    __syncthreads();
+    // lanes of roots past the degree compute on the last root and write nothing
+    // (every lane of the warp takes part in the shuffles)
+    const bool live = i < d;
+    const int ii = live ? i : d - 1;
+    const cdd Z = {{Rt[4 * ii], Rt[4 * ii + 1]}, {Rt[4 * ii + 2], Rt[4 * ii + 3]}};
+    const cx<double> zh = z[ii];
     const double az = cabsv(zh);
     const bool rev = az > 1.0;
-    double lp;
-    if (!rev) {
-        cdd P = eval_dd(a, d, Z, false);
-        double mag = 0.0;
-        for (int k = d; k >= 0; --k) mag = mag * az + fabs(a[k]);
-        double pv = hypot(P.re.hi, P.im.hi);
-        double err = (double)(2 * d + 8) * 0x1p-100 * mag;
-        lp = log2(pv + err);
-    } else {
-        cdd W = cdd_inv(Z);
-        cdd P = eval_dd(a, d, W, true);
-        double aw = 1.0 / az, mag = 0.0;
-        for (int k = 0; k <= d; ++k) mag = mag * aw + fabs(a[k]);
-        double pv = hypot(P.re.hi, P.im.hi);
-        double err = (double)(2 * d + 8) * 0x1p-100 * mag;
-        lp = (double)d * log2(az) + log2(pv + err);
-    }
+    // |z| > 1: |p(z)| = |z|^d |P(1/z)| (same call either way, as in k_polish)
+    const cdd X = rev ? cdd_inv(Z) : Z;
+    const cdd P = warp_poly_dd(d, X, [&](int k) { return a[rev ? d - k : k]; });
+    const double mag = warp_poly_r(d, rev ? 1.0 / az : az, [&](int k) { return fabs(a[rev ? d - k : k]); });
+    const double pv = hypot(P.re.hi, P.im.hi);
+    const double err = (double)(2 * d + 8) * 0x1p-100 * mag;
+    const double lp = (rev ? (double)d * log2(az) : 0.0) + log2(pv + err);
     // log2 of prod_{j != i} |z_i - z_j| in FP32 (d <= 128 terms, each with
     // relative error ~1e-7: the sum is within 2e-5 of the exact value,
-    // far inside the 1.01 safety factor below)
+    // far inside the 1.01 safety factor below), lanes over j
     float lprodf = 0.f;
     bool coincide = false;
-    for (int j = 0; j < d; ++j) {
-        if (j == i) continue;
+    for (int j = R.lane; j < d; j += SL) {
+        if (j == ii) continue;
         const float dist = (float)cabsv(zh - z[j]);
         if (!(dist > 0.f)) coincide = true; else lprodf += log2f(dist);
     }
-    const double lprod = (double)lprodf;
-    double r = coincide ? INFINITY : exp2(log2((double)d) + lp - lprod) * 1.01 + 0x1p-96 * az;
-    if (d == 1) r = 0x1p-96 * az + 0x1p-100;
-    radius[(size_t)R.prob * DMAX + i] = r;
+    int co = coincide ? 1 : 0;
+    for (int o = SL / 2; o; o >>= 1) {
+        lprodf += __shfl_xor_sync(0xffffffffu, lprodf, o, SL);
+        co |= __shfl_xor_sync(0xffffffffu, co, o, SL);
+    }
+    coincide = co != 0;
+    if (R.lane == 0 && live) {
+        const double lprod = (double)lprodf;
+        double r = coincide ? INFINITY : exp2(log2((double)d) + lp - lprod) * 1.01 + 0x1p-96 * az;
+        if (d == 1) r = 0x1p-96 * az + 0x1p-100;
+        radius[(size_t)R.prob * DMAX + i] = r;
+    }
 }
 
 }  // namespace rfr
@@ -333,7 +397,7 @@ extern "C" int rfr_stage_roots(const int64_t* coeffs, const int32_t* degrees, in
     if (batch == 0) return RFR_OK;
     cudaStream_t s = (cudaStream_t)stream;
     k_aberth<<<batch, DMAX, 0, s>>>(coeffs, degrees, root_mode, roots, status);
-    k_polish<<<batch * CHUNKS, 32, 0, s>>>(coeffs, degrees, status, roots);
-    k_radius<<<batch * CHUNKS, 32, 0, s>>>(coeffs, degrees, status, roots, radius);
+    k_polish<<<batch * RCHUNKS, RPC * SL, 0, s>>>(coeffs, degrees, status, roots);
+    k_radius<<<batch * RCHUNKS, RPC * SL, 0, s>>>(coeffs, degrees, status, roots, radius);
     return cudaGetLastError() == cudaSuccess ? RFR_OK : RFR_E_CUDA;
 }
