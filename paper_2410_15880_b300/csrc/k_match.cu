@@ -928,7 +928,7 @@ void match_layout(const MatchGeom& g, char* ws, ProbJob* pj) {
     HalfJob& B = pj->B;
     pj->fused = g.fused ? 1 : 0;
     pj->nbl = g.nbl; pj->slab = g.slab; pj->wf = g.wf;
-    A.kb1 = B.kb1 = nullptr;
+    A.kb1 = B.kb1 = nullptr; A.ysplit = B.ysplit = nullptr;
     pj->hits = nullptr; pj->hcap = 0;
     if (g.fused) {
         mitm_layout_half(g.l_a, p, &A);

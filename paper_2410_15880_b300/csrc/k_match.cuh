@@ -45,6 +45,7 @@ struct HalfJob {
     uint32_t* hcount;       // [NB] (half b)
     // fused match (k_mitm): list-building buffers; ytmp is the first one
     uint64_t* kb1;          // [2^(l-1)] second buffer (l > 12)
+    uint32_t* ysplit;       // merge-path tile starts of one level (l > 12)
 };
 
 // One problem's match.

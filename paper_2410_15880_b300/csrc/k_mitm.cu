@@ -102,6 +102,7 @@ struct YJob {
     int l, neg;                 // list bits; keys are negated sums for half b
     uint64_t* kb[2];            // [2^(l-1)] intermediate levels, ping-pong (l > YS_LOG only)
     uint64_t* ylist;            // [2^l] result, ascending
+    uint32_t* splits;           // [2^l / YM_TILE + 2]: a level's tile starts on the merge path, then its rotation
 };
 
 // Levels 0 .. min(l, 12) - 1 of one half's list in shared memory.
@@ -129,22 +130,78 @@ __global__ void __launch_bounds__(YS_THREADS) k_ybuild_smem(const YJob* __restri
 }
 
 // Level i >= 12 (2^i entries -> 2^(i+1)) for every half with l > i; cpl CTAs per
-// half, YM_PER outputs per thread.  The last level writes the list itself.
+// half, each writing a tile of YM_TILE outputs.  The CTA finds where its tile
+// starts and ends on the merge path (two binary searches over the list), reads
+// the two input stretches into shared memory with coalesced loads, merges them
+// there (YM_PER outputs per thread) and writes the tile back coalesced.  The
+// last level writes the list itself.
+constexpr int YM_TILE = YM_THREADS * YM_PER;
+constexpr size_t YM_SMEM = (size_t)2 * YM_TILE * 8;
+
+__device__ __forceinline__ uint32_t merge_split(const uint64_t* __restrict__ K, uint32_t n, uint32_t r,
+                                                uint64_t c, uint32_t d) {
+    const uint32_t nm = n - 1;
+    uint32_t lo = d > n ? d - n : 0, hi = d < n ? d : n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (K[mid] <= K[(r + d - mid - 1) & nm] + c) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Tile boundaries of level i: thread (half h, boundary c) finds how many of the
+// first c * YM_TILE merged entries come from the list itself (merge path), and
+// boundary 0 also stores the rotation of the shifted copy.
+__global__ void __launch_bounds__(128) k_ysplit(const YJob* __restrict__ js, int nh, int i, int cpl) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nh * (cpl + 1)) return;
+    const YJob& J = js[t / (cpl + 1)];
+    const int c = t % (cpl + 1);
+    const uint32_t n = 1u << i;
+    const uint64_t* __restrict__ K = J.kb[(i - YS_LOG) & 1];
+    const uint64_t cs = list_step(J.w, J.neg, i, J.l);
+    const uint32_t r = lower_bound_keys(K, n, 0ull - cs);
+    J.splits[c] = merge_split(K, n, r, cs, (uint32_t)c * YM_TILE);
+    if (c == 0) J.splits[cpl + 1] = r;
+}
+
 __global__ void __launch_bounds__(YM_THREADS) k_ymerge(const YJob* __restrict__ js, int i, int cpl) {
-    __shared__ uint32_t s_r;
+    extern __shared__ __align__(16) uint64_t ym_sm[];
+    uint64_t* tin = ym_sm;                        // [YM_TILE]: the stretch of K, then of the shifted copy
+    uint64_t* tout = ym_sm + YM_TILE;             // [YM_TILE]: merged tile
     const YJob& J = js[blockIdx.x / cpl];
     const int c = blockIdx.x % cpl;
-    const uint32_t n = 1u << i;
+    const uint32_t n = 1u << i, nm = n - 1;
     const int p = (i - YS_LOG) & 1;
-    const uint64_t* K = J.kb[p];
+    const uint64_t* __restrict__ K = J.kb[p];
     const uint64_t cs = list_step(J.w, J.neg, i, J.l);
-    if (threadIdx.x == 0) s_r = lower_bound_keys(K, n, 0ull - cs);
+    const uint32_t r = J.splits[cpl + 1];
+    const uint32_t o0 = (uint32_t)c * YM_TILE;
+    const uint32_t a0 = J.splits[c], a1 = J.splits[c + 1], b0 = o0 - a0;
+    const uint32_t na = a1 - a0;                  // nb = YM_TILE - na
+    for (uint32_t j = threadIdx.x; j < (uint32_t)YM_TILE; j += blockDim.x)
+        tin[j] = j < na ? K[a0 + j] : K[(r + b0 + (j - na)) & nm] + cs;
     __syncthreads();
-    const uint32_t r = s_r;
-    const uint32_t per_cta = 2 * n / (uint32_t)cpl;
-    const uint32_t d0 = (uint32_t)c * per_cta + threadIdx.x * YM_PER, d1 = d0 + YM_PER;
+    // local merge of tin[0..na) with tin[na..YM_TILE)
+    const uint32_t nb = YM_TILE - na, dl = threadIdx.x * YM_PER;
+    const uint64_t* A = tin;
+    const uint64_t* Bv = tin + na;
+    uint32_t lo = dl > nb ? dl - nb : 0, hi = dl < na ? dl : na;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (A[mid] <= Bv[dl - mid - 1]) lo = mid + 1; else hi = mid;
+    }
+    uint32_t ia = lo, ib = dl - lo;
+    for (int q = 0; q < YM_PER; ++q) {
+        const uint64_t ka = ia < na ? A[ia] : ~0ull;
+        const uint64_t kb = ib < nb ? Bv[ib] : ~0ull;
+        const bool ta = ib >= nb || (ia < na && ka <= kb);
+        tout[dl + q] = ta ? ka : kb;
+        if (ta) ++ia; else ++ib;
+    }
+    __syncthreads();
     uint64_t* KO = i == J.l - 1 ? J.ylist : J.kb[p ^ 1];
-    merge_range(K, n, r, cs, d0, d1, [&](uint32_t d, uint64_t k) { KO[d] = k; });
+    for (uint32_t j = threadIdx.x; j < (uint32_t)YM_TILE; j += blockDim.x) KO[o0 + j] = tout[j];
 }
 
 struct MitmJob {
@@ -205,7 +262,7 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
     uint32_t* tb = j0b + MT_RUNS;
     uint16_t* fpr = reinterpret_cast<uint16_t*>(tb + MT_RUNS);          // [ACAP] table-a fingerprints
     uint16_t* nxt = fpr + MT_ACAP;                                      // [ACAP] next key of the same bin
-    __shared__ uint64_t wa[32], w2a[32], wb[32], w2b[32];
+    __shared__ uint64_t wa[32], wb[32];
     __shared__ uint32_t s_count;
 
     int jl = 0, jh = np - 1;                                            // last job with cta_base <= blockIdx.x
@@ -222,7 +279,7 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
     const int d1 = P.d1, su = 64 - d1, nbl = P.nbl, bsh = su - nbl, fsh = bsh - 16;
     const uint32_t NB = 1u << d1;
     const uint64_t U = 1ull << su;
-    const uint64_t Wc = P.Wc, W = P.W, W2 = P.W2;
+    const uint64_t Wc = P.Wc;
     const int wf = P.wf;
     const int nbins = 1 << nbl;
     // cells of 2^rsh fingerprint positions, wider than 2 wf, shifted by one cell so
@@ -246,8 +303,8 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
     const uint32_t gslots = (uint32_t)((MT_ACAP - MT_POOL) / gact);
     uint2* wq = queue + warp * MT_QCAP;
 
-    if (threadIdx.x < n_a) { wa[threadIdx.x] = P.w_a[threadIdx.x]; w2a[threadIdx.x] = P.w2_a[threadIdx.x]; }
-    if (threadIdx.x < n_b) { wb[threadIdx.x] = P.w_b[threadIdx.x]; w2b[threadIdx.x] = P.w2_b[threadIdx.x]; }
+    if (threadIdx.x < n_a) wa[threadIdx.x] = P.w_a[threadIdx.x];
+    if (threadIdx.x < n_b) wb[threadIdx.x] = P.w_b[threadIdx.x];
     __syncthreads();
     // run state: offset x, rotation j0 (index of the smallest key), cursor at the slab's first unit
     for (int g = threadIdx.x; g < RA; g += blockDim.x) {
@@ -548,7 +605,7 @@ uint64_t mitm_hit_cap(const MatchGeom& g) {
 size_t mitm_half_bytes(int l) {
     auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t b = a256((size_t)8 << l);
-    if (l > YS_LOG) b += 2 * a256((size_t)8 << (l - 1));
+    if (l > YS_LOG) b += 2 * a256((size_t)8 << (l - 1)) + a256((((size_t)1 << l) / YM_TILE + 2) * 4);
     return b;
 }
 
@@ -556,16 +613,18 @@ void mitm_layout_half(int l, char*& p, HalfJob* h) {
     auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~(size_t)255; return q; };
     h->ylist = (uint64_t*)take((size_t)8 << l);
     h->ytmp = h->kb1 = nullptr;
+    h->ysplit = nullptr;
     if (l > YS_LOG) {
         h->ytmp = (uint64_t*)take((size_t)8 << (l - 1));
         h->kb1 = (uint64_t*)take((size_t)8 << (l - 1));
+        h->ysplit = (uint32_t*)take((((size_t)1 << l) / YM_TILE + 2) * 4);
     }
 }
 
 int mitm_launches(const ProbJob* const* F, int nF) {
     int maxl = 0;
     for (int i = 0; i < nF; ++i) maxl = std::max(maxl, std::max(F[i]->A.l, F[i]->B.l));
-    return nF ? 3 + std::max(0, maxl - YS_LOG) : 0;
+    return nF ? 3 + 2 * std::max(0, maxl - YS_LOG) : 0;
 }
 
 cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev_yjobs, cudaStream_t s,
@@ -576,6 +635,7 @@ cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev
     cudaError_t e;
     if (!g_mitm_attr) {
         e = cudaFuncSetAttribute(k_ybuild_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)YS_SMEM);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ymerge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)YM_SMEM);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mitm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MT_SMEM);
         if (e != cudaSuccess) return e;
         g_mitm_attr = true;
@@ -588,6 +648,7 @@ cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev
             YJob y;
             y.w = h->w; y.l = h->l; y.neg = h->neg;
             y.kb[0] = h->ytmp; y.kb[1] = h->kb1;
+            y.splits = h->ysplit;
             y.ylist = h->ylist;
             yj.push_back(y);
         }
@@ -600,8 +661,9 @@ cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev
     for (int i = YS_LOG; i < yj[0].l; ++i) {
         int nh = 0;
         while (nh < (int)yj.size() && yj[nh].l > i) ++nh;
-        const int cpl = 1 << (i + 1 - YS_LOG);
-        k_ymerge<<<nh * cpl, YM_THREADS, 0, s>>>(d_yj, i, cpl);
+        const int cpl = (2 << i) / YM_TILE;
+        k_ysplit<<<(nh * (cpl + 1) + 127) / 128, 128, 0, s>>>(d_yj, nh, i, cpl);
+        k_ymerge<<<nh * cpl, YM_THREADS, YM_SMEM, s>>>(d_yj, i, cpl);
     }
     if (ev_lists) cudaEventRecord(ev_lists, s);
     if (ev_lists2) cudaEventRecord(ev_lists2, s);
