@@ -102,7 +102,7 @@ struct TuneParams {
 // Which match a problem gets: tables in device memory, or the fused match
 // (k_mitm) for halves of at least FUSED_MIN_NA elements, or only the fused one.
 enum { FUSE_NEVER = 0, FUSE_AUTO = 1, FUSE_ALWAYS = 2 };
-constexpr int FUSED_MIN_NA = 18;
+constexpr int FUSED_MIN_NA = 14;
 
 // Choose bucket bits and coarse window; returns false if the window is too
 // wide for any bucket layout.  optimistic = false always gives the table
