@@ -84,7 +84,16 @@ typedef struct {
                                    SM) on the first problem of each (n_a, n_b) class and keep the best */
     const char* tune_cache_path;/* NULL, or a text file that stores tuned layouts across runs (read at
                                    create, appended when a class is tuned); the string is copied */
+    int      match_path;        /* RFR_MATCH_AUTO: halves of n_b <= 13 in one shared-memory kernel,
+                                   14 <= n_a <= n_b <= 28 by the fused match, the rest by the table
+                                   match; RFR_MATCH_TABLES: every problem with n_b > 13 by the
+                                   table match with the count-pass layout (same results)            */
+    int      reserved0;
 } rfr_config;
+
+/* rfr_config.match_path */
+#define RFR_MATCH_AUTO   0
+#define RFR_MATCH_TABLES 1
 
 /* Per-polynomial diagnostics returned with each result.  The stage times,
  * copy bytes and launch count describe the whole batch the polynomial was

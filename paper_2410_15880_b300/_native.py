@@ -41,7 +41,8 @@ class Config(C.Structure):
     _fields_ = [("device", C.c_int), ("mem_budget_bytes", C.c_size_t), ("max_inflight", C.c_int),
                 ("max_batch", C.c_int), ("root_mode", C.c_int), ("timing", C.c_int),
                 ("max_candidates", C.c_uint64), ("eps_override", C.c_double),
-                ("use_graphs", C.c_int), ("autotune", C.c_int), ("tune_cache_path", C.c_char_p)]
+                ("use_graphs", C.c_int), ("autotune", C.c_int), ("tune_cache_path", C.c_char_p),
+                ("match_path", C.c_int), ("reserved0", C.c_int)]
 
 
 class Diag(C.Structure):
@@ -156,7 +157,7 @@ class Context:
     def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_inflight: int = 2,
                  max_batch: int = 64, root_mode: int = RFR_ROOTS_FP32_BULK, timing: bool = False,
                  max_candidates: int = 1 << 16, eps_override: float = 0.0, use_graphs: bool = True,
-                 autotune: bool = False, tune_cache_path: Optional[str] = None):
+                 autotune: bool = False, tune_cache_path: Optional[str] = None, tables_only: bool = False):
         L = lib()
         cfg = Config()
         L.rfr_config_default(C.byref(cfg))
@@ -165,6 +166,7 @@ class Context:
         cfg.max_candidates, cfg.eps_override = max_candidates, eps_override
         cfg.use_graphs, cfg.autotune = int(bool(use_graphs)), int(bool(autotune))
         cfg.tune_cache_path = tune_cache_path.encode() if tune_cache_path else None
+        cfg.match_path = 1 if tables_only else 0
         h = C.c_void_p()
         st = L.rfr_create(C.byref(cfg), C.byref(h))
         if st != RFR_OK:

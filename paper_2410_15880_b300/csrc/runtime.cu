@@ -409,6 +409,7 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
         Work w;
         w.item = (int)i;
         w.slot = (int)work.size();
+        w.full_halo = C.cfg.match_path == RFR_MATCH_TABLES;     // tables with the count-pass layout
         work.push_back(std::move(w));
     }
     const int B = (int)work.size();
@@ -856,6 +857,7 @@ int rfr_config_default(rfr_config* cfg) {
     cfg->use_graphs = 1;
     cfg->autotune = 0;
     cfg->tune_cache_path = nullptr;
+    cfg->match_path = RFR_MATCH_AUTO;
     return RFR_OK;
 }
 
@@ -864,7 +866,8 @@ int rfr_create(const rfr_config* cfg_in, rfr_ctx** out) {
     *out = nullptr;
     rfr_config cfg;
     if (cfg_in) cfg = *cfg_in; else rfr_config_default(&cfg);
-    if (cfg.max_inflight < 1 || cfg.max_batch < 1 || (cfg.root_mode != RFR_ROOTS_FP64 && cfg.root_mode != RFR_ROOTS_FP32_BULK))
+    if (cfg.max_inflight < 1 || cfg.max_batch < 1 || (cfg.root_mode != RFR_ROOTS_FP64 && cfg.root_mode != RFR_ROOTS_FP32_BULK) ||
+        (cfg.match_path != RFR_MATCH_AUTO && cfg.match_path != RFR_MATCH_TABLES))
         return RFR_E_INVALID;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg.device < 0 || cfg.device >= ndev) { cudaGetLastError(); return RFR_E_CUDA; }

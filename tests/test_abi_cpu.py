@@ -43,6 +43,7 @@ def test_host_only_calls(L):
     assert L.rfr_config_default(ctypes.byref(cfg)) == 0
     assert cfg.max_inflight == 2 and cfg.max_candidates == 1 << 16 and cfg.root_mode == 1
     assert cfg.use_graphs == 1 and cfg.autotune == 0 and not cfg.tune_cache_path
+    assert cfg.match_path == 0
     assert L.rfr_config_default(None) == -1
     assert L.rfr_destroy(None) == 0
     f = N.Factors()
@@ -52,7 +53,7 @@ def test_host_only_calls(L):
 def test_struct_layout(L):
     import paper_2410_15880_b300._native as N
     assert N.PLAN_DTYPE.itemsize == 2512
-    assert ctypes.sizeof(N.Config) == 64 and ctypes.sizeof(N.Diag) == 176
+    assert ctypes.sizeof(N.Config) == 72 and ctypes.sizeof(N.Diag) == 176
 
 
 def test_create_without_gpu_fails_cleanly(L):

@@ -164,3 +164,19 @@ def test_autotune_and_graphs_do_not_change_results(tmp_path):
     assert len(lines) >= 2 and all(len(l.split("\t")[1].split()) == 5 for l in lines)
     with Context(device=0, use_graphs=False, tune_cache_path=cache) as c:
         check_batch(c, recs)
+
+
+def test_tables_only_equals_fused():
+    """The same batch through the table match only (rfr_config.match_path =
+    RFR_MATCH_TABLES) and through the automatic choice (the fused match for
+    these sizes): identical factorisations, equal to the oracle's goldens."""
+    from paper_2410_15880_b300 import Context
+    recs = golden("cfg3")[:6] + golden("cfg2")[:8]
+    polys = [r["coeffs"] for r in recs]
+    with Context(device=0) as auto, Context(device=0, tables_only=True) as tab:
+        ra = auto.factor_batch(polys)
+        rt = tab.factor_batch(polys)
+    for r, a, t in zip(recs, ra, rt):
+        assert a.ok and t.ok
+        assert a.factors == t.factors == r["factors"]
+        assert a.diag["cand_post"] == t.diag["cand_post"]
