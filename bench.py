@@ -41,9 +41,9 @@ def parse():
     ap.add_argument("--config", default="cfg3", choices=["cfg1", "cfg2", "cfg3", "cfg5"])
     ap.add_argument("--count", type=int, default=0, help="use only the first C polynomials")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=2000,
+    ap.add_argument("--serving-requests", type=int, default=10000,
                     help="requests of the serving stream (0 = skip the serving leg)")
-    ap.add_argument("--serving-loads", default="0.5,0.8",
+    ap.add_argument("--serving-loads", default="0.5,0.8,0.95",
                     help="Poisson arrival rates as fractions of the measured closed-loop capacity")
     ap.add_argument("--root-mode", type=int, default=1,
                     help="0 = FP64 Aberth, 1 = FP32 bulk + FP64 (default)")

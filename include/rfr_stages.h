@@ -101,6 +101,19 @@ int rfr_stage_enumerate(const uint64_t* w, int h, uint64_t* keys, void* stream);
  * of n_a and n_b elements. */
 size_t rfr_stage_match_workspace(int n_a, int n_b);
 
+/* K-d for the fused match: one half's sorted list of low-subset sums.
+ * list[0 .. 2^l) receives, for every subset s of the weights w[0..l), the
+ * entry (S(s) & ~(2^l - 1)) | s, ascending as uint64, where S(s) is the sum
+ * modulo 2^64 over i in s of round(w_i) = (w_i + 2^(l-1)) & ~(2^l - 1)
+ * (of -w_i when negate != 0).  The rounding moves a sum by at most
+ * l * 2^(l-1); the fused match widens its coarse window by that much.
+ * 0 <= l <= 21; workspace: rfr_stage_lowlist_workspace(l) bytes, 256-byte
+ * aligned; list: 2^l entries.  Built by merging: the list of i elements and
+ * its copy shifted by round(w_i) + 2^i (EXPAND's sort, Section 3.3). */
+size_t rfr_stage_lowlist_workspace(int l);
+int rfr_stage_lowlist(const uint64_t* w, int l, int negate, uint64_t* list,
+                      void* workspace, size_t workspace_bytes, void* stream);
+
 /* K-c + K-d + K-e for one problem given its weights: enumerate both halves
  * (keys of half b negated), radix-partition them by key (first digit fused
  * into the enumeration, second digit in shared memory inside the match),

@@ -104,6 +104,8 @@ def lib():
         "rfr_stage_weights": (i32, [vp, vp, i32, vp, vp, vp, C.c_double, vp, vp]),
         "rfr_stage_enumerate": (i32, [vp, i32, vp, vp]),
         "rfr_stage_match_workspace": (C.c_size_t, [i32, i32]),
+        "rfr_stage_lowlist_workspace": (C.c_size_t, [i32]),
+        "rfr_stage_lowlist": (i32, [vp, i32, i32, vp, vp, C.c_size_t, vp]),
         "rfr_stage_match": (i32, [vp, vp, i32, vp, vp, i32, u64, u64, vp, C.c_size_t, vp, u64, vp, vp]),
         "rfr_stage_match_noalloc": (i32, [vp, vp, i32, vp, vp, i32, u64, u64, vp, u64, vp, vp]),
         "rfr_stage_match_exact": (i32, [vp, vp, i32, vp, vp, i32, u64, u64, vp, C.c_size_t, vp, u64, vp, vp]),
@@ -352,6 +354,19 @@ def stage_match(w_a, w2_a, w_b, w2_b, window: int, window2: int, cap: int, exact
                                  int(window), int(window2), C.c_void_p(aligned), ws_bytes,
                                  _ptr(cand), int(cap), _ptr(ctr), _stream()), "rfr_stage_match")
     return cand, ctr, ws
+
+
+def stage_lowlist(w, l: int, negate: bool = False):
+    """Sorted low-subset list of the first l weights (int64 cuda tensor,
+    uint64 bits): int64 tensor [2^l] of (rounded sum high bits) | mask."""
+    import torch
+    ws_bytes = int(lib().rfr_stage_lowlist_workspace(l))
+    ws = torch.empty((ws_bytes // 8 + 64,), dtype=torch.int64, device=w.device)
+    aligned = (ws.data_ptr() + 255) & ~255
+    out = torch.empty((1 << l,), dtype=torch.int64, device=w.device)
+    _check(lib().rfr_stage_lowlist(_ptr(w) if l else None, l, int(bool(negate)), _ptr(out),
+                                   C.c_void_p(aligned), ws_bytes, _stream()), "rfr_stage_lowlist")
+    return out, ws
 
 
 def stage_verify(coeffs, degrees, roots, plans, prob, pat_lo, pat_hi, want_coeffs: bool = False):

@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 #include "k_match.cuh"
 #include "rfr_device.cuh"
+#include "rfr_stages.h"
 
 namespace rfr {
 namespace {
@@ -559,6 +560,27 @@ __global__ void __launch_bounds__(256) k_mitm_check(const MitmJob* __restrict__ 
 
 bool g_mitm_attr = false;
 
+cudaError_t mitm_attrs() {
+    if (g_mitm_attr) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_ybuild_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)YS_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ymerge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)YM_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mitm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MT_SMEM);
+    if (e == cudaSuccess) g_mitm_attr = true;
+    return e;
+}
+
+// Launch the list build for the jobs d_yj[0..nh), sorted by l descending (host copy yj).
+void build_lists(const YJob* yj, int nh, YJob* d_yj, cudaStream_t s) {
+    k_ybuild_smem<<<nh, YS_THREADS, YS_SMEM, s>>>(d_yj);
+    for (int i = YS_LOG; i < yj[0].l; ++i) {
+        int nhi = 0;
+        while (nhi < nh && yj[nhi].l > i) ++nhi;
+        const int cpl = (2 << i) / YM_TILE;
+        k_ysplit<<<(nhi * (cpl + 1) + 127) / 128, 128, 0, s>>>(d_yj, nhi, i, cpl);
+        k_ymerge<<<nhi * cpl, YM_THREADS, YM_SMEM, s>>>(d_yj, i, cpl);
+    }
+}
+
 }  // namespace
 
 bool mitm_geometry(int n_a, int n_b, uint64_t W, MatchGeom* g) {
@@ -633,13 +655,8 @@ cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev
     static_assert(sizeof(YJob) <= sizeof(HalfJob), "YJob must fit a HalfJob slot");
     if (nF <= 0) return cudaSuccess;
     cudaError_t e;
-    if (!g_mitm_attr) {
-        e = cudaFuncSetAttribute(k_ybuild_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)YS_SMEM);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ymerge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)YM_SMEM);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mitm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MT_SMEM);
-        if (e != cudaSuccess) return e;
-        g_mitm_attr = true;
-    }
+    e = mitm_attrs();
+    if (e != cudaSuccess) return e;
     std::vector<YJob> yj;
     yj.reserve(2 * (size_t)nF);
     for (int i = 0; i < nF; ++i) {
@@ -657,14 +674,7 @@ cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev
     YJob* d_yj = (YJob*)dev_yjobs;
     e = cudaMemcpyAsync(d_yj, yj.data(), sizeof(YJob) * yj.size(), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
-    k_ybuild_smem<<<(int)yj.size(), YS_THREADS, YS_SMEM, s>>>(d_yj);
-    for (int i = YS_LOG; i < yj[0].l; ++i) {
-        int nh = 0;
-        while (nh < (int)yj.size() && yj[nh].l > i) ++nh;
-        const int cpl = (2 << i) / YM_TILE;
-        k_ysplit<<<(nh * (cpl + 1) + 127) / 128, 128, 0, s>>>(d_yj, nh, i, cpl);
-        k_ymerge<<<nh * cpl, YM_THREADS, YM_SMEM, s>>>(d_yj, i, cpl);
-    }
+    build_lists(yj.data(), (int)yj.size(), d_yj, s);
     if (ev_lists) cudaEventRecord(ev_lists, s);
     if (ev_lists2) cudaEventRecord(ev_lists2, s);
     std::vector<MitmJob> mj(nF);
@@ -692,3 +702,36 @@ cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev
 }
 
 }  // namespace rfr
+
+using namespace rfr;
+
+// Stage entry: one half's sorted low-subset list (see include/rfr_stages.h).
+extern "C" size_t rfr_stage_lowlist_workspace(int l) {
+    if (l < 0 || l > 21) return 0;
+    size_t b = 512;                                           // the job
+    if (l > YS_LOG) b += 2 * (((size_t)8 << (l - 1)) + 256) + ((((size_t)1 << l) / YM_TILE + 2) * 4 + 256);
+    return b;
+}
+
+extern "C" int rfr_stage_lowlist(const uint64_t* w, int l, int negate, uint64_t* list,
+                                 void* workspace, size_t workspace_bytes, void* stream) {
+    if (l < 0 || l > 21 || (l && !w) || !list || !workspace) return RFR_E_INVALID;
+    if (((uintptr_t)workspace) & 255) return RFR_E_INVALID;
+    if (workspace_bytes < rfr_stage_lowlist_workspace(l)) return RFR_E_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (mitm_attrs() != cudaSuccess) return RFR_E_CUDA;
+    char* p = (char*)workspace;
+    YJob* d_yj = (YJob*)p;
+    p += 512;
+    YJob y;
+    memset(&y, 0, sizeof(y));
+    y.w = w; y.l = l; y.neg = negate ? 1 : 0; y.ylist = list;
+    if (l > YS_LOG) {
+        y.kb[0] = (uint64_t*)p; p += ((size_t)8 << (l - 1)) + 256;
+        y.kb[1] = (uint64_t*)p; p += ((size_t)8 << (l - 1)) + 256;
+        y.splits = (uint32_t*)p;
+    }
+    if (cudaMemcpyAsync(d_yj, &y, sizeof(y), cudaMemcpyHostToDevice, s) != cudaSuccess) return RFR_E_CUDA;
+    build_lists(&y, 1, d_yj, s);
+    return cudaGetLastError() == cudaSuccess ? RFR_OK : RFR_E_CUDA;
+}

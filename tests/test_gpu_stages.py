@@ -111,6 +111,28 @@ def test_enumerate_large_properties(P):
         assert int(keys[s]) == value(s, w, M64)
 
 
+# ---------------------------------------------------------------- K-d sorted low lists (fused match)
+@pytest.mark.parametrize("l,negate", [(0, False), (1, False), (5, True), (12, False), (13, True), (16, False), (20, True)])
+def test_lowlist_sorted_and_complete(P, l, negate):
+    """The list is non-decreasing and, as a multiset, equals (S(s) & ~(2^l-1)) | s
+    over all subsets s, S(s) the sum of the rounded weights (its definition)."""
+    rng = random.Random(100 + l)
+    w = [rng.randrange(M64) for _ in range(max(l, 1))]
+    out, _ = P.stage_lowlist(u64_tensor(w), l, negate)
+    torch.cuda.synchronize()
+    got = to_u64(out)
+    assert np.all(got[1:] >= got[:-1])                        # sorted
+    half = (1 << (l - 1)) if l else 0
+    keep = (~((1 << l) - 1)) % M64
+    r = [(((-x if negate else x) + half) % M64) & keep for x in w[:l]]
+    s_ = np.zeros(1, dtype=np.int64)                          # sums modulo 2^64 on the int64 view
+    for x in r:
+        s_ = np.concatenate([s_, s_ + (x - M64 if x >= (1 << 63) else x)])
+    exp = np.sort((s_.view(np.uint64) & np.uint64(keep)) | np.arange(1 << l, dtype=np.uint64))
+    assert np.array_equal(np.sort(got), exp)
+    assert int((got & np.uint64((1 << l) - 1)).astype(np.int64).sum()) == (1 << l) * ((1 << l) - 1) // 2
+
+
 # ---------------------------------------------------------------- K-c/K-d/K-e match
 def _expected_pairs(wa, w2a, wb, w2b, W, W2):
     from oracle.recombine import accept, band_pairs, expand_values
