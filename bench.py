@@ -247,6 +247,42 @@ def cpu_oracle_sample(insts, budget_s=15.0, max_polys=8):
     return done, dt
 
 
+def cpu_mt_sample(d_co, d_dg, root_mode, budget_s=15.0, max_polys=8):
+    """The multithreaded CPU Horowitz-Sahni band join (baseline/hs_mt.cpp) on
+    the match stage of the first polynomials of the workload, over all host
+    cores.  Its inputs (weights, windows, half split) come from the GPU
+    path's roots and weights stages; the first polynomial is run once untimed
+    to allocate and first-touch the buffers."""
+    import baseline
+    from paper_2410_15880_b300 import PLAN_DTYPE, stage_roots, stage_weights
+    roots, radius, status = stage_roots(d_co, d_dg, root_mode)
+    plans = stage_weights(d_co, d_dg, roots, radius, status).cpu().numpy().view(PLAN_DTYPE).reshape(-1)
+    plans = [p for p in plans if p["status"] == 0 and int(p["window"]) < (1 << 63)]
+    cores = baseline.host_cores()
+
+    def run(p):
+        na, nb = int(p["n_a"]), int(p["n_b"])
+        w, w2 = [int(x) for x in p["w"]], [int(x) for x in p["w2"]]
+        _, counts, _ = baseline.hs_mt_match(w[:na], w2[:na], w[na:na + nb], w2[na:na + nb],
+                                            int(p["window"]), int(p["window2"]), threads=cores)
+        return (1 << na) + (1 << nb), counts[1]
+
+    if not plans:
+        return None
+    run(plans[0])
+    done, hs, cands, t0 = 0, 0, 0, time.perf_counter()
+    for p in plans[:max_polys]:
+        h, c = run(p)
+        done, hs, cands = done + 1, hs + h, cands + c
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "horowitz-sahni-mt",
+            "half_sums_per_s": hs / dt, "candidates": cands,
+            "sample": f"match stage only (enumerate, LSD radix sort, band join, Tr2 test; C++ std::thread) of "
+                      f"the first {done} polynomials ({dt:.1f} s), weights from the GPU path's weights stage"}
+
+
 def max_over_ranks(value: float, world: int) -> float:
     """Max of a per-rank time over all ranks (the slowest replica sets the
     step time).  Uses a CUDA tensor under NCCL, a CPU tensor under gloo."""
@@ -435,6 +471,10 @@ def main():
         n, dt = cpu_oracle_sample(workload(a.config, 0, a.count), budget_s=15.0)
         line["cpu_baseline"] = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"first {n} polynomials of the workload ({dt:.1f} s): roots, Sturm, DDF certificates"}
+        if world == 1:
+            mt = cpu_mt_sample(d_co, d_dg, a.root_mode)
+            if mt is not None:
+                line["cpu_mt"] = mt
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
