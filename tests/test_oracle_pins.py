@@ -361,3 +361,90 @@ def test_certificates():
     assert certify_irreducible(cyclotomic(7))[0]
     assert not certify_irreducible([1, 0, 0, 0, 1], max_primes=20)[0]   # x^4+1: reducible mod every prime
     assert not certify_irreducible(pmul([1, 0, 1], [2, 0, 1]), max_primes=20)[0]
+
+
+# ---------------------------------------------------------------- splat sort and query (Algorithms D, E)
+def test_splat_sorts_and_keeps_every_value():
+    """SPLAT's compacted output is the sorted input (Section 3.4): random
+    values, values crowded into a few home cells, and values at the top end
+    that overflow past the last home cell."""
+    from oracle.splat import compact, home_cell, splat
+    rng = random.Random(3)
+    for vals, k in ([rng.randrange(1 << 64) for _ in range(3000)], 4096), \
+                   (rng.sample(range(1 << 20), 500), 1024), \
+                   ([(1 << 64) - 1 - i for i in range(300)], 512):
+        cells, visited = splat(vals, k, home_cell(k, 64))
+        assert compact(cells) == sorted(vals)
+        assert visited >= len(vals)
+        for i, c in enumerate(cells):                # at or after its home cell, no gap in between
+            if c is not None:
+                h = (c * k) >> 64
+                assert h <= i and all(x is not None for x in cells[h:i + 1])
+
+
+def test_splat_layout_does_not_depend_on_insertion_order():
+    """The final array is the same for any insertion order: what lets a
+    concurrent build be compared with the sequential one cell by cell."""
+    from oracle.splat import home_cell, splat
+    rng = random.Random(4)
+    vals = [rng.randrange(1 << 40) for _ in range(1500)]
+    vals += [v + 1 for v in vals[:200]]               # neighbours: long runs of full cells
+    vals = list(set(vals))
+    ref, _ = splat(vals, 2048, home_cell(2048, 40))
+    for _ in range(3):
+        rng.shuffle(vals)
+        assert splat(vals, 2048, home_cell(2048, 40))[0] == ref
+
+
+@pytest.mark.parametrize("c,lo,hi", [(2, 2 * np.log(2), 2.0), (4, 4 * np.log(4 / 3), 4 / 3)])
+def test_splat_constant_within_theorem_bounds(c, lo, hi):
+    """Theorem 3.4.2: for k uniform values in c*k cells, INSERT looks at C*k
+    cells with c log(c/(c-1)) < C < c/(c-1) (1.386 < C < 2 for c = 2)."""
+    from oracle.splat import home_cell, splat
+    rng = random.Random(5)
+    k = 1 << 14
+    vals = [rng.randrange(1 << 64) for _ in range(k)]
+    _, visited = splat(vals, c * k, home_cell(c * k, 64))
+    assert lo < visited / k < hi
+
+
+def test_query_band_is_a_filter():
+    from oracle.splat import home_cell, query_band, splat
+    rng = random.Random(6)
+    k = 1 << 11
+    vals = list({rng.randrange(1 << 32) for _ in range(k)})
+    home = home_cell(2 * k, 32)
+    cells, _ = splat(vals, 2 * k, home)
+    for _ in range(300):
+        a = rng.randrange(1 << 32)
+        b = min((1 << 32) - 1, a + rng.choice([0, 5, 1 << 16, 1 << 22]))
+        got = query_band(cells, home, a, b)
+        assert sorted(v for _, v in got) == sorted(v for v in vals if a <= v <= b)
+        assert all(cells[i] == v for i, v in got)
+
+
+def test_printed_query_misses_what_the_band_query_finds():
+    """Reading of QUERY: starting at the target's home cell, the printed QUERY
+    never looks at an accepted value whose home cell is the one before."""
+    from oracle.splat import home_cell, query_band, query_printed, splat
+    bits, k, W = 16, 8, 4
+    y, x = (1 << bits) // 8 - 1, (1 << bits) // 8 + 1   # home cells 0 and 1, |x - y| = 2 <= W
+    cells, _ = splat([y], k, home_cell(k, bits), tail=4)
+    assert not query_printed(cells, k, bits, x, lambda d: abs(d) <= W)
+    assert query_band(cells, home_cell(k, bits), x - W, x + W) == [(0, y)]
+
+
+@pytest.mark.parametrize("n_a,n_b,shift", [(5, 6, 3), (7, 8, 8), (8, 8, 10)])
+def test_splat_match_equals_brute_force(n_a, n_b, shift):
+    """RECOMBINE_E with the band query finds exactly the pairs in the circular
+    window, including windows that wrap past 0."""
+    from oracle.splat import splat_match
+    rng = random.Random(n_a + 17 * n_b)
+    M = 1 << 64
+    wa = [rng.randrange(M) for _ in range(n_a)]
+    wb = [rng.randrange(M) for _ in range(n_b)]
+    wb[1] = (-(wa[0] + wa[2])) % M
+    W = M >> shift
+    exp = band_pairs(expand_values(wa, M), expand_values(wb, M), M, W)
+    assert (0, 0) in exp and (5, 2) in exp
+    assert splat_match(wa, wb, W) == exp
