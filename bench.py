@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--root-mode", type=int, default=1,
                     help="0 = FP64 Aberth, 1 = FP32 bulk + FP64 (default)")
     ap.add_argument("--no-autotune", action="store_true", help="use the default match layout")
+    ap.add_argument("--match-path", default="auto", choices=["auto", "tables", "splat"],
+                    help="rfr_config.match_path: automatic choice, table match only, or the splat match")
     ap.add_argument("--tune-cache", default="", help="file that stores tuned match layouts")
     return ap.parse_args()
 
@@ -350,8 +352,9 @@ def main():
             dist.barrier()
 
     flush = torch.empty((256 << 20,), dtype=torch.uint8, device="cuda")     # larger than L2 (126 MB)
+    match_path = {"auto": 0, "tables": 1, "splat": 2}[a.match_path]
     with Context(device=local, timing=True, root_mode=a.root_mode, autotune=not a.no_autotune,
-                 tune_cache_path=a.tune_cache) as ctx:
+                 tune_cache_path=a.tune_cache, match_path=match_path) as ctx:
         for i in range(a.warmup):
             flush.fill_(i & 255)                   # the flush kernel's first use loads it (not timed)
             torch.cuda.current_stream().synchronize()
@@ -424,7 +427,15 @@ def main():
     roots_us = statistics.mean(d["stage_us"][0] for d in per_step)
     peak, peak_kind = peaks()
     fused = all(d["stage_us"][3] < 0.05 * d["stage_us"][4] for d in per_step)
-    if fused:
+    if a.match_path == "splat":
+        # splat match: fill 2 cells (16 B) and one exchange (8 B read + 8 B write) per
+        # half-b sum, one 8 B cell read per half-a sum, at the least
+        alg_bytes = sum(32.0 * (1 << r.diag["n_b"]) + 8.0 * (1 << r.diag["n_a"]) for r in res)
+        achieved = alg_bytes / (join_us * 1e-6) / 1e9
+        roof = {"bound": "hbm", "kernel": "k_splat_insert+k_splat_query", "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "algorithmic_bytes": alg_bytes, "avg_launch_us": join_us}
+    elif fused:
         # the fused match (k_mitm) is the match stage; no table scatter ran
         apeak, apeak_kind = alu_peak()
         ops = ALU_OPS_PER_HALF_SUM * half_sums
@@ -449,7 +460,8 @@ def main():
         "config": {"workload": WORKLOAD_NAME[a.config], "polys_per_step": B,
                    "half_sums_per_step": half_sums, "parallelism": f"replicas x{world}",
                    "l2": "256 MiB buffer written before every timed step (L2 flush)", "root_mode": a.root_mode,
-                   "autotune": ("off" if a.no_autotune else "layouts tuned per (n_a, n_b) during warm-up")},
+                   "autotune": ("off" if a.no_autotune else "layouts tuned per (n_a, n_b) during warm-up"),
+                   "match_path": a.match_path},
         "half_sums_per_s": half_sums * world * a.steps / (ms / 1e3),
         "roofline": roof,
         "stage_us_per_step": {"validate+roots": roots_us,

@@ -87,13 +87,17 @@ typedef struct {
     int      match_path;        /* RFR_MATCH_AUTO: halves of n_b <= 13 in one shared-memory kernel,
                                    14 <= n_a <= n_b <= 28 by the fused match, the rest by the table
                                    match; RFR_MATCH_TABLES: every problem with n_b > 13 by the
-                                   table match with the count-pass layout (same results)            */
+                                   table match with the count-pass layout; RFR_MATCH_SPLAT: every
+                                   problem with 13 < n_b <= 30 by the splat match (Section 4,
+                                   Algorithm E), falling back to the table match when an insertion
+                                   overflows (same results on every path)                          */
     int      reserved0;
 } rfr_config;
 
 /* rfr_config.match_path */
 #define RFR_MATCH_AUTO   0
 #define RFR_MATCH_TABLES 1
+#define RFR_MATCH_SPLAT  2
 
 /* Per-polynomial diagnostics returned with each result.  The stage times,
  * copy bytes and launch count describe the whole batch the polynomial was

@@ -114,6 +114,37 @@ size_t rfr_stage_lowlist_workspace(int l);
 int rfr_stage_lowlist(const uint64_t* w, int l, int negate, uint64_t* list,
                       void* workspace, size_t workspace_bytes, void* stream);
 
+/* K-d + K-e as the paper designs them for the GPU (Section 4, Algorithm E):
+ * SPLAT of half b (Algorithm D, c = 2, with the atomic-exchange INSERT of
+ * Section 4) and a band QUERY from every pattern of half a.
+ *
+ * gamma: caller-owned device buffer of rfr_stage_splat_cells(n_b) uint64
+ * cells, 256-byte aligned (0 if n_b is outside 0..30).  After either call its
+ * first 2^(n_b+1) + 4096 cells hold the splat array: cell i is ~0 (empty) or
+ * e(s) = ((S_b(s) >> 1) & ~(2^n_b - 1)) | s for a pattern s of half b with
+ * S_b(s) = sum_{j in s} w_b[j] mod 2^64.  Each e(s) sits at or after its home
+ * cell e(s) >> (62 - n_b), every cell in between is full, and the full cells
+ * are increasing in index order (the step past a full cell is linear, into
+ * 4096 overflow cells, instead of the paper's circular step).  The last 256
+ * bytes hold the launch descriptor.
+ * counters: 8 device words, zeroed by the call:
+ *   [0] cells within a scanned range   [1] pairs within W (Eq. 9, circular)
+ *   [2] candidates (also within W2 for the w2 weights, not the empty pair)
+ *   [3] 1 when the empty pair was met  [4] 1 when an insertion ran past the
+ *   overflow cells or its step limit (the array then misses values)
+ *   [5] cells INSERT looked at (Theorem 3.4.2's C = [5] / 2^n_b)
+ *   [6] atomic exchanges                [7] cells QUERY read
+ * Candidates are s_a | s_b << n_a, at most cap of them written (any order).
+ * QUERY reports every pair in the window: the printed QUERY stops at its
+ * first hit and starts at the target's home cell, which misses pairs. */
+size_t rfr_stage_splat_cells(int n_b);
+int rfr_stage_splat(const uint64_t* w_b, int n_b, uint64_t* gamma, size_t gamma_cells,
+                    unsigned long long* counters, void* stream);
+int rfr_stage_splat_match(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
+                          const uint64_t* w_b, const uint64_t* w2_b, int n_b,
+                          uint64_t window, uint64_t window2, uint64_t* gamma, size_t gamma_cells,
+                          uint64_t* cand, uint64_t cap, unsigned long long* counters, void* stream);
+
 /* K-c + K-d + K-e for one problem given its weights: enumerate both halves
  * (keys of half b negated), radix-partition them by key (first digit fused
  * into the enumeration, second digit in shared memory inside the match),

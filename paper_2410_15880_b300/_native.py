@@ -17,6 +17,9 @@ RFR_OK = 0
 RFR_PENDING = 1
 RFR_ROOTS_FP64 = 0
 RFR_ROOTS_FP32_BULK = 1
+RFR_MATCH_AUTO = 0
+RFR_MATCH_TABLES = 1
+RFR_MATCH_SPLAT = 2
 
 _STATUS = {
     0: "RFR_OK", 1: "RFR_PENDING", -1: "RFR_E_INVALID", -2: "RFR_E_NOT_MONIC",
@@ -106,6 +109,9 @@ def lib():
         "rfr_stage_match_workspace": (C.c_size_t, [i32, i32]),
         "rfr_stage_lowlist_workspace": (C.c_size_t, [i32]),
         "rfr_stage_lowlist": (i32, [vp, i32, i32, vp, vp, C.c_size_t, vp]),
+        "rfr_stage_splat_cells": (C.c_size_t, [i32]),
+        "rfr_stage_splat": (i32, [vp, i32, vp, C.c_size_t, vp, vp]),
+        "rfr_stage_splat_match": (i32, [vp, vp, i32, vp, vp, i32, u64, u64, vp, C.c_size_t, vp, u64, vp, vp]),
         "rfr_stage_match": (i32, [vp, vp, i32, vp, vp, i32, u64, u64, vp, C.c_size_t, vp, u64, vp, vp]),
         "rfr_stage_match_noalloc": (i32, [vp, vp, i32, vp, vp, i32, u64, u64, vp, u64, vp, vp]),
         "rfr_stage_match_exact": (i32, [vp, vp, i32, vp, vp, i32, u64, u64, vp, C.c_size_t, vp, u64, vp, vp]),
@@ -159,7 +165,8 @@ class Context:
     def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_inflight: int = 2,
                  max_batch: int = 64, root_mode: int = RFR_ROOTS_FP32_BULK, timing: bool = False,
                  max_candidates: int = 1 << 16, eps_override: float = 0.0, use_graphs: bool = True,
-                 autotune: bool = False, tune_cache_path: Optional[str] = None, tables_only: bool = False):
+                 autotune: bool = False, tune_cache_path: Optional[str] = None, tables_only: bool = False,
+                 match_path: Optional[int] = None):
         L = lib()
         cfg = Config()
         L.rfr_config_default(C.byref(cfg))
@@ -168,7 +175,7 @@ class Context:
         cfg.max_candidates, cfg.eps_override = max_candidates, eps_override
         cfg.use_graphs, cfg.autotune = int(bool(use_graphs)), int(bool(autotune))
         cfg.tune_cache_path = tune_cache_path.encode() if tune_cache_path else None
-        cfg.match_path = 1 if tables_only else 0
+        cfg.match_path = match_path if match_path is not None else (RFR_MATCH_TABLES if tables_only else RFR_MATCH_AUTO)
         h = C.c_void_p()
         st = L.rfr_create(C.byref(cfg), C.byref(h))
         if st != RFR_OK:
@@ -367,6 +374,40 @@ def stage_lowlist(w, l: int, negate: bool = False):
     _check(lib().rfr_stage_lowlist(_ptr(w) if l else None, l, int(bool(negate)), _ptr(out),
                                    C.c_void_p(aligned), ws_bytes, _stream()), "rfr_stage_lowlist")
     return out, ws
+
+
+def _splat_buffer(n_b: int, device):
+    import torch
+    cells = int(lib().rfr_stage_splat_cells(n_b))
+    if cells == 0:
+        raise RFRError(-1, f"splat: n_b = {n_b} out of range")
+    return torch.empty((cells,), dtype=torch.int64, device=device), cells
+
+
+def stage_splat(w_b, n_b: Optional[int] = None):
+    """SPLAT of half b: (gamma int64 [cells] with the uint64 cells, counters int64 [8])."""
+    import torch
+    n_b = int(w_b.numel()) if n_b is None else n_b
+    gamma, cells = _splat_buffer(n_b, w_b.device)
+    ctr = torch.zeros((8,), dtype=torch.int64, device=w_b.device)
+    _check(lib().rfr_stage_splat(_ptr(w_b) if n_b else None, n_b, _ptr(gamma), cells, _ptr(ctr), _stream()),
+           "rfr_stage_splat")
+    return gamma, ctr
+
+
+def stage_splat_match(w_a, w2_a, w_b, w2_b, window: int, window2: int, cap: int):
+    """Splat match (Algorithm E with the band query): (cand int64 [cap],
+    counters int64 [8], gamma)."""
+    import torch
+    n_a, n_b = int(w_a.numel()), int(w_b.numel())
+    gamma, cells = _splat_buffer(n_b, w_b.device)
+    cand = torch.zeros((max(cap, 1),), dtype=torch.int64, device=w_b.device)
+    ctr = torch.zeros((8,), dtype=torch.int64, device=w_b.device)
+    _check(lib().rfr_stage_splat_match(_ptr(w_a) if n_a else None, _ptr(w2_a) if n_a else None, n_a,
+                                       _ptr(w_b) if n_b else None, _ptr(w2_b) if n_b else None, n_b,
+                                       int(window), int(window2), _ptr(gamma), cells, _ptr(cand), int(cap),
+                                       _ptr(ctr), _stream()), "rfr_stage_splat_match")
+    return cand, ctr, gamma
 
 
 def stage_verify(coeffs, degrees, roots, plans, prob, pat_lo, pat_hi, want_coeffs: bool = False):

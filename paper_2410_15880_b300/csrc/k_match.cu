@@ -844,6 +844,7 @@ static uint64_t default_halo_cap(int n_b, int d1, uint64_t wc) {
 }
 
 size_t match_bytes(const MatchGeom& g) {
+    if (g.splat) return g.bytes;
     if (g.fused) return mitm_half_bytes(g.l_a) + mitm_half_bytes(g.l_b) + align256(mitm_hit_cap(g) * 8);
     const size_t NB = (size_t)1 << g.d1;
     size_t b = 0;
@@ -880,6 +881,8 @@ static int clamp_ctas(int h, int l, int want) {
 bool match_geometry(int n_a, int n_b, uint64_t W, int ctas_a, int ctas_b, MatchGeom* g, bool optimistic,
                     const TuneParams* tp, int fuse) {
     if (n_a < 0 || n_b < n_a || n_b > 32) return false;
+    g->splat = false;
+    if (optimistic && fuse == FUSE_SPLAT && splat_geometry(n_a, n_b, g)) return true;
     if (optimistic && (fuse == FUSE_ALWAYS || (fuse == FUSE_AUTO && n_a >= FUSED_MIN_NA))) {
         if (mitm_geometry(n_a, n_b, W, g)) return true;
         if (fuse == FUSE_ALWAYS) return false;
@@ -926,6 +929,12 @@ void match_layout(const MatchGeom& g, char* ws, ProbJob* pj) {
     auto take = [&](size_t bytes) { char* q = p; p += align256(bytes); return q; };
     HalfJob& A = pj->A;
     HalfJob& B = pj->B;
+    pj->splat = 0;
+    pj->gamma = nullptr;
+    if (g.splat) {
+        splat_layout(g, ws, pj);
+        return;
+    }
     pj->fused = g.fused ? 1 : 0;
     pj->nbl = g.nbl; pj->slab = g.slab; pj->wf = g.wf;
     A.kb1 = B.kb1 = nullptr; A.ysplit = B.ysplit = nullptr;
@@ -1036,12 +1045,13 @@ cudaError_t run_match(ProbJob* jobs, int np, ProbJob* dev_jobs, HalfJob* dev_hal
     }
     // table problems first (compacted to the front of a copy), fused ones after
     std::vector<ProbJob> T;
-    std::vector<const ProbJob*> F;
+    std::vector<const ProbJob*> F, Sp;
     for (int i = 0; i < np; ++i) {
-        if (jobs[i].fused) F.push_back(&jobs[i]);
+        if (jobs[i].splat) Sp.push_back(&jobs[i]);
+        else if (jobs[i].fused) F.push_back(&jobs[i]);
         else T.push_back(jobs[i]);
     }
-    const int nT = (int)T.size(), nF = (int)F.size();
+    const int nT = (int)T.size(), nF = (int)F.size(), nS = (int)Sp.size();
     int nl = 0;
     cudaError_t e = cudaSuccess;
     if (nT) {
@@ -1073,9 +1083,14 @@ cudaError_t run_match(ProbJob* jobs, int np, ProbJob* dev_jobs, HalfJob* dev_hal
         e = run_mitm(F.data(), nF, dev_jobs + nT, dev_halves + 2 * nT, s, nT ? nullptr : ev_count,
                      nT ? nullptr : ev_scatter);
         nl += mitm_launches(F.data(), nF);
+        if (e != cudaSuccess) return e;
     } else if (!nT) {
         if (ev_count) cudaEventRecord(ev_count, s);
         if (ev_scatter) cudaEventRecord(ev_scatter, s);
+    }
+    if (nS) {
+        e = run_splat(Sp.data(), nS, dev_jobs + nT + nF, s);
+        nl += 2;
     }
     if (launches) *launches = nl;
     return e;

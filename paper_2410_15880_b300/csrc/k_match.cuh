@@ -63,6 +63,8 @@ struct ProbJob {
     int nbl, slab, wf;      // k_mitm: bins per unit (log2), units per CTA, fingerprint window
     uint64_t* hits;         // k_mitm: fingerprint hits awaiting the exact check (count in ctr[5])
     uint64_t hcap;
+    int splat;              // 1: matched by splat sort + query (Algorithm E; ctr has 8 words)
+    uint64_t* gamma;        // splat array of half b
 };
 
 // One small problem (n_b <= SMALL_MAX_H) matched entirely in shared memory.
@@ -90,6 +92,7 @@ struct MatchGeom {
     size_t bytes;           // device workspace bytes (tables + histograms + halo)
     bool fused;             // k_mitm: sorted lists only, units of 2^(64-d1) keys
     int nbl, slab, wf;
+    bool splat;             // splat sort + query: one array of 2^(n_b+1) + SPLAT_TAIL cells
 };
 
 // Layout knobs chosen by the autotuner (defaults: 16, 13, 16).
@@ -101,8 +104,17 @@ struct TuneParams {
 
 // Which match a problem gets: tables in device memory, or the fused match
 // (k_mitm) for halves of at least FUSED_MIN_NA elements, or only the fused one.
-enum { FUSE_NEVER = 0, FUSE_AUTO = 1, FUSE_ALWAYS = 2 };
+// FUSE_SPLAT: the splat match (Algorithm E) for every problem it fits.
+enum { FUSE_NEVER = 0, FUSE_AUTO = 1, FUSE_ALWAYS = 2, FUSE_SPLAT = 3 };
 constexpr int FUSED_MIN_NA = 14;
+
+// Splat match (k_splat.cu): overflow cells past the 2^(n_b+1) home cells.
+constexpr uint64_t SPLAT_TAIL = 4096;
+bool splat_geometry(int n_a, int n_b, MatchGeom* g);
+uint64_t* splat_layout(const MatchGeom& g, char* ws, ProbJob* pj);
+// Fill the splat arrays and launch insert + query for S[0..nS); dev_jobs holds
+// nS ProbJob slots of device memory.  Two kernel launches.
+cudaError_t run_splat(const ProbJob* const* S, int nS, void* dev_jobs, cudaStream_t s);
 
 // Choose bucket bits and coarse window; returns false if the window is too
 // wide for any bucket layout.  optimistic = false always gives the table

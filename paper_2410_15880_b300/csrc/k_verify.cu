@@ -5,8 +5,9 @@
 // lower degree (so the built factor has degree e <= d/2), is multiplied out
 // in double-double arithmetic from the DD roots: one linear factor x - u or
 // one quadratic x^2 - (z + z')x + z z' per element; lane l owns coefficients
-// l, l+32, l+64.  Each coefficient must lie within 1/4 of an integer and
-// below 2^62 in magnitude, otherwise the pattern is rejected.  The rounded
+// l, l+32, l+64.  Each coefficient must lie within 1/4 of an integer, and
+// within 2^20 times the bound that the inclusion radii put on its error,
+// and below 2^62 in magnitude, otherwise the pattern is rejected.  The rounded
 // monic q then divides p exactly: long division in 128-bit integers, each
 // quotient coefficient required below 2^62 in magnitude, and the remainder
 // must vanish.  Only this exact step decides acceptance.
@@ -51,10 +52,24 @@ k_verify(const int64_t* __restrict__ coeffs, const double* __restrict__ roots,
     // ---- multiply out the chosen side in double-double
     for (int j = lane; j <= QMAX; j += 32) qs[w][j] = dd_make(j == 0 ? 1.0 : 0.0);
     __syncwarp();
+    // Integrality tolerance.  Moving each root z_k by at most the inclusion
+    // radius r moves every coefficient of q = prod (x - z_k) by at most
+    // B = prod_k (1 + |z_k| + r) - prod_k (1 + |z_k|) <= r * PA * sum_k 1 / (1 + |z_k| + r)
+    // with PA = prod_k (1 + |z_k| + r); the double-double products add about
+    // PA * 2^-90.  A coefficient must lie within 2^20 times that of an integer
+    // (and within 1/4): with only the 1/4 test, a pattern that is not a
+    // divisor but whose coefficients all fall near integers by chance rounds
+    // to some other divisor of p, passes the exact division, and ties the
+    // wrong roots to that divisor.
+    const double rr = P.max_radius;
+    double pa = 1.0, sinv = 0.0;
+    auto acc = [&](double m) { const double a = 1.0 + m + rr; pa *= a; sinv += 1.0 / a; };
     int cur = 0;
     for (int k = 0; k < n; ++k) {
         if (patbit(lo, hi, k) == comp) continue;
         const double* r0 = R + 4 * P.root0[k];
+        if (P.kind[k] == 1) acc(fabs(r0[0]));
+        else { acc(hypot(r0[0], r0[2])); acc(hypot(R[4 * P.root1[k]], R[4 * P.root1[k] + 2])); }
         dd old[3], prev[3], prev2[3];
         for (int t = 0; t < 3; ++t) {
             const int j = lane + 32 * t;
@@ -88,11 +103,12 @@ k_verify(const int64_t* __restrict__ coeffs, const double* __restrict__ roots,
 
     // ---- round and test integrality
     bool ok = true;
+    const double tol = fmin(0.25, 0x1p20 * (rr * pa * sinv + pa * 0x1p-90));
     for (int j = lane; j <= e; j += 32) {
         const dd v = qs[w][j];
         const double r = rint(v.hi);
         const double f = (v.hi - r) + v.lo;
-        if (!(fabs(f) < 0.25) || !(fabs(r) < 0x1p62)) ok = false;
+        if (!(fabs(f) < tol) || !(fabs(r) < 0x1p62)) ok = false;
         else qi[w][j] = (long long)r;
     }
     ok = __all_sync(0xffffffffu, ok);
