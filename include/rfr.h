@@ -135,6 +135,24 @@ typedef struct {
     rfr_diag diag;
 } rfr_factors;
 
+/* A factorisation of any nonzero p in Z[x] (rfr_factor_general):
+ * p = content * prod_i f_i^multiplicities[i], each f_i primitive,
+ * irreducible over Z and with a positive leading coefficient (content
+ * carries the sign), in canonical order (degree ascending, then the
+ * coefficients a_0 .. a_e lexicographic as signed int64, then the
+ * multiplicity).  coeffs holds the f_i one after the other, degrees[i] + 1
+ * ascending coefficients each.  rfr_squarefree fills the same structure
+ * with the square-free parts instead (each f_i square-free, not necessarily
+ * irreducible, pairwise coprime, distinct multiplicities apart from the
+ * factor x). */
+typedef struct {
+    int64_t  content;
+    int      n_factors;
+    int*     degrees;
+    int*     multiplicities;
+    int64_t* coeffs;
+} rfr_factorization;
+
 /* Device allocator hook (e.g. PyTorch's caching allocator).  alloc returns a
  * device pointer of at least `bytes` bytes usable on `stream` (a
  * cudaStream_t), or NULL; free releases it. */
@@ -163,6 +181,27 @@ int rfr_set_allocator(rfr_ctx* ctx, rfr_alloc_fn alloc, rfr_free_fn free_fn, voi
 /* Factor one polynomial (blocking).  On RFR_OK *out holds the factors; on
  * error *out is zeroed except out->diag.  Algorithm FACTOR, Section 2. */
 int rfr_factor(rfr_ctx* ctx, const int64_t* coeffs, int degree, rfr_factors* out);
+
+/* Factor any nonzero p in Z[x] of degree <= 128 (blocking), by the
+ * reductions Section 2 names: content and sign, the power of x, the monic
+ * transform q(y) = lc^(d-1) p(y / lc), Yun's square-free decomposition of q
+ * (modulo 61-bit primes, lifted and checked exactly), the GPU factorisation
+ * of every square-free part as one batch, and the back transform (primitive
+ * part of g(lc x)).  content * prod f^m == p is checked exactly.
+ * Errors: RFR_E_INVALID (NULL, zero polynomial, degree outside 0..128),
+ * RFR_E_RANGE (a transformed part has a coefficient of 2^53 or more),
+ * RFR_E_OVERFLOW (a lift or a back transform leaves 128-bit or int64
+ * range), and the errors of rfr_factor_batch.  Free *out with
+ * rfr_factorization_free. */
+int rfr_factor_general(rfr_ctx* ctx, const int64_t* coeffs, int degree, rfr_factorization* out);
+
+/* Square-free decomposition only (steps above up to Yun, mapped back to p),
+ * on the host: needs no context and no GPU. */
+int rfr_squarefree(const int64_t* coeffs, int degree, rfr_factorization* out);
+
+/* Free what rfr_factor_general / rfr_squarefree allocated; zeroes *f.
+ * NULL and zeroed structures are accepted. */
+void rfr_factorization_free(rfr_factorization* f);
 
 /* Factor `count` polynomials as one batch (blocking): the stages run once
  * over the whole batch.  coeffs[i] points at degrees[i]+1 coefficients.

@@ -57,6 +57,11 @@ class Diag(C.Structure):
                 ("launches", C.c_uint32), ("batch_size", C.c_uint32)]
 
 
+class Factorization(C.Structure):
+    _fields_ = [("content", C.c_int64), ("n_factors", C.c_int), ("degrees", C.POINTER(C.c_int)),
+                ("multiplicities", C.POINTER(C.c_int)), ("coeffs", C.POINTER(C.c_int64))]
+
+
 class Factors(C.Structure):
     _fields_ = [("n_factors", C.c_int), ("degrees", C.POINTER(C.c_int)),
                 ("coeffs", C.POINTER(C.c_int64)), ("diag", Diag)]
@@ -103,6 +108,9 @@ def lib():
         "rfr_wait": (i32, [vp, u64, i32, C.POINTER(Factors)]),
         "rfr_cancel": (i32, [vp, u64]),
         "rfr_factors_free": (None, [C.POINTER(Factors)]),
+        "rfr_factor_general": (i32, [vp, i64p, i32, C.POINTER(Factorization)]),
+        "rfr_squarefree": (i32, [i64p, i32, C.POINTER(Factorization)]),
+        "rfr_factorization_free": (None, [C.POINTER(Factorization)]),
         "rfr_stage_roots": (i32, [vp, vp, i32, i32, vp, vp, vp, vp]),
         "rfr_stage_weights": (i32, [vp, vp, i32, vp, vp, vp, C.c_double, vp, vp]),
         "rfr_stage_enumerate": (i32, [vp, i32, vp, vp]),
@@ -152,6 +160,38 @@ def _to_result(status: int, f: Factors) -> Result:
             off += e + 1
     lib().rfr_factors_free(C.byref(f))
     return res
+
+
+@dataclass
+class GeneralResult:
+    """p = content * prod f^m over `factors` [(f, m), ...] in canonical order."""
+    status: int
+    content: int = 0
+    factors: List[tuple] = field(default_factory=list)
+
+    @property
+    def ok(self) -> bool:
+        return self.status == RFR_OK
+
+
+def _to_general(status: int, f: Factorization) -> GeneralResult:
+    res = GeneralResult(status=int(status))
+    if status == RFR_OK:
+        res.content = int(f.content)
+        off = 0
+        for i in range(f.n_factors):
+            e = f.degrees[i]
+            res.factors.append(([int(f.coeffs[off + k]) for k in range(e + 1)], int(f.multiplicities[i])))
+            off += e + 1
+    lib().rfr_factorization_free(C.byref(f))
+    return res
+
+
+def squarefree(coeffs: Sequence[int]) -> GeneralResult:
+    """Square-free decomposition of any nonzero p in Z[x] (rfr_squarefree, host only)."""
+    f = Factorization()
+    st = lib().rfr_squarefree(_coeff_array(coeffs), len(coeffs) - 1, C.byref(f))
+    return _to_general(st, f)
 
 
 def _coeff_array(coeffs: Sequence[int]):
@@ -222,6 +262,12 @@ class Context:
         arr = _coeff_array(coeffs)
         st = lib().rfr_factor(self._h, arr, len(coeffs) - 1, C.byref(f))
         return _to_result(st, f)
+
+    def factor_general(self, coeffs: Sequence[int]) -> GeneralResult:
+        """Any nonzero p in Z[x]: content, multiplicities, irreducible factors."""
+        f = Factorization()
+        st = lib().rfr_factor_general(self._h, _coeff_array(coeffs), len(coeffs) - 1, C.byref(f))
+        return _to_general(st, f)
 
     def factor_batch(self, polys: Sequence[Sequence[int]]) -> List[Result]:
         n = len(polys)

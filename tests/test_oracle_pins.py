@@ -5,6 +5,8 @@ worked example of the paper, or brute force on tiny inputs, so that a
 dropped term, a wrong sign or a swapped index in the oracle fails here.
 """
 import itertools
+import json
+import os
 import random
 
 import mpmath
@@ -20,7 +22,7 @@ from oracle.reduction import reduce_poly
 from oracle.roots import complex_roots
 from oracle.sturm import real_root_count
 from oracle.zpoly import (is_squarefree, pdivmod_monic, peval, pmul, psub,
-                          padd, trim)
+                          padd, primitive, trim)
 from workloads import poly_mul, random_monic
 
 
@@ -448,3 +450,100 @@ def test_splat_match_equals_brute_force(n_a, n_b, shift):
     exp = band_pairs(expand_values(wa, M), expand_values(wb, M), M, W)
     assert (0, 0) in exp and (5, 2) in exp
     assert splat_match(wa, wb, W) == exp
+
+
+# ---------------------------------------------------------------- any p in Z[x] (Section 2's reductions)
+def _group_by_mult(parts):
+    """Multiply the parts of equal multiplicity together: {m: product}."""
+    out = {}
+    for f, m in parts:
+        out[m] = pmul(out.get(m, [1]), f)
+    return out
+
+
+def test_yun_textbook_example():
+    from oracle.squarefree import yun
+    pp = [1]
+    for f, m in (([-1, 1], 1), ([2, 1], 2), ([1, 0, 1], 3)):
+        for _ in range(m):
+            pp = pmul(pp, f)
+    assert yun(pp) == [([-1, 1], 1), ([2, 1], 2), ([1, 0, 1], 3)]
+
+
+def test_yun_invariants_on_random_constructions():
+    """prod a_i^i == pp, every a_i square-free, pairwise coprime, and equal
+    to the product of the construction's pieces of multiplicity i."""
+    from oracle.squarefree import expand, yun
+    from oracle.zpoly import is_squarefree
+    rng = random.Random(21)
+    for _ in range(12):
+        pieces = []
+        while len(pieces) < 4:
+            f = [rng.randint(-5, 5) for _ in range(rng.randint(1, 4))] + [rng.choice([1, 2, 3])]
+            f = trim(f)
+            if len(f) > 1 and f[0] != 0:
+                pieces.append((f, rng.randint(1, 3)))
+        pp = expand(1, pieces)
+        if not all(is_squarefree(primitive(g)) for g, _ in pieces):
+            continue
+        res = yun(primitive(pp))
+        assert expand(1, res) == primitive(pp)
+        for a, _ in res:
+            assert is_squarefree(a)
+        for (a, _), (b, _) in itertools.combinations(res, 2):
+            assert is_squarefree(pmul(a, b))                      # coprime square-free parts
+        if len({tuple(primitive(g)) for g, _ in pieces}) == 4 and is_squarefree(expand(1, [(g, 1) for g, _ in pieces])):
+            want = {m: primitive(f) for m, f in _group_by_mult(pieces).items()}
+            assert {m: f for f, m in res} == want
+
+
+def test_factor_general_constructions():
+    """content * prod f^m with irreducible f of known factorisation: monic
+    factors the oracle certified (degree 12, coefficients in [-10, 10]) and
+    Eisenstein polynomials (2x + 1; 3x^2 - 2 at 2; 5x^3 + 3x + 3 at 3)."""
+    from oracle.squarefree import expand, factor_general
+    recs = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "cfg1.json")))
+    monic = [f for r in recs for f in r["factors"] if len(f) > 2][:2]
+    eis = [[1, 2], [-2, 0, 3], [3, 3, 0, 5]]
+    for c, fs in ((-6, [(eis[0], 2), (eis[1], 1), ([0, 1], 3)]),
+                  (1, [(monic[0], 2), (eis[2], 1)]),
+                  (5, [(eis[1], 3), ([-1, 1], 1), ([1, 1], 2)])):
+        got_c, got = factor_general(expand(c, fs))
+        assert got_c == c
+        assert got == sorted(fs, key=lambda fm: (len(fm[0]) - 1, tuple(fm[0]), fm[1]))
+
+
+def test_squarefree_host_call_equals_oracle():
+    """rfr_squarefree (host code of the library, no GPU) against the oracle's
+    Yun: the same content, and per multiplicity the same product of parts."""
+    from paper_2410_15880_b300.build import build
+    build()
+    import paper_2410_15880_b300 as P
+    from oracle.squarefree import content, expand, yun
+    rng = random.Random(8)
+    cases = [[1, 0, -10, 0, 1], [0, 0, 3, 6], [-4, 0, 9], [7], [1, 2, 1], [2, 3, 1]]
+    for _ in range(20):
+        pieces = [(trim([rng.randint(-4, 4) for _ in range(rng.randint(1, 3))] + [rng.choice([1, 2, 3, -2])]),
+                   rng.randint(1, 3)) for _ in range(3)]
+        pieces = [(f, m) for f, m in pieces if len(f) > 1]
+        p = expand(rng.choice([1, -1, 3, -10]), pieces)
+        if max(abs(x) for x in p) < 1 << 40 and len(p) > 1:
+            cases.append(p)
+    for p in cases:
+        r = P.squarefree(p)
+        assert r.ok, p
+        c, pp = content(p)
+        assert r.content == c
+        assert _group_by_mult(r.factors) == _group_by_mult(yun(pp)), p
+        assert expand(r.content, r.factors) == trim(p)
+
+
+def test_squarefree_host_call_errors():
+    from paper_2410_15880_b300.build import build
+    build()
+    import paper_2410_15880_b300 as P
+    assert P.squarefree([0, 0, 0]).status == -1                   # the zero polynomial
+    assert P.squarefree([5]).ok and P.squarefree([5]).content == 5
+    big = [1] * 20 + [1000]                                        # no monic transform on this path
+    r = P.squarefree(big)
+    assert r.ok and r.content == 1 and r.factors == [(big, 1)]
