@@ -547,3 +547,49 @@ def test_squarefree_host_call_errors():
     big = [1] * 20 + [1000]                                        # no monic transform on this path
     r = P.squarefree(big)
     assert r.ok and r.content == 1 and r.factors == [(big, 1)]
+
+
+# ---------------------------------------------------------------- Algorithm B (search-tree pruning)
+def test_prune_jump_paper_example():
+    """Section 3.2's example: rho = (0.1, 0.2, 0.4, 0.8, ...), s ends in 1000
+    and has value 0.2; 0.2 + 0.1 + 0.2 + 0.4 = 0.9 < 1, so the next seven
+    patterns are skipped (a jump of 2^3).  From value 0.5 only 2^2."""
+    from oracle.prune import jump_exponent
+    M, W = 1000, 5
+    ws = [100, 200, 400, 800]
+    sigma = [0, 100, 300, 700, 1500]
+    assert jump_exponent(200, 3, ws, sigma, M, W) == 3
+    assert jump_exponent(500, 3, ws, sigma, M, W) == 2
+    assert jump_exponent(200, 1, ws, sigma, M, W) == 1              # at most the trailing zeros of s
+    assert jump_exponent(2, 3, ws, sigma, M, W) == 3                # 2 + 100 > W: nothing near 0 either
+    assert jump_exponent(960, 3, ws, sigma, M, W) == 0              # 960 + 100 reaches the band at 1
+
+
+@pytest.mark.parametrize("m,shift", [(10, 3), (12, 6), (14, 10)])
+def test_prune_equals_recombine_a(m, shift):
+    """RECOMBINE_B accepts exactly the patterns RECOMBINE_A accepts."""
+    from oracle.prune import dist, recombine_b
+    rng = random.Random(m)
+    M = 1 << 64
+    w = [rng.randrange(M) for _ in range(m)]
+    w[3] = (-(w[0] + w[5])) % M
+    W = M >> shift
+    got, visited, _ = recombine_b(w, M, W)
+    exp = {s for s in range(1 << m) if dist(sum(w[i] for i in range(m) if (s >> i) & 1), M) <= W}
+    assert set(got) == exp and len(got) == len(exp)
+    assert (1 | (1 << 3) | (1 << 5)) in exp and 0 in exp
+    assert visited < (1 << m)
+
+
+def test_prune_theorem_3_2_1_ratio():
+    """Theorem 3.2.1: patterns / visited is about 2^l / l, l = floor(sqrt(2m))
+    (for uniform values; the theorem's estimate drops the largest jumps)."""
+    from oracle.prune import improvement_ratio, recombine_b
+    M, m = 1 << 64, 16
+    ratios = []
+    for seed in range(6):
+        rng = random.Random(100 + seed)
+        w = [rng.randrange(M) for _ in range(m)]
+        ratios.append((1 << m) / recombine_b(w, M, M >> 40)[1])
+    mean = sum(ratios) / len(ratios)
+    assert 0.5 < mean / improvement_ratio(m) < 2.0
