@@ -48,8 +48,9 @@ def parse():
     ap.add_argument("--root-mode", type=int, default=1,
                     help="0 = FP64 Aberth, 1 = FP32 bulk + FP64 (default)")
     ap.add_argument("--no-autotune", action="store_true", help="use the default match layout")
-    ap.add_argument("--match-path", default="auto", choices=["auto", "tables", "splat"],
-                    help="rfr_config.match_path: automatic choice, table match only, or the splat match")
+    ap.add_argument("--match-path", default="auto", choices=["auto", "tables", "splat", "prune"],
+                    help="rfr_config.match_path: automatic choice, table match only, the splat match "
+                         "(Algorithm E) or the pruned search (Algorithm B)")
     ap.add_argument("--tune-cache", default="", help="file that stores tuned match layouts")
     return ap.parse_args()
 
@@ -352,7 +353,7 @@ def main():
             dist.barrier()
 
     flush = torch.empty((256 << 20,), dtype=torch.uint8, device="cuda")     # larger than L2 (126 MB)
-    match_path = {"auto": 0, "tables": 1, "splat": 2}[a.match_path]
+    match_path = {"auto": 0, "tables": 1, "splat": 2, "prune": 3}[a.match_path]
     with Context(device=local, timing=True, root_mode=a.root_mode, autotune=not a.no_autotune,
                  tune_cache_path=a.tune_cache, match_path=match_path) as ctx:
         for i in range(a.warmup):
@@ -435,6 +436,16 @@ def main():
         roof = {"bound": "hbm", "kernel": "k_splat_insert+k_splat_query", "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None, "algorithmic_bytes": alg_bytes, "avg_launch_us": join_us}
+    elif a.match_path == "prune":
+        # Algorithm B: integer ALU work per visited pattern (acceptance test, trailing
+        # zeros, jump search, O(1) value update), about 20 operations
+        apeak, apeak_kind = alu_peak()
+        visited = sum(r.diag["cand_coarse"] for r in res)
+        ops = 20.0 * visited
+        achieved = ops / (join_us * 1e-6) / 1e9
+        roof = {"bound": "alu", "kernel": "k_prune", "achieved": achieved, "peak": apeak,
+                "peak_kind": apeak_kind, "unit": "Gop/s", "frac": achieved / apeak, "traffic": None,
+                "algorithmic_ops": ops, "patterns_visited": visited, "avg_launch_us": join_us}
     elif fused:
         # the fused match (k_mitm) is the match stage; no table scatter ran
         apeak, apeak_kind = alu_peak()

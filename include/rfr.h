@@ -90,7 +90,9 @@ typedef struct {
                                    table match with the count-pass layout; RFR_MATCH_SPLAT: every
                                    problem with 13 < n_b <= 30 by the splat match (Section 4,
                                    Algorithm E), falling back to the table match when an insertion
-                                   overflows (same results on every path)                          */
+                                   overflows; RFR_MATCH_PRUNE: every problem with n_b > 13 and
+                                   n_a + n_b <= 40 by Algorithm B's pruned search (Section 3.2)
+                                   (same results on every path)                                    */
     int      reserved0;
 } rfr_config;
 
@@ -98,6 +100,7 @@ typedef struct {
 #define RFR_MATCH_AUTO   0
 #define RFR_MATCH_TABLES 1
 #define RFR_MATCH_SPLAT  2
+#define RFR_MATCH_PRUNE  3
 
 /* Per-polynomial diagnostics returned with each result.  The stage times,
  * copy bytes and launch count describe the whole batch the polynomial was

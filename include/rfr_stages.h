@@ -145,6 +145,23 @@ int rfr_stage_splat_match(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
                           uint64_t window, uint64_t window2, uint64_t* gamma, size_t gamma_cells,
                           uint64_t* cand, uint64_t cap, unsigned long long* counters, void* stream);
 
+/* Algorithm B (Section 3.2, RECOMBINE_B): every pattern s of the m searched
+ * elements w[0..m) (the fixed element left out) with
+ * dist(sum_{i in s} w_i mod 2^64) <= window (Eq. 9, circular), found by the
+ * pruned search: the elements are sorted ascending, and after a pattern with
+ * value x the search jumps over the next 2^j - 1 patterns when their values,
+ * all in [x + w_min, x + (sum of the j smallest)], miss both acceptance
+ * bands.  0 <= m <= 44 (the work is about 2^m / (2^l / l), l =
+ * floor(sqrt(2m)), Theorem 3.2.1).  Candidates are the accepted non-empty
+ * patterns whose w2 sum is within window2, as bit masks over w's order, at
+ * most cap written (any order).  counters: 8 device words, zeroed by the call:
+ * [0] patterns visited, [1] patterns within W (the empty one included),
+ * [2] candidates, [3] 1 when the empty pattern was met.
+ * workspace: 256 device bytes, 256-byte aligned (the launch descriptor). */
+int rfr_stage_prune(const uint64_t* w, const uint64_t* w2, int m, uint64_t window, uint64_t window2,
+                    uint64_t* cand, uint64_t cap, unsigned long long* counters,
+                    void* workspace, size_t workspace_bytes, void* stream);
+
 /* K-c + K-d + K-e for one problem given its weights: enumerate both halves
  * (keys of half b negated), radix-partition them by key (first digit fused
  * into the enumeration, second digit in shared memory inside the match),

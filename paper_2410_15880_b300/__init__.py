@@ -12,8 +12,8 @@ and importing the binding without the built library raises.
 """
 from ._native import (  # noqa: F401
     RFR_OK, RFR_PENDING, RFRError, Context, Result, GeneralResult, lib, status_name, squarefree,
-    stage_validate, stage_roots, stage_weights, stage_enumerate, stage_match, stage_lowlist, stage_splat, stage_splat_match,
+    stage_validate, stage_roots, stage_weights, stage_enumerate, stage_match, stage_lowlist, stage_splat, stage_splat_match, stage_prune,
     stage_verify,
     match_workspace_bytes, PLAN_DTYPE, RFR_MAX_DEGREE, RFR_LDC,
-    RFR_ROOTS_FP64, RFR_ROOTS_FP32_BULK, RFR_MATCH_AUTO, RFR_MATCH_TABLES, RFR_MATCH_SPLAT,
+    RFR_ROOTS_FP64, RFR_ROOTS_FP32_BULK, RFR_MATCH_AUTO, RFR_MATCH_TABLES, RFR_MATCH_SPLAT, RFR_MATCH_PRUNE,
 )

@@ -20,6 +20,7 @@ RFR_ROOTS_FP32_BULK = 1
 RFR_MATCH_AUTO = 0
 RFR_MATCH_TABLES = 1
 RFR_MATCH_SPLAT = 2
+RFR_MATCH_PRUNE = 3
 
 _STATUS = {
     0: "RFR_OK", 1: "RFR_PENDING", -1: "RFR_E_INVALID", -2: "RFR_E_NOT_MONIC",
@@ -117,6 +118,7 @@ def lib():
         "rfr_stage_match_workspace": (C.c_size_t, [i32, i32]),
         "rfr_stage_lowlist_workspace": (C.c_size_t, [i32]),
         "rfr_stage_lowlist": (i32, [vp, i32, i32, vp, vp, C.c_size_t, vp]),
+        "rfr_stage_prune": (i32, [vp, vp, i32, u64, u64, vp, u64, vp, vp, C.c_size_t, vp]),
         "rfr_stage_splat_cells": (C.c_size_t, [i32]),
         "rfr_stage_splat": (i32, [vp, i32, vp, C.c_size_t, vp, vp]),
         "rfr_stage_splat_match": (i32, [vp, vp, i32, vp, vp, i32, u64, u64, vp, C.c_size_t, vp, u64, vp, vp]),
@@ -454,6 +456,21 @@ def stage_splat_match(w_a, w2_a, w_b, w2_b, window: int, window2: int, cap: int)
                                        int(window), int(window2), _ptr(gamma), cells, _ptr(cand), int(cap),
                                        _ptr(ctr), _stream()), "rfr_stage_splat_match")
     return cand, ctr, gamma
+
+
+def stage_prune(w, w2, window: int, window2: int, cap: int):
+    """Algorithm B over the m = len(w) elements: (cand int64 [cap], counters int64 [8])."""
+    import torch
+    m = int(w.numel())
+    dev = w.device
+    ws = torch.empty((64,), dtype=torch.int64, device=dev)
+    aligned = (ws.data_ptr() + 255) & ~255
+    cand = torch.zeros((max(cap, 1),), dtype=torch.int64, device=dev)
+    ctr = torch.zeros((8,), dtype=torch.int64, device=dev)
+    _check(lib().rfr_stage_prune(_ptr(w) if m else None, _ptr(w2) if m else None, m, int(window), int(window2),
+                                 _ptr(cand), int(cap), _ptr(ctr), C.c_void_p(aligned), 256, _stream()),
+           "rfr_stage_prune")
+    return cand, ctr, ws
 
 
 def stage_verify(coeffs, degrees, roots, plans, prob, pat_lo, pat_hi, want_coeffs: bool = False):

@@ -844,7 +844,7 @@ static uint64_t default_halo_cap(int n_b, int d1, uint64_t wc) {
 }
 
 size_t match_bytes(const MatchGeom& g) {
-    if (g.splat) return g.bytes;
+    if (g.splat || g.prune) return g.bytes;
     if (g.fused) return mitm_half_bytes(g.l_a) + mitm_half_bytes(g.l_b) + align256(mitm_hit_cap(g) * 8);
     const size_t NB = (size_t)1 << g.d1;
     size_t b = 0;
@@ -882,7 +882,15 @@ bool match_geometry(int n_a, int n_b, uint64_t W, int ctas_a, int ctas_b, MatchG
                     const TuneParams* tp, int fuse) {
     if (n_a < 0 || n_b < n_a || n_b > 32) return false;
     g->splat = false;
-    if (optimistic && fuse == FUSE_SPLAT && splat_geometry(n_a, n_b, g)) return true;
+    g->prune = false;
+    if (optimistic && fuse == FUSE_SPLAT) {
+        if (splat_geometry(n_a, n_b, g)) return true;
+        fuse = FUSE_AUTO;
+    }
+    if (optimistic && fuse == FUSE_PRUNE) {
+        if (prune_geometry(n_a, n_b, g)) return true;
+        fuse = FUSE_AUTO;
+    }
     if (optimistic && (fuse == FUSE_ALWAYS || (fuse == FUSE_AUTO && n_a >= FUSED_MIN_NA))) {
         if (mitm_geometry(n_a, n_b, W, g)) return true;
         if (fuse == FUSE_ALWAYS) return false;
@@ -931,8 +939,15 @@ void match_layout(const MatchGeom& g, char* ws, ProbJob* pj) {
     HalfJob& B = pj->B;
     pj->splat = 0;
     pj->gamma = nullptr;
+    pj->prune = 0;
     if (g.splat) {
         splat_layout(g, ws, pj);
+        return;
+    }
+    if (g.prune) {
+        pj->prune = 1;
+        pj->fused = 0;
+        pj->n_a = g.n_a; pj->n_b = g.n_b;
         return;
     }
     pj->fused = g.fused ? 1 : 0;
@@ -1045,13 +1060,14 @@ cudaError_t run_match(ProbJob* jobs, int np, ProbJob* dev_jobs, HalfJob* dev_hal
     }
     // table problems first (compacted to the front of a copy), fused ones after
     std::vector<ProbJob> T;
-    std::vector<const ProbJob*> F, Sp;
+    std::vector<const ProbJob*> F, Sp, Pr;
     for (int i = 0; i < np; ++i) {
-        if (jobs[i].splat) Sp.push_back(&jobs[i]);
+        if (jobs[i].prune) Pr.push_back(&jobs[i]);
+        else if (jobs[i].splat) Sp.push_back(&jobs[i]);
         else if (jobs[i].fused) F.push_back(&jobs[i]);
         else T.push_back(jobs[i]);
     }
-    const int nT = (int)T.size(), nF = (int)F.size(), nS = (int)Sp.size();
+    const int nT = (int)T.size(), nF = (int)F.size(), nS = (int)Sp.size(), nP = (int)Pr.size();
     int nl = 0;
     cudaError_t e = cudaSuccess;
     if (nT) {
@@ -1091,6 +1107,11 @@ cudaError_t run_match(ProbJob* jobs, int np, ProbJob* dev_jobs, HalfJob* dev_hal
     if (nS) {
         e = run_splat(Sp.data(), nS, dev_jobs + nT + nF, s);
         nl += 2;
+        if (e != cudaSuccess) return e;
+    }
+    if (nP) {
+        e = run_prune(Pr.data(), nP, dev_jobs + nT + nF + nS, s);
+        nl += 1;
     }
     if (launches) *launches = nl;
     return e;

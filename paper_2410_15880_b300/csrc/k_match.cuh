@@ -65,6 +65,7 @@ struct ProbJob {
     uint64_t hcap;
     int splat;              // 1: matched by splat sort + query (Algorithm E; ctr has 8 words)
     uint64_t* gamma;        // splat array of half b
+    int prune;              // 1: searched by Algorithm B over all n_a + n_b elements
 };
 
 // One small problem (n_b <= SMALL_MAX_H) matched entirely in shared memory.
@@ -93,6 +94,7 @@ struct MatchGeom {
     bool fused;             // k_mitm: sorted lists only, units of 2^(64-d1) keys
     int nbl, slab, wf;
     bool splat;             // splat sort + query: one array of 2^(n_b+1) + SPLAT_TAIL cells
+    bool prune;             // Algorithm B: no tables at all
 };
 
 // Layout knobs chosen by the autotuner (defaults: 16, 13, 16).
@@ -104,8 +106,10 @@ struct TuneParams {
 
 // Which match a problem gets: tables in device memory, or the fused match
 // (k_mitm) for halves of at least FUSED_MIN_NA elements, or only the fused one.
-// FUSE_SPLAT: the splat match (Algorithm E) for every problem it fits.
-enum { FUSE_NEVER = 0, FUSE_AUTO = 1, FUSE_ALWAYS = 2, FUSE_SPLAT = 3 };
+// FUSE_SPLAT: the splat match (Algorithm E) for every problem it fits;
+// FUSE_PRUNE: Algorithm B for every problem of at most PRUNE_RUNTIME_MAX_M
+// searched elements; other problems get the automatic choice.
+enum { FUSE_NEVER = 0, FUSE_AUTO = 1, FUSE_ALWAYS = 2, FUSE_SPLAT = 3, FUSE_PRUNE = 4 };
 constexpr int FUSED_MIN_NA = 14;
 
 // Splat match (k_splat.cu): overflow cells past the 2^(n_b+1) home cells.
@@ -115,6 +119,14 @@ uint64_t* splat_layout(const MatchGeom& g, char* ws, ProbJob* pj);
 // Fill the splat arrays and launch insert + query for S[0..nS); dev_jobs holds
 // nS ProbJob slots of device memory.  Two kernel launches.
 cudaError_t run_splat(const ProbJob* const* S, int nS, void* dev_jobs, cudaStream_t s);
+
+// Algorithm B (k_prune.cu): at most PRUNE_MAX_M searched elements per stage
+// call, PRUNE_RUNTIME_MAX_M in the runtime (its work grows as 2^m / (2^l / l)).
+constexpr int PRUNE_MAX_M = 44;
+constexpr int PRUNE_RUNTIME_MAX_M = 40;
+bool prune_geometry(int n_a, int n_b, MatchGeom* g);
+// One kernel launch for P[0..nP); dev_jobs holds nP ProbJob slots.
+cudaError_t run_prune(const ProbJob* const* P, int nP, void* dev_jobs, cudaStream_t s);
 
 // Choose bucket bits and coarse window; returns false if the window is too
 // wide for any bucket layout.  optimistic = false always gives the table

@@ -527,7 +527,7 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
             if (rc != RFR_OK) return rc;
         }
     }
-    if (C.cfg.autotune && C.cfg.match_path != RFR_MATCH_SPLAT) {
+    if (C.cfg.autotune && C.cfg.match_path != RFR_MATCH_SPLAT && C.cfg.match_path != RFR_MATCH_PRUNE) {
         for (int sl : todo) {
             Work& w = work[sl];
             const std::pair<int, int> key{w.plan.n_a, w.plan.n_b};
@@ -560,7 +560,8 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
             const TuneParams tp = params_for(w);
             if (!match_geometry(w.plan.n_a, w.plan.n_b, w.plan.window, part_ctas(w.plan.n_a, tot_elems, tp.cta_per_sm),
                                 part_ctas(w.plan.n_b, tot_elems, tp.cta_per_sm), &g, !w.full_halo, &tp,
-                                C.cfg.match_path == RFR_MATCH_SPLAT ? FUSE_SPLAT : FUSE_AUTO)) { w.status = RFR_E_WINDOW; continue; }
+                                C.cfg.match_path == RFR_MATCH_SPLAT ? FUSE_SPLAT :
+                                C.cfg.match_path == RFR_MATCH_PRUNE ? FUSE_PRUNE : FUSE_AUTO)) { w.status = RFR_E_WINDOW; continue; }
             if (w.full_halo) { g.hcap = 1ull << g.n_b; g.bytes = match_bytes(g); }
             const size_t need = g.bytes + (size_t)cap * 8 + 6 * 8 + 512;
             if (need > C.budget) { w.status = RFR_E_BUDGET; continue; }
@@ -598,7 +599,7 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
             pj.ctr = (unsigned long long*)ctr;
             pj.A.err = pj.B.err = (int*)(ctr + 4);
             cudaMemsetAsync(ctr, 0, 8 * 8, s);
-            if (w.geom.fused || w.geom.splat)
+            if (w.geom.fused || w.geom.splat || w.geom.prune)
                 ;                                       // no tables (the splat arrays are filled by run_splat)
             else if (w.geom.optimistic)
                 cudaMemsetAsync(pj.A.bcount, 0, 3 * (((((size_t)1 << w.geom.d1) * 4) + 255) & ~(size_t)255), s);
@@ -868,7 +869,7 @@ int rfr_create(const rfr_config* cfg_in, rfr_ctx** out) {
     rfr_config cfg;
     if (cfg_in) cfg = *cfg_in; else rfr_config_default(&cfg);
     if (cfg.max_inflight < 1 || cfg.max_batch < 1 || (cfg.root_mode != RFR_ROOTS_FP64 && cfg.root_mode != RFR_ROOTS_FP32_BULK) ||
-        (cfg.match_path != RFR_MATCH_AUTO && cfg.match_path != RFR_MATCH_TABLES && cfg.match_path != RFR_MATCH_SPLAT))
+        (cfg.match_path < RFR_MATCH_AUTO || cfg.match_path > RFR_MATCH_PRUNE))
         return RFR_E_INVALID;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg.device < 0 || cfg.device >= ndev) { cudaGetLastError(); return RFR_E_CUDA; }
