@@ -214,6 +214,27 @@ void rfr_factorization_free(rfr_factorization* f);
 int rfr_factor_batch(rfr_ctx* ctx, int count, const int64_t* const* coeffs,
                      const int* degrees, rfr_factors* outs, int* statuses);
 
+/* Key-range sharding of one batch over nshards processes (one per GPU),
+ * each calling this with its own shard index (0 .. nshards-1) on the same
+ * inputs.  The fused match of every problem searches only this shard's
+ * contiguous share of the key units (the slabs of half a's key space); the
+ * other matches (small halves, table match) run on shard 0, and a problem
+ * that a shard redoes with the table match is searched whole there.  After
+ * verifying its own candidates, every shard calls gather once (even with
+ * nothing to send):
+ *   mine/n_mine: this shard's verified divisor sets as n_mine triples
+ *   (item index, pattern bits 0-63, pattern bits 64-127);
+ *   *all/*n_all: the caller returns every shard's triples (malloc'ed; the
+ *   library frees them), e.g. an all-gather over a process group.
+ * gather returns 0, or non-zero to fail the batch (RFR_E_INVALID).  Every
+ * shard then builds the atoms from the union, so all shards return the same
+ * factorisation.  A shard whose batch fails before the gather does not call
+ * it: give the exchange a timeout.  nshards == 1 is rfr_factor_batch. */
+typedef int (*rfr_gather_fn)(const uint64_t* mine, size_t n_mine, uint64_t** all, size_t* n_all, void* user);
+int rfr_factor_batch_sharded(rfr_ctx* ctx, int count, const int64_t* const* coeffs, const int* degrees,
+                             int shard, int nshards, rfr_gather_fn gather, void* user,
+                             rfr_factors* outs, int* statuses);
+
 /* As rfr_factor_batch, for inputs already in device memory:
  * d_coeffs is int64 [count][RFR_MAX_DEGREE+1] (ascending, row i holds
  * polynomial i, entries above its degree ignored) and d_degrees int32

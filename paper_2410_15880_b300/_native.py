@@ -80,6 +80,11 @@ PLAN_DTYPE = np.dtype([
 
 _lib = None
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+GATHER_FN = C.CFUNCTYPE(C.c_int, C.POINTER(C.c_uint64), C.c_size_t, C.POINTER(C.POINTER(C.c_uint64)),
+                        C.POINTER(C.c_size_t), C.c_void_p)
+_libc = C.CDLL(None)
+_libc.malloc.restype = C.c_void_p
+_libc.malloc.argtypes = [C.c_size_t]
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
 
@@ -103,6 +108,8 @@ def lib():
         "rfr_factor": (i32, [vp, i64p, i32, C.POINTER(Factors)]),
         "rfr_factor_batch": (i32, [vp, i32, C.POINTER(i64p), C.POINTER(C.c_int), C.POINTER(Factors), C.POINTER(C.c_int)]),
         "rfr_factor_batch_device": (i32, [vp, i32, vp, vp, C.POINTER(Factors), C.POINTER(C.c_int)]),
+        "rfr_factor_batch_sharded": (i32, [vp, i32, C.POINTER(i64p), C.POINTER(C.c_int), i32, i32, GATHER_FN, vp,
+                                           C.POINTER(Factors), C.POINTER(C.c_int)]),
         "rfr_stage_validate": (i32, [vp, vp, i32, vp, vp]),
         "rfr_submit": (i32, [vp, i64p, i32, C.POINTER(u64)]),
         "rfr_poll": (i32, [vp, u64, C.POINTER(Factors)]),
@@ -283,6 +290,37 @@ class Context:
             for i in range(n):
                 lib().rfr_factors_free(C.byref(outs[i]))
             raise RFRError(rc, "rfr_factor_batch")
+        return [_to_result(sts[i], outs[i]) for i in range(n)]
+
+    def factor_batch_sharded(self, polys: Sequence[Sequence[int]], shard: int, nshards: int, gather) -> List[Result]:
+        """This process's key-range shard of the batch (rfr_factor_batch_sharded).
+        gather(list of (item, lo, hi)) -> every shard's triples, e.g.
+        sharding.torch_gather()."""
+        def _cb(mine, n_mine, all_pp, n_all_p, user):
+            try:
+                triples = [(int(mine[3 * i]), int(mine[3 * i + 1]), int(mine[3 * i + 2])) for i in range(n_mine)]
+                allt = list(gather(triples))
+                buf = _libc.malloc(max(1, 24 * len(allt)))
+                if not buf:
+                    return 1
+                arr = (C.c_uint64 * max(1, 3 * len(allt))).from_address(buf)
+                for i, (it, lo, hi) in enumerate(allt):
+                    arr[3 * i], arr[3 * i + 1], arr[3 * i + 2] = it, lo, hi
+                all_pp[0] = C.cast(buf, C.POINTER(C.c_uint64))
+                n_all_p[0] = len(allt)
+                return 0
+            except Exception:
+                return 1
+        cb = GATHER_FN(_cb)
+        n = len(polys)
+        arrs = [_coeff_array(p) for p in polys]
+        ptrs = (C.POINTER(C.c_int64) * n)(*[C.cast(a, C.POINTER(C.c_int64)) for a in arrs])
+        degs = (C.c_int * n)(*[len(p) - 1 for p in polys])
+        outs = (Factors * n)()
+        sts = (C.c_int * n)()
+        rc = lib().rfr_factor_batch_sharded(self._h, n, ptrs, degs, int(shard), int(nshards), cb, None, outs, sts)
+        if rc != RFR_OK:
+            raise RFRError(rc, "rfr_factor_batch_sharded")
         return [_to_result(sts[i], outs[i]) for i in range(n)]
 
     def factor_batch_device(self, coeffs, degrees) -> List[Result]:

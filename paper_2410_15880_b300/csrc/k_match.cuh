@@ -66,6 +66,7 @@ struct ProbJob {
     int splat;              // 1: matched by splat sort + query (Algorithm E; ctr has 8 words)
     uint64_t* gamma;        // splat array of half b
     int prune;              // 1: searched by Algorithm B over all n_a + n_b elements
+    int shard, nshards;     // fused match: only key-range shard `shard` of `nshards` (0 = all)
 };
 
 // One small problem (n_b <= SMALL_MAX_H) matched entirely in shared memory.

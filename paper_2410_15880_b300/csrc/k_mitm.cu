@@ -211,7 +211,7 @@ struct MitmJob {
     const uint64_t* w_b; const uint64_t* w2_b;
     int n_a, n_b, l_a, l_b;
     int d1, nbl, slab, wf;                                    // units, bins per unit, units per CTA, fingerprint window
-    int cta_base, pad0;
+    int cta_base, c_lo;                                       // first CTA in the grid; first slab (key-range shard)
     uint64_t W, W2, Wc;
     uint64_t* cand;
     uint64_t cap;
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
         if (js[mid].cta_base <= (int)blockIdx.x) jl = mid; else jh = mid - 1;
     }
     const MitmJob& P = js[jl];
-    const int c = blockIdx.x - P.cta_base;
+    const int c = blockIdx.x - P.cta_base + P.c_lo;
     const int n_a = P.n_a, n_b = P.n_b, la = P.l_a, lb = P.l_b;
     const uint32_t Na = 1u << la, Nb = 1u << lb;
     const int RA = 1 << (n_a - la), RB = 1 << (n_b - lb);
@@ -691,12 +691,17 @@ cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev
         m.W = P.W; m.W2 = P.W2; m.Wc = P.Wc;
         m.cand = P.cand; m.cap = P.cap; m.ctr = P.ctr; m.err = P.A.err;
         m.hits = P.hits; m.nhits = P.ctr + 5; m.hcap = P.hcap;          // counters[5]: fingerprint hits
-        ctas += (1 << P.d1) / P.slab;
+        // key-range shard: slabs [lo, hi) of this problem's (1 << d1) / slab
+        const int slabs = (1 << P.d1) / P.slab;
+        const int ns = P.nshards > 1 ? P.nshards : 1, sh = P.nshards > 1 ? P.shard : 0;
+        const int lo = (int)((int64_t)slabs * sh / ns), hi = (int)((int64_t)slabs * (sh + 1) / ns);
+        m.c_lo = lo;
+        ctas += hi - lo;
     }
     MitmJob* d_mj = (MitmJob*)dev_mjobs;
     e = cudaMemcpyAsync(d_mj, mj.data(), sizeof(MitmJob) * nF, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
-    k_mitm<<<ctas, MT_THREADS, MT_SMEM, s>>>(d_mj, nF);
+    if (ctas > 0) k_mitm<<<ctas, MT_THREADS, MT_SMEM, s>>>(d_mj, nF);
     k_mitm_check<<<nF * 64, 256, 0, s>>>(d_mj, 64);
     return cudaGetLastError();
 }

@@ -135,6 +135,13 @@ struct Pipeline {
     // dev_coeffs/dev_deg: device rows for every item in order (device inputs),
     // or null (host inputs, copied in).
     int run(std::vector<Item>& items, const int64_t* dev_coeffs = nullptr, const int32_t* dev_deg = nullptr);
+    // Key-range sharding of the batch (rfr_factor_batch_sharded): the fused
+    // match searches only this shard's slabs, other matches run on shard 0
+    // (and on any shard that redoes a problem with the table match), and the
+    // verified divisor sets of all shards are exchanged through `gather`
+    // before the atoms.
+    struct Shard { int index = 0, count = 1; rfr_gather_fn gather = nullptr; void* user = nullptr; } shard;
+    bool sharded() const { return shard.count > 1; }
 };
 
 struct Request {
@@ -479,6 +486,10 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
         std::vector<int> small, big;
         for (int sl : todo) (work[sl].plan.n_b <= SMALL_MAX_H && work[sl].plan.window < (1ull << 62) ? small : big).push_back(sl);
         todo.swap(big);
+        if (sharded() && shard.index != 0) {              // shard 0 matches the small problems
+            for (int sl : small) work[sl].matched = true;
+            small.clear();
+        }
         if (!small.empty()) {
             const int ns = (int)small.size();
             const size_t per = (((size_t)cap * 8 + 255) & ~(size_t)255) + 256;
@@ -515,7 +526,7 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
             for (int i = 0; i < ns && rc == RFR_OK; ++i) {
                 Work& w = work[small[i]];
                 memcpy(w.ctr, &h_ctr[6 * i], sizeof(w.ctr));
-                if (w.ctr[3] == 0) { w.status = RFR_E_INTERNAL; continue; }
+                if (w.ctr[3] == 0 && shard.index == 0) { w.status = RFR_E_INTERNAL; continue; }
                 if (w.ctr[2] > cap) { w.status = RFR_E_CAND_OVERFLOW; continue; }
                 w.cand.resize(w.ctr[2]);
                 if (w.ctr[2]) rc = cuda_ok(cudaMemcpyAsync(w.cand.data(), cands[i], w.ctr[2] * 8, cudaMemcpyDeviceToHost, s));
@@ -563,6 +574,7 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
                                 C.cfg.match_path == RFR_MATCH_SPLAT ? FUSE_SPLAT :
                                 C.cfg.match_path == RFR_MATCH_PRUNE ? FUSE_PRUNE : FUSE_AUTO)) { w.status = RFR_E_WINDOW; continue; }
             if (w.full_halo) { g.hcap = 1ull << g.n_b; g.bytes = match_bytes(g); }
+            if (sharded() && shard.index != 0 && !g.fused && !w.full_halo) { w.matched = true; continue; }
             const size_t need = g.bytes + (size_t)cap * 8 + 6 * 8 + 512;
             if (need > C.budget) { w.status = RFR_E_BUDGET; continue; }
             if (!sub.empty() && bytes + need > share) { rest.push_back(sl); continue; }
@@ -595,6 +607,7 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
             pj.w_a = dp->w;                     pj.w2_a = dp->w2;
             pj.w_b = dp->w + w.plan.n_a;        pj.w2_b = dp->w2 + w.plan.n_a;
             pj.W = w.plan.window;               pj.W2 = w.plan.window2;
+            pj.shard = shard.index;             pj.nshards = shard.count;
             pj.cand = cbuf;                     pj.cap = cap;
             pj.ctr = (unsigned long long*)ctr;
             pj.A.err = pj.B.err = (int*)(ctr + 4);
@@ -626,7 +639,8 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
             Work& w = work[sub[i]];
             memcpy(w.ctr, &h_ctr[6 * i], sizeof(w.ctr));
             if (w.ctr[4]) { w.full_halo = true; todo.push_back(w.slot); continue; }   // retry with a full halo
-            if (w.ctr[3] == 0) { w.status = RFR_E_INTERNAL; continue; }               // empty pattern must match
+            // the empty pattern must match (in the shard that holds key 0, or on a full redo)
+            if (w.ctr[3] == 0 && (shard.index == 0 || !w.geom.fused)) { w.status = RFR_E_INTERNAL; continue; }
             if (w.ctr[2] > cap) { w.status = RFR_E_CAND_OVERFLOW; continue; }
             w.cand.resize(w.ctr[2]);
             if (w.ctr[2]) rc = cuda_ok(cudaMemcpyAsync(w.cand.data(), jobs[i].cand, w.ctr[2] * 8, cudaMemcpyDeviceToHost, s));
@@ -691,6 +705,28 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
             if (res[j] == 1) { Bits b; b.lo = jlo[j]; w.verified.push_back(b); }
             else if (res[j] == RFR_E_OVERFLOW) w.status = RFR_E_OVERFLOW;
         }
+    }
+    if (sharded()) {
+        // every shard's verified divisor sets, as (item, lo, hi) triples
+        std::vector<uint64_t> mine;
+        for (auto& w : work)
+            for (auto& v : w.verified) { mine.push_back((uint64_t)w.item); mine.push_back(v.lo); mine.push_back(v.hi); }
+        uint64_t* all = nullptr;
+        size_t n_all = 0;
+        if (!shard.gather || shard.gather(mine.data(), mine.size() / 3, &all, &n_all, shard.user) != 0)
+            { free(all); return RFR_E_INVALID; }
+        std::vector<int> by_item(items.size(), -1);
+        for (auto& w : work) by_item[w.item] = w.slot;
+        for (size_t t = 0; t < n_all; ++t) {
+            const uint64_t it = all[3 * t];
+            if (it >= items.size() || by_item[it] < 0) continue;
+            Work& w = work[by_item[it]];
+            const Bits b{all[3 * t + 1], all[3 * t + 2]};
+            bool seen = false;
+            for (auto& x : w.verified) if (x == b) { seen = true; break; }
+            if (!seen) w.verified.push_back(b);
+        }
+        free(all);
     }
     {
         std::vector<int32_t> jp, res;
@@ -959,6 +995,27 @@ int rfr_factor_batch(rfr_ctx* x, int count, const int64_t* const* coeffs, const 
     std::vector<Item> items(count);
     for (int i = 0; i < count; ++i) items[i] = {coeffs[i], degrees[i], RFR_OK, &outs[i]};
     int rc = C.sync_pipe.run(items);
+    for (int i = 0; i < count; ++i) {
+        const int st = rc == RFR_OK ? items[i].status : rc;
+        if (statuses) statuses[i] = st;
+        if (st != RFR_OK) { rfr_factors_free(&outs[i]); }
+    }
+    return rc;
+}
+
+int rfr_factor_batch_sharded(rfr_ctx* x, int count, const int64_t* const* coeffs, const int* degrees,
+                             int shard, int nshards, rfr_gather_fn gather, void* user,
+                             rfr_factors* outs, int* statuses) {
+    if (!x || count < 0 || (count && (!coeffs || !degrees || !outs))) return RFR_E_INVALID;
+    if (nshards < 1 || shard < 0 || shard >= nshards || (nshards > 1 && !gather)) return RFR_E_INVALID;
+    Ctx& C = x->c;
+    std::lock_guard<std::mutex> lk(C.sync_mu);
+    cudaSetDevice(C.device);
+    std::vector<Item> items(count);
+    for (int i = 0; i < count; ++i) items[i] = {coeffs[i], degrees[i], RFR_OK, &outs[i]};
+    C.sync_pipe.shard = {shard, nshards, gather, user};
+    int rc = C.sync_pipe.run(items);
+    C.sync_pipe.shard = Pipeline::Shard();
     for (int i = 0; i < count; ++i) {
         const int st = rc == RFR_OK ? items[i].status : rc;
         if (statuses) statuses[i] = st;

@@ -180,3 +180,35 @@ def test_tables_only_equals_fused():
         assert a.ok and t.ok
         assert a.factors == t.factors == r["factors"]
         assert a.diag["cand_post"] == t.diag["cand_post"]
+
+
+def test_key_range_shards_equal_whole_batch():
+    """Two key-range shards of one batch, run by two threads with their own
+    contexts on this GPU and exchanging verified sets on the host (no kernel
+    waits on another): both return the goldens' factorisations, and the fused
+    problems' candidates split between the shards without overlap."""
+    import threading
+    from paper_2410_15880_b300 import Context
+    from paper_2410_15880_b300.sharding import ThreadExchange
+    recs = golden("cfg3")[:4] + golden("cfg2")[:4] + golden("cfg1") + golden("special")
+    polys = [r["coeffs"] for r in recs]
+    with Context(device=0, mem_budget_bytes=16 << 30) as c:
+        whole = c.factor_batch(polys)
+    ex = ThreadExchange(2, timeout=120)
+    out = [None, None]
+
+    def run(s):
+        with Context(device=0, mem_budget_bytes=16 << 30) as c:
+            out[s] = c.factor_batch_sharded(polys, s, 2, ex.gather_for(s))
+    th = [threading.Thread(target=run, args=(s,)) for s in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(timeout=600)
+    for r, w, a, b in zip(recs, whole, out[0], out[1]):
+        assert w.ok and a.ok and b.ok, r.get("name")
+        assert a.factors == b.factors == w.factors == r["factors"]
+        if w.diag["n_a"] >= 14:                       # fused: the shards partition the key units
+            assert a.diag["cand_post"] + b.diag["cand_post"] == w.diag["cand_post"]
+        else:                                         # small halves: matched on shard 0
+            assert b.diag["cand_post"] == 0
