@@ -200,8 +200,8 @@ int rfr_stage_match_exact(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
  * in device memory: sorted lists of the halves' low-subset sums are built
  * by merging, and each CTA generates a range of half a's keys into a
  * shared-memory table and looks half b's keys of that range up in it.
- * rfr_stage_match uses it by itself for 14 <= n_a <= n_b <= 28.  Returns
- * RFR_E_WINDOW if a half has more than 28 elements or the window is too wide
+ * rfr_stage_match uses it by itself for 14 <= n_a <= n_b <= 31.  Returns
+ * RFR_E_WINDOW if a half has more than 31 elements or the window is too wide
  * for it (about
  * W >= 2^(59 - max(n_a - 13, 2))); counters[4] = 1 when one key range holds
  * more than 12288 keys of half a (clustered keys), or when the workspace has

@@ -433,8 +433,8 @@ def stage_match(w_a, w2_a, w_b, w2_b, window: int, window2: int, cap: int, exact
     n_a, n_b = int(w_a.numel()), int(w_b.numel())
     dev = w_b.device
     ws_bytes = match_workspace_bytes(n_a, n_b)
-    if fused:                                   # room for every pair as a fingerprint hit (wide windows)
-        ws_bytes += 8 * min(1 << (n_a + n_b), 1 << 24)
+    if fused:                                   # room for fingerprint hits (wide windows, largest halves)
+        ws_bytes += 8 * min(1 << (n_a + n_b), 1 << 26)
     ws = torch.empty((ws_bytes // 8 + 64,), dtype=torch.int64, device=dev)
     base = ws.data_ptr()
     aligned = (base + 255) & ~255

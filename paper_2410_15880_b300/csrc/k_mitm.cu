@@ -298,10 +298,8 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
     const int gid = warp * (32 / GL) + gi, NG = (int)blockDim.x / GL;
     const uint32_t gbits = (1u << GL) - 1u;
     const uint32_t lma = Na - 1u, lmb = Nb - 1u;                      // low-list masks (l <= 21)
-    // table slots: the groups holding a run of half a (RA <= groups, one run each)
-    // share all but MT_POOL slots equally
-    const int gact = RA < (int)blockDim.x / GL ? RA : (int)blockDim.x / GL;
-    const uint32_t gslots = (uint32_t)((MT_ACAP - MT_POOL) / gact);
+    // table slots: the runs of half a share all but MT_POOL slots equally
+    const uint32_t gslots = (uint32_t)((MT_ACAP - MT_POOL) / RA);
     uint2* wq = queue + warp * MT_QCAP;
 
     if (threadIdx.x < n_a) wa[threadIdx.x] = P.w_a[threadIdx.x];
@@ -413,8 +411,9 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
                 const uint32_t jj = j0a[rr];
                 uint32_t t = act ? ta[rr] : 0u;
                 const uint32_t tfirst = t;
-                // this group's slots: gslots from gbase; keys beyond them go to the shared pool
-                const uint32_t gbase = MT_POOL + (uint32_t)(act ? gid : 0) * gslots;
+                // this run's slots: gslots from gbase (one region per run, so a group that walks
+                // several runs in turn keeps all their keys); keys beyond them go to the shared pool
+                const uint32_t gbase = MT_POOL + (uint32_t)(act ? run : 0) * gslots;
                 // chunks are read unconditionally: the index is taken modulo Na
                 uint64_t y0 = Ya[(jj + t + gl) & lma], y1 = Ya[(jj + t + GL + gl) & lma];
                 uint64_t y2 = Ya[(jj + t + 2 * GL + gl) & lma], y3 = Ya[(jj + t + 3 * GL + gl) & lma];

@@ -339,3 +339,39 @@ def test_match_fused_clustered_keys_overflow(P):
     assert ctr2[4] == 0
     scan = set(recombine_a(wa + wb + [0], M64, W)) - {0}
     assert got == {(s & ((1 << na) - 1), s >> na) for s in scan} and (1, 0) in got
+
+
+@pytest.mark.parametrize("seed,na,nb,compare_tables", [(41, 29, 30, True), (42, 30, 31, False)])
+def test_match_fused_largest_halves(P, seed, na, nb, compare_tables):
+    """The fused match at its largest halves (up to 2^10 runs per half, 2^30
+    + 2^31 half-sums).  Every reported pair is re-checked one by one from its
+    masks; the planted pairs (across the circular wrap, and three integral
+    subsets) must all be found; at 2^29 + 2^30 the candidate set also equals
+    the table match's (exact layout)."""
+    from oracle.recombine import accept
+    rng = random.Random(seed)
+    wa = [rng.randrange(M64) for _ in range(na)]
+    wb = [rng.randrange(M64) for _ in range(nb)]
+    wa[0], wb[0] = M64 - 3, M64 - 2
+    wa[1], wb[1] = 3, 2
+    wb[5] = (-(wa[4] + wa[7] + wb[9])) % M64
+    wa[11] = (-(wb[12] + wb[13])) % M64
+    wb[20] = (-(wa[2] + wa[na - 1])) % M64
+    W = 1 << 6                                        # about 2^(na+nb) * 2^7 / 2^64 random pairs
+    torch.cuda.empty_cache()
+    got, ctr, raw = _run_match(P, wa, [0] * na, wb, [0] * nb, W, 0, cap=1 << 16, fused=True)
+    assert ctr[4] == 0 and ctr[3] == 1 and len(raw) == len(set(raw)) == ctr[2]
+    for i, j in got:                                  # each reported pair, from its masks
+        s = sum(wa[k] for k in range(na) if (i >> k) & 1) + sum(wb[k] for k in range(nb) if (j >> k) & 1)
+        assert accept(s % M64, M64, W)
+    planted = {(1, 0), (0, 1), (1 << 1, 1 << 1), (0, (1 << 5) | (1 << 9)), (1 << 11, (1 << 12) | (1 << 13)),
+               ((1 << 4) | (1 << 7), (1 << 5) | (1 << 9)), ((1 << 2) | (1 << (na - 1)), 1 << 20)}
+    planted = {(i, j) for i, j in planted
+               if accept((sum(wa[k] for k in range(na) if (i >> k) & 1) +
+                          sum(wb[k] for k in range(nb) if (j >> k) & 1)) % M64, M64, W)}
+    assert len(planted) >= 5 and planted <= got
+    if compare_tables:
+        torch.cuda.empty_cache()
+        got_t, ctr_t, _ = _run_match(P, wa, [0] * na, wb, [0] * nb, W, 0, cap=1 << 16, exact=True)
+        assert ctr_t[4] == 0 and got_t == got
+    torch.cuda.empty_cache()
