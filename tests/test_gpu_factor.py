@@ -212,3 +212,23 @@ def test_key_range_shards_equal_whole_batch():
             assert a.diag["cand_post"] + b.diag["cand_post"] == w.diag["cand_post"]
         else:                                         # small halves: matched on shard 0
             assert b.diag["cand_post"] == 0
+
+
+def test_poll_batch_serving():
+    """rfr_poll_batch: many requests tracked with one call per sweep; every
+    result equals its golden and each ticket is released once."""
+    import time
+    from paper_2410_15880_b300 import Context
+    recs = golden("cfg4_sample")[:24] + golden("cfg2")[:8]
+    with Context(device=0, max_inflight=2, max_batch=16) as c:
+        tickets = [c.submit(r["coeffs"]) for r in recs]
+        results, pending = {}, list(range(len(recs)))
+        deadline = time.time() + 120
+        while pending and time.time() < deadline:
+            got = c.poll_batch([tickets[i] for i in pending])
+            pending = [i for i, r in zip(pending, got) if r is None or results.setdefault(i, r) is None]
+            time.sleep(0.001)
+        assert not pending
+        assert all(results[i].ok and results[i].factors == r["factors"] for i, r in enumerate(recs))
+        again = c.poll_batch(tickets[:3])                  # released tickets are unknown now
+        assert all(x is not None and x.status == -1 for x in again)
