@@ -512,6 +512,13 @@ def main():
                    "autotune": ("off" if a.no_autotune else "layouts tuned per (n_a, n_b) during warm-up"),
                    "match_path": a.match_path},
         "half_sums_per_s": half_sums * world * a.steps / (ms / 1e3),
+        # what a design that keeps the sorted halves in HBM would need to move for the same
+        # half-sums/s: 128 B per half-sum for enumerate + 4 LSD passes + join, 24 B at the
+        # method's floor (each table written once and read once)
+        "hbm_model": {"bytes_per_half_sum_sorted_tables": 128, "bytes_per_half_sum_floor": 24,
+                      "equivalent_GBps_sorted_tables": 128 * half_sums * a.steps / (ms / 1e3) / 1e9,
+                      "equivalent_GBps_floor": 24 * half_sums * a.steps / (ms / 1e3) / 1e9,
+                      "hbm_peak_GBps": peak},
         "roofline": roof,
         "stage_us_per_step": {"validate+roots": roots_us,
                               "weights": statistics.mean(d["stage_us"][1] for d in per_step),
