@@ -1,8 +1,11 @@
 // k_roots.cu — K-a: batched root finder (the "black box" of Section 2).
 //
-// Three kernels: k_aberth (one CTA per polynomial, one thread per root,
-// d <= 128) for steps 1-2; k_polish and k_radius (one warp per root, the
-// polynomial split over its lanes, spread over the whole GPU) for steps 3 and 4.
+// Three kernels: k_aberth (one CTA per polynomial, SL = 4 lanes per root,
+// d <= 128) for steps 1-2; k_polish and k_radius (SL lanes per root, the
+// polynomial split over them, spread over the whole GPU) for steps 3 and 4.
+// Every evaluation of p is a split Horner scheme over the root's SL lanes:
+// the dependent chain is about d / SL steps, and a CTA holds SL times the
+// warps of one thread per root, so the iteration is not latency-bound.
 //  1. Starting points from the Newton polygon of p (upper convex hull of
 //     (k, log|a_k|)): for each hull edge of width m, m points on a circle
 //     whose radius is the edge's geometric-mean root modulus (Bini 1996).
@@ -47,53 +50,94 @@ template <typename T> struct eps_of;
 template <> struct eps_of<double> { static constexpr double v = 1.1102230246251565e-16; };
 template <> struct eps_of<float> { static constexpr float v = 5.9604645e-8f; };
 
-// Newton ratio p(z)/p'(z); *noise = |p(z)| is below its evaluation error bound.
+constexpr int SL = 4;                         // lanes per root in every kernel of this file
+
+// p(x), p'(x) and sum_k |c(k)| |x|^k for the polynomial sum_{k=0}^{n} c(k) x^k,
+// split over the root's SL lanes (mask: the lanes of the warp taking part, whole
+// roots only).  Lane l of a root takes the B = ceil((n+1)/SL) coefficients k in
+// [lB, lB + B) by Horner (three independent chains); a shuffle tree adds the
+// lanes' parts times x^(lB).  The root's first lane holds the result.
+template <typename T> struct Eval3 { cx<T> p, dp; T mag; };
+template <typename T, class Coef>
+__device__ __forceinline__ Eval3<T> split_eval3(unsigned mask, int n, cx<T> x, T ax, Coef c) {
+    const int lane = threadIdx.x % SL, B = (n + SL) / SL, k0 = lane * B;
+    const int k1 = k0 + B - 1 < n ? k0 + B - 1 : n;
+    cx<T> q = cxm<T>(0, 0), dq = cxm<T>(0, 0);
+    T m = 0;
+    for (int k = k1; k >= k0; --k) {
+        const T ck = c(k);
+        q = q * x + cxm<T>(ck, 0);
+        if (k < n) dq = dq * x + cxm<T>(T(k + 1) * c(k + 1), 0);
+        m = m * ax + fabs(ck);
+    }
+    cx<T> xp = x;
+    T rp = ax;
+    for (int t = 1; t < B; ++t) { xp = xp * x; rp *= ax; }
+    for (int sft = 1; sft < SL; sft <<= 1) {
+        cx<T> o, od;
+        o.x = __shfl_down_sync(mask, q.x, sft, SL);
+        o.y = __shfl_down_sync(mask, q.y, sft, SL);
+        od.x = __shfl_down_sync(mask, dq.x, sft, SL);
+        od.y = __shfl_down_sync(mask, dq.y, sft, SL);
+        const T om = __shfl_down_sync(mask, m, sft, SL);
+        if ((lane & (2 * sft - 1)) == 0) { q = q + xp * o; dq = dq + xp * od; m += rp * om; }
+        xp = xp * xp;
+        rp *= rp;
+    }
+    return {q, dq, m};
+}
+
+// p(z)/p'(z) by one thread alone (plain Horner), for the rare fallback of
+// the polish step; the reversed polynomial at 1/z for |z| > 1.
+__device__ cx<double> newton_ratio_serial(const double* a, int d, cx<double> z) {
+    const bool rev = cabsv(z) > 1.0;
+    const cx<double> x = rev ? cdivv(cxm<double>(1.0, 0.0), z) : z;
+    cx<double> p = cxm<double>(rev ? a[0] : a[d], 0.0), dp = cxm<double>(0.0, 0.0);
+    for (int k = d - 1; k >= 0; --k) {
+        dp = dp * x + p;
+        p = p * x + cxm<double>(rev ? a[d - k] : a[k], 0.0);
+    }
+    return rev ? cdivv(z * p, cscale(p, (double)d) - x * dp) : cdivv(p, dp);
+}
+
+// Newton ratio p(z)/p'(z) on every lane of the root; *noise = |p(z)| is below
+// its evaluation error bound.  For |z| > 1 the reversed polynomial is
+// evaluated at w = 1/z (the same code path: the coefficient order flips).
 template <typename T>
-__device__ cx<T> newton_ratio(const T* a, int d, cx<T> z, bool* noise) {
-    T az = cabsv(z);
-    const T g = T(4 * (2 * d + 2)) * eps_of<T>::v;
-    if (az <= T(1)) {
-        cx<T> p = cxm<T>(a[d], 0), dp = cxm<T>(0, 0);
-        T mag = fabs(a[d]);
-        for (int k = d - 1; k >= 0; --k) {
-            dp = dp * z + p;
-            p = p * z + cxm<T>(a[k], 0);
-            mag = mag * az + fabs(a[k]);
-        }
-        *noise = cabsv(p) <= g * mag;
-        return cdivv(p, dp);
-    }
-    cx<T> w = cdivv(cxm<T>(1, 0), z);
-    T aw = cabsv(w);
-    cx<T> P = cxm<T>(a[0], 0), dP = cxm<T>(0, 0);
-    T mag = fabs(a[0]);
-    for (int k = 1; k <= d; ++k) {
-        dP = dP * w + P;
-        P = P * w + cxm<T>(a[k], 0);
-        mag = mag * aw + fabs(a[k]);
-    }
-    *noise = cabsv(P) <= g * mag;
-    cx<T> den = cscale(P, T(d)) - w * dP;
-    return cdivv(z * P, den);
+__device__ cx<T> newton_ratio(unsigned mask, const T* a, int d, cx<T> z, bool* noise) {
+    const T az = cabsv(z);
+    const T g = T(4 * (2 * d + 2 + 2 * SL)) * eps_of<T>::v;
+    const bool rev = az > T(1);
+    const cx<T> x = rev ? cdivv(cxm<T>(1, 0), z) : z;
+    const T ax = rev ? T(1) / az : az;
+    const Eval3<T> e = split_eval3<T>(mask, d, x, ax, [&](int k) { return rev ? a[d - k] : a[k]; });
+    cx<T> N = rev ? cdivv(z * e.p, cscale(e.p, T(d)) - x * e.dp) : cdivv(e.p, e.dp);
+    int nz = cabsv(e.p) <= g * e.mag;
+    N.x = __shfl_sync(mask, N.x, 0, SL);
+    N.y = __shfl_sync(mask, N.y, 0, SL);
+    *noise = __shfl_sync(mask, nz, 0, SL) != 0;
+    return N;
 }
 
 // Aberth iterations on the shared approximations z[0..d); returns true when
-// every root stopped moving.
+// every root stopped moving.  Thread t works on root t / SL.
 template <typename T>
-__device__ bool aberth(const T* a, int d, cx<T>* z, int max_iter, int* s_flag) {
-    const int i = threadIdx.x;
+__device__ bool aberth(const T* a, int d, cx<T>* z, int max_iter) {
+    const int i = threadIdx.x / SL, lane = threadIdx.x % SL;
     bool done = i >= d;
     for (int it = 0; it < max_iter; ++it) {
         cx<T> zi = i < d ? z[i] : cxm<T>(0, 0);
         cx<T> corr = cxm<T>(0, 0);
+        const unsigned am = __ballot_sync(0xffffffffu, !done);
         if (!done) {
             bool noise;
-            cx<T> N = newton_ratio<T>(a, d, zi, &noise);
+            cx<T> N = newton_ratio<T>(am, a, d, zi, &noise);
             // The Aberth sum sum_j 1/(z_i - z_j) only steers the step (near
             // convergence N S << 1 damps its error), so it is accumulated in
             // FP32 from differences taken in T; the Newton ratio N keeps T.
+            // Lane l of the root adds the terms j = l (mod SL).
             float sx = 0.f, sy = 0.f;
-            for (int j = 0; j < d; ++j) {
+            for (int j = lane; j < d; j += SL) {
                 if (j == i) continue;
                 const float dx = (float)(zi.x - z[j].x), dy = (float)(zi.y - z[j].y);
                 const float m = dx * dx + dy * dy;
@@ -103,6 +147,10 @@ __device__ bool aberth(const T* a, int d, cx<T>* z, int max_iter, int* s_flag) {
                     sy -= dy * r;
                 }
             }
+            for (int o = 1; o < SL; o <<= 1) {
+                sx += __shfl_xor_sync(am, sx, o, SL);
+                sy += __shfl_xor_sync(am, sy, o, SL);
+            }
             const cx<T> S = cxm<T>((T)sx, (T)sy);
             cx<T> den = cxm<T>(1, 0) - N * S;
             corr = cdivv(N, den);
@@ -110,15 +158,16 @@ __device__ bool aberth(const T* a, int d, cx<T>* z, int max_iter, int* s_flag) {
             if (noise || cabsv(corr) <= T(4) * eps_of<T>::v * cabsv(zi)) done = true;
         }
         __syncthreads();
-        if (i < d) z[i] = zi - corr;
+        if (i < d && lane == 0) z[i] = zi - corr;
         if (!__syncthreads_or(!done)) return true;
     }
     return false;
 }
 
-// Kernel 1: Aberth iterations, one CTA per polynomial.  Writes the FP64
-// approximations to roots[.., 0] / roots[.., 2] and the convergence status.
-__global__ void __launch_bounds__(DMAX)
+// Kernel 1: Aberth iterations, one CTA of DMAX * SL threads per polynomial.
+// Writes the FP64 approximations to roots[.., 0] / roots[.., 2] and the
+// convergence status.
+__global__ void __launch_bounds__(DMAX * SL)
 k_aberth(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees,
          int root_mode, double* __restrict__ roots, int32_t* __restrict__ status) {
     __shared__ double a[DMAX + 1];
@@ -126,26 +175,26 @@ k_aberth(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees
     __shared__ cx<double> z[DMAX];
     __shared__ cx<float> zf[DMAX];
     __shared__ int hull[DMAX + 2];
-    __shared__ int nhull, kmin, s_flag;
+    __shared__ int nhull, kmin;
 
-    const int prob = blockIdx.x, i = threadIdx.x;
+    const int prob = blockIdx.x, i = threadIdx.x / SL, lane = threadIdx.x % SL;
     const int d = degrees[prob];
     const int64_t* c = coeffs + (size_t)prob * LDC;
     const int pre = status[prob];
     if (pre < 0) return;                       // rejected by the input checks
     if (d < 1 || d > DMAX) {
-        if (i == 0) status[prob] = RFR_E_RANGE;
+        if (threadIdx.x == 0) status[prob] = RFR_E_RANGE;
         return;
     }
-    for (int k = i; k <= d; k += blockDim.x) { a[k] = (double)c[k]; af[k] = (float)c[k]; }
+    for (int k = threadIdx.x; k <= d; k += blockDim.x) { a[k] = (double)c[k]; af[k] = (float)c[k]; }
     __syncthreads();
 
     // Newton polygon: upper hull of (k, log2|a_k|) over a_k != 0.  The starting
     // points only steer the iteration, so the logs are taken once, in FP32.
     __shared__ float la[DMAX + 1];
-    for (int k = i; k <= d; k += blockDim.x) la[k] = a[k] != 0.0 ? log2f(fabsf(af[k])) : 0.f;
+    for (int k = threadIdx.x; k <= d; k += blockDim.x) la[k] = a[k] != 0.0 ? log2f(fabsf(af[k])) : 0.f;
     __syncthreads();
-    if (i == 0) {
+    if (threadIdx.x == 0) {
         int km = 0;
         while (km < d && a[km] == 0.0) ++km;
         kmin = km;
@@ -163,7 +212,7 @@ k_aberth(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees
         nhull = h;
     }
     __syncthreads();
-    if (i < d) {
+    if (i < d && lane == 0) {
         cx<double> z0 = cxm<double>(0.0, 0.0);
         if (i >= kmin) {
             int e = 0;
@@ -181,18 +230,18 @@ k_aberth(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees
 
     bool conv;
     if (root_mode == RFR_ROOTS_FP32_BULK) {
-        aberth<float>(af, d, zf, 400, &s_flag);
-        if (i < d) z[i] = cxm<double>((double)zf[i].x, (double)zf[i].y);
+        aberth<float>(af, d, zf, 400);
+        if (i < d && lane == 0) z[i] = cxm<double>((double)zf[i].x, (double)zf[i].y);
         __syncthreads();
-        conv = aberth<double>(a, d, z, 200, &s_flag);
+        conv = aberth<double>(a, d, z, 200);
     } else {
-        conv = aberth<double>(a, d, z, 600, &s_flag);
+        conv = aberth<double>(a, d, z, 600);
     }
-    if (i < d) {
+    if (i < d && lane == 0) {
         double* out = roots + ((size_t)prob * DMAX + i) * 4;
         out[0] = z[i].x; out[1] = 0.0; out[2] = z[i].y; out[3] = 0.0;
     }
-    if (i == 0) {
+    if (threadIdx.x == 0) {
         const bool suspect = pre == RFR_SF_SUSPECT;
         status[prob] = conv ? (suspect ? RFR_SF_SUSPECT : RFR_OK)
                             : (suspect ? RFR_E_NOT_SQUAREFREE : RFR_E_NO_CONVERGENCE);
@@ -206,7 +255,6 @@ k_aberth(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees
 // a shuffle tree forms p(z) = sum_l z^(lB) q_l(z) with the powers z^(sB),
 // s = 1, 2.  The chain is about d / 4 steps and the total work stays about d
 // steps per root (the FP64 rate of the part, not latency, is the limit).
-constexpr int SL = 4;                         // lanes per root
 constexpr int RPC = 32;                       // roots per CTA (RPC * SL threads)
 constexpr int RCHUNKS = DMAX / RPC;
 struct RootWarp { int prob, d, i, lane; };
@@ -321,10 +369,7 @@ k_polish(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees
     const cx<double> Ph = cxm<double>(P.re.hi, P.im.hi);
     cx<double> N = rev ? cdivv(zh * Ph, cscale(Ph, (double)d) - xh * dP) : cdivv(Ph, dP);
     if (R.lane == 0 && live) {
-        if (!(cabsv(N) < 1e300)) {                              // degenerate: plain FP64 Newton ratio
-            bool noise;
-            N = newton_ratio<double>(a, d, zh, &noise);
-        }
+        if (!(cabsv(N) < 1e300)) N = newton_ratio_serial(a, d, zh);   // degenerate: plain FP64 Newton ratio
         Z.re = dd_add_d(Z.re, -N.x);
         Z.im = dd_add_d(Z.im, -N.y);
         out[0] = Z.re.hi; out[1] = Z.re.lo; out[2] = Z.im.hi; out[3] = Z.im.lo;
@@ -396,7 +441,7 @@ extern "C" int rfr_stage_roots(const int64_t* coeffs, const int32_t* degrees, in
     if (batch < 0 || !coeffs || !degrees || !roots || !radius || !status) return RFR_E_INVALID;
     if (batch == 0) return RFR_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    k_aberth<<<batch, DMAX, 0, s>>>(coeffs, degrees, root_mode, roots, status);
+    k_aberth<<<batch, DMAX * SL, 0, s>>>(coeffs, degrees, root_mode, roots, status);
     k_polish<<<batch * RCHUNKS, RPC * SL, 0, s>>>(coeffs, degrees, status, roots);
     k_radius<<<batch * RCHUNKS, RPC * SL, 0, s>>>(coeffs, degrees, status, roots, radius);
     return cudaGetLastError() == cudaSuccess ? RFR_OK : RFR_E_CUDA;
