@@ -1,6 +1,6 @@
 // k_roots.cu — K-a: batched root finder (the "black box" of Section 2).
 //
-// Three kernels: k_aberth (one CTA per polynomial, SL = 4 lanes per root,
+// Three kernels: k_aberth (one CTA per polynomial, SL = 8 lanes per root,
 // d <= 128) for steps 1-2; k_polish and k_radius (SL lanes per root, the
 // polynomial split over them, spread over the whole GPU) for steps 3 and 4.
 // Every evaluation of p is a split Horner scheme over the root's SL lanes:
@@ -50,7 +50,20 @@ template <typename T> struct eps_of;
 template <> struct eps_of<double> { static constexpr double v = 1.1102230246251565e-16; };
 template <> struct eps_of<float> { static constexpr float v = 5.9604645e-8f; };
 
-constexpr int SL = 4;                         // lanes per root in every kernel of this file
+constexpr int SL = 8;                         // lanes per root in every kernel of this file
+
+// x^e for e >= 1 by squaring (a chain of about 2 log2 e products, not e - 1)
+template <typename V, class Mul>
+__device__ __forceinline__ V pow_sq(V x, int e, Mul mul) {
+    V r = x;
+    bool have = false;
+    while (e) {
+        if (e & 1) { r = have ? mul(r, x) : x; have = true; }
+        e >>= 1;
+        if (e) x = mul(x, x);
+    }
+    return r;
+}
 
 // p(x), p'(x) and sum_k |c(k)| |x|^k for the polynomial sum_{k=0}^{n} c(k) x^k,
 // split over the root's SL lanes (mask: the lanes of the warp taking part, whole
@@ -70,9 +83,8 @@ __device__ __forceinline__ Eval3<T> split_eval3(unsigned mask, int n, cx<T> x, T
         if (k < n) dq = dq * x + cxm<T>(T(k + 1) * c(k + 1), 0);
         m = m * ax + fabs(ck);
     }
-    cx<T> xp = x;
-    T rp = ax;
-    for (int t = 1; t < B; ++t) { xp = xp * x; rp *= ax; }
+    cx<T> xp = pow_sq(x, B, [](cx<T> u, cx<T> v) { return u * v; });
+    T rp = pow_sq(ax, B, [](T u, T v) { return u * v; });
     for (int sft = 1; sft < SL; sft <<= 1) {
         cx<T> o, od;
         o.x = __shfl_down_sync(mask, q.x, sft, SL);
@@ -248,14 +260,14 @@ k_aberth(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees
     }
 }
 
-// Steps 3 and 4 take SL = 4 lanes per root, RPC roots of one polynomial per
+// Steps 3 and 4 take SL = 8 lanes per root, RPC roots of one polynomial per
 // CTA: blockIdx.x = problem * (DMAX / RPC) + chunk.  A polynomial is evaluated
 // by a split Horner scheme: lane l of a root sums the B = ceil((d+1)/SL)
 // coefficients k in [lB, lB + B) as q_l(z) = sum a_k z^(k - lB) (Horner), and
 // a shuffle tree forms p(z) = sum_l z^(lB) q_l(z) with the powers z^(sB),
-// s = 1, 2.  The chain is about d / 4 steps and the total work stays about d
-// steps per root (the FP64 rate of the part, not latency, is the limit).
-constexpr int RPC = 32;                       // roots per CTA (RPC * SL threads)
+// s = 1, 2, 4.  The chain is about d / SL steps plus the power's log2 B
+// squarings, and the total work stays about d steps per root.
+constexpr int RPC = 16;                       // roots per CTA (RPC * SL threads)
 constexpr int RCHUNKS = DMAX / RPC;
 struct RootWarp { int prob, d, i, lane; };
 __device__ __forceinline__ bool root_warp(const int32_t* degrees, const int32_t* status, RootWarp* r) {
@@ -287,8 +299,7 @@ __device__ cdd warp_poly_dd(int n, cdd Z, Coef c) {
         q = cdd_make(c(k1), 0.0);
         for (int k = k1 - 1; k >= k0; --k) q = cdd_add_d(cdd_mul(q, Z), c(k));
     }
-    cdd zp = Z;
-    for (int t = 1; t < B; ++t) zp = cdd_mul(zp, Z);
+    cdd zp = pow_sq(Z, B, [](cdd u, cdd v) { return cdd_mul(u, v); });
     for (int s = 1; s < SL; s <<= 1) {
         const cdd o = shfl_down_cdd(q, s);
         if ((lane & (2 * s - 1)) == 0) q = cdd_add(q, cdd_mul(zp, o));
@@ -307,8 +318,7 @@ __device__ cx<double> warp_poly_c(int n, cx<double> z, Coef c) {
         q = cxm<double>(c(k1), 0.0);
         for (int k = k1 - 1; k >= k0; --k) q = q * z + cxm<double>(c(k), 0.0);
     }
-    cx<double> zp = z;
-    for (int t = 1; t < B; ++t) zp = zp * z;
+    cx<double> zp = pow_sq(z, B, [](cx<double> u, cx<double> v) { return u * v; });
     for (int s = 1; s < SL; s <<= 1) {
         cx<double> o;
         o.x = __shfl_down_sync(0xffffffffu, q.x, s, SL);
@@ -329,8 +339,7 @@ __device__ double warp_poly_r(int n, double r, Coef c) {
         q = c(k1);
         for (int k = k1 - 1; k >= k0; --k) q = q * r + c(k);
     }
-    double rp = r;
-    for (int t = 1; t < B; ++t) rp *= r;
+    double rp = pow_sq(r, B, [](double u, double v) { return u * v; });
     for (int s = 1; s < SL; s <<= 1) {
         const double o = __shfl_down_sync(0xffffffffu, q, s, SL);
         if ((lane & (2 * s - 1)) == 0) q += rp * o;
