@@ -156,18 +156,32 @@ class Result:
         return self.status == RFR_OK
 
 
+_DIAG_FIELDS = [k for k, _ in Diag._fields_]
+
+
 def _diag_dict(d: Diag) -> dict:
-    return {k: (list(getattr(d, k)) if k == "stage_us" else getattr(d, k)) for k, _ in Diag._fields_}
+    out = {k: getattr(d, k) for k in _DIAG_FIELDS}
+    out["stage_us"] = list(out["stage_us"])
+    return out
+
+
+def _factor_lists(n: int, degrees, coeffs) -> List[List[int]]:
+    """n factors stored one after the other (degrees[i] + 1 coefficients each)."""
+    if n <= 0:
+        return []
+    degs = np.ctypeslib.as_array(degrees, shape=(n,)).tolist()
+    co = np.ctypeslib.as_array(coeffs, shape=(sum(degs) + n,)).tolist()
+    out, off = [], 0
+    for e in degs:
+        out.append(co[off:off + e + 1])
+        off += e + 1
+    return out
 
 
 def _to_result(status: int, f: Factors) -> Result:
     res = Result(status=int(status), diag=_diag_dict(f.diag))
     if status == RFR_OK:
-        off = 0
-        for i in range(f.n_factors):
-            e = f.degrees[i]
-            res.factors.append([int(f.coeffs[off + k]) for k in range(e + 1)])
-            off += e + 1
+        res.factors = _factor_lists(f.n_factors, f.degrees, f.coeffs)
     lib().rfr_factors_free(C.byref(f))
     return res
 
@@ -188,11 +202,8 @@ def _to_general(status: int, f: Factorization) -> GeneralResult:
     res = GeneralResult(status=int(status))
     if status == RFR_OK:
         res.content = int(f.content)
-        off = 0
-        for i in range(f.n_factors):
-            e = f.degrees[i]
-            res.factors.append(([int(f.coeffs[off + k]) for k in range(e + 1)], int(f.multiplicities[i])))
-            off += e + 1
+        fs = _factor_lists(f.n_factors, f.degrees, f.coeffs)
+        res.factors = [(g, int(f.multiplicities[i])) for i, g in enumerate(fs)]
     lib().rfr_factorization_free(C.byref(f))
     return res
 
@@ -205,8 +216,7 @@ def squarefree(coeffs: Sequence[int]) -> GeneralResult:
 
 
 def _coeff_array(coeffs: Sequence[int]):
-    arr = (C.c_int64 * len(coeffs))(*[int(c) for c in coeffs])
-    return arr
+    return (C.c_int64 * len(coeffs))(*coeffs)
 
 
 class Context:
