@@ -89,11 +89,15 @@ k_weights(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degree
     if (i < d) {
         double ri = rr[i];
         bool isolated = isfinite(ri), strong = true;
+        // squared distances against squared radius sums (no square roots: FP64
+        // is this part's limit; an infinite or NaN radius fails both tests)
         for (int j = 0; j < d; ++j) {
             if (j == i) continue;
-            double dist = hypot(zx[i] - zx[j], zy[i] - zy[j]);
-            if (!(dist > ri + rr[j])) isolated = false;
-            if (!(dist > 3.0 * ri + rr[j])) strong = false;
+            const double dx = zx[i] - zx[j], dy = zy[i] - zy[j];
+            const double d2 = dx * dx + dy * dy;
+            const double s1 = ri + rr[j], s3 = 3.0 * ri + rr[j];
+            if (!(d2 > s1 * s1)) isolated = false;
+            if (!(d2 > s3 * s3)) strong = false;
         }
         int k;
         if (!isolated) k = -1;
@@ -110,13 +114,15 @@ k_weights(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degree
     }
     if (i < d && cls[i] == 1) {
         int best = -1;
-        double bd = INFINITY;
+        double bd2 = INFINITY;                    // squared distance to the conjugate
         for (int j = 0; j < d; ++j) {
             if (cls[j] != 2) continue;
-            double dist = hypot(zx[j] - zx[i], zy[j] + zy[i]);
-            if (dist < bd) { bd = dist; best = j; }
+            const double dx = zx[j] - zx[i], dy = zy[j] + zy[i];
+            const double d2 = dx * dx + dy * dy;
+            if (d2 < bd2) { bd2 = d2; best = j; }
         }
-        if (best < 0 || !(bd <= rr[i] + rr[best])) atomicExch(&s_err, 1);
+        const double sr = best < 0 ? 0.0 : rr[i] + rr[best];
+        if (best < 0 || !(bd2 <= sr * sr)) atomicExch(&s_err, 1);
         else { partner[i] = best; atomicAdd(&taken[best], 1); }
     }
     __syncthreads();
