@@ -31,6 +31,8 @@ k_verify(const int64_t* __restrict__ coeffs, const double* __restrict__ roots,
     __shared__ long long qi[VW][QMAX + 1];
     __shared__ __int128 rs[VW][DMAX + 1];
     __shared__ long long quo[VW][DMAX + 1];
+    __shared__ dd cA[VW][DMAX], cB[VW][DMAX];     // per element of the built side: u, or z + z' and Re(z z')
+    __shared__ signed char ek[VW][DMAX];          // 0: not in the built side, else its kind (1 or 2)
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int job = blockIdx.x * VW + w;
     if (job >= jobs) return;
@@ -64,34 +66,64 @@ k_verify(const int64_t* __restrict__ coeffs, const double* __restrict__ roots,
     const double rr = P.max_radius;
     double pa = 1.0, sinv = 0.0;
     auto acc = [&](double m) { const double a = 1.0 + m + rr; pa *= a; sinv += 1.0 / a; };
+    // The built side's factors, read from the plan and the roots by all lanes at
+    // once into shared memory (the product below walks them in order).
+    for (int k = lane; k < n; k += 32) {
+        const bool in = patbit(lo, hi, k) != comp;
+        const int kind = in ? P.kind[k] : 0;
+        if (in) {
+            const double* r0 = R + 4 * P.root0[k];
+            if (kind == 1) {
+                cA[w][k] = {r0[0], r0[1]};
+                acc(fabs(r0[0]));
+            } else {
+                const double* r1 = R + 4 * P.root1[k];
+                const dd x0 = {r0[0], r0[1]}, y0 = {r0[2], r0[3]};
+                const dd x1 = {r1[0], r1[1]}, y1 = {r1[2], r1[3]};
+                cA[w][k] = dd_add(x0, x1);                                 // z + z'
+                cB[w][k] = dd_sub(dd_mul(x0, x1), dd_mul(y0, y1));         // Re(z z')
+                acc(hypot(r0[0], r0[2]));
+                acc(hypot(r1[0], r1[2]));
+            }
+        }
+        ek[w][k] = (signed char)kind;
+    }
+    for (int o = 16; o; o >>= 1) {
+        pa *= __shfl_xor_sync(0xffffffffu, pa, o);
+        sinv += __shfl_xor_sync(0xffffffffu, sinv, o);
+    }
+    __syncwarp();
     int cur = 0;
     for (int k = 0; k < n; ++k) {
-        if (patbit(lo, hi, k) == comp) continue;
-        const double* r0 = R + 4 * P.root0[k];
-        if (P.kind[k] == 1) acc(fabs(r0[0]));
-        else { acc(hypot(r0[0], r0[2])); acc(hypot(R[4 * P.root1[k]], R[4 * P.root1[k] + 2])); }
+        const int kind = ek[w][k];
+        if (!kind) continue;
+        // slots of 32 coefficients that the product reaches after this step (warp-uniform):
+        // the others are skipped whole, which saves their FP64 work
+        const int ns = min(3, (cur + 2) / 32 + 1);
         dd old[3], prev[3], prev2[3];
+#pragma unroll
         for (int t = 0; t < 3; ++t) {
+            if (t >= ns) break;
             const int j = lane + 32 * t;
             old[t] = (j <= QMAX) ? qs[w][j] : dd_make(0.0);
             prev[t] = (j >= 1 && j - 1 <= QMAX) ? qs[w][j - 1] : dd_make(0.0);
             prev2[t] = (j >= 2 && j - 2 <= QMAX) ? qs[w][j - 2] : dd_make(0.0);
         }
         __syncwarp();
-        if (P.kind[k] == 1) {
-            const dd u = {r0[0], r0[1]};
+        if (kind == 1) {
+            const dd u = cA[w][k];
+#pragma unroll
             for (int t = 0; t < 3; ++t) {
+                if (t >= ns) break;
                 const int j = lane + 32 * t;
                 if (j <= cur + 1 && j <= QMAX) qs[w][j] = dd_sub(prev[t], dd_mul(u, old[t]));
             }
             cur += 1;
         } else {
-            const double* r1 = R + 4 * P.root1[k];
-            const dd x0 = {r0[0], r0[1]}, y0 = {r0[2], r0[3]};
-            const dd x1 = {r1[0], r1[1]}, y1 = {r1[2], r1[3]};
-            const dd tt = dd_add(x0, x1);                                  // z + z'
-            const dd mm = dd_sub(dd_mul(x0, x1), dd_mul(y0, y1));          // Re(z z')
+            const dd tt = cA[w][k], mm = cB[w][k];
+#pragma unroll
             for (int t = 0; t < 3; ++t) {
+                if (t >= ns) break;
                 const int j = lane + 32 * t;
                 if (j <= cur + 2 && j <= QMAX)
                     qs[w][j] = dd_add(dd_sub(prev2[t], dd_mul(tt, prev[t])), dd_mul(mm, old[t]));
