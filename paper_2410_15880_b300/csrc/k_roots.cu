@@ -65,35 +65,44 @@ __device__ __forceinline__ V pow_sq(V x, int e, Mul mul) {
     return r;
 }
 
-// p(x), p'(x) and sum_k |c(k)| |x|^k for the polynomial sum_{k=0}^{n} c(k) x^k,
-// split over the root's SL lanes (mask: the lanes of the warp taking part, whole
-// roots only).  Lane l of a root takes the B = ceil((n+1)/SL) coefficients k in
-// [lB, lB + B) by Horner (three independent chains); a shuffle tree adds the
-// lanes' parts times x^(lB).  The root's first lane holds the result.
-template <typename T> struct Eval3 { cx<T> p, dp; T mag; };
+// p(x) in T, and p'(x) and sum_k |c(k)| |x|^k in FP32, for the polynomial
+// sum_{k=0}^{n} c(k) x^k, split over the root's SL lanes (mask: the lanes of the
+// warp taking part, whole roots only).  Lane l of a root takes the
+// B = ceil((n+1)/SL) coefficients k in [lB, lB + B) by Horner (three
+// independent chains); a shuffle tree adds the lanes' parts times x^(lB).  The
+// root's first lane holds the result.  Only p needs T: near a root the Newton
+// ratio p / p' keeps the relative accuracy of p' (1e-7 in FP32), so each FP64
+// step still shrinks the error by about that factor, and the error bound
+// needs no more; FP64 is the slow part of this GPU.
+template <typename T> struct Eval3 { cx<T> p; cx<float> dp; float mag; };
 template <typename T, class Coef>
-__device__ __forceinline__ Eval3<T> split_eval3(unsigned mask, int n, cx<T> x, T ax, Coef c) {
+__device__ __forceinline__ Eval3<T> split_eval3(unsigned mask, int n, cx<T> x, float axf, Coef c) {
     const int lane = threadIdx.x % SL, B = (n + SL) / SL, k0 = lane * B;
     const int k1 = k0 + B - 1 < n ? k0 + B - 1 : n;
-    cx<T> q = cxm<T>(0, 0), dq = cxm<T>(0, 0);
-    T m = 0;
+    const cx<float> xf = cxm<float>((float)x.x, (float)x.y);
+    cx<T> q = cxm<T>(0, 0);
+    cx<float> dq = cxm<float>(0.f, 0.f);
+    float m = 0.f;
     for (int k = k1; k >= k0; --k) {
         const T ck = c(k);
         q = q * x + cxm<T>(ck, 0);
-        if (k < n) dq = dq * x + cxm<T>(T(k + 1) * c(k + 1), 0);
-        m = m * ax + fabs(ck);
+        if (k < n) dq = dq * xf + cxm<float>((float)(k + 1) * (float)c(k + 1), 0.f);
+        m = m * axf + fabsf((float)ck);
     }
     cx<T> xp = pow_sq(x, B, [](cx<T> u, cx<T> v) { return u * v; });
-    T rp = pow_sq(ax, B, [](T u, T v) { return u * v; });
+    cx<float> xpf = pow_sq(xf, B, [](cx<float> u, cx<float> v) { return u * v; });
+    float rp = pow_sq(axf, B, [](float u, float v) { return u * v; });
     for (int sft = 1; sft < SL; sft <<= 1) {
-        cx<T> o, od;
+        cx<T> o;
+        cx<float> od;
         o.x = __shfl_down_sync(mask, q.x, sft, SL);
         o.y = __shfl_down_sync(mask, q.y, sft, SL);
         od.x = __shfl_down_sync(mask, dq.x, sft, SL);
         od.y = __shfl_down_sync(mask, dq.y, sft, SL);
-        const T om = __shfl_down_sync(mask, m, sft, SL);
-        if ((lane & (2 * sft - 1)) == 0) { q = q + xp * o; dq = dq + xp * od; m += rp * om; }
+        const float om = __shfl_down_sync(mask, m, sft, SL);
+        if ((lane & (2 * sft - 1)) == 0) { q = q + xp * o; dq = dq + xpf * od; m += rp * om; }
         xp = xp * xp;
+        xpf = xpf * xpf;
         rp *= rp;
     }
     return {q, dq, m};
@@ -112,19 +121,33 @@ __device__ cx<double> newton_ratio_serial(const double* a, int d, cx<double> z) 
     return rev ? cdivv(z * p, cscale(p, (double)d) - x * dp) : cdivv(p, dp);
 }
 
+// 1 / b in FP32 complex arithmetic (scaled, so tiny or huge b stay in range);
+// {0, 0} for b = 0.
+__device__ __forceinline__ cx<float> crecip_f(cx<float> b) { return cdivv(cxm<float>(1.f, 0.f), b); }
+
 // Newton ratio p(z)/p'(z) on every lane of the root; *noise = |p(z)| is below
 // its evaluation error bound.  For |z| > 1 the reversed polynomial is
-// evaluated at w = 1/z (the same code path: the coefficient order flips).
+// evaluated at w = 1/z = conj(z) / |z|^2 (the same code path: the coefficient
+// order flips).  The quotient takes an FP32 reciprocal of the denominator:
+// its relative error (about 1e-7) is that of p' already, and it avoids FP64
+// divisions, the slow part of this GPU.
 template <typename T>
 __device__ cx<T> newton_ratio(unsigned mask, const T* a, int d, cx<T> z, bool* noise) {
-    const T az = cabsv(z);
     const T g = T(4 * (2 * d + 2 + 2 * SL)) * eps_of<T>::v;
-    const bool rev = az > T(1);
-    const cx<T> x = rev ? cdivv(cxm<T>(1, 0), z) : z;
-    const T ax = rev ? T(1) / az : az;
-    const Eval3<T> e = split_eval3<T>(mask, d, x, ax, [&](int k) { return rev ? a[d - k] : a[k]; });
-    cx<T> N = rev ? cdivv(z * e.p, cscale(e.p, T(d)) - x * e.dp) : cdivv(e.p, e.dp);
-    int nz = cabsv(e.p) <= g * e.mag;
+    const T z2 = cabs2(z);
+    const bool rev = z2 > T(1);
+    const T r2 = rev ? T(1) / z2 : T(0);
+    const cx<T> x = rev ? cxm<T>(z.x * r2, -z.y * r2) : z;
+    const float azf = sqrtf((float)z2);
+    const float axf = rev ? 1.f / azf : azf;
+    const Eval3<T> e = split_eval3<T>(mask, d, x, axf, [&](int k) { return rev ? a[d - k] : a[k]; });
+    cx<float> den = e.dp;
+    if (rev) den = cxm<float>((float)(T(d) * e.p.x), (float)(T(d) * e.p.y)) -
+                   cxm<float>((float)x.x, (float)x.y) * e.dp;
+    const cx<float> inv = crecip_f(den);
+    cx<T> N = (rev ? z * e.p : e.p) * cxm<T>((T)inv.x, (T)inv.y);
+    const T gm = g * (T)e.mag;
+    int nz = cabs2(e.p) <= gm * gm;
     N.x = __shfl_sync(mask, N.x, 0, SL);
     N.y = __shfl_sync(mask, N.y, 0, SL);
     *noise = __shfl_sync(mask, nz, 0, SL) != 0;
@@ -164,10 +187,15 @@ __device__ bool aberth(const T* a, int d, cx<T>* z, int max_iter) {
                 sy += __shfl_xor_sync(am, sy, o, SL);
             }
             const cx<T> S = cxm<T>((T)sx, (T)sy);
-            cx<T> den = cxm<T>(1, 0) - N * S;
-            corr = cdivv(N, den);
-            if (!(cabsv(corr) < T(1e30))) corr = N;               // degenerate denominator: Newton step
-            if (noise || cabsv(corr) <= T(4) * eps_of<T>::v * cabsv(zi)) done = true;
+            const cx<T> den = cxm<T>(1, 0) - N * S;
+            // N / den with an FP32 reciprocal (den is near 1 at convergence; its
+            // 1e-7 relative error only scales the step)
+            const cx<float> inv = crecip_f(cxm<float>((float)den.x, (float)den.y));
+            corr = N * cxm<T>((T)inv.x, (T)inv.y);
+            const T huge = sizeof(T) == 8 ? T(1e60) : T(1e36);
+            if (!(cabs2(corr) < huge) || (inv.x == 0.f && inv.y == 0.f)) corr = N;   // degenerate: Newton step
+            const T tol = T(4) * eps_of<T>::v;
+            if (noise || cabs2(corr) <= tol * tol * cabs2(zi)) done = true;
         }
         __syncthreads();
         if (i < d && lane == 0) z[i] = zi - corr;
