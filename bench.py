@@ -536,14 +536,13 @@ def main():
     if a.serving_requests > 0 and world == 1:
         line["serving"] = serving_leg(local, a.serving_requests, [float(x) for x in a.serving_loads.split(",")],
                                       trace_path=a.serving_trace)
-    if not a.no_cpu_baseline:
+    if not a.no_cpu_baseline and world == 1:         # the CPU baselines run at N = 1 only
         n, dt = cpu_oracle_sample(workload(a.config, 0, a.count), budget_s=15.0)
         line["cpu_baseline"] = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"first {n} polynomials of the workload ({dt:.1f} s): roots, Sturm, DDF certificates"}
-        if world == 1:
-            mt = cpu_mt_sample(d_co, d_dg, a.root_mode)
-            if mt is not None:
-                line["cpu_mt"] = mt
+        mt = cpu_mt_sample(d_co, d_dg, a.root_mode)
+        if mt is not None:
+            line["cpu_mt"] = mt
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
