@@ -41,7 +41,7 @@ constexpr int YS_LOG = 12;                                     // list levels bu
 constexpr int YS_THREADS = 1024;
 constexpr size_t YS_SMEM = ((size_t)2 << YS_LOG) * 8;          // two buffers of 2^12 entries
 constexpr int YM_THREADS = 256;
-constexpr int YM_PER = 16;                                     // merge outputs per thread
+constexpr int YM_PER = 8;                                      // merge outputs per thread (2048-output tiles: 32 KB of shared memory, 7 CTAs per SM)
 
 constexpr int MT_THREADS = 1024;
 constexpr int MT_ACAP = 12288;                                 // table-a keys of one unit (mean 8192)
