@@ -232,3 +232,32 @@ def test_poll_batch_serving():
         assert all(results[i].ok and results[i].factors == r["factors"] for i, r in enumerate(recs))
         again = c.poll_batch(tickets[:3])                  # released tickets are unknown now
         assert all(x is not None and x.status == -1 for x in again)
+
+
+def test_key_range_shards_with_table_redo():
+    """x^60 - 1 (clustered keys: the fused match overflows and the problem is
+    redone whole with the table match) plus a degree-100 golden, in two
+    key-range shards: both shards return the cyclotomic factors and the
+    golden, the same as the unsharded batch."""
+    import threading
+    from oracle import canonical
+    from paper_2410_15880_b300 import Context
+    from paper_2410_15880_b300.sharding import ThreadExchange
+    from test_oracle_pins import cyclotomic
+    m = 60
+    polys = [[-1] + [0] * (m - 1) + [1], golden("cfg3")[0]["coeffs"]]
+    expect = [canonical([cyclotomic(k) for k in range(1, m + 1) if m % k == 0]), golden("cfg3")[0]["factors"]]
+    ex = ThreadExchange(2, timeout=120)
+    out = [None, None]
+
+    def run(s):
+        with Context(device=0, mem_budget_bytes=16 << 30) as c:
+            out[s] = c.factor_batch_sharded(polys, s, 2, ex.gather_for(s))
+    th = [threading.Thread(target=run, args=(s,)) for s in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(timeout=600)
+    for s in range(2):
+        assert [r.ok for r in out[s]] == [True, True], [r.status for r in out[s]]
+        assert [r.factors for r in out[s]] == expect
