@@ -102,16 +102,18 @@ int rfr_stage_enumerate(const uint64_t* w, int h, uint64_t* keys, void* stream);
 size_t rfr_stage_match_workspace(int n_a, int n_b);
 
 /* K-d for the fused match: one half's sorted list of low-subset sums.
- * list[0 .. 2^l) receives, for every subset s of the weights w[0..l), the
- * entry (S(s) & ~(2^l - 1)) | s, ascending as uint64, where S(s) is the sum
- * modulo 2^64 over i in s of round(w_i) = (w_i + 2^(l-1)) & ~(2^l - 1)
- * (of -w_i when negate != 0).  The rounding moves a sum by at most
- * l * 2^(l-1); the fused match widens its coarse window by that much.
- * 0 <= l <= 21; workspace: rfr_stage_lowlist_workspace(l) bytes, 256-byte
- * aligned; list: 2^l entries.  Built by merging: the list of i elements and
- * its copy shifted by round(w_i) + 2^i (EXPAND's sort, Section 3.3). */
+ * For every subset s of the weights w[0..l), list[] receives the exact sum
+ * S(s) = sum over i in s of w_i modulo 2^64 (of -w_i when negate != 0) and
+ * masks[] the subset s at the same position; list is ascending as uint64
+ * (ties in any order).  0 <= l <= 25; workspace:
+ * rfr_stage_lowlist_workspace(l) bytes, 256-byte aligned; list: 2^l uint64,
+ * masks: 2^l uint32, both caller-owned device memory.  Built by merging: the
+ * list of i elements and its copy shifted by w_i (rotated where the shifted
+ * sums wrap past 2^64), with bit i added to the copy's masks (EXPAND's sort,
+ * Section 3.3).  RFR_E_INVALID for null pointers, l out of range, an
+ * unaligned or short workspace. */
 size_t rfr_stage_lowlist_workspace(int l);
-int rfr_stage_lowlist(const uint64_t* w, int l, int negate, uint64_t* list,
+int rfr_stage_lowlist(const uint64_t* w, int l, int negate, uint64_t* list, uint32_t* masks,
                       void* workspace, size_t workspace_bytes, void* stream);
 
 /* K-d + K-e as the paper designs them for the GPU (Section 4, Algorithm E):

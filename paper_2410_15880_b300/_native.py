@@ -125,7 +125,7 @@ def lib():
         "rfr_stage_enumerate": (i32, [vp, i32, vp, vp]),
         "rfr_stage_match_workspace": (C.c_size_t, [i32, i32]),
         "rfr_stage_lowlist_workspace": (C.c_size_t, [i32]),
-        "rfr_stage_lowlist": (i32, [vp, i32, i32, vp, vp, C.c_size_t, vp]),
+        "rfr_stage_lowlist": (i32, [vp, i32, i32, vp, vp, vp, C.c_size_t, vp]),
         "rfr_stage_prune": (i32, [vp, vp, i32, u64, u64, vp, u64, vp, vp, C.c_size_t, vp]),
         "rfr_stage_splat_cells": (C.c_size_t, [i32]),
         "rfr_stage_splat": (i32, [vp, i32, vp, C.c_size_t, vp, vp]),
@@ -478,15 +478,17 @@ def stage_match(w_a, w2_a, w_b, w2_b, window: int, window2: int, cap: int, exact
 
 def stage_lowlist(w, l: int, negate: bool = False):
     """Sorted low-subset list of the first l weights (int64 cuda tensor,
-    uint64 bits): int64 tensor [2^l] of (rounded sum high bits) | mask."""
+    uint64 bits): (sums int64 [2^l] ascending as uint64, masks int32 [2^l],
+    workspace)."""
     import torch
     ws_bytes = int(lib().rfr_stage_lowlist_workspace(l))
     ws = torch.empty((ws_bytes // 8 + 64,), dtype=torch.int64, device=w.device)
     aligned = (ws.data_ptr() + 255) & ~255
     out = torch.empty((1 << l,), dtype=torch.int64, device=w.device)
-    _check(lib().rfr_stage_lowlist(_ptr(w) if l else None, l, int(bool(negate)), _ptr(out),
+    masks = torch.empty((1 << l,), dtype=torch.int32, device=w.device)
+    _check(lib().rfr_stage_lowlist(_ptr(w) if l else None, l, int(bool(negate)), _ptr(out), _ptr(masks),
                                    C.c_void_p(aligned), ws_bytes, _stream()), "rfr_stage_lowlist")
-    return out, ws
+    return out, masks, ws
 
 
 def _splat_buffer(n_b: int, device):

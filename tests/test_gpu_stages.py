@@ -112,25 +112,24 @@ def test_enumerate_large_properties(P):
 
 
 # ---------------------------------------------------------------- K-d sorted low lists (fused match)
-@pytest.mark.parametrize("l,negate", [(0, False), (1, False), (5, True), (12, False), (13, True), (16, False), (20, True)])
+@pytest.mark.parametrize("l,negate", [(0, False), (1, False), (5, True), (12, False), (13, True), (16, False),
+                                      (20, True), (24, False)])
 def test_lowlist_sorted_and_complete(P, l, negate):
-    """The list is non-decreasing and, as a multiset, equals (S(s) & ~(2^l-1)) | s
-    over all subsets s, S(s) the sum of the rounded weights (its definition)."""
+    """The list is non-decreasing, its masks are every subset once, and each
+    entry is the exact sum (mod 2^64) of the weights its mask names: the
+    sorted EXPAND of Section 3.3 by its definition."""
     rng = random.Random(100 + l)
     w = [rng.randrange(M64) for _ in range(max(l, 1))]
-    out, _ = P.stage_lowlist(u64_tensor(w), l, negate)
+    out, masks, _ = P.stage_lowlist(u64_tensor(w), l, negate)
     torch.cuda.synchronize()
     got = to_u64(out)
+    m = masks.cpu().numpy().view(np.uint32).astype(np.int64)
     assert np.all(got[1:] >= got[:-1])                        # sorted
-    half = (1 << (l - 1)) if l else 0
-    keep = (~((1 << l) - 1)) % M64
-    r = [(((-x if negate else x) + half) % M64) & keep for x in w[:l]]
-    s_ = np.zeros(1, dtype=np.int64)                          # sums modulo 2^64 on the int64 view
-    for x in r:
-        s_ = np.concatenate([s_, s_ + (x - M64 if x >= (1 << 63) else x)])
-    exp = np.sort((s_.view(np.uint64) & np.uint64(keep)) | np.arange(1 << l, dtype=np.uint64))
-    assert np.array_equal(np.sort(got), exp)
-    assert int((got & np.uint64((1 << l) - 1)).astype(np.int64).sum()) == (1 << l) * ((1 << l) - 1) // 2
+    assert np.array_equal(np.sort(m), np.arange(1 << l))      # every subset once
+    s_ = np.zeros(1, dtype=np.uint64)                          # S(s) for s in pattern order, modulo 2^64
+    for x in w[:l]:
+        s_ = np.concatenate([s_, s_ + np.uint64((-x if negate else x) % M64)])
+    assert np.array_equal(got, s_[m])
 
 
 # ---------------------------------------------------------------- K-c/K-d/K-e match
@@ -266,12 +265,30 @@ def test_verify_true_and_false_patterns(P):
             assert list(co[j, :len(f)]) == f
 
 
-def test_match_clustered_keys_overflow_then_exact(P):
-    """Weights below 2^40 put every key in one bucket: the slack layout must
-    report the overflow, and the exact layout must give the scan's answer."""
+def test_match_clustered_keys_fit_one_unit(P):
+    """Weights below 2^40 put all 2^14 keys of half a in one key unit, which
+    the fused match's table still holds: its answer is the scan's, with no
+    overflow."""
     from oracle.recombine import recombine_a
     rng = random.Random(77)
     na, nb = 14, 15
+    wa = [rng.randrange(1 << 40) for _ in range(na)]
+    wb = [rng.randrange(1 << 40) for _ in range(nb)]
+    wa[0] = 0                                           # {a0} sums to an integer
+    W = 1 << 20
+    got, ctr, _ = _run_match(P, wa, [0] * na, wb, [0] * nb, W, 0, fused=True)
+    assert ctr[4] == 0
+    scan = set(recombine_a(wa + wb + [0], M64, W)) - {0}
+    assert got == {(s & ((1 << na) - 1), s >> na) for s in scan} and (1, 0) in got
+
+
+def test_match_clustered_keys_overflow_then_exact(P):
+    """Weights below 2^40 put every key in one bucket: the fused match (the
+    automatic choice) must report the overflow of its table, and the exact
+    layout must give the scan's answer."""
+    from oracle.recombine import recombine_a
+    rng = random.Random(77)
+    na, nb = 15, 15
     wa = [rng.randrange(1 << 40) for _ in range(na)]
     wb = [rng.randrange(1 << 40) for _ in range(nb)]
     wa[0] = 0                                           # {a0} sums to an integer
