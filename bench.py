@@ -55,6 +55,8 @@ def parse():
                     help="rfr_config.match_path: automatic choice, table match only, the splat match "
                          "(Algorithm E) or the pruned search (Algorithm B)")
     ap.add_argument("--tune-cache", default="", help="file that stores tuned match layouts")
+    ap.add_argument("--degree120-steps", type=int, default=5,
+                    help="timed steps of the degree-120 sub-measurement (0 = skip it)")
     return ap.parse_args()
 
 
@@ -158,20 +160,37 @@ def alu_peak():
 KERNEL_SOURCE = {"k_join": "k_match.cu", "k_runs": "k_match.cu", "k_mitm": "k_mitm.cu"}
 
 
-def kernel_traffic(name, half_sums):
-    """DRAM bytes per launch for kernel `name` from its committed ncu summary
-    (profiles/<name>_*.md: 'dram_bytes_per_half_sum: X', 'source_sha256: H'),
-    scaled to the launch's half-sums; None if no summary or the kernel source
-    changed since the counters were taken."""
+def profile_figure(name, key):
+    """Figure `key` (per half-sum) of kernel `name` from its committed ncu
+    summary (profiles/<name>_*.md: '<key>: X', 'source_sha256: H'); None if
+    there is no summary or the kernel source changed since it was taken."""
     import glob
+    src = os.path.join(ROOT, "paper_2410_15880_b300", "csrc", KERNEL_SOURCE[name])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     for f in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{name}_*.md"))):
         txt = open(f).read()
-        m = re.search(r"dram_bytes_per_half_sum:\s*([0-9.eE+-]+)", txt)
+        m = re.search(rf"{key}:\s*([0-9.eE+-]+)", txt)
         h = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
-        src = os.path.join(ROOT, "paper_2410_15880_b300", "csrc", KERNEL_SOURCE[name])
-        if m and h and hashlib.sha256(open(src, "rb").read()).hexdigest() == h.group(1):
-            return float(m.group(1)) * half_sums
+        if m and h and h.group(1) == sha:
+            return float(m.group(1))
     return None
+
+
+def kernel_traffic(name, half_sums):
+    """DRAM bytes per launch for kernel `name` from its committed ncu summary
+    (dram_bytes_per_half_sum, scaled to the launch's half-sums), or None."""
+    x = profile_figure(name, "dram_bytes_per_half_sum")
+    return None if x is None else x * half_sums
+
+
+def issue_peak():
+    """Warp-instruction issue peak: 148 SMs x 4 schedulers x the measured
+    maximum SM clock, one warp instruction per scheduler per clock (G/s)."""
+    try:
+        mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+    except (OSError, KeyError, ValueError):
+        mhz = 2032.0
+    return 148 * 4 * mhz * 1e6 / 1e9
 
 
 def serving_leg(device, n_requests, loads, max_inflight=3, max_batch=64, trace_path=""):
@@ -324,6 +343,43 @@ def cpu_mt_sample(d_co, d_dg, root_mode, budget_s=15.0, max_polys=8):
                       f"the first {done} polynomials ({dt:.1f} s), weights from the GPU path's weights stage"}
 
 
+def degree120_leg(ctx, flush, steps, warmup=2):
+    """The degree-120 workload (one product of two random degree-60 factors,
+    halves of about 2^31 + 2^32 half-sums) through the same context, timed the
+    same way as the headline (device-resident input, L2 flush before each
+    step, CUDA events), checked against its golden factor list."""
+    import numpy as np
+    import torch
+    inst = workload("cfg5", 0, 0)[0]
+    arr = np.zeros((1, 129), dtype=np.int64)
+    arr[0, :len(inst.coeffs)] = inst.coeffs
+    d_co = torch.from_numpy(arr).cuda()
+    d_dg = torch.tensor([inst.degree], dtype=torch.int32, device="cuda")
+    for i in range(warmup):
+        ctx.factor_batch_device(d_co, d_dg)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    diags = []
+    e0.record()
+    for i in range(steps):
+        flush.fill_(i & 255)
+        torch.cuda.current_stream().synchronize()
+        res = ctx.factor_batch_device(d_co, d_dg)
+        diags.append(res[0].diag)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    d = diags[-1]
+    gpath = os.path.join(ROOT, "tests", "golden", "cfg5.json")
+    gold = json.load(open(gpath))[0]["factors"] if os.path.exists(gpath) else None
+    return {"workload": WORKLOAD_NAME["cfg5"], "steps": steps, "ms_per_poly": ms, "polys_per_s": 1e3 / ms,
+            "n": d["n"], "n_a": d["n_a"], "n_b": d["n_b"], "half_sums": d["half_sums"],
+            "half_sums_per_s": d["half_sums"] / (ms / 1e3),
+            "match_ms": statistics.mean(x["stage_us"][4] for x in diags) / 1e3,
+            "lists_ms": statistics.mean(x["stage_us"][2] for x in diags) / 1e3,
+            "matches_golden": (gold is not None and res[0].ok and res[0].factors == gold)}
+
+
 def max_over_ranks(value: float, world: int) -> float:
     """Max of a per-rank time over all ranks (the slowest replica sets the
     step time).  Uses a CUDA tensor under NCCL, a CPU tensor under gloo."""
@@ -440,6 +496,10 @@ def main():
         torch.cuda.synchronize()
         barrier()
         ms_e2e = max_over_ranks(e0.elapsed_time(e1), world)
+        # ---- the degree-120 workload (rank 0, default headline workload only)
+        deg120 = None
+        if rank == 0 and world == 1 and a.config == "cfg3" and a.degree120_steps > 0:
+            deg120 = degree120_leg(ctx, flush, a.degree120_steps)
         # ---- one launch per polynomial (same inputs, host buffers)
         one_ms = None
         if rank == 0:
@@ -485,14 +545,28 @@ def main():
                 "peak_kind": apeak_kind, "unit": "Gop/s", "frac": achieved / apeak, "traffic": None,
                 "algorithmic_ops": ops, "patterns_visited": visited, "avg_launch_us": join_us}
     elif fused:
-        # the fused match (k_mitm) is the match stage; no table scatter ran
+        # the fused match (k_mitm) is the match stage; no table scatter ran.  Three
+        # fractions: integer operations against the INT32 peak (the primary line),
+        # the method's HBM floor (each half written once and read once, 24 B per
+        # half-sum) against the measured HBM peak, and the warp instructions the
+        # committed ncu summary counts per half-sum against the issue peak.
         apeak, apeak_kind = alu_peak()
         ops = ALU_OPS_PER_HALF_SUM * half_sums
         achieved = ops / (join_us * 1e-6) / 1e9
+        hbm_eq = 24.0 * half_sums / (join_us * 1e-6) / 1e9
+        ipk = issue_peak()
+        inst = profile_figure("k_mitm", "warp_inst_per_half_sum")
+        issue = None if inst is None else inst * half_sums / (join_us * 1e-6) / 1e9
         roof = {"bound": "alu", "kernel": "k_mitm", "achieved": achieved, "peak": apeak,
                 "peak_kind": apeak_kind, "unit": "Gop/s", "frac": achieved / apeak,
                 "traffic": kernel_traffic("k_mitm", half_sums),
-                "algorithmic_ops": ops, "avg_launch_us": join_us}
+                "algorithmic_ops": ops, "avg_launch_us": join_us,
+                "hbm_equivalent": {"bytes_per_half_sum": 24, "achieved_GBps": hbm_eq, "peak_GBps": peak,
+                                   "peak_kind": peak_kind, "frac": hbm_eq / peak},
+                "issue": {"warp_inst_per_half_sum": inst, "achieved_Ginst_per_s": issue, "peak_Ginst_per_s": ipk,
+                          "peak_kind": "148 SMs x 4 schedulers x measured sm_max_mhz",
+                          "frac": None if issue is None else issue / ipk,
+                          "source": "profiles/k_mitm_deg100.md (null if the kernel changed since)"}}
     else:
         kern = {"k_join": (join_us, 8.0 * half_sums), "k_runs": (scat_us, 8.0 * half_sums)}
         dom = max(kern, key=lambda k: kern[k][0])
@@ -509,7 +583,9 @@ def main():
         "config": {"workload": WORKLOAD_NAME[a.config], "polys_per_step": B,
                    "half_sums_per_step": half_sums, "parallelism": f"replicas x{world}",
                    "l2": "256 MiB buffer written before every timed step (L2 flush)", "root_mode": a.root_mode,
-                   "autotune": ("off" if a.no_autotune else "layouts tuned per (n_a, n_b) during warm-up"),
+                   "autotune": ("off" if a.no_autotune else
+                                "on; the fused match has no layout knobs, the autotuner tunes the table match "
+                                "(which takes only halves the fused match does not)"),
                    "match_path": a.match_path},
         "half_sums_per_s": half_sums * world * a.steps / (ms / 1e3),
         # what a design that keeps the sorted halves in HBM would need to move for the same
@@ -533,6 +609,8 @@ def main():
         "clocks": clk,
         "correct": {"statuses_ok": all(s == 0 for s in statuses), "matches_golden": ok_golden},
     }
+    if deg120 is not None:
+        line["degree120"] = deg120
     if a.serving_requests > 0 and world == 1:
         line["serving"] = serving_leg(local, a.serving_requests, [float(x) for x in a.serving_loads.split(",")],
                                       trace_path=a.serving_trace)

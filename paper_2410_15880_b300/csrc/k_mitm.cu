@@ -50,14 +50,22 @@ constexpr int YM_THREADS = 256;
 constexpr int YM_PER = 8;                                      // merge outputs per thread (2048-output tiles)
 constexpr int L_MAX = 25;                                      // list bits (2^7 runs of a 32-element half)
 
-constexpr int MT_THREADS = 1024;
+#ifndef RFR_MT_THREADS
+#define RFR_MT_THREADS 1024
+#endif
+constexpr int MT_THREADS = RFR_MT_THREADS;
 constexpr int MT_WARPS = MT_THREADS / 32;
 constexpr int MT_UNIT_LOG = 14;                                // table-a keys of one unit: 2^14 on average
 constexpr int MT_CAP = 24576;                                  // table slots (1.5 x the mean)
 constexpr int MT_NBL = 12;                                     // at most 2^12 bins per unit
 constexpr int MT_HEADS = (1 << MT_NBL) + 4;                    // bins 0 .. 2^nbl (positions carry an offset)
-constexpr int MT_RPW = 4;                                      // runs of each half per warp
-constexpr int MT_RUNS = MT_WARPS * MT_RPW;                     // at most 128 runs per half
+constexpr int MT_RUNS = 128;                                   // at most 128 runs per half
+constexpr int MT_RPW = MT_RUNS / MT_WARPS;                     // runs of each half per warp
+constexpr int GL = 32 / MT_RPW;                                // lanes walking one run together
+#ifndef RFR_MT_UR
+#define RFR_MT_UR 4
+#endif
+constexpr int MT_UR = RFR_MT_UR;                               // list loads in flight per lane
 constexpr int MT_CH = 8;                                       // units whose stretches are found together
 constexpr int MT_BM_LOG = 19;                                  // occupancy bitmap: about 2^19 cells per unit
 constexpr int MT_BMW = (1 << (MT_BM_LOG - 5)) + 4;             // + margin cells (16-byte multiple)
@@ -294,6 +302,70 @@ __device__ __forceinline__ uint32_t dir_lower_bound(const uint64_t* __restrict__
     return lo;
 }
 
+// The table-a keys of the bins around position pb (a half-b key with pattern
+// bits mb): those within wf are fingerprint hits.  A hit's table slot e gives
+// the half-a run (the last run whose slots start at or before e) and the list
+// index; k_mitm_check re-checks the pair exactly.  Not inlined: only the few
+// half-b keys whose bitmap cell is marked come here, and keeping this code out
+// of the key loops leaves their registers alone.
+__device__ __noinline__ void mitm_walk(uint32_t pbu, uint32_t mb, const uint32_t* E, const uint32_t* head,
+                                       const uint32_t* rsb, const uint32_t* rp0, int wf, int pmax, int la,
+                                       const MitmJob* P) {
+    const int pb = (int)pbu;
+    const int plo = pb - wf < 0 ? 0 : pb - wf;
+    const int phi = pb + wf > pmax ? pmax : pb + wf;
+    const uint32_t lma = (1u << la) - 1u;
+    for (int bin = plo >> 16; bin <= (phi >> 16); ++bin) {
+        uint32_t e = head[bin];
+        for (int steps = 0; e < (uint32_t)MT_CAP && steps < MT_CAP; ++steps) {   // lists end in NIL; bounded anyway
+            const uint32_t en = E[e];
+            const int d = ((bin << 16) | (int)(en & 0xffffu)) - pb;
+            if (d >= -wf && d <= wf) {
+                int lo_o = 0, hi_o = MT_RUNS - 1;
+                while (lo_o < hi_o) {
+                    const int mid = (lo_o + hi_o + 1) >> 1;
+                    if (rsb[mid] <= e) lo_o = mid; else hi_o = mid - 1;
+                }
+                const uint32_t run = (uint32_t)(lo_o / MT_RPW + MT_WARPS * (lo_o % MT_RPW));
+                const uint32_t ma = (run << la) | ((rp0[lo_o] + (e - rsb[lo_o])) & lma);
+                const unsigned long long idx = atomicAdd(P->nhits, 1ull);
+                if (idx < P->hcap) P->hits[idx] = (uint64_t)ma | ((uint64_t)mb << 32);
+                else atomicExch(P->err, 1);                          // more hits than room: redo with tables
+            }
+            e = en >> 16;
+        }
+    }
+}
+
+// Stretches of one warp's runs in units k .. k + CH - 1 (lane by lane): half
+// a's stretch of unit k + v starts at apos[i][v] (and ends where unit k + v + 1
+// starts); half b's, within Wc of the unit, spans bpos[i][v][0 .. 1].  Not
+// inlined: it runs once per CH units.
+__device__ __noinline__ void mitm_stretches(uint32_t k, int su, uint64_t Wc, int qa, int qb,
+                                            const uint64_t* Ya, const uint32_t* Da, int la,
+                                            const uint64_t* Yb, const uint32_t* Db, int lb,
+                                            const uint64_t* wxa, const uint64_t* wxb, uint32_t* wap, uint32_t* wbp) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t U = 1ull << su;
+    for (int e = lane; e < MT_APOS + MT_BPOS; e += 32) {
+        if (e < MT_APOS) {
+            const int i = e / (MT_CH + 1), v = e % (MT_CH + 1);
+            if (i < qa) {
+                const uint64_t val = ((uint64_t)(k + v) << su) - wxa[i];
+                wap[e] = dir_lower_bound(Ya, Da, la, val);
+            }
+        } else {
+            const int e2 = e - MT_APOS, i = e2 / (2 * MT_CH), v = (e2 % (2 * MT_CH)) >> 1, side = e2 & 1;
+            if (i < qb) {
+                const uint64_t l0 = (uint64_t)(k + v) << su;
+                const uint64_t val = (side ? l0 + U + Wc : l0 - Wc) - wxb[i];
+                wbp[e2] = dir_lower_bound(Yb, Db, lb, val);
+            }
+        }
+    }
+    __syncwarp();
+}
+
 // Key positions.  A key K of unit [lo, lo + U) (half b: within Wc of it) sits at
 // position p = (K - lo + Off) >> fsh, Off = coff 2^fsh, so that every position
 // and the window around it are >= 0.  For a run with offset x, K = x + y over
@@ -347,10 +419,10 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
     const uint32_t k0 = (uint32_t)c * (uint32_t)P.slab, k1 = k0 + (uint32_t)P.slab;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
-    const int g = lane >> 3, gl = lane & 7;                             // run group of this lane
-    // this warp's runs: run warp + 32 i for i < qa (half a), i < qb (half b)
-    const int qa = RA > warp ? min(MT_RPW, (RA - warp + 31) >> 5) : 0;
-    const int qb = RB > warp ? min(MT_RPW, (RB - warp + 31) >> 5) : 0;
+    const int g = lane / GL, gl = lane % GL;                            // run group of this lane
+    // this warp's runs: run warp + MT_WARPS i for i < qa (half a), i < qb (half b)
+    const int qa = RA > warp ? min(MT_RPW, (RA - warp + MT_WARPS - 1) / MT_WARPS) : 0;
+    const int qb = RB > warp ? min(MT_RPW, (RB - warp + MT_WARPS - 1) / MT_WARPS) : 0;
     uint32_t* wap = apos + warp * MT_APOS;
     uint32_t* wbp = bpos + warp * MT_BPOS;
     uint64_t* wxa = xs + warp * (2 * MT_RPW);
@@ -362,44 +434,15 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
     __syncthreads();
     if (lane < qa) {
         uint64_t x = 0;
-        for (uint32_t t = (uint32_t)(warp + 32 * lane); t; t &= t - 1) x += wa[la + __ffs(t) - 1];
+        for (uint32_t t = (uint32_t)(warp + MT_WARPS * lane); t; t &= t - 1) x += wa[la + __ffs(t) - 1];
         wxa[lane] = x;
     } else if (lane >= MT_RPW && lane < MT_RPW + qb) {
         uint64_t x = 0;
-        for (uint32_t t = (uint32_t)(warp + 32 * (lane - MT_RPW)); t; t &= t - 1) x -= wb[lb + __ffs(t) - 1];
+        for (uint32_t t = (uint32_t)(warp + MT_WARPS * (lane - MT_RPW)); t; t &= t - 1) x -= wb[lb + __ffs(t) - 1];
         wxb[lane - MT_RPW] = x;
     }
     __syncwarp();
 
-    // a fingerprint hit: table slot e -> (run, list index) of half a; re-checked
-    // exactly by k_mitm_check
-    auto hit = [&](uint32_t e, uint32_t mb) {
-        int lo_o = 0, hi_o = MT_RUNS - 1;                              // last run whose slots start at or before e
-        while (lo_o < hi_o) {
-            const int mid = (lo_o + hi_o + 1) >> 1;
-            if (rsb[mid] <= e) lo_o = mid; else hi_o = mid - 1;
-        }
-        const uint32_t run = (uint32_t)((lo_o >> 2) + 32 * (lo_o & 3));
-        const uint32_t ma = (run << la) | ((rp0[lo_o] + (e - rsb[lo_o])) & lma);
-        const unsigned long long idx = atomicAdd(P.nhits, 1ull);
-        if (idx < P.hcap) P.hits[idx] = (uint64_t)ma | ((uint64_t)mb << 32);
-        else atomicExch(P.err, 1);                                   // more hits than room: redo with tables
-    };
-    // The table-a keys of the bins around position pb: those within wf are hits.
-    auto scan_bins = [&](uint32_t pbu, uint32_t mb) {
-        const int pb = (int)pbu;
-        const int plo = pb - wf < 0 ? 0 : pb - wf;
-        const int phi = pb + wf > pmax ? pmax : pb + wf;
-        for (int bin = plo >> 16; bin <= (phi >> 16); ++bin) {
-            uint32_t e = head[bin];
-            for (int steps = 0; e < (uint32_t)MT_CAP && steps < MT_CAP; ++steps) {   // lists end in NIL; bounded anyway
-                const uint32_t en = E[e];
-                const int d = ((bin << 16) | (int)(en & 0xffffu)) - pb;
-                if (d >= -wf && d <= wf) hit(e, mb);
-                e = en >> 16;
-            }
-        }
-    };
     // Warp-uniform: queue the lanes whose lookup may hit; scan 32 queued lookups at a time.
     uint32_t qn = 0;
     auto enqueue = [&](bool need, uint32_t pb, uint32_t mb) {
@@ -414,34 +457,14 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
             __syncwarp();
             if (lane + 32 < (int)qn) wq[lane] = e2;
             qn -= 32;
-            scan_bins(e.x, e.y);
+            mitm_walk(e.x, e.y, E, head, rsb, rp0, wf, pmax, la, &P);
         }
     };
 
     for (uint32_t k = k0; k < k1; ++k) {
         const uint32_t u = (k - k0) % MT_CH;
         const uint64_t lo = (uint64_t)k << su;
-        if (u == 0) {
-            // stretches of this warp's runs in units k .. k + CH - 1: half a's stretch of
-            // unit k + v starts at apos[i][v]; half b's spans bpos[i][v][0 .. 1]
-            for (int e = lane; e < MT_APOS + MT_BPOS; e += 32) {
-                if (e < MT_APOS) {
-                    const int i = e / (MT_CH + 1), v = e % (MT_CH + 1);
-                    if (i < qa) {
-                        const uint64_t val = ((uint64_t)(k + v) << su) - wxa[i];
-                        wap[e] = dir_lower_bound(Ya, Da, la, val);
-                    }
-                } else {
-                    const int e2 = e - MT_APOS, i = e2 / (2 * MT_CH), v = (e2 % (2 * MT_CH)) >> 1, side = e2 & 1;
-                    if (i < qb) {
-                        const uint64_t l0 = (uint64_t)(k + v) << su;
-                        const uint64_t val = (side ? l0 + U + Wc : l0 - Wc) - wxb[i];
-                        wbp[e2] = dir_lower_bound(Yb, Db, lb, val);
-                    }
-                }
-            }
-            __syncwarp();
-        }
+        if (u == 0) mitm_stretches(k, su, Wc, qa, qb, Ya, Da, la, Yb, Db, lb, wxa, wxb, wap, wbp);
         // reset the table heads and the bitmap with 16-byte stores
         {
             uint4* h4 = reinterpret_cast<uint4*>(head);
@@ -458,13 +481,17 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
             acnt = v0 >= 0ull - U ? Na - pa0 + p1 : p1 - pa0;              // the stretch wraps past the list's end
             apx = (uint32_t)((Off - v0) >> fsh);
         }
-        const uint32_t c0 = __shfl_sync(0xffffffffu, acnt, 0), c1 = __shfl_sync(0xffffffffu, acnt, 8);
-        const uint32_t c2 = __shfl_sync(0xffffffffu, acnt, 16), c3 = __shfl_sync(0xffffffffu, acnt, 24);
-        const uint32_t gpre = (g > 0 ? c0 : 0u) + (g > 1 ? c1 : 0u) + (g > 2 ? c2 : 0u);
-        if (lane == 0) s_tot[warp] = c0 + c1 + c2 + c3;
+        uint32_t gpre = 0, wtot = 0;                                     // keys of the lower groups; of the warp
+#pragma unroll
+        for (int i = 0; i < MT_RPW; ++i) {
+            const uint32_t ci = __shfl_sync(0xffffffffu, acnt, i * GL);
+            gpre += i < g ? ci : 0u;
+            wtot += ci;
+        }
+        if (lane == 0) s_tot[warp] = wtot;
         __syncthreads();
         // slot base of this warp: table-a keys of the lower warps
-        const uint32_t tv = s_tot[lane];
+        const uint32_t tv = lane < MT_WARPS ? s_tot[lane] : 0u;
         uint32_t incl = tv;
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
@@ -479,15 +506,16 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
         if (gl == 0) { rsb[warp * MT_RPW + g] = sbg; rp0[warp * MT_RPW + g] = pa0; }
         // ---- table a: every key of the unit, 8 lanes per run, 4 runs per warp
         {
-            const uint32_t itn = (__reduce_max_sync(0xffffffffu, acnt) + 7) >> 3;
-            for (uint32_t it = 0; it < itn; it += 2) {
-                const uint32_t t0 = it * 8 + gl, t1 = t0 + 8;
-                const uint32_t y0 = Ya32[(pa0 + t0) & lma], y1 = Ya32[(pa0 + t1) & lma];
+            const uint32_t itn = (__reduce_max_sync(0xffffffffu, acnt) + GL - 1) / GL;
+            for (uint32_t it = 0; it < itn; it += MT_UR) {
+                uint32_t yv[MT_UR];
 #pragma unroll
-                for (int s = 0; s < 2; ++s) {
-                    const uint32_t t = s ? t1 : t0;
+                for (int s = 0; s < MT_UR; ++s) yv[s] = Ya32[(pa0 + (it + s) * GL + gl) & lma];
+#pragma unroll
+                for (int s = 0; s < MT_UR; ++s) {
+                    const uint32_t t = (it + s) * GL + gl;
                     if (t < acnt) {
-                        const uint32_t p = ((s ? y1 : y0) + apx) & kmask;
+                        const uint32_t p = (yv[s] + apx) & kmask;
                         const uint32_t slot = sbg + t;
                         const uint32_t old = atomicExch(&head[min(p >> 16, (uint32_t)nbins)], slot);
                         E[slot] = (p & 0xffffu) | (old << 16);
@@ -509,15 +537,16 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
                 bcnt = v0 + U + 2 * Wc < v0 ? Nb - pb0 + p1 : p1 - pb0;
                 bpx = (uint32_t)((wxb[g] - lo + Off) >> fsh);
             }
-            const uint32_t gbits = (uint32_t)(warp + 32 * g) << lb;
-            const uint32_t itn = (__reduce_max_sync(0xffffffffu, bcnt) + 7) >> 3;
-            for (uint32_t it = 0; it < itn; it += 2) {
-                const uint32_t t0 = it * 8 + gl, t1 = t0 + 8;
-                const uint32_t y0 = Yb32[(pb0 + t0) & lmb], y1 = Yb32[(pb0 + t1) & lmb];
+            const uint32_t gbits = (uint32_t)(warp + MT_WARPS * g) << lb;
+            const uint32_t itn = (__reduce_max_sync(0xffffffffu, bcnt) + GL - 1) / GL;
+            for (uint32_t it = 0; it < itn; it += MT_UR) {
+                uint32_t yv[MT_UR];
 #pragma unroll
-                for (int s = 0; s < 2; ++s) {
-                    const uint32_t t = s ? t1 : t0;
-                    const uint32_t p = ((s ? y1 : y0) + bpx) & kmask;
+                for (int s = 0; s < MT_UR; ++s) yv[s] = Yb32[(pb0 + (it + s) * GL + gl) & lmb];
+#pragma unroll
+                for (int s = 0; s < MT_UR; ++s) {
+                    const uint32_t t = (it + s) * GL + gl;
+                    const uint32_t p = (yv[s] + bpx) & kmask;
                     const uint32_t qc = p >> rsh;
                     const uint32_t wv = bm[min(qc >> 5, (uint32_t)(MT_BMW - 1))];
                     const bool need = t < bcnt && ((wv >> (qc & 31)) & 1u);
@@ -529,7 +558,7 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
             __syncwarp();
             if (lane < (int)qn) {
                 const uint2 e = wq[lane];
-                scan_bins(e.x, e.y);
+                mitm_walk(e.x, e.y, E, head, rsb, rp0, wf, pmax, la, &P);
             }
             qn = 0;
         }
