@@ -101,6 +101,12 @@ int rfr_stage_enumerate(const uint64_t* w, int h, uint64_t* keys, void* stream);
  * of n_a and n_b elements. */
 size_t rfr_stage_match_workspace(int n_a, int n_b);
 
+/* Bytes of device scratch rfr_stage_match_fused needs for halves of n_a and
+ * n_b elements (2 <= n_a <= n_b <= 32): its sorted lists, their masks and
+ * directories, and room for 2^20 fingerprint hits; 0 if the fused match does
+ * not take these halves.  Section 3.3. */
+size_t rfr_stage_match_fused_workspace(int n_a, int n_b);
+
 /* K-d for the fused match: one half's sorted list of low-subset sums.
  * For every subset s of the weights w[0..l), list[] receives the exact sum
  * S(s) = sum over i in s of w_i modulo 2^64 (of -w_i when negate != 0) and
@@ -199,17 +205,19 @@ int rfr_stage_match_exact(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
                           void* stream);
 
 /* As rfr_stage_match, always with the fused match that keeps no key tables
- * in device memory: sorted lists of the halves' low-subset sums are built
- * by merging, and each CTA generates a range of half a's keys into a
+ * in device memory: sorted lists of the halves' exact low-subset sums are
+ * built by merging, and each CTA generates a range of half a's keys into a
  * shared-memory table and looks half b's keys of that range up in it.
- * rfr_stage_match uses it by itself for 14 <= n_a <= n_b <= 31.  Returns
- * RFR_E_WINDOW if a half has more than 31 elements or the window is too wide
- * for it (about
- * W >= 2^(59 - max(n_a - 13, 2))); counters[4] = 1 when one key range holds
- * more than 12288 keys of half a (clustered keys), or when the workspace has
- * no room for all fingerprint hits (very wide windows; every hit takes 8
- * bytes beyond rfr_stage_match_workspace, which has room for 2^20): use
- * rfr_stage_match_exact, or pass more workspace.  Section 3.3. */
+ * rfr_stage_match uses it by itself for 14 <= n_a <= n_b <= 32.  Returns
+ * RFR_E_WINDOW if a half has more than 32 elements or the window is too wide
+ * for it (about W >= 2^(60 - max(n_a - 14, 2) - 4)); counters[4] = 1 when one
+ * key range holds more than 24576 keys of half a (clustered keys), or when
+ * the workspace has no room for all fingerprint hits (very wide windows;
+ * every hit takes 8 bytes beyond rfr_stage_match_fused_workspace, which has
+ * room for 2^20): use rfr_stage_match_exact, or pass more workspace.  The
+ * workspace may be rfr_stage_match_fused_workspace(n_a, n_b) bytes (the
+ * fused match's own buffers) instead of rfr_stage_match_workspace.
+ * Section 3.3. */
 int rfr_stage_match_fused(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
                           const uint64_t* w_b, const uint64_t* w2_b, int n_b,
                           uint64_t window, uint64_t window2,

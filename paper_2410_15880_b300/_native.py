@@ -124,6 +124,7 @@ def lib():
         "rfr_stage_weights": (i32, [vp, vp, i32, vp, vp, vp, C.c_double, vp, vp]),
         "rfr_stage_enumerate": (i32, [vp, i32, vp, vp]),
         "rfr_stage_match_workspace": (C.c_size_t, [i32, i32]),
+        "rfr_stage_match_fused_workspace": (C.c_size_t, [i32, i32]),
         "rfr_stage_lowlist_workspace": (C.c_size_t, [i32]),
         "rfr_stage_lowlist": (i32, [vp, i32, i32, vp, vp, vp, C.c_size_t, vp]),
         "rfr_stage_prune": (i32, [vp, vp, i32, u64, u64, vp, u64, vp, vp, C.c_size_t, vp]),
@@ -459,9 +460,13 @@ def stage_match(w_a, w2_a, w_b, w2_b, window: int, window2: int, cap: int, exact
     import torch
     n_a, n_b = int(w_a.numel()), int(w_b.numel())
     dev = w_b.device
-    ws_bytes = match_workspace_bytes(n_a, n_b)
-    if fused:                                   # room for fingerprint hits (wide windows, largest halves)
+    if fused:                                   # its own buffers, and room for fingerprint hits
+        ws_bytes = int(lib().rfr_stage_match_fused_workspace(n_a, n_b))
+        if ws_bytes == 0:
+            raise RFRError(-1, f"the fused match does not take halves of {n_a} and {n_b} elements")
         ws_bytes += 8 * min(1 << (n_a + n_b), 1 << 26)
+    else:
+        ws_bytes = match_workspace_bytes(n_a, n_b)
     ws = torch.empty((ws_bytes // 8 + 64,), dtype=torch.int64, device=dev)
     base = ws.data_ptr()
     aligned = (base + 255) & ~255

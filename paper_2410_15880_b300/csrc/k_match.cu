@@ -1167,6 +1167,13 @@ extern "C" size_t rfr_stage_match_workspace(int n_a, int n_b) {
     return g.bytes + hist_extra + 2048;
 }
 
+extern "C" size_t rfr_stage_match_fused_workspace(int n_a, int n_b) {
+    MatchGeom gf;
+    if (!stage_geom(n_a, n_b, 0, &gf, true, FUSE_ALWAYS)) return 0;
+    const int e = n_a + n_b < 20 ? n_a + n_b : 20;
+    return gf.bytes + ((size_t)8 << e) + 2048;
+}
+
 static int stage_match(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
                        const uint64_t* w_b, const uint64_t* w2_b, int n_b,
                        uint64_t window, uint64_t window2,

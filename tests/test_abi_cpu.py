@@ -71,6 +71,9 @@ def test_stage_argument_checks(L):
     assert L.rfr_stage_enumerate(None, 4, None, None) == -1
     assert L.rfr_stage_match_workspace(5, 3) == 0          # n_b < n_a is not a valid split
     assert L.rfr_stage_match_workspace(10, 11) > (1 << 11) * 8
+    assert L.rfr_stage_match_fused_workspace(1, 2) == 0    # the fused match needs two elements per half
+    assert L.rfr_stage_match_fused_workspace(12, 33) == 0  # and at most 32
+    assert L.rfr_stage_match_fused_workspace(26, 27) > (1 << 20) * (8 + 4 + 4 + 4)   # lists, masks, directory, positions
     assert L.rfr_stage_splat_cells(-1) == 0 and L.rfr_stage_splat_cells(31) == 0
     assert L.rfr_stage_splat_cells(10) == (2 << 10) + 4096 + 32   # home cells, overflow cells, descriptor
     assert L.rfr_stage_splat(None, 40, None, 0, None, None) == -1

@@ -330,7 +330,7 @@ def test_match_fused_large_against_sorted_mitm(P, seed, na, nb, logW, tr2):
     pairs = band_pairs_sorted(wa, wb, W)
     if tr2:
         a2, b2 = expand_values_u64(w2a), expand_values_u64(w2b)
-        pairs = {(i, j) for (i, j) in pairs if accept(int(a2[i] + b2[j]), M64, W2)}
+        pairs = {(i, j) for (i, j) in pairs if accept((int(a2[i]) + int(b2[j])) % M64, M64, W2)}
     assert ctr[4] == 0 and ctr[3] == 1
     assert got == pairs - {(0, 0)}
     assert len(raw) == len(set(raw)) and ctr[2] == len(raw)
@@ -338,6 +338,79 @@ def test_match_fused_large_against_sorted_mitm(P, seed, na, nb, logW, tr2):
     if not tr2:                                       # planted pairs (Tr_2 may reject them otherwise)
         for pl in [(1, 1), (2, 2), (4, 4), (1 | 2, 1 | 2)]:
             assert pl in got
+
+
+# ---------------------------------------------------------------- completeness at production sizes
+_PROD_CACHE = {}
+
+
+def _production_case(seed, na, nb, logW, tr2):
+    """Weights (with planted integral subsets and pairs across the circular
+    wrap) and the oracle's pair set (sorted meet in the middle, then the Tr_2
+    test) for halves of na and nb elements; cached per argument tuple."""
+    key = (seed, na, nb, logW, tr2)
+    if key in _PROD_CACHE:
+        return _PROD_CACHE[key]
+    from oracle.recombine import accept, band_pairs_sorted, expand_values_u64
+    rng = random.Random(seed)
+    wa = [rng.randrange(M64) for _ in range(na)]
+    wb = [rng.randrange(M64) for _ in range(nb)]
+    wa[0], wb[0] = M64 - 3, M64 - 2                   # K_a = 2^64 - 3 meets K_b = 2 (over the wrap)
+    wa[1], wb[1] = 3, 2
+    wb[5] = (-(wa[4] + wa[7] + wb[9])) % M64
+    wa[11] = (-(wb[12] + wb[13])) % M64
+    W = 1 << logW
+    if tr2:
+        w2a = [rng.randrange(M64) for _ in range(na)]
+        w2b = [rng.randrange(M64) for _ in range(nb)]
+        W2 = 1 << 62
+    else:
+        w2a, w2b, W2 = [0] * na, [0] * nb, 0
+    pairs = band_pairs_sorted(wa, wb, W)
+    if tr2:
+        a2, b2 = expand_values_u64(w2a), expand_values_u64(w2b)
+        pairs = {(i, j) for (i, j) in pairs if accept((int(a2[i]) + int(b2[j])) % M64, M64, W2)}
+    _PROD_CACHE[key] = (wa, wb, w2a, w2b, W, W2, pairs)
+    return _PROD_CACHE[key]
+
+
+@pytest.mark.parametrize("seed,na,nb,logW,tr2", [(61, 26, 27, 21, True), (62, 27, 27, 21, False)])
+def test_match_fused_production_size_against_sorted_mitm(P, seed, na, nb, logW, tr2):
+    """Completeness at the sizes the degree-100 problems run (2^26 + 2^27 and
+    2^27 + 2^27 half-sums, 128 runs per half, 2^12 and 2^13 key units): the
+    fused match's candidate set equals the oracle's sorted meet in the middle
+    (every pair in the circular window, Eq. 9, then the Tr_2 test), with a
+    window wide enough for thousands of pairs."""
+    wa, wb, w2a, w2b, W, W2, pairs = _production_case(seed, na, nb, logW, tr2)
+    assert len(pairs) >= 1000
+    torch.cuda.empty_cache()
+    got, ctr, raw = _run_match(P, wa, w2a, wb, w2b, W, W2, cap=1 << 16, fused=True)
+    torch.cuda.empty_cache()
+    assert ctr[4] == 0 and ctr[3] == 1
+    assert len(raw) == len(set(raw)) == ctr[2]
+    assert got == pairs - {(0, 0)}
+
+
+def test_match_fused_32_element_halves_against_sorted_mitm(P):
+    """Halves of 32 elements (2^32 + 2^32 half-sums, the degree-120 geometry:
+    lists of 2^25 entries, 2^18 key units) whose top five weights are zero: the
+    pair set is then exactly the oracle's pair set of the other 27 + 27
+    elements times every choice of the zero elements (2^5 x 2^5), which the
+    oracle computes by its sorted meet in the middle."""
+    from oracle.recombine import accept, value
+    wa27, wb27, _, _, _, _, wide = _production_case(62, 27, 27, 21, False)
+    W = 1 << 10
+    narrow = {(i, j) for (i, j) in wide
+              if accept((value(i, wa27, M64) + value(j, wb27, M64)) % M64, M64, W)}
+    wa, wb = wa27 + [0] * 5, wb27 + [0] * 5
+    exp = {(i | (za << 27), j | (zb << 27)) for (i, j) in narrow for za in range(32) for zb in range(32)}
+    assert len(narrow) >= 4 and len(exp) <= (1 << 17)
+    torch.cuda.empty_cache()
+    got, ctr, raw = _run_match(P, wa, [0] * 32, wb, [0] * 32, W, 0, cap=1 << 17, fused=True)
+    torch.cuda.empty_cache()
+    assert ctr[4] == 0 and ctr[3] == 1
+    assert len(raw) == len(set(raw)) == ctr[2]
+    assert got == exp - {(0, 0)}
 
 
 def test_match_fused_clustered_keys_overflow(P):
