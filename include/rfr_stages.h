@@ -237,7 +237,10 @@ int rfr_stage_match_fused(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
  * call made with a device current; make that first call before any stream
  * capture.  All calls on a device share the array: calls that overlap on
  * the GPU race and must be serialised by the caller.  The parts of the array
- * that must start at zero are cleared by every call. */
+ * that must start at zero are cleared by every call.  The address is cached
+ * for the life of the process: after a cudaDeviceReset of that device the
+ * cached address is stale, so do not call this entry point on a device that
+ * has been reset. */
 #define RFR_NOALLOC_SCRATCH_BYTES (16u << 20)
 int rfr_stage_match_noalloc(const uint64_t* w_a, const uint64_t* w2_a, int n_a,
                             const uint64_t* w_b, const uint64_t* w2_b, int n_b,

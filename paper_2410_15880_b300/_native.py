@@ -261,22 +261,28 @@ class Context:
         except Exception:
             pass
 
+    def set_allocator(self, alloc, free):
+        """Route device allocations through alloc(nbytes, stream) -> address
+        (0 when it cannot) and free(address, nbytes, stream) (rfr_set_allocator);
+        both None restores the built-in stream-ordered pool."""
+        if alloc is None and free is None:
+            st = lib().rfr_set_allocator(self._h, C.cast(None, ALLOC_FN), C.cast(None, FREE_FN), None)
+            self._keep = []
+        else:
+            fa = ALLOC_FN(lambda nbytes, user, stream: alloc(int(nbytes), stream or 0) or None)
+            ff = FREE_FN(lambda ptr, nbytes, user, stream: free(ptr, int(nbytes), stream or 0))
+            st = lib().rfr_set_allocator(self._h, fa, ff, None)
+            if st == RFR_OK:
+                self._keep = [fa, ff]
+        if st != RFR_OK:
+            raise RFRError(st, "rfr_set_allocator")
+
     def use_torch_allocator(self):
         """Route device allocations through PyTorch's caching allocator."""
         import torch
         dev = torch.cuda.current_device()
-
-        def _alloc(nbytes, user, stream):
-            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream or 0)
-
-        def _free(ptr, nbytes, user, stream):
-            torch.cuda.caching_allocator_delete(ptr)
-
-        fa, ff = ALLOC_FN(_alloc), FREE_FN(_free)
-        self._keep = [fa, ff]
-        st = lib().rfr_set_allocator(self._h, fa, ff, None)
-        if st != RFR_OK:
-            raise RFRError(st, "rfr_set_allocator")
+        self.set_allocator(lambda nbytes, stream: torch.cuda.caching_allocator_alloc(nbytes, dev, stream),
+                           lambda ptr, nbytes, stream: torch.cuda.caching_allocator_delete(ptr))
 
     def factor(self, coeffs: Sequence[int]) -> Result:
         f = Factors()

@@ -818,16 +818,15 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2) k_small(const SmallJob* __re
 }
 
 static const size_t SMALL_SMEM = ((size_t)1 << SMALL_MAX_H) * 8 + (size_t)pad32(1 << SUB_BITS) * 4;
-static bool g_small_attr = false;
+static PerDeviceOnce g_small_attr;
 
 cudaError_t run_small(const SmallJob* jobs, int np, SmallJob* dev_jobs, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
-    if (!g_small_attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMALL_SMEM);
-        if (e != cudaSuccess) return e;
-        g_small_attr = true;
-    }
-    cudaError_t e = cudaMemcpyAsync(dev_jobs, jobs, sizeof(SmallJob) * np, cudaMemcpyHostToDevice, s);
+    cudaError_t e = g_small_attr.run([] {
+        return cudaFuncSetAttribute(k_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMALL_SMEM);
+    });
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(dev_jobs, jobs, sizeof(SmallJob) * np, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
     k_small<<<np, SMALL_THREADS, SMALL_SMEM, s>>>(dev_jobs, np);
     return cudaGetLastError();
@@ -1041,7 +1040,7 @@ static MatchGrid assign_bases(ProbJob* jobs, int np, HalfJob* halves) {
     return g;
 }
 
-static bool g_attr_set = false;
+static PerDeviceOnce g_attr_set;
 static const size_t JOIN_SMEM = (size_t)JOIN_CAP * 8 + ((size_t)1 << SUB_BITS) * 4 + ((size_t)1 << SUB_BITS) / 32 * 4;
 
 // Upload jobs (from host memory that stays valid until the copies finish:
@@ -1049,14 +1048,16 @@ static const size_t JOIN_SMEM = (size_t)JOIN_CAP * 8 + ((size_t)1 << SUB_BITS) *
 cudaError_t run_match(ProbJob* jobs, int np, ProbJob* dev_jobs, HalfJob* dev_halves,
                       HalfJob* host_halves, cudaStream_t s, cudaEvent_t ev_count, cudaEvent_t ev_scatter,
                       int* launches) {
-    if (!g_attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_join, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)JOIN_SMEM);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_runs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RUNS_SMEM_MAX);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_runs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RUNS_SMEM_MAX);
+    {
+        cudaError_t e = g_attr_set.run([] {
+            cudaError_t r = cudaFuncSetAttribute(k_join, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)JOIN_SMEM);
+            if (r == cudaSuccess)
+                r = cudaFuncSetAttribute(k_runs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, RUNS_SMEM_MAX);
+            if (r == cudaSuccess)
+                r = cudaFuncSetAttribute(k_runs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RUNS_SMEM_MAX);
+            return r;
+        });
         if (e != cudaSuccess) return e;
-        g_attr_set = true;
     }
     // table problems first (compacted to the front of a copy), fused ones after
     std::vector<ProbJob> T;

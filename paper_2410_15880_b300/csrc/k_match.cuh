@@ -2,9 +2,31 @@
 // kernels (K-c, K-d, K-e) and their host-side planners.
 #pragma once
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 
 namespace rfr {
+
+// A kernel attribute set with cudaFuncSetAttribute holds for the current
+// device only: run `set` once per device ordinal (thread-safe), so that a
+// process that drives several GPUs sets it on each.
+struct PerDeviceOnce {
+    static constexpr int kMaxDevices = 64;
+    std::mutex mu;
+    bool done[kMaxDevices] = {};
+    template <class F>
+    cudaError_t run(F set) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+        std::lock_guard<std::mutex> lk(mu);
+        if (done[dev]) return cudaSuccess;
+        e = set();
+        if (e == cudaSuccess) done[dev] = true;
+        return e;
+    }
+};
 
 constexpr int SUB_BITS = 13;          // second radix digit, sorted in shared memory
 constexpr int JOIN_CAP = 9216;        // table-a entries per shared-memory chunk

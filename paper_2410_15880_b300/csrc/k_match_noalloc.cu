@@ -15,7 +15,9 @@
 // two host threads) race on it and must be serialised by the caller.  The
 // match zeroes the parts of the workspace that must start at zero (its
 // counters and halo counts) on every call, so results do not depend on what
-// an earlier call left behind.
+// an earlier call left behind.  The cached address is not looked up again:
+// after a cudaDeviceReset of a device it is stale, and the header says not to
+// call this entry point on a device that has been reset.
 #include <cuda_runtime.h>
 
 #include <mutex>

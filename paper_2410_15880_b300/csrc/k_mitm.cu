@@ -603,23 +603,15 @@ __global__ void __launch_bounds__(256) k_mitm_check(const MitmJob* __restrict__ 
     if (c == 0 && threadIdx.x == 0) atomicAdd(&P.ctr[0], nh);
 }
 
-// cudaFuncSetAttribute applies to the current device only: remember it per device.
-constexpr int kMaxDev = 64;
-std::mutex g_attr_mu;
-bool g_mitm_attr[kMaxDev] = {};
+PerDeviceOnce g_mitm_attr;
 
 cudaError_t mitm_attrs() {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_attr_mu);
-    if (g_mitm_attr[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(k_ybuild_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)YS_SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ymerge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)YM_SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mitm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MT_SMEM);
-    if (e == cudaSuccess) g_mitm_attr[dev] = true;
-    return e;
+    return g_mitm_attr.run([] {
+        cudaError_t e = cudaFuncSetAttribute(k_ybuild_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)YS_SMEM);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ymerge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)YM_SMEM);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mitm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MT_SMEM);
+        return e;
+    });
 }
 
 // Launch the list build for the jobs d_yj[0..nh), sorted by l descending (host

@@ -555,6 +555,7 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
         auto it = C.tuned.find({w.plan.n_a, w.plan.n_b});
         return it == C.tuned.end() ? TuneParams() : it->second;
     };
+    bool one_at_a_time = false;                       // set when a sub-batch's workspace could not be allocated
     while (!todo.empty()) {
         // take a sub-batch that fits this pipeline's share of the budget
         double tot_elems = 0;
@@ -577,7 +578,7 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
             if (sharded() && shard.index != 0 && !g.fused && !w.full_halo) { w.matched = true; continue; }
             const size_t need = g.bytes + (size_t)cap * 8 + 6 * 8 + 512;
             if (need > C.budget) { w.status = RFR_E_BUDGET; continue; }
-            if (!sub.empty() && bytes + need > share) { rest.push_back(sl); continue; }
+            if (!sub.empty() && (one_at_a_time || bytes + need > share)) { rest.push_back(sl); continue; }
             w.geom = g;
             bytes += need;
             sub.push_back(sl);
@@ -588,7 +589,17 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
         const int np = (int)sub.size();
         const size_t jobs_bytes = (size_t)np * sizeof(ProbJob) + 2 * (size_t)np * sizeof(HalfJob) + 1024;
         char* ws = (char*)C.alloc.get(bytes + jobs_bytes, s);
-        if (!ws) { C.release(bytes); for (int sl : sub) work[sl].status = RFR_E_OOM; continue; }
+        if (!ws) {
+            C.release(bytes);
+            if (np > 1) {                             // retry its problems one at a time: only those whose
+                one_at_a_time = true;                 // own tables cannot be allocated end with RFR_E_OOM
+                sub.insert(sub.end(), todo.begin(), todo.end());
+                todo.swap(sub);
+            } else {
+                work[sub[0]].status = RFR_E_OOM;
+            }
+            continue;
+        }
         std::vector<ProbJob> jobs(np);
         std::vector<HalfJob> halves(2 * np);
         char* p = ws;

@@ -182,29 +182,46 @@ def test_tables_only_equals_fused():
         assert a.diag["cand_post"] == t.diag["cand_post"]
 
 
+def _run_shards(polys, nshards, timeout=600.0):
+    """factor_batch_sharded for every shard, one thread and context each, the
+    verified sets exchanged on the host.  The exchange gives up well before
+    the join limit, so a stuck shard ends with its own error; every shard's
+    exception is re-raised here, and no shard is left running."""
+    import threading
+    from paper_2410_15880_b300 import Context
+    from paper_2410_15880_b300.sharding import ThreadExchange
+    ex = ThreadExchange(nshards, timeout=timeout / 4)
+    out, err = [None] * nshards, [None] * nshards
+
+    def run(s):
+        try:
+            with Context(device=0, mem_budget_bytes=16 << 30) as c:
+                out[s] = c.factor_batch_sharded(polys, s, nshards, ex.gather_for(s))
+        except BaseException as e:                     # noqa: BLE001 - handed to the test thread
+            err[s] = e
+    th = [threading.Thread(target=run, args=(s,)) for s in range(nshards)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(timeout=timeout)
+    assert not any(t.is_alive() for t in th), "a shard did not finish"
+    for e in err:
+        if e is not None:
+            raise e
+    return out
+
+
 def test_key_range_shards_equal_whole_batch():
     """Two key-range shards of one batch, run by two threads with their own
     contexts on this GPU and exchanging verified sets on the host (no kernel
     waits on another): both return the goldens' factorisations, and the fused
     problems' candidates split between the shards without overlap."""
-    import threading
     from paper_2410_15880_b300 import Context
-    from paper_2410_15880_b300.sharding import ThreadExchange
     recs = golden("cfg3")[:4] + golden("cfg2")[:4] + golden("cfg1") + golden("special")
     polys = [r["coeffs"] for r in recs]
     with Context(device=0, mem_budget_bytes=16 << 30) as c:
         whole = c.factor_batch(polys)
-    ex = ThreadExchange(2, timeout=120)
-    out = [None, None]
-
-    def run(s):
-        with Context(device=0, mem_budget_bytes=16 << 30) as c:
-            out[s] = c.factor_batch_sharded(polys, s, 2, ex.gather_for(s))
-    th = [threading.Thread(target=run, args=(s,)) for s in range(2)]
-    for t in th:
-        t.start()
-    for t in th:
-        t.join(timeout=600)
+    out = _run_shards(polys, 2)
     for r, w, a, b in zip(recs, whole, out[0], out[1]):
         assert w.ok and a.ok and b.ok, r.get("name")
         assert a.factors == b.factors == w.factors == r["factors"]
@@ -239,25 +256,12 @@ def test_key_range_shards_with_table_redo():
     redone whole with the table match) plus a degree-100 golden, in two
     key-range shards: both shards return the cyclotomic factors and the
     golden, the same as the unsharded batch."""
-    import threading
     from oracle import canonical
-    from paper_2410_15880_b300 import Context
-    from paper_2410_15880_b300.sharding import ThreadExchange
     from test_oracle_pins import cyclotomic
     m = 60
     polys = [[-1] + [0] * (m - 1) + [1], golden("cfg3")[0]["coeffs"]]
     expect = [canonical([cyclotomic(k) for k in range(1, m + 1) if m % k == 0]), golden("cfg3")[0]["factors"]]
-    ex = ThreadExchange(2, timeout=120)
-    out = [None, None]
-
-    def run(s):
-        with Context(device=0, mem_budget_bytes=16 << 30) as c:
-            out[s] = c.factor_batch_sharded(polys, s, 2, ex.gather_for(s))
-    th = [threading.Thread(target=run, args=(s,)) for s in range(2)]
-    for t in th:
-        t.start()
-    for t in th:
-        t.join(timeout=600)
+    out = _run_shards(polys, 2)
     for s in range(2):
         assert [r.ok for r in out[s]] == [True, True], [r.status for r in out[s]]
         assert [r.factors for r in out[s]] == expect

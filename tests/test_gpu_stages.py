@@ -2,6 +2,7 @@
 
 K-a roots, K-b weights, K-c enumerate, K-c/K-d/K-e match and K-f verify, each
 on seeded inputs, element by element where the result is unique."""
+import functools
 import random
 
 import mpmath
@@ -206,6 +207,13 @@ def test_match_candidate_cap(P):
     assert ctr[2] == (1 << 9) - 1 and len(raw) == 10
 
 
+@functools.lru_cache(maxsize=4)
+def _scan(w, W):
+    """RECOMBINE_A's accepted patterns (the oracle), shared by the layouts."""
+    from oracle.recombine import recombine_a
+    return frozenset(recombine_a(list(w), M64, W))
+
+
 @pytest.mark.parametrize("layout", ["slack", "exact", "fused"])
 @pytest.mark.parametrize("seed,na,nb", [(11, 14, 15), (12, 16, 16), (13, 17, 18)])
 def test_match_several_tiles_against_scan(P, seed, na, nb, layout):
@@ -213,7 +221,6 @@ def test_match_several_tiles_against_scan(P, seed, na, nb, layout):
     with the slack-region layout, the exact (count pass) layout and the fused
     match (many key units, several runs per half)."""
     exact, fused = layout == "exact", layout == "fused"
-    from oracle.recombine import recombine_a
     rng = random.Random(seed)
     wa = [rng.randrange(M64) for _ in range(na)]
     wb = [rng.randrange(M64) for _ in range(nb)]
@@ -223,7 +230,7 @@ def test_match_several_tiles_against_scan(P, seed, na, nb, layout):
     W = 1 << 30
     got, ctr, _ = _run_match(P, wa, [0] * na, wb, [0] * nb, W, 0, exact=exact, fused=fused)
     assert ctr[4] == 0
-    scan = set(recombine_a(wa + wb + [0], M64, W)) - {0}
+    scan = _scan(tuple(wa + wb + [0]), W) - {0}
     exp = {(s & ((1 << na) - 1), s >> na) for s in scan}
     assert got == exp and len(exp) >= 2
 
