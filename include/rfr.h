@@ -273,6 +273,9 @@ int rfr_cancel(rfr_ctx* ctx, uint64_t ticket);
 /* Release the arrays of a result; safe on a zeroed or already freed struct. */
 void rfr_factors_free(rfr_factors* f);
 
+/* rfr_factors_free on each of f[0 .. count) (the results of one batch call). */
+void rfr_factors_free_n(rfr_factors* f, int count);
+
 /* Static English description of a status code. */
 const char* rfr_strerror(int status);
 

@@ -2,6 +2,7 @@
 from __future__ import annotations
 
 import ctypes as C
+import itertools
 import os
 from dataclasses import dataclass, field
 from typing import List, Optional, Sequence
@@ -107,6 +108,7 @@ def lib():
         "rfr_set_allocator": (i32, [vp, ALLOC_FN, FREE_FN, vp]),
         "rfr_factor": (i32, [vp, i64p, i32, C.POINTER(Factors)]),
         "rfr_factor_batch": (i32, [vp, i32, C.POINTER(i64p), C.POINTER(C.c_int), C.POINTER(Factors), C.POINTER(C.c_int)]),
+        "rfr_factors_free_n": (None, [C.POINTER(Factors), i32]),
         "rfr_factor_batch_device": (i32, [vp, i32, vp, vp, C.POINTER(Factors), C.POINTER(C.c_int)]),
         "rfr_factor_batch_sharded": (i32, [vp, i32, C.POINTER(i64p), C.POINTER(C.c_int), i32, i32, GATHER_FN, vp,
                                            C.POINTER(Factors), C.POINTER(C.c_int)]),
@@ -147,14 +149,21 @@ def lib():
 
 @dataclass
 class Result:
-    """One factorisation: canonical factor list plus diagnostics."""
+    """One factorisation: canonical factor list plus diagnostics (the diag
+    dict is built from the library's record when first read)."""
     status: int
     factors: List[List[int]] = field(default_factory=list)
-    diag: dict = field(default_factory=dict)
+    _diag: object = field(default=None, repr=False)
 
     @property
     def ok(self) -> bool:
         return self.status == RFR_OK
+
+    @property
+    def diag(self) -> dict:
+        if not isinstance(self._diag, dict):
+            self._diag = _diag_dict(self._diag) if self._diag is not None else {}
+        return self._diag
 
 
 _DIAG_FIELDS = [k for k, _ in Diag._fields_]
@@ -170,8 +179,8 @@ def _factor_lists(n: int, degrees, coeffs) -> List[List[int]]:
     """n factors stored one after the other (degrees[i] + 1 coefficients each)."""
     if n <= 0:
         return []
-    degs = np.ctypeslib.as_array(degrees, shape=(n,)).tolist()
-    co = np.ctypeslib.as_array(coeffs, shape=(sum(degs) + n,)).tolist()
+    degs = degrees[:n]                                   # pointer slices: lists of Python ints
+    co = coeffs[:sum(degs) + n]
     out, off = [], 0
     for e in degs:
         out.append(co[off:off + e + 1])
@@ -180,10 +189,23 @@ def _factor_lists(n: int, degrees, coeffs) -> List[List[int]]:
 
 
 def _to_result(status: int, f: Factors) -> Result:
-    res = Result(status=int(status), diag=_diag_dict(f.diag))
+    res = Result(status=int(status), _diag=Diag.from_buffer_copy(f.diag))
     if status == RFR_OK:
         res.factors = _factor_lists(f.n_factors, f.degrees, f.coeffs)
     lib().rfr_factors_free(C.byref(f))
+    return res
+
+
+def _to_results(n: int, sts, outs) -> List[Result]:
+    """The n results of a batch call; their arrays are released with one call."""
+    res = []
+    for i in range(n):
+        f, st = outs[i], sts[i]
+        r = Result(status=st, _diag=Diag.from_buffer_copy(f.diag))
+        if st == RFR_OK:
+            r.factors = _factor_lists(f.n_factors, f.degrees, f.coeffs)
+        res.append(r)
+    lib().rfr_factors_free_n(outs, n)
     return res
 
 
@@ -296,19 +318,33 @@ class Context:
         st = lib().rfr_factor_general(self._h, _coeff_array(coeffs), len(coeffs) - 1, C.byref(f))
         return _to_general(st, f)
 
-    def factor_batch(self, polys: Sequence[Sequence[int]]) -> List[Result]:
-        n = len(polys)
-        arrs = [_coeff_array(p) for p in polys]
-        ptrs = (C.POINTER(C.c_int64) * n)(*[C.cast(a, C.POINTER(C.c_int64)) for a in arrs])
-        degs = (C.c_int * n)(*[len(p) - 1 for p in polys])
+    def factor_batch(self, polys, degrees=None) -> List[Result]:
+        """polys: a sequence of ascending coefficient lists, or an int64 numpy
+        array [n, m] whose row i holds polynomial i (then degrees[i] gives its
+        degree).  The rows are passed to rfr_factor_batch in place."""
+        if len(polys) == 0:
+            return []
+        if isinstance(polys, np.ndarray):
+            arr = np.ascontiguousarray(polys, dtype=np.int64)
+            n = arr.shape[0]
+            degs = np.ascontiguousarray(degrees, dtype=np.int32)
+            addrs = (arr.ctypes.data + np.arange(n, dtype=np.uint64) * np.uint64(arr.strides[0])).astype(np.uint64)
+        else:                                   # all rows one after the other in one flat buffer
+            n = len(polys)
+            lens = np.fromiter(map(len, polys), dtype=np.int64, count=n)
+            degs = (lens - 1).astype(np.int32)
+            arr = np.fromiter(itertools.chain.from_iterable(polys), dtype=np.int64, count=int(lens.sum()))
+            starts = np.concatenate([np.zeros(1, dtype=np.int64), np.cumsum(lens)[:-1]]).astype(np.uint64)
+            addrs = (np.uint64(arr.ctypes.data) + starts[:n] * np.uint64(8)).astype(np.uint64)
+        ptrs = (C.POINTER(C.c_int64) * n).from_buffer(addrs)
+        degs_c = degs.ctypes.data_as(C.POINTER(C.c_int))
         outs = (Factors * n)()
         sts = (C.c_int * n)()
-        rc = lib().rfr_factor_batch(self._h, n, ptrs, degs, outs, sts)
+        rc = lib().rfr_factor_batch(self._h, n, ptrs, degs_c, outs, sts)
         if rc != RFR_OK:
-            for i in range(n):
-                lib().rfr_factors_free(C.byref(outs[i]))
+            lib().rfr_factors_free_n(outs, n)
             raise RFRError(rc, "rfr_factor_batch")
-        return [_to_result(sts[i], outs[i]) for i in range(n)]
+        return _to_results(n, sts, outs)
 
     def factor_batch_sharded(self, polys: Sequence[Sequence[int]], shard: int, nshards: int, gather) -> List[Result]:
         """This process's key-range shard of the batch (rfr_factor_batch_sharded).
@@ -339,7 +375,7 @@ class Context:
         rc = lib().rfr_factor_batch_sharded(self._h, n, ptrs, degs, int(shard), int(nshards), cb, None, outs, sts)
         if rc != RFR_OK:
             raise RFRError(rc, "rfr_factor_batch_sharded")
-        return [_to_result(sts[i], outs[i]) for i in range(n)]
+        return _to_results(n, sts, outs)
 
     def factor_batch_device(self, coeffs, degrees) -> List[Result]:
         """coeffs: int64 cuda tensor [count, 129] (ascending rows); degrees:
@@ -350,10 +386,9 @@ class Context:
         rc = lib().rfr_factor_batch_device(self._h, n, C.c_void_p(coeffs.data_ptr()),
                                            C.c_void_p(degrees.data_ptr()), outs, sts)
         if rc != RFR_OK:
-            for i in range(n):
-                lib().rfr_factors_free(C.byref(outs[i]))
+            lib().rfr_factors_free_n(outs, n)
             raise RFRError(rc, "rfr_factor_batch_device")
-        return [_to_result(sts[i], outs[i]) for i in range(n)]
+        return _to_results(n, sts, outs)
 
     def submit(self, coeffs) -> int:
         """Queue one polynomial (a sequence of ints, or an int64 ctypes array made

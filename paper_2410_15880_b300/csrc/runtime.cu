@@ -118,6 +118,20 @@ struct Pipeline {
     int64_t* h_coeffs = nullptr;      // pinned
     int32_t* h_deg = nullptr;         // pinned
     rfr_plan* h_plans = nullptr;      // pinned
+    char* h_stage = nullptr;          // pinned staging of counters, candidates and verify jobs
+    size_t h_stage_cap = 0;
+    // h_stage grown to at least `bytes` (null if pinned memory is short); the
+    // stream is idle whenever this is called, so the old buffer is unused
+    char* stage(size_t bytes) {
+        if (bytes <= h_stage_cap) return h_stage;
+        if (h_stage) cudaFreeHost(h_stage);
+        h_stage = nullptr;
+        h_stage_cap = 0;
+        const size_t nb = std::max(bytes, (size_t)1 << 20);
+        if (cudaMallocHost(&h_stage, nb) != cudaSuccess) { cudaGetLastError(); h_stage = nullptr; return nullptr; }
+        h_stage_cap = nb;
+        return h_stage;
+    }
     const int64_t* cur_coeffs = nullptr;   // coefficient rows of the running batch (device)
     const int32_t* cur_deg = nullptr;
     // captured prologue graphs (copy in, validate, roots, weights, plans out) per batch shape
@@ -212,6 +226,9 @@ void Pipeline::destroy() {
     if (h_coeffs) cudaFreeHost(h_coeffs);
     if (h_deg) cudaFreeHost(h_deg);
     if (h_plans) cudaFreeHost(h_plans);
+    if (h_stage) cudaFreeHost(h_stage);
+    h_stage = nullptr;
+    h_stage_cap = 0;
     for (auto& e : ev) if (e) cudaEventDestroy(e);
     if (s) cudaStreamDestroy(s);
     s = nullptr;
@@ -239,6 +256,32 @@ bool Pipeline::reserve(int n) {
     ok = ok && cudaMallocHost(&h_plans, (size_t)nc * sizeof(rfr_plan)) == cudaSuccess;
     cap = ok ? nc : 0;
     return ok;
+}
+
+// Candidates of a sub-batch's np problems into one buffer: problem i's
+// min(counters[8 i + 2], cap) patterns, from cand[i cap ..), land at
+// out[offs[i] ..); offs[np] = their total.  One block (the candidates are few);
+// nothing is copied when the total exceeds out_cap (the host then copies
+// problem by problem).
+__global__ void __launch_bounds__(256) k_compact_cands(const uint64_t* __restrict__ cand, uint64_t cap,
+                                                        const unsigned long long* __restrict__ ctr, int np,
+                                                        uint64_t* __restrict__ out, uint64_t out_cap,
+                                                        uint64_t* __restrict__ offs) {
+    if (threadIdx.x == 0) {
+        uint64_t o = 0;
+        for (int i = 0; i < np; ++i) {
+            offs[i] = o;
+            const uint64_t n = ctr[8 * i + 2];
+            o += n < cap ? n : cap;
+        }
+        offs[np] = o;
+    }
+    __syncthreads();
+    if (offs[np] > out_cap) return;
+    for (int i = 0; i < np; ++i) {
+        const uint64_t o = offs[i], n = offs[i + 1] - o;
+        for (uint64_t j = threadIdx.x; j < n; j += blockDim.x) out[o + j] = cand[(uint64_t)i * cap + j];
+    }
 }
 
 static double ms_between(cudaEvent_t a, cudaEvent_t b) {
@@ -492,48 +535,75 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
         }
         if (!small.empty()) {
             const int ns = (int)small.size();
-            const size_t per = (((size_t)cap * 8 + 255) & ~(size_t)255) + 256;
-            const size_t bytes = (size_t)ns * per + (((size_t)ns * sizeof(SmallJob)) + 255 & ~(size_t)255);
+            auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+            const uint64_t out_cap = std::min<uint64_t>((uint64_t)ns * cap, 1ull << 18);
+            const size_t cb = (size_t)ns * 64 + ((size_t)ns + 1) * 8;      // counters [ns][8], offsets [ns + 1]
+            const size_t bytes = a256((size_t)ns * sizeof(SmallJob)) + a256(cb) + a256((size_t)ns * cap * 8) +
+                                 a256((size_t)out_cap * 8);
             char* ws = (char*)C.alloc.get(bytes, s);
             if (!ws) return RFR_E_OOM;
-            SmallJob* d_sj = (SmallJob*)ws;
-            char* p = ws + ((((size_t)ns * sizeof(SmallJob)) + 255) & ~(size_t)255);
+            char* p = ws;
+            SmallJob* d_sj = (SmallJob*)p; p += a256((size_t)ns * sizeof(SmallJob));
+            unsigned long long* d_ctrs = (unsigned long long*)p; p += a256(cb);
+            uint64_t* d_offs = (uint64_t*)(d_ctrs + 8 * (size_t)ns);
+            uint64_t* d_cands = (uint64_t*)p; p += a256((size_t)ns * cap * 8);
+            uint64_t* d_compact = (uint64_t*)p;
+            cudaMemsetAsync(d_ctrs, 0, (size_t)ns * 64, s);
             std::vector<SmallJob> sj(ns);
-            std::vector<uint64_t*> ctrs(ns), cands(ns);
             for (int i = 0; i < ns; ++i) {
                 Work& w = work[small[i]];
                 const rfr_plan* dp = d_plans + w.slot;
-                cands[i] = (uint64_t*)p; p += ((size_t)cap * 8 + 255) & ~(size_t)255;
-                ctrs[i] = (uint64_t*)p; p += 256;
                 sj[i].w_a = dp->w; sj[i].w2_a = dp->w2;
                 sj[i].w_b = dp->w + w.plan.n_a; sj[i].w2_b = dp->w2 + w.plan.n_a;
                 sj[i].n_a = w.plan.n_a; sj[i].n_b = w.plan.n_b;
                 sj[i].W = w.plan.window; sj[i].W2 = w.plan.window2;
-                sj[i].cand = cands[i]; sj[i].cap = cap; sj[i].ctr = (unsigned long long*)ctrs[i];
-                cudaMemsetAsync(ctrs[i], 0, 6 * 8, s);
+                sj[i].cand = d_cands + (size_t)i * cap; sj[i].cap = cap; sj[i].ctr = d_ctrs + 8 * (size_t)i;
             }
             h2d += (uint64_t)ns * sizeof(SmallJob);
             cudaEventRecord(ev[5], s);
             rc = cuda_ok(run_small(sj.data(), ns, d_sj, s));
             launches += 1;
+            if (rc == RFR_OK) {
+                k_compact_cands<<<1, 256, 0, s>>>(d_cands, cap, d_ctrs, ns, d_compact, out_cap, d_offs);
+                rc = cuda_ok(cudaGetLastError());
+                launches += 1;
+            }
             cudaEventRecord(ev[6], s);
-            std::vector<uint64_t> h_ctr(6 * (size_t)ns);
-            for (int i = 0; i < ns && rc == RFR_OK; ++i)
-                rc = cuda_ok(cudaMemcpyAsync(&h_ctr[6 * i], ctrs[i], 6 * 8, cudaMemcpyDeviceToHost, s));
-            d2h += 48ull * ns;
+            std::vector<uint64_t> h_ctr(cb / 8);
+            char* hs = stage(cb);
+            if (rc == RFR_OK) rc = cuda_ok(cudaMemcpyAsync(hs ? (void*)hs : (void*)h_ctr.data(), d_ctrs, cb, cudaMemcpyDeviceToHost, s));
+            d2h += cb;
             if (rc == RFR_OK) rc = cuda_ok(cudaStreamSynchronize(s));
+            if (rc == RFR_OK && hs) memcpy(h_ctr.data(), hs, cb);
             if (timing && rc == RFR_OK) t_match += ms_between(ev[5], ev[6]);
+            const uint64_t* h_offs = h_ctr.data() + 8 * (size_t)ns;
+            const uint64_t total = rc == RFR_OK ? h_offs[ns] : 0;
+            const bool compacted = total <= out_cap;
+            char* hc = nullptr;
+            if (rc == RFR_OK && compacted && total) {
+                hc = stage((size_t)total * 8);
+                rc = hc ? cuda_ok(cudaMemcpyAsync(hc, d_compact, total * 8, cudaMemcpyDeviceToHost, s)) : RFR_E_OOM;
+                d2h += total * 8;
+                if (rc == RFR_OK) rc = cuda_ok(cudaStreamSynchronize(s));
+            }
             for (int i = 0; i < ns && rc == RFR_OK; ++i) {
                 Work& w = work[small[i]];
-                memcpy(w.ctr, &h_ctr[6 * i], sizeof(w.ctr));
+                memcpy(w.ctr, &h_ctr[8 * (size_t)i], sizeof(w.ctr));
                 if (w.ctr[3] == 0 && shard.index == 0) { w.status = RFR_E_INTERNAL; continue; }
                 if (w.ctr[2] > cap) { w.status = RFR_E_CAND_OVERFLOW; continue; }
                 w.cand.resize(w.ctr[2]);
-                if (w.ctr[2]) rc = cuda_ok(cudaMemcpyAsync(w.cand.data(), cands[i], w.ctr[2] * 8, cudaMemcpyDeviceToHost, s));
-                d2h += w.ctr[2] * 8;
+                if (w.ctr[2]) {
+                    if (compacted) {
+                        memcpy(w.cand.data(), hc + h_offs[i] * 8, w.ctr[2] * 8);
+                    } else {
+                        rc = cuda_ok(cudaMemcpyAsync(w.cand.data(), d_cands + (size_t)i * cap, w.ctr[2] * 8,
+                                                     cudaMemcpyDeviceToHost, s));
+                        d2h += w.ctr[2] * 8;
+                    }
+                }
                 w.matched = true;
             }
-            if (rc == RFR_OK) rc = cuda_ok(cudaStreamSynchronize(s));
+            if (rc == RFR_OK && !compacted) rc = cuda_ok(cudaStreamSynchronize(s));
             C.alloc.put(ws, bytes, s);
             if (rc != RFR_OK) return rc;
         }
@@ -587,7 +657,10 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
         if (sub.empty()) continue;
         if (!C.reserve(bytes)) { for (int sl : sub) work[sl].status = RFR_E_BUDGET; continue; }
         const int np = (int)sub.size();
-        const size_t jobs_bytes = (size_t)np * sizeof(ProbJob) + 2 * (size_t)np * sizeof(HalfJob) + 1024;
+        // candidates of all problems are compacted into one buffer before they come back
+        const uint64_t out_cap = std::min<uint64_t>((uint64_t)np * cap, 1ull << 18);
+        const size_t jobs_bytes = (size_t)np * sizeof(ProbJob) + 2 * (size_t)np * sizeof(HalfJob) +
+                                  (((size_t)out_cap * 8 + 255) & ~(size_t)255) + 2048;
         char* ws = (char*)C.alloc.get(bytes + jobs_bytes, s);
         if (!ws) {
             C.release(bytes);
@@ -603,16 +676,23 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
         std::vector<ProbJob> jobs(np);
         std::vector<HalfJob> halves(2 * np);
         char* p = ws;
-        ProbJob* d_jobs = (ProbJob*)p; p += ((np * sizeof(ProbJob)) + 255) & ~(size_t)255;
-        HalfJob* d_halves = (HalfJob*)p; p += ((2 * np * sizeof(HalfJob)) + 255) & ~(size_t)255;
+        auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+        ProbJob* d_jobs = (ProbJob*)p; p += a256(np * sizeof(ProbJob));
+        HalfJob* d_halves = (HalfJob*)p; p += a256(2 * np * sizeof(HalfJob));
+        // counters [np][8] and the compacted candidates' offsets [np + 1], copied back together
+        unsigned long long* d_ctrs = (unsigned long long*)p; p += a256((size_t)np * 64 + ((size_t)np + 1) * 8);
+        uint64_t* d_offs = (uint64_t*)(d_ctrs + 8 * (size_t)np);
+        uint64_t* d_cands = (uint64_t*)p; p += a256((size_t)np * cap * 8);     // [np][cap]
+        uint64_t* d_compact = (uint64_t*)p; p += a256((size_t)out_cap * 8);
+        cudaMemsetAsync(d_ctrs, 0, (size_t)np * 64, s);
         for (int i = 0; i < np; ++i) {
             Work& w = work[sub[i]];
             ProbJob& pj = jobs[i];
             memset(&pj, 0, sizeof(pj));
             match_layout(w.geom, p, &pj);
             p += w.geom.bytes;
-            uint64_t* cbuf = (uint64_t*)p; p += ((size_t)cap * 8 + 255) & ~(size_t)255;
-            uint64_t* ctr = (uint64_t*)p; p += 256;
+            uint64_t* cbuf = d_cands + (size_t)i * cap;
+            uint64_t* ctr = (uint64_t*)(d_ctrs + 8 * (size_t)i);
             const rfr_plan* dp = d_plans + w.slot;
             pj.A.w = dp->w;                     pj.B.w = dp->w + w.plan.n_a;
             pj.w_a = dp->w;                     pj.w2_a = dp->w2;
@@ -622,7 +702,6 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
             pj.cand = cbuf;                     pj.cap = cap;
             pj.ctr = (unsigned long long*)ctr;
             pj.A.err = pj.B.err = (int*)(ctr + 4);
-            cudaMemsetAsync(ctr, 0, 8 * 8, s);
             if (w.geom.fused || w.geom.splat || w.geom.prune)
                 ;                                       // no tables (the splat arrays are filled by run_splat)
             else if (w.geom.optimistic)
@@ -635,30 +714,55 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
         int nl = 0;
         rc = cuda_ok(run_match(jobs.data(), np, d_jobs, d_halves, halves.data(), s, ev[4], ev[5], &nl));
         launches += (uint32_t)nl;
+        if (rc == RFR_OK) {
+            k_compact_cands<<<1, 256, 0, s>>>(d_cands, cap, d_ctrs, np, d_compact, out_cap, d_offs);
+            rc = cuda_ok(cudaGetLastError());
+            launches += 1;
+        }
         cudaEventRecord(ev[6], s);
-        std::vector<uint64_t> h_ctr(6 * (size_t)np);
-        for (int i = 0; i < np && rc == RFR_OK; ++i)
-            rc = cuda_ok(cudaMemcpyAsync(&h_ctr[6 * i], jobs[i].ctr, 6 * 8, cudaMemcpyDeviceToHost, s));
-        d2h += 48ull * np;
+        // counters and offsets in one copy (pinned staging when available)
+        const size_t cb = (size_t)np * 64 + ((size_t)np + 1) * 8;
+        std::vector<uint64_t> h_ctr(cb / 8);
+        char* hs = stage(cb);
+        if (rc == RFR_OK) rc = cuda_ok(cudaMemcpyAsync(hs ? (void*)hs : (void*)h_ctr.data(), d_ctrs, cb, cudaMemcpyDeviceToHost, s));
+        d2h += cb;
         if (rc == RFR_OK) rc = cuda_ok(cudaStreamSynchronize(s));
+        if (rc == RFR_OK && hs) memcpy(h_ctr.data(), hs, cb);
+        const uint64_t* h_offs = h_ctr.data() + 8 * (size_t)np;
+        const uint64_t total = rc == RFR_OK ? h_offs[np] : 0;
+        const bool compacted = total <= out_cap;
         if (timing && rc == RFR_OK) {
             t_count += ms_between(ev[3], ev[4]);
             t_scatter += ms_between(ev[4], ev[5]);
             t_match += ms_between(ev[5], ev[6]);
         }
+        // all candidates in one copy when they were compacted, else problem by problem
+        char* hc = nullptr;
+        if (rc == RFR_OK && compacted && total) {
+            hc = stage((size_t)total * 8);
+            rc = hc ? cuda_ok(cudaMemcpyAsync(hc, d_compact, total * 8, cudaMemcpyDeviceToHost, s)) : RFR_E_OOM;
+            d2h += total * 8;
+            if (rc == RFR_OK) rc = cuda_ok(cudaStreamSynchronize(s));
+        }
         for (int i = 0; i < np && rc == RFR_OK; ++i) {
             Work& w = work[sub[i]];
-            memcpy(w.ctr, &h_ctr[6 * i], sizeof(w.ctr));
+            memcpy(w.ctr, &h_ctr[8 * (size_t)i], sizeof(w.ctr));
             if (w.ctr[4]) { w.full_halo = true; todo.push_back(w.slot); continue; }   // retry with a full halo
             // the empty pattern must match (in the shard that holds key 0, or on a full redo)
             if (w.ctr[3] == 0 && (shard.index == 0 || !w.geom.fused)) { w.status = RFR_E_INTERNAL; continue; }
             if (w.ctr[2] > cap) { w.status = RFR_E_CAND_OVERFLOW; continue; }
             w.cand.resize(w.ctr[2]);
-            if (w.ctr[2]) rc = cuda_ok(cudaMemcpyAsync(w.cand.data(), jobs[i].cand, w.ctr[2] * 8, cudaMemcpyDeviceToHost, s));
-            d2h += w.ctr[2] * 8;
+            if (w.ctr[2]) {
+                if (compacted) {
+                    memcpy(w.cand.data(), hc + h_offs[i] * 8, w.ctr[2] * 8);
+                } else {
+                    rc = cuda_ok(cudaMemcpyAsync(w.cand.data(), jobs[i].cand, w.ctr[2] * 8, cudaMemcpyDeviceToHost, s));
+                    d2h += w.ctr[2] * 8;
+                }
+            }
             w.matched = true;
         }
-        if (rc == RFR_OK) rc = cuda_ok(cudaStreamSynchronize(s));
+        if (rc == RFR_OK && !compacted) rc = cuda_ok(cudaStreamSynchronize(s));
         C.alloc.put(ws, bytes + jobs_bytes, s);
         C.release(bytes);
         if (rc != RFR_OK) return rc;
@@ -673,25 +777,45 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
         const size_t bytes = (size_t)J * (4 + 8 + 8 + 4) + (coeffs_out ? (size_t)J * LDC * 8 : 0) + 1024;
         char* buf = (char*)C.alloc.get(bytes, s);
         if (!buf) return RFR_E_OOM;
+        // jobs: [prob J x 4][pad to 16][lo J x 8][hi J x 8], one copy from pinned staging
+        const size_t off_lo = (((size_t)J * 4) + 15) & ~(size_t)15, in_bytes = off_lo + (size_t)J * 16;
         int32_t* dp = (int32_t*)buf;
-        uint64_t* dlo = (uint64_t*)(((uintptr_t)(dp + J) + 15) & ~(uintptr_t)15);
+        uint64_t* dlo = (uint64_t*)(buf + off_lo);
         uint64_t* dhi = dlo + J;
         int32_t* dres = (int32_t*)(dhi + J);
         int64_t* dco = coeffs_out ? (int64_t*)(((uintptr_t)(dres + J) + 15) & ~(uintptr_t)15) : nullptr;
-        int r = cuda_ok(cudaMemcpyAsync(dp, jp.data(), J * 4, cudaMemcpyHostToDevice, s));
-        if (r == RFR_OK) r = cuda_ok(cudaMemcpyAsync(dlo, jlo.data(), J * 8, cudaMemcpyHostToDevice, s));
-        if (r == RFR_OK) r = cuda_ok(cudaMemcpyAsync(dhi, jhi.data(), J * 8, cudaMemcpyHostToDevice, s));
+        const size_t out_bytes = (size_t)J * 4 + (coeffs_out ? (size_t)J * LDC * 8 : 0);
+        char* hs = stage(std::max(in_bytes, out_bytes));
+        int r = RFR_OK;
+        if (hs) {
+            memcpy(hs, jp.data(), (size_t)J * 4);
+            memcpy(hs + off_lo, jlo.data(), (size_t)J * 8);
+            memcpy(hs + off_lo + (size_t)J * 8, jhi.data(), (size_t)J * 8);
+            r = cuda_ok(cudaMemcpyAsync(buf, hs, in_bytes, cudaMemcpyHostToDevice, s));
+        } else {
+            r = cuda_ok(cudaMemcpyAsync(dp, jp.data(), J * 4, cudaMemcpyHostToDevice, s));
+            if (r == RFR_OK) r = cuda_ok(cudaMemcpyAsync(dlo, jlo.data(), J * 8, cudaMemcpyHostToDevice, s));
+            if (r == RFR_OK) r = cuda_ok(cudaMemcpyAsync(dhi, jhi.data(), J * 8, cudaMemcpyHostToDevice, s));
+        }
         h2d += (uint64_t)J * 20;
         if (r == RFR_OK) r = rfr_stage_verify(d_co, d_dg, d_roots, d_plans, dp, dlo, dhi, J, dres, dco, s);
         launches += 1;
-        if (r == RFR_OK) r = cuda_ok(cudaMemcpyAsync(res.data(), dres, J * 4, cudaMemcpyDeviceToHost, s));
+        // results (and coefficients) back through the same staging: the copy in is
+        // ordered before them on the stream
+        char* ho = hs;
+        if (r == RFR_OK) r = cuda_ok(cudaMemcpyAsync(ho ? (void*)ho : (void*)res.data(), dres, J * 4, cudaMemcpyDeviceToHost, s));
         d2h += (uint64_t)J * 4;
         if (r == RFR_OK && coeffs_out) {
             coeffs_out->resize((size_t)J * LDC);
-            r = cuda_ok(cudaMemcpyAsync(coeffs_out->data(), dco, (size_t)J * LDC * 8, cudaMemcpyDeviceToHost, s));
+            r = cuda_ok(cudaMemcpyAsync(ho ? (void*)(ho + (size_t)J * 4) : (void*)coeffs_out->data(), dco,
+                                        (size_t)J * LDC * 8, cudaMemcpyDeviceToHost, s));
             d2h += (uint64_t)J * LDC * 8;
         }
         if (r == RFR_OK) r = cuda_ok(cudaStreamSynchronize(s));
+        if (r == RFR_OK && ho) {
+            memcpy(res.data(), ho, (size_t)J * 4);
+            if (coeffs_out) memcpy(coeffs_out->data(), ho + (size_t)J * 4, (size_t)J * LDC * 8);
+        }
         C.alloc.put(buf, bytes, s);
         return r;
     };
@@ -1156,6 +1280,11 @@ void rfr_factors_free(rfr_factors* f) {
     f->degrees = nullptr;
     f->coeffs = nullptr;
     f->n_factors = 0;
+}
+
+void rfr_factors_free_n(rfr_factors* f, int count) {
+    if (!f) return;
+    for (int i = 0; i < count; ++i) rfr_factors_free(&f[i]);
 }
 
 }  // extern "C"
