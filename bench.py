@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--tune-cache", default="", help="file that stores tuned match layouts")
     ap.add_argument("--degree120-steps", type=int, default=5,
                     help="timed steps of the degree-120 sub-measurement (0 = skip it)")
+    ap.add_argument("--shard", action="store_true",
+                    help="key-range sharding of one batch over the ranks (rfr_factor_batch_sharded; the "
+                         "degree-120 workload unless --config names another) instead of replicas")
     return ap.parse_args()
 
 
@@ -380,6 +383,72 @@ def degree120_leg(ctx, flush, steps, warmup=2):
             "matches_golden": (gold is not None and res[0].ok and res[0].factors == gold)}
 
 
+def sharded_leg(ctx, polys, rank, world, steps, warmup, gather, golden=None, sync=None, barrier=None):
+    """Key-range shard `rank` of `world` of one batch: every rank factors the
+    same polynomials, its fused matches searching only its share of the key
+    units, and the verified divisor sets of all shards meet through `gather`
+    before the atoms, so every rank returns the whole factorisation.  The
+    steps are bracketed by `sync` (the device) and `barrier` (the ranks); the
+    time is the max over ranks.  Returns (ms per step, last results, every
+    result equal to `golden`)."""
+    sync = sync or (lambda: None)
+    barrier = barrier or (lambda: None)
+    for _ in range(warmup):
+        ctx.factor_batch_sharded(polys, rank, world, gather)
+    sync()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        res = ctx.factor_batch_sharded(polys, rank, world, gather)
+    sync()
+    barrier()
+    ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / steps, world)
+    ok = golden is not None and all(r.ok and r.factors == g for r, g in zip(res, golden))
+    return ms, res, ok
+
+
+def run_sharded(a):
+    """`--shard`: one batch split by key range over the ranks (strong scaling),
+    the exchange through torch.distributed's all-gather, checked on every rank
+    against the golden factor lists."""
+    import torch
+    import torch.distributed as dist
+    from paper_2410_15880_b300 import Context
+    from paper_2410_15880_b300.sharding import torch_gather
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    cfg = a.config if a.config != "cfg3" else "cfg5"
+    insts = workload(cfg, 0, a.count)                       # the same batch on every rank
+    polys = [inst.coeffs for inst in insts]
+    gpath = os.path.join(ROOT, "tests", "golden", f"{cfg}.json")
+    golden = [g["factors"] for g in json.load(open(gpath))][:len(polys)] if os.path.exists(gpath) else None
+    gather = torch_gather() if world > 1 else None                 # one shard: no exchange
+    with Context(device=local) as ctx:
+        ms, res, ok = sharded_leg(ctx, polys, rank, world, a.steps, a.warmup, gather, golden,
+                                  sync=torch.cuda.synchronize, barrier=(dist.barrier if world > 1 else None))
+    oks = [ok]
+    if world > 1:
+        oks = [None] * world
+        dist.all_gather_object(oks, ok)
+    if rank == 0:
+        half_sums = sum(r.diag["half_sums"] for r in res)
+        print(json.dumps({
+            "metric": f"polynomials factored/sec, one batch key-range sharded over {world} GPU(s)",
+            "value": len(polys) / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "int64+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME[cfg], "polys_per_step": len(polys), "half_sums_per_step": half_sums,
+                       "parallelism": f"key-range shards x{world}", "exchange": "torch.distributed all_gather_object"},
+            "half_sums_per_s": half_sums / (ms / 1e3),
+            "correct": {"matches_golden_every_rank": all(oks)}}), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def max_over_ranks(value: float, world: int) -> float:
     """Max of a per-rank time over all ranks (the slowest replica sets the
     step time).  Uses a CUDA tensor under NCCL, a CPU tensor under gloo."""
@@ -423,6 +492,8 @@ def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.shard:
+        return run_sharded(a)
     import numpy as np
     import torch
     import torch.distributed as dist

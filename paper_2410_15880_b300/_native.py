@@ -349,7 +349,10 @@ class Context:
     def factor_batch_sharded(self, polys: Sequence[Sequence[int]], shard: int, nshards: int, gather) -> List[Result]:
         """This process's key-range shard of the batch (rfr_factor_batch_sharded).
         gather(list of (item, lo, hi)) -> every shard's triples, e.g.
-        sharding.torch_gather()."""
+        sharding.torch_gather(); None with one shard."""
+        if gather is None:
+            gather = list
+
         def _cb(mine, n_mine, all_pp, n_all_p, user):
             try:
                 triples = [(int(mine[3 * i]), int(mine[3 * i + 1]), int(mine[3 * i + 2])) for i in range(n_mine)]
@@ -374,6 +377,7 @@ class Context:
         sts = (C.c_int * n)()
         rc = lib().rfr_factor_batch_sharded(self._h, n, ptrs, degs, int(shard), int(nshards), cb, None, outs, sts)
         if rc != RFR_OK:
+            lib().rfr_factors_free_n(outs, n)
             raise RFRError(rc, "rfr_factor_batch_sharded")
         return _to_results(n, sts, outs)
 

@@ -68,3 +68,23 @@ def test_rejects_bad_arguments(hs):
         hs.hs_mt_match([1] * 33, [0] * 33, [1], [0], 10, 0)
     with pytest.raises(ValueError):
         hs.hs_mt_match([1], [0], [1], [0], 1 << 63, 0)
+
+
+@pytest.mark.parametrize("n_a,n_b,logW,threads", [(16, 16, 30, 3), (17, 18, 36, 8), (20, 21, 24, 16)])
+def test_runs_design_against_sorted_mitm(hs, n_a, n_b, logW, threads):
+    """Halves of 16 elements and more take the runs design (sorted low lists,
+    runs, key units, binned half a): its pair set is the oracle's, with pairs
+    planted across the circular wrap and integral subsets."""
+    rng = random.Random(n_a * 7 + n_b)
+    wa = [rng.randrange(M64) for _ in range(n_a)]
+    wb = [rng.randrange(M64) for _ in range(n_b)]
+    wa[0], wb[0] = M64 - 3, M64 - 2                    # K_a = 2^64 - 3 meets K_b = 2 (over the wrap)
+    wa[1], wb[1] = 3, 2
+    wb[5] = (-(wa[4] + wa[7] + wb[9])) % M64
+    wa[n_a - 1] = (-(wb[n_b - 1] + wb[12])) % M64     # a high element of each half
+    W = 1 << logW
+    exp = band_pairs_sorted(wa, wb, W)
+    cands, counts, secs = hs.hs_mt_match(wa, [0] * n_a, wb, [0] * n_b, W, 0, threads=threads, cap=1 << 20)
+    assert secs[1] == 0.0                              # no sort: the runs design ran
+    assert counts[0] == len(exp) and counts[2] == 1
+    assert _pairs(cands, n_a) == exp - {(0, 0)}
