@@ -342,8 +342,9 @@ def cpu_mt_sample(d_co, d_dg, root_mode, budget_s=15.0, max_polys=8):
     dt = time.perf_counter() - t0
     return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "horowitz-sahni-mt",
             "half_sums_per_s": hs / dt, "candidates": cands,
-            "sample": f"match stage only (enumerate, LSD radix sort, band join, Tr2 test; C++ std::thread) of "
-                      f"the first {done} polynomials ({dt:.1f} s), weights from the GPU path's weights stage"}
+            "sample": f"match stage only (sorted low lists by merging, runs, key units with a binned half a and "
+                      f"an occupancy bitmap, Tr2 test; C++ std::thread) of the first {done} polynomials ({dt:.1f} s), "
+                      f"weights from the GPU path's weights stage"}
 
 
 def degree120_leg(ctx, flush, steps, warmup=2):
