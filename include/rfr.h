@@ -85,7 +85,7 @@ typedef struct {
     const char* tune_cache_path;/* NULL, or a text file that stores tuned layouts across runs (read at
                                    create, appended when a class is tuned); the string is copied */
     int      match_path;        /* RFR_MATCH_AUTO: halves of n_b <= 13 in one shared-memory kernel,
-                                   14 <= n_a <= n_b <= 31 by the fused match, the rest by the table
+                                   14 <= n_a <= n_b <= 32 by the fused match, the rest by the table
                                    match; RFR_MATCH_TABLES: every problem with n_b > 13 by the
                                    table match with the count-pass layout; RFR_MATCH_SPLAT: every
                                    problem with 13 < n_b <= 30 by the splat match (Section 4,
