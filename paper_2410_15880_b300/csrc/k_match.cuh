@@ -67,11 +67,11 @@ struct HalfJob {
     uint32_t* hcount;       // [NB] (half b)
     // fused match (k_mitm): ylist holds the exact low-subset sums, ascending;
     // list-building buffers: ytmp is the first key buffer
-    uint64_t* kb1;          // [2^(l-1)] second key buffer (l > 12)
-    uint32_t* ysplit;       // merge-path tile starts of one level (l > 12)
+    uint64_t* kb1;          // [2^(l-1)] second key buffer (l > 13)
+    uint32_t* ysplit;       // merge-path tile starts of one level (l > 13)
     uint32_t* ymask;        // [2^l] low-subset mask of each list entry
     uint32_t* ydir;         // [2^l + 1] directory: first entry >= q * 2^(64-l)
-    uint32_t* ymtmp[2];     // [2^(l-1)] mask buffers of the levels (l > 12)
+    uint32_t* ymtmp[2];     // [2^(l-1)] mask buffers of the levels (l > 13)
     uint32_t* y32;          // [2^l] fused match: bits fsh .. fsh+31 of each list entry
 };
 

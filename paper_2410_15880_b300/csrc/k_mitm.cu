@@ -43,9 +43,9 @@
 namespace rfr {
 namespace {
 
-constexpr int YS_LOG = 12;                                     // list levels built in shared memory
+constexpr int YS_LOG = 13;                                     // list levels built in shared memory
 constexpr int YS_THREADS = 1024;
-constexpr size_t YS_SMEM = ((size_t)2 << YS_LOG) * (8 + 4);    // two (key, mask) buffers of 2^12 entries
+constexpr size_t YS_SMEM = ((size_t)2 << YS_LOG) * (8 + 4);    // two (key, mask) buffers of 2^13 entries
 constexpr int YM_THREADS = 256;
 constexpr int YM_PER = 8;                                      // merge outputs per thread (2048-output tiles)
 constexpr int L_MAX = 25;                                      // list bits (2^7 runs of a 32-element half)
@@ -127,7 +127,7 @@ struct YJob {
     uint32_t* splits;           // [2^l / YM_TILE + 2]: a level's tile starts on the merge path, then its rotation
 };
 
-// Levels 0 .. min(l, 12) - 1 of one half's list in shared memory.
+// Levels 0 .. min(l, 13) - 1 of one half's list in shared memory.
 __global__ void __launch_bounds__(YS_THREADS) k_ybuild_smem(const YJob* __restrict__ js) {
     extern __shared__ __align__(16) uint64_t ys_sm[];
     uint64_t* Kb[2] = {ys_sm, ys_sm + (1 << YS_LOG)};
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(YS_THREADS) k_ybuild_smem(const YJob* __restri
     for (uint32_t j = threadIdx.x; j < (1u << s); j += blockDim.x) { out[j] = K[j]; mout[j] = M[j]; }
 }
 
-// Level i >= 12 (2^i entries -> 2^(i+1)) for every half with l > i; cpl CTAs per
+// Level i >= 13 (2^i entries -> 2^(i+1)) for every half with l > i; cpl CTAs per
 // half, each writing a tile of YM_TILE outputs.  The CTA finds where its tile
 // starts and ends on the merge path (precomputed by k_ysplit), reads the two
 // input stretches into shared memory with coalesced loads, merges them there
@@ -242,7 +242,28 @@ __global__ void __launch_bounds__(YM_THREADS) k_ymerge(const YJob* __restrict__ 
     const bool last = i == J.l - 1;
     uint64_t* KO = last ? J.ylist : J.kb[p ^ 1];
     uint32_t* MO = last ? J.ymask : J.mb[p ^ 1];
-    for (uint32_t j = threadIdx.x; j < (uint32_t)YM_TILE; j += blockDim.x) { KO[o0 + j] = tout[j]; MO[o0 + j] = mout[j]; }
+    if (!(last && J.ydir)) {
+        for (uint32_t j = threadIdx.x; j < (uint32_t)YM_TILE; j += blockDim.x) { KO[o0 + j] = tout[j]; MO[o0 + j] = mout[j]; }
+        return;
+    }
+    // the last level also writes the list's directory and positions (as k_ydir does):
+    // D[q] = j for every q in (Y[j-1] >> (64-l), Y[j] >> (64-l)], the entry before the
+    // tile being the larger of the two inputs' last entries taken before it
+    const int sh = 64 - J.l;
+    const uint32_t N = 2u * n;
+    const uint64_t pa = a0 ? K[a0 - 1] : 0ull, pb = b0 ? K[(r + b0 - 1) & nm] + cs : 0ull;
+    const uint64_t prev = !a0 ? pb : (!b0 ? pa : (pa > pb ? pa : pb));
+    for (uint32_t j = threadIdx.x; j < (uint32_t)YM_TILE; j += blockDim.x) {
+        const uint32_t d = o0 + j;
+        const uint64_t v = tout[j];
+        KO[d] = v;
+        MO[d] = mout[j];
+        J.y32[d] = (uint32_t)(v >> J.fsh);
+        const uint64_t qp = d ? ((j ? tout[j - 1] : prev) >> sh) + 1 : 0ull;
+        for (uint64_t q = qp; q <= (v >> sh); ++q) J.ydir[q] = d;
+        if (d == N - 1)
+            for (uint64_t q = (v >> sh) + 1; q <= N; ++q) J.ydir[q] = N;
+    }
 }
 
 // Directory of each finished list: D[q] = the first index j with Y[j] >= q 2^(64-l),
@@ -251,7 +272,7 @@ __global__ void __launch_bounds__(YM_THREADS) k_ymerge(const YJob* __restrict__ 
 // grid: blockIdx.y = half.
 __global__ void __launch_bounds__(256) k_ydir(const YJob* __restrict__ js) {
     const YJob& J = js[blockIdx.y];
-    if (!J.ydir || J.l < 1) return;
+    if (!J.ydir || J.l < 1 || J.l > YS_LOG) return;           // longer lists: the last merge level wrote it
     const uint32_t N = 1u << J.l;
     const int s = 64 - J.l;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j <= N; j += gridDim.x * blockDim.x) {
@@ -625,10 +646,12 @@ void build_lists(const YJob* yj, int nh, YJob* d_yj, cudaStream_t s) {
         k_ysplit<<<(nhi * (cpl + 1) + 127) / 128, 128, 0, s>>>(d_yj, nhi, i, cpl);
         k_ymerge<<<nhi * cpl, YM_THREADS, YM_SMEM, s>>>(d_yj, i, cpl);
     }
-    bool dir = false;
-    for (int h = 0; h < nh; ++h) dir = dir || yj[h].ydir;
+    bool dir = false;                                          // lists finished in shared memory
+    int lmax_small = 0;
+    for (int h = 0; h < nh; ++h)
+        if (yj[h].ydir && yj[h].l <= YS_LOG) { dir = true; lmax_small = std::max(lmax_small, yj[h].l); }
     if (dir) {
-        const int bx = (int)std::min<uint64_t>(((1ull << yj[0].l) + 1 + 255) / 256, 4096);
+        const int bx = (int)std::min<uint64_t>(((1ull << lmax_small) + 1 + 255) / 256, 4096);
         k_ydir<<<dim3(bx, nh), 256, 0, s>>>(d_yj);
     }
 }
