@@ -57,7 +57,7 @@ constexpr int MT_THREADS = RFR_MT_THREADS;
 constexpr int MT_WARPS = MT_THREADS / 32;
 constexpr int MT_UNIT_LOG = 14;                                // table-a keys of one unit: 2^14 on average
 constexpr int MT_CAP = 24576;                                  // table slots (1.5 x the mean)
-constexpr int MT_NBL = 12;                                     // at most 2^12 bins per unit
+constexpr int MT_NBL = 13;                                     // at most 2^13 bins per unit (2 keys per bin)
 constexpr int MT_HEADS = (1 << MT_NBL) + 4;                    // bins 0 .. 2^nbl (positions carry an offset)
 constexpr int MT_RUNS = 128;                                   // at most 128 runs per half
 constexpr int MT_RPW = MT_RUNS / MT_WARPS;                     // runs of each half per warp
