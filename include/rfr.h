@@ -244,6 +244,28 @@ int rfr_factor_batch_sharded(rfr_ctx* ctx, int count, const int64_t* const* coef
 int rfr_factor_batch_device(rfr_ctx* ctx, int count, const int64_t* d_coeffs,
                             const int32_t* d_degrees, rfr_factors* outs, int* statuses);
 
+/* rfr_factor_batch without blocking: the batch is queued whole for one of
+ * the serving workers (ahead of single requests) and runs on that worker's
+ * pipeline and stream, so the caller can prepare the next batch, or read the
+ * last one's results, while this one runs; batches queued back to back run
+ * on different workers and overlap on the device.  The rows are copied
+ * before the call returns.  outs[count] and statuses[count] (statuses may be
+ * NULL) belong to the caller and must stay valid until rfr_batch_wait has
+ * returned for *ticket; they are zeroed / set to RFR_PENDING here.
+ * Returns RFR_OK with *ticket set, or RFR_E_INVALID (bad arguments, a context
+ * without workers, or one being destroyed). */
+int rfr_factor_batch_async(rfr_ctx* ctx, int count, const int64_t* const* coeffs, const int* degrees,
+                           rfr_factors* outs, int* statuses, uint64_t* ticket);
+
+/* Wait for a batch queued by rfr_factor_batch_async (timeout_ms < 0: no
+ * limit).  Returns what rfr_factor_batch would have returned, with outs /
+ * statuses filled the same way, and releases the ticket; RFR_E_TIMEOUT
+ * leaves the batch in place (wait again); RFR_E_INVALID for an unknown or
+ * released ticket.  rfr_destroy drops batches still queued (their statuses
+ * become RFR_E_CANCELLED) and waits for running ones: wait for every batch
+ * before destroying its context. */
+int rfr_batch_wait(rfr_ctx* ctx, uint64_t ticket, int timeout_ms);
+
 /* Serving API (continuous batching).  rfr_submit copies the input and
  * queues it; workers admit queued requests into batches as slots and device
  * memory free up, and batches in flight overlap on the device.
@@ -275,6 +297,17 @@ void rfr_factors_free(rfr_factors* f);
 
 /* rfr_factors_free on each of f[0 .. count) (the results of one batch call). */
 void rfr_factors_free_n(rfr_factors* f, int count);
+
+/* Copy the factors of f[0 .. count) (the results of one batch call) into flat
+ * caller arrays: n_factors[i] = f[i].n_factors; the degrees of all factors,
+ * result by result, into degrees[]; their coefficients, one factor after the
+ * other, into coeffs[].  Nothing is freed.  Returns the number of
+ * coefficients written, RFR_E_RANGE if coeffs_cap or degrees_cap is too
+ * small (the arrays are then partly written), RFR_E_INVALID on bad
+ * arguments.  The factors of a degree-d polynomial hold at most 2 (d + 1)
+ * coefficients. */
+int64_t rfr_factors_flatten(rfr_factors* f, int count, int64_t* coeffs, size_t coeffs_cap,
+                            int32_t* degrees, size_t degrees_cap, int32_t* n_factors);
 
 /* Static English description of a status code. */
 const char* rfr_strerror(int status);

@@ -11,7 +11,7 @@ and importing the binding without the built library raises.
         res.factors                               # [[1, 0, -10, 0, 1]]
 """
 from ._native import (  # noqa: F401
-    RFR_OK, RFR_PENDING, RFRError, Context, Result, GeneralResult, lib, status_name, squarefree,
+    RFR_OK, RFR_PENDING, RFRError, Context, PendingBatch, Result, GeneralResult, lib, status_name, squarefree,
     stage_validate, stage_roots, stage_weights, stage_enumerate, stage_match, stage_lowlist, stage_splat, stage_splat_match, stage_prune,
     stage_verify,
     match_workspace_bytes, PLAN_DTYPE, RFR_MAX_DEGREE, RFR_LDC,

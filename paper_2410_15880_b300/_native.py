@@ -16,6 +16,7 @@ RFR_MAX_DEGREE = 128
 RFR_LDC = RFR_MAX_DEGREE + 1
 RFR_OK = 0
 RFR_PENDING = 1
+RFR_E_TIMEOUT = -12
 RFR_ROOTS_FP64 = 0
 RFR_ROOTS_FP32_BULK = 1
 RFR_MATCH_AUTO = 0
@@ -109,7 +110,11 @@ def lib():
         "rfr_factor": (i32, [vp, i64p, i32, C.POINTER(Factors)]),
         "rfr_factor_batch": (i32, [vp, i32, C.POINTER(i64p), C.POINTER(C.c_int), C.POINTER(Factors), C.POINTER(C.c_int)]),
         "rfr_factors_free_n": (None, [C.POINTER(Factors), i32]),
+        "rfr_factors_flatten": (C.c_int64, [C.POINTER(Factors), i32, vp, C.c_size_t, vp, C.c_size_t, vp]),
         "rfr_factor_batch_device": (i32, [vp, i32, vp, vp, C.POINTER(Factors), C.POINTER(C.c_int)]),
+        "rfr_factor_batch_async": (i32, [vp, i32, C.POINTER(i64p), C.POINTER(C.c_int), C.POINTER(Factors),
+                                         C.POINTER(C.c_int), C.POINTER(u64)]),
+        "rfr_batch_wait": (i32, [vp, u64, i32]),
         "rfr_factor_batch_sharded": (i32, [vp, i32, C.POINTER(i64p), C.POINTER(C.c_int), i32, i32, GATHER_FN, vp,
                                            C.POINTER(Factors), C.POINTER(C.c_int)]),
         "rfr_stage_validate": (i32, [vp, vp, i32, vp, vp]),
@@ -162,7 +167,10 @@ class Result:
     @property
     def diag(self) -> dict:
         if not isinstance(self._diag, dict):
-            self._diag = _diag_dict(self._diag) if self._diag is not None else {}
+            d = self._diag
+            if isinstance(d, tuple):                     # (the batch's result array, index)
+                d = d[0][d[1]].diag
+            self._diag = _diag_dict(d) if d is not None else {}
         return self._diag
 
 
@@ -197,16 +205,78 @@ def _to_result(status: int, f: Factors) -> Result:
 
 
 def _to_results(n: int, sts, outs) -> List[Result]:
-    """The n results of a batch call; their arrays are released with one call."""
-    res = []
-    for i in range(n):
-        f, st = outs[i], sts[i]
-        r = Result(status=st, _diag=Diag.from_buffer_copy(f.diag))
-        if st == RFR_OK:
-            r.factors = _factor_lists(f.n_factors, f.degrees, f.coeffs)
+    """The n results of a batch call: their factors come over in one flat copy
+    (rfr_factors_flatten), their arrays are released with one call, and each
+    result's diagnostics are read from `outs` when first asked for."""
+    L = lib()
+    nf = np.empty(n, dtype=np.int32)
+    co = np.empty(n * 2 * RFR_LDC, dtype=np.int64)
+    dg = np.empty(n * RFR_LDC, dtype=np.int32)
+    tot = L.rfr_factors_flatten(outs, n, co.ctypes.data, co.size, dg.ctypes.data, dg.size, nf.ctypes.data)
+    L.rfr_factors_free_n(outs, n)
+    if tot < 0:
+        raise RFRError(int(tot), "rfr_factors_flatten")
+    nfl = nf.tolist()
+    cl, dl = co[:tot].tolist(), dg[:sum(nfl)].tolist()
+    res, oc, od = [], 0, 0
+    for i, st in enumerate(sts[:n]):
+        r = Result(status=st, _diag=(outs, i))
+        k = nfl[i]
+        if k:
+            fl = []
+            for e in dl[od:od + k]:
+                fl.append(cl[oc:oc + e + 1])
+                oc += e + 1
+            od += k
+            r.factors = fl
         res.append(r)
-    lib().rfr_factors_free_n(outs, n)
     return res
+
+
+def _marshal(polys, degrees=None):
+    """(n, row pointers, degrees, arrays to keep alive) for a batch call: the
+    rows of an int64 array in place, or a sequence of coefficient lists
+    copied one after the other into one flat buffer."""
+    if isinstance(polys, np.ndarray):
+        arr = np.ascontiguousarray(polys, dtype=np.int64)
+        n = arr.shape[0]
+        degs = np.ascontiguousarray(degrees, dtype=np.int32)
+        addrs = (arr.ctypes.data + np.arange(n, dtype=np.uint64) * np.uint64(arr.strides[0])).astype(np.uint64)
+    else:
+        n = len(polys)
+        lens = np.fromiter(map(len, polys), dtype=np.int64, count=n)
+        degs = (lens - 1).astype(np.int32)
+        arr = np.fromiter(itertools.chain.from_iterable(polys), dtype=np.int64, count=int(lens.sum()))
+        starts = np.concatenate([np.zeros(1, dtype=np.int64), np.cumsum(lens)[:-1]]).astype(np.uint64)
+        addrs = (np.uint64(arr.ctypes.data) + starts[:n] * np.uint64(8)).astype(np.uint64)
+    ptrs = (C.POINTER(C.c_int64) * n).from_buffer(addrs)
+    degs_c = degs.ctypes.data_as(C.POINTER(C.c_int))
+    return n, ptrs, degs_c, (arr, degs, addrs)
+
+
+class PendingBatch:
+    """A batch queued by Context.factor_batch_async.  result() waits for it
+    (rfr_batch_wait) and returns what factor_batch would have; it may be
+    called again and returns the same list."""
+
+    def __init__(self, ctx, n, outs, sts, ticket):
+        self._ctx, self._n, self._outs, self._sts, self._ticket = ctx, n, outs, sts, ticket
+        self._res = [] if n == 0 else None
+
+    def result(self, timeout_ms: int = -1) -> List[Result]:
+        if self._res is None:
+            rc = lib().rfr_batch_wait(self._ctx._h, self._ticket, int(timeout_ms))
+            if rc == RFR_E_TIMEOUT:
+                raise RFRError(rc, "rfr_batch_wait")
+            if rc != RFR_OK:
+                lib().rfr_factors_free_n(self._outs, self._n)
+                self._res = RFRError(rc, "rfr_factor_batch_async")
+            else:
+                self._res = _to_results(self._n, self._sts, self._outs)
+            self._outs = self._sts = None
+        if isinstance(self._res, RFRError):
+            raise self._res
+        return self._res
 
 
 @dataclass
@@ -324,20 +394,7 @@ class Context:
         degree).  The rows are passed to rfr_factor_batch in place."""
         if len(polys) == 0:
             return []
-        if isinstance(polys, np.ndarray):
-            arr = np.ascontiguousarray(polys, dtype=np.int64)
-            n = arr.shape[0]
-            degs = np.ascontiguousarray(degrees, dtype=np.int32)
-            addrs = (arr.ctypes.data + np.arange(n, dtype=np.uint64) * np.uint64(arr.strides[0])).astype(np.uint64)
-        else:                                   # all rows one after the other in one flat buffer
-            n = len(polys)
-            lens = np.fromiter(map(len, polys), dtype=np.int64, count=n)
-            degs = (lens - 1).astype(np.int32)
-            arr = np.fromiter(itertools.chain.from_iterable(polys), dtype=np.int64, count=int(lens.sum()))
-            starts = np.concatenate([np.zeros(1, dtype=np.int64), np.cumsum(lens)[:-1]]).astype(np.uint64)
-            addrs = (np.uint64(arr.ctypes.data) + starts[:n] * np.uint64(8)).astype(np.uint64)
-        ptrs = (C.POINTER(C.c_int64) * n).from_buffer(addrs)
-        degs_c = degs.ctypes.data_as(C.POINTER(C.c_int))
+        n, ptrs, degs_c, _keep = _marshal(polys, degrees)
         outs = (Factors * n)()
         sts = (C.c_int * n)()
         rc = lib().rfr_factor_batch(self._h, n, ptrs, degs_c, outs, sts)
@@ -345,6 +402,22 @@ class Context:
             lib().rfr_factors_free_n(outs, n)
             raise RFRError(rc, "rfr_factor_batch")
         return _to_results(n, sts, outs)
+
+    def factor_batch_async(self, polys, degrees=None) -> "PendingBatch":
+        """Queue a batch (rfr_factor_batch_async) and return at once; the
+        handle's result() waits for it.  Inputs as for factor_batch; they are
+        copied before this returns."""
+        n = len(polys)
+        if n == 0:
+            return PendingBatch(self, 0, None, None, None)
+        n, ptrs, degs_c, _keep = _marshal(polys, degrees)
+        outs = (Factors * n)()
+        sts = (C.c_int * n)()
+        t = C.c_uint64(0)
+        rc = lib().rfr_factor_batch_async(self._h, n, ptrs, degs_c, outs, sts, C.byref(t))
+        if rc != RFR_OK:
+            raise RFRError(rc, "rfr_factor_batch_async")
+        return PendingBatch(self, n, outs, sts, t.value)
 
     def factor_batch_sharded(self, polys: Sequence[Sequence[int]], shard: int, nshards: int, gather) -> List[Result]:
         """This process's key-range shard of the batch (rfr_factor_batch_sharded).

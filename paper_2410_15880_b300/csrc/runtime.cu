@@ -167,6 +167,19 @@ struct Request {
     rfr_factors result{};
 };
 
+// One whole batch queued by rfr_factor_batch_async: the rows are copied at
+// submit; outs / statuses are the caller's, filled by the worker that runs it.
+struct BatchJob {
+    uint64_t ticket;
+    std::vector<int64_t> flat;
+    std::vector<const int64_t*> rows;
+    std::vector<int> degrees;
+    rfr_factors* outs;
+    int* statuses;
+    int rc = RFR_PENDING;
+    bool done = false;
+};
+
 struct Ctx {
     rfr_config cfg;
     int device = 0;
@@ -182,6 +195,8 @@ struct Ctx {
     std::condition_variable q_cv, done_cv;
     std::deque<Request*> pending;
     std::unordered_map<uint64_t, Request*> reqs;
+    std::deque<BatchJob*> batch_q;                 // whole batches, run before single requests
+    std::unordered_map<uint64_t, BatchJob*> batch_jobs;
     uint64_t next_ticket = 1;
     bool stop = false;
     int running_batches = 0;
@@ -193,11 +208,13 @@ struct Ctx {
     std::string tune_path, device_name;
 
     // Reserve `bytes` of the device budget; waits while other batches hold it.
+    // A batch holds at most one reservation at a time and every holder runs to
+    // completion, so the wait ends, also while the context is being destroyed
+    // (running batches finish normally).
     bool reserve(size_t bytes) {
         std::unique_lock<std::mutex> lk(budget_mu);
         if (bytes > budget) return false;
-        budget_cv.wait(lk, [&] { return budget_used + bytes <= budget || stop; });
-        if (stop) return false;
+        budget_cv.wait(lk, [&] { return budget_used + bytes <= budget; });
         budget_used += bytes;
         return true;
     }
@@ -909,7 +926,30 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
     if (timing) t_verify = ms_between(ev[7], ev[8]);
     const double t_dev = timing ? ms_between(ev[0], ev[8]) : 0.0;
 
-    // ---- results
+    // ---- results: factor lists (host inputs: checked exactly against p), then
+    // the diagnostics, whose host total covers this phase too
+    for (auto& w : work) {
+        Item& it = items[w.item];
+        if (w.status != RFR_OK) continue;
+        std::vector<std::vector<int64_t>> fs;
+        if (!w.factors.empty()) fs = std::move(w.factors);
+        else fs.emplace_back(it.coeffs, it.coeffs + it.degree + 1);
+        if (!device_in && fs.size() > 1) {
+            // the product of the factors equals p
+            std::vector<__int128> prod(fs[0].begin(), fs[0].end());
+            for (size_t f = 1; f < fs.size(); ++f) {
+                std::vector<__int128> nx(prod.size() + fs[f].size() - 1, 0);
+                for (size_t i = 0; i < prod.size(); ++i)
+                    for (size_t j = 0; j < fs[f].size(); ++j) nx[i + j] += prod[i] * (__int128)fs[f][j];
+                prod.swap(nx);
+            }
+            bool same = (int)prod.size() == it.degree + 1;
+            for (int k = 0; same && k <= it.degree; ++k) same = prod[k] == (__int128)it.coeffs[k];
+            if (!same) { w.status = RFR_E_INTERNAL; continue; }
+        }
+        canonical_sort(fs);
+        fill_factors(it.out, fs);
+    }
     const double t_host = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_host0).count();
     for (auto& w : work) {
         Item& it = items[w.item];
@@ -925,39 +965,59 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
         dg.stage_us[3] = t_scatter * 1e3; dg.stage_us[4] = t_match * 1e3; dg.stage_us[5] = t_verify * 1e3;
         dg.stage_us[6] = t_dev * 1e3; dg.stage_us[7] = t_host * 1e3;
         dg.h2d_bytes = h2d; dg.d2h_bytes = d2h; dg.launches = launches; dg.batch_size = (uint32_t)B;
-        if (w.status != RFR_OK) { it.status = w.status; continue; }
-        std::vector<std::vector<int64_t>> fs;
-        if (!w.factors.empty()) fs = w.factors;
-        else fs.emplace_back(it.coeffs, it.coeffs + it.degree + 1);
-        if (!device_in) {
-            // exact check: the product of the factors equals p
-            std::vector<__int128> prod(1, 1);
-            for (auto& f : fs) {
-                std::vector<__int128> nx(prod.size() + f.size() - 1, 0);
-                for (size_t i = 0; i < prod.size(); ++i)
-                    for (size_t j = 0; j < f.size(); ++j) nx[i + j] += prod[i] * (__int128)f[j];
-                prod.swap(nx);
-            }
-            bool same = (int)prod.size() == it.degree + 1;
-            for (int k = 0; same && k <= it.degree; ++k) same = prod[k] == (__int128)it.coeffs[k];
-            if (!same) { it.status = RFR_E_INTERNAL; continue; }
-        }
-        canonical_sort(fs);
-        fill_factors(it.out, fs);
+        if (w.status != RFR_OK) it.status = w.status;
     }
     return RFR_OK;
 }
 
 // ---------------------------------------------------------------- serving
+// Run a queued whole batch on this worker's pipeline.
+static void run_batch_job(Ctx* C, Pipeline* P, BatchJob* J) {
+    const int n = (int)J->rows.size();
+    std::vector<Item> items(n);
+    for (int i = 0; i < n; ++i) items[i] = {J->rows[i], J->degrees[i], RFR_OK, &J->outs[i]};
+    const int rc = n ? P->run(items) : RFR_OK;
+    for (int i = 0; i < n; ++i) {
+        const int st = rc == RFR_OK ? items[i].status : rc;
+        if (J->statuses) J->statuses[i] = st;
+        if (st != RFR_OK) rfr_factors_free(&J->outs[i]);
+    }
+    std::lock_guard<std::mutex> lk(C->q_mu);
+    J->rc = rc;
+    J->done = true;
+    --C->running_batches;
+}
+
 static void worker_loop(Ctx* C, Pipeline* P) {
     cudaSetDevice(C->device);
     for (;;) {
         std::vector<Request*> batch;
+        BatchJob* job = nullptr;
         {
             std::unique_lock<std::mutex> lk(C->q_mu);
-            C->q_cv.wait(lk, [&] { return C->stop || !C->pending.empty(); });
+            C->q_cv.wait(lk, [&] { return C->stop || !C->pending.empty() || !C->batch_q.empty(); });
             if (C->stop) return;
-            while (!C->pending.empty() && (int)batch.size() < C->cfg.max_batch) {
+            if (!C->batch_q.empty()) {
+                job = C->batch_q.front();
+                C->batch_q.pop_front();
+                ++C->running_batches;
+            }
+        }
+        if (job) {
+            run_batch_job(C, P, job);
+            C->done_cv.notify_all();
+            continue;
+        }
+        {
+            std::unique_lock<std::mutex> lk(C->q_mu);
+            if (C->stop) return;
+            // this worker's share of the queue: the idle workers (this one included)
+            // split it, so that a burst is spread over them instead of one worker
+            // taking it all while the others wait; a long queue still fills
+            // batches of max_batch
+            const int idle = std::max(1, (int)C->workers.size() - C->running_batches);
+            const int share = (int)std::min<size_t>((size_t)C->cfg.max_batch, (C->pending.size() + idle - 1) / idle);
+            while (!C->pending.empty() && (int)batch.size() < share) {
                 Request* r = C->pending.front();
                 C->pending.pop_front();
                 if (r->cancelled) continue;
@@ -1083,6 +1143,15 @@ int rfr_destroy(rfr_ctx* x) {
         C.stop = true;
         for (Request* r : C.pending) { r->status = RFR_E_CANCELLED; r->done = true; }
         C.pending.clear();
+        for (BatchJob* J : C.batch_q) {               // queued batches that never ran
+            for (size_t i = 0; i < J->rows.size(); ++i) {
+                memset(&J->outs[i], 0, sizeof(rfr_factors));
+                if (J->statuses) J->statuses[i] = RFR_E_CANCELLED;
+            }
+            J->rc = RFR_E_CANCELLED;
+            J->done = true;
+        }
+        C.batch_q.clear();
     }
     { std::lock_guard<std::mutex> lk(C.budget_mu); }
     C.budget_cv.notify_all();
@@ -1091,6 +1160,7 @@ int rfr_destroy(rfr_ctx* x) {
     for (auto& p : C.worker_pipes) p->destroy();
     C.sync_pipe.destroy();
     for (auto& kv : C.reqs) { rfr_factors_free(&kv.second->result); delete kv.second; }
+    for (auto& kv : C.batch_jobs) delete kv.second;
     delete x;
     return RFR_OK;
 }
@@ -1173,6 +1243,59 @@ int rfr_factor_batch_device(rfr_ctx* x, int count, const int64_t* d_coeffs, cons
         if (statuses) statuses[i] = st;
         if (st != RFR_OK) rfr_factors_free(&outs[i]);
     }
+    return rc;
+}
+
+int rfr_factor_batch_async(rfr_ctx* x, int count, const int64_t* const* coeffs, const int* degrees,
+                           rfr_factors* outs, int* statuses, uint64_t* ticket) {
+    if (!x || !ticket || count < 0 || (count && (!coeffs || !degrees || !outs))) return RFR_E_INVALID;
+    Ctx& C = x->c;
+    if (C.workers.empty()) return RFR_E_INVALID;
+    static const int64_t k_unread = 0;              // rows rejected by degree alone are never read
+    auto* J = new BatchJob;
+    J->outs = outs;
+    J->statuses = statuses;
+    J->degrees.assign(degrees, degrees + count);
+    size_t tot = 0;
+    for (int i = 0; i < count; ++i)
+        if (coeffs[i] && degrees[i] >= 1 && degrees[i] <= DMAX) tot += (size_t)degrees[i] + 1;
+    J->flat.resize(tot);
+    J->rows.resize(count);
+    size_t o = 0;
+    for (int i = 0; i < count; ++i) {
+        memset(&outs[i], 0, sizeof(rfr_factors));
+        if (statuses) statuses[i] = RFR_PENDING;
+        if (!coeffs[i]) { J->rows[i] = nullptr; continue; }
+        if (degrees[i] < 1 || degrees[i] > DMAX) { J->rows[i] = &k_unread; continue; }
+        memcpy(J->flat.data() + o, coeffs[i], ((size_t)degrees[i] + 1) * 8);
+        J->rows[i] = J->flat.data() + o;
+        o += (size_t)degrees[i] + 1;
+    }
+    {
+        std::lock_guard<std::mutex> lk(C.q_mu);
+        if (C.stop) { delete J; return RFR_E_INVALID; }
+        J->ticket = C.next_ticket++;
+        C.batch_jobs[J->ticket] = J;
+        C.batch_q.push_back(J);
+        *ticket = J->ticket;
+    }
+    C.q_cv.notify_one();
+    return RFR_OK;
+}
+
+int rfr_batch_wait(rfr_ctx* x, uint64_t ticket, int timeout_ms) {
+    if (!x) return RFR_E_INVALID;
+    Ctx& C = x->c;
+    std::unique_lock<std::mutex> lk(C.q_mu);
+    auto it = C.batch_jobs.find(ticket);
+    if (it == C.batch_jobs.end()) return RFR_E_INVALID;
+    BatchJob* J = it->second;
+    auto pred = [&] { return J->done; };
+    if (timeout_ms < 0) C.done_cv.wait(lk, pred);
+    else if (!C.done_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred)) return RFR_E_TIMEOUT;
+    const int rc = J->rc;
+    C.batch_jobs.erase(ticket);
+    delete J;
     return rc;
 }
 
@@ -1285,6 +1408,25 @@ void rfr_factors_free(rfr_factors* f) {
 void rfr_factors_free_n(rfr_factors* f, int count) {
     if (!f) return;
     for (int i = 0; i < count; ++i) rfr_factors_free(&f[i]);
+}
+
+int64_t rfr_factors_flatten(rfr_factors* f, int count, int64_t* coeffs, size_t coeffs_cap,
+                            int32_t* degrees, size_t degrees_cap, int32_t* n_factors) {
+    if (count < 0 || (count && (!f || !n_factors))) return RFR_E_INVALID;
+    size_t nc = 0, nd = 0;
+    for (int i = 0; i < count; ++i) {
+        n_factors[i] = f[i].n_factors;
+        size_t off = 0;                                   // within result i's coefficients
+        for (int k = 0; k < f[i].n_factors; ++k) {
+            const size_t len = (size_t)f[i].degrees[k] + 1;
+            if (nd + 1 > degrees_cap || nc + len > coeffs_cap) return RFR_E_RANGE;
+            degrees[nd++] = f[i].degrees[k];
+            memcpy(coeffs + nc, f[i].coeffs + off, len * 8);
+            nc += len;
+            off += len;
+        }
+    }
+    return (int64_t)nc;
 }
 
 }  // extern "C"

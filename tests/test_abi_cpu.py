@@ -90,3 +90,46 @@ def test_golden_files_are_consistent():
                 assert f[-1] == 1
                 acc = pmul(acc, f)
             assert acc == r["coeffs"], r["name"]
+
+
+def test_batch_results_flattened_and_released(L):
+    """A batch's results as the library hands them over (malloc'ed arrays per
+    result) become factor lists through one rfr_factors_flatten copy; every
+    array is released, error results carry no factors, and the diagnostics are
+    read from the result array itself."""
+    import paper_2410_15880_b300._native as N
+    libc = ctypes.CDLL(None)
+    libc.malloc.restype = ctypes.c_void_p
+    libc.malloc.argtypes = [ctypes.c_size_t]
+    facs = [[[-7, 1], [1, 0, 1], [3, 2, 1]], None, [[5, 0, 0, 1]], []]
+    n = len(facs)
+    outs = (N.Factors * n)()
+    sts = (ctypes.c_int * n)(0, -5, 0, 0)
+    for i, fs in enumerate(facs):
+        outs[i].diag.n = 10 + i
+        if not fs:
+            continue
+        co = [c for f in fs for c in f]
+        d = libc.malloc(4 * len(fs))
+        c = libc.malloc(8 * len(co))
+        (ctypes.c_int * len(fs)).from_address(d)[:] = [len(f) - 1 for f in fs]
+        (ctypes.c_int64 * len(co)).from_address(c)[:] = co
+        outs[i].n_factors = len(fs)
+        outs[i].degrees = ctypes.cast(d, type(outs[i].degrees))
+        outs[i].coeffs = ctypes.cast(c, type(outs[i].coeffs))
+    res = N._to_results(n, sts, outs)
+    assert [r.factors for r in res] == [facs[0], [], facs[2], []]
+    assert [r.status for r in res] == [0, -5, 0, 0]
+    assert [r.diag["n"] for r in res] == [10, 11, 12, 13]
+    assert all(outs[i].n_factors == 0 and not outs[i].coeffs for i in range(n))
+    # too little room: an error, nothing written past the caps
+    one = (N.Factors * 1)()
+    d, c = libc.malloc(4), libc.malloc(16)
+    (ctypes.c_int * 1).from_address(d)[0] = 1
+    (ctypes.c_int64 * 2).from_address(c)[:] = [3, 1]
+    one[0].n_factors, one[0].degrees, one[0].coeffs = 1, ctypes.cast(d, type(one[0].degrees)), ctypes.cast(c, type(one[0].coeffs))
+    co, dg, nf = (ctypes.c_int64 * 1)(), (ctypes.c_int32 * 1)(), (ctypes.c_int32 * 1)()
+    assert L.rfr_factors_flatten(one, 1, co, 1, dg, 1, nf) == -3
+    assert L.rfr_factors_flatten(one, 1, (ctypes.c_int64 * 2)(), 2, dg, 1, nf) == 2
+    assert L.rfr_factors_flatten(None, 1, co, 1, dg, 1, nf) == -1
+    L.rfr_factors_free_n(one, 1)

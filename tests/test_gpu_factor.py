@@ -265,3 +265,61 @@ def test_key_range_shards_with_table_redo():
     for s in range(2):
         assert [r.ok for r in out[s]] == [True, True], [r.status for r in out[s]]
         assert [r.factors for r in out[s]] == expect
+
+
+def test_async_batches_in_flight_equal_golden():
+    """rfr_factor_batch_async: three batches queued back to back (two run at
+    once on the two workers) give the golden factorisations, error statuses
+    included, whatever order they are waited in; result() is idempotent."""
+    from paper_2410_15880_b300 import Context
+    from paper_2410_15880_b300._native import status_name
+    recs2, recs3 = golden("cfg2")[:20], golden("cfg3")[:6]
+    bad = [[1, 2, 3], [1 << 60, 1], [2, -3, 0, 1], [5]]   # not monic, range, not square-free, degree 0
+    want_bad = ["RFR_E_NOT_MONIC", "RFR_E_RANGE", "RFR_E_NOT_SQUAREFREE", "RFR_E_RANGE"]
+    with Context(device=0, max_inflight=2) as c:
+        h1 = c.factor_batch_async([r["coeffs"] for r in recs2])
+        h2 = c.factor_batch_async([r["coeffs"] for r in recs3] + bad)
+        h3 = c.factor_batch_async([r["coeffs"] for r in recs2[::-1]])
+        r3, r1, r2 = h3.result(), h1.result(), h2.result()
+        assert h1.result() is r1
+        sync = c.factor_batch([r["coeffs"] for r in recs3])
+        assert c.factor_batch_async([]).result() == []
+    assert [x.factors for x in r1] == [r["factors"] for r in recs2] and all(x.ok for x in r1)
+    assert [x.factors for x in r3] == [r["factors"] for r in recs2[::-1]]
+    assert [x.factors for x in r2[:6]] == [r["factors"] for r in recs3] == [x.factors for x in sync]
+    assert [status_name(x.status) for x in r2[6:]] == want_bad
+    assert r2[0].diag["n"] == sync[0].diag["n"] and r2[0].diag["window"] == sync[0].diag["window"]
+
+
+def test_async_wait_unknown_ticket_and_destroy_with_queued_batches():
+    """rfr_batch_wait on an unknown ticket is RFR_E_INVALID; rfr_destroy with
+    batches still queued drops them (statuses RFR_E_CANCELLED, outs zeroed)
+    and lets the running ones finish (their results are the caller's)."""
+    import ctypes as C
+    from paper_2410_15880_b300._native import Config, Factors, lib, _marshal
+    L = lib()
+    cfg = Config()
+    assert L.rfr_config_default(C.byref(cfg)) == 0
+    cfg.device, cfg.max_inflight = 0, 1
+    h = C.c_void_p()
+    assert L.rfr_create(C.byref(cfg), C.byref(h)) == 0
+    assert L.rfr_batch_wait(h, 12345, 0) == -1
+    recs = golden("cfg2")[:10]
+    keep, jobs = [], []
+    for _ in range(6):
+        n, ptrs, degs, k = _marshal([r["coeffs"] for r in recs])
+        outs, sts, t = (Factors * n)(), (C.c_int * n)(), C.c_uint64(0)
+        assert L.rfr_factor_batch_async(h, n, ptrs, degs, outs, sts, C.byref(t)) == 0
+        keep.append(k)
+        jobs.append((outs, sts, n))
+    assert L.rfr_destroy(h) == 0
+    cancelled = 0
+    for outs, sts, n in jobs:
+        st = list(sts)
+        if st == [-14] * n:
+            cancelled += 1
+            assert all(outs[i].n_factors == 0 for i in range(n))
+        else:
+            assert st == [0] * n
+        L.rfr_factors_free_n(outs, n)
+    assert 0 <= cancelled <= 6
