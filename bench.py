@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--tune-cache", default="", help="file that stores tuned match layouts")
     ap.add_argument("--degree120-steps", type=int, default=5,
                     help="timed steps of the degree-120 sub-measurement (0 = skip it)")
+    ap.add_argument("--e2e-depth", type=int, default=E2E_DEPTH,
+                    help="batches in flight in the end-to-end leg (worker pipelines of the context)")
     ap.add_argument("--shard", action="store_true",
                     help="key-range sharding of one batch over the ranks (rfr_factor_batch_sharded; the "
                          "degree-120 workload unless --config names another) instead of replicas")
@@ -526,7 +528,7 @@ def main():
     flush = torch.empty((256 << 20,), dtype=torch.uint8, device="cuda")     # larger than L2 (126 MB)
     match_path = {"auto": 0, "tables": 1, "splat": 2, "prune": 3}[a.match_path]
     with Context(device=local, timing=True, root_mode=a.root_mode, autotune=not a.no_autotune,
-                 tune_cache_path=a.tune_cache, match_path=match_path, max_inflight=E2E_DEPTH) as ctx:
+                 tune_cache_path=a.tune_cache, match_path=match_path, max_inflight=max(1, a.e2e_depth)) as ctx:
         for i in range(a.warmup):
             flush.fill_(i & 255)                   # the flush kernel's first use loads it (not timed)
             torch.cuda.current_stream().synchronize()
@@ -561,18 +563,20 @@ def main():
         if rank == 0 and os.path.exists(gpath):
             gold = json.load(open(gpath))[:B]
             ok_golden = all(r.ok and r.factors == g["factors"] for r, g in zip(res, gold))
-        # ---- e2e: host buffers through rfr_factor_batch_async, E2E_DEPTH batches
+        # ---- e2e: host buffers through rfr_factor_batch_async, `depth` batches
         # in flight, one per worker pipeline (each on its own stream): while
         # they run, this thread queues the next batch and turns the oldest
         # finished one's results into Python objects
+        depth = max(1, a.e2e_depth)
+
         def e2e_pipelined(steps, lat, stages):
             pend, last = [], None
             for i in range(steps):
                 flush.fill_(i & 255)
                 torch.cuda.current_stream().synchronize()
                 pend.append((ctx.factor_batch_async(h_co, h_dg), time.perf_counter()))
-                if len(pend) == E2E_DEPTH or i == steps - 1:
-                    while pend and (len(pend) == E2E_DEPTH or i == steps - 1):
+                if len(pend) == depth or i == steps - 1:
+                    while pend and (len(pend) == depth or i == steps - 1):
                         h, t0 = pend.pop(0)
                         last = h.result()
                         lat.append((time.perf_counter() - t0) * 1e3)
@@ -719,7 +723,7 @@ def main():
         "e2e": {"value": polys_total / (ms_e2e / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(e2e_diag["h2d_bytes"]), "d2h_bytes_per_step": int(e2e_diag["d2h_bytes"]),
                 "ms_per_step": ms_e2e / a.steps,
-                "api": f"rfr_factor_batch_async + rfr_batch_wait, {E2E_DEPTH} batches in flight (L2 flush before each submit); "
+                "api": f"rfr_factor_batch_async + rfr_batch_wait, {depth} batches in flight (L2 flush before each submit); "
                        "inputs: int64 rows in pinned host memory",
                 "batch_latency_ms_median": statistics.median(e2e_lat), "batch_latency_ms_max": max(e2e_lat),
                 "library_host_us_per_step": statistics.mean(x[7] for x in e2e_stage),

@@ -201,6 +201,7 @@ struct Ctx {
     bool stop = false;
     int running_batches = 0;
     std::vector<std::thread> workers;
+    int n_workers = 0;                            // set before the first worker starts
     std::vector<std::unique_ptr<Pipeline>> worker_pipes;
     // autotuned layouts per (n_a, n_b)
     std::mutex tune_mu;
@@ -1015,7 +1016,7 @@ static void worker_loop(Ctx* C, Pipeline* P) {
             // split it, so that a burst is spread over them instead of one worker
             // taking it all while the others wait; a long queue still fills
             // batches of max_batch
-            const int idle = std::max(1, (int)C->workers.size() - C->running_batches);
+            const int idle = std::max(1, C->n_workers - C->running_batches);
             const int share = (int)std::min<size_t>((size_t)C->cfg.max_batch, (C->pending.size() + idle - 1) / idle);
             while (!C->pending.empty() && (int)batch.size() < share) {
                 Request* r = C->pending.front();
@@ -1130,6 +1131,8 @@ int rfr_create(const rfr_config* cfg_in, rfr_ctx** out) {
         C.worker_pipes.emplace_back(new Pipeline());
         if (!C.worker_pipes.back()->init(&C)) { rfr_destroy(x); return RFR_E_CUDA; }
     }
+    C.n_workers = cfg.max_inflight;
+    C.workers.reserve(cfg.max_inflight);
     for (int i = 0; i < cfg.max_inflight; ++i) C.workers.emplace_back(worker_loop, &C, C.worker_pipes[i].get());
     *out = x;
     return RFR_OK;
@@ -1250,7 +1253,7 @@ int rfr_factor_batch_async(rfr_ctx* x, int count, const int64_t* const* coeffs, 
                            rfr_factors* outs, int* statuses, uint64_t* ticket) {
     if (!x || !ticket || count < 0 || (count && (!coeffs || !degrees || !outs))) return RFR_E_INVALID;
     Ctx& C = x->c;
-    if (C.workers.empty()) return RFR_E_INVALID;
+    if (C.n_workers == 0) return RFR_E_INVALID;
     static const int64_t k_unread = 0;              // rows rejected by degree alone are never read
     auto* J = new BatchJob;
     J->outs = outs;
