@@ -63,9 +63,9 @@ constexpr int MT_RUNS = 128;                                   // at most 128 ru
 constexpr int MT_RPW = MT_RUNS / MT_WARPS;                     // runs of each half per warp
 constexpr int GL = 32 / MT_RPW;                                // lanes walking one run together
 #ifndef RFR_MT_UR
-#define RFR_MT_UR 4
+#define RFR_MT_UR 3
 #endif
-constexpr int MT_UR = RFR_MT_UR;                               // list loads in flight per lane
+constexpr int MT_UR = RFR_MT_UR;                               // list loads per lane and block (the next block's in flight)
 constexpr int MT_CH = 8;                                       // units whose stretches are found together
 constexpr int MT_BM_LOG = 19;                                  // occupancy bitmap: about 2^19 cells per unit
 constexpr int MT_BMW = (1 << (MT_BM_LOG - 5)) + 4;             // + margin cells (16-byte multiple)
@@ -527,11 +527,20 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
         if (gl == 0) { rsb[warp * MT_RPW + g] = sbg; rp0[warp * MT_RPW + g] = pa0; }
         // ---- table a: every key of the unit, 8 lanes per run, 4 runs per warp
         {
+            // blocks of MT_UR positions per lane; the next block's loads are issued
+            // before this block's keys are inserted
             const uint32_t itn = (__reduce_max_sync(0xffffffffu, acnt) + GL - 1) / GL;
+            uint32_t yn[MT_UR];
+#pragma unroll
+            for (int s = 0; s < MT_UR; ++s) yn[s] = Ya32[(pa0 + s * GL + gl) & lma];
             for (uint32_t it = 0; it < itn; it += MT_UR) {
                 uint32_t yv[MT_UR];
 #pragma unroll
-                for (int s = 0; s < MT_UR; ++s) yv[s] = Ya32[(pa0 + (it + s) * GL + gl) & lma];
+                for (int s = 0; s < MT_UR; ++s) yv[s] = yn[s];
+                if (it + MT_UR < itn) {
+#pragma unroll
+                    for (int s = 0; s < MT_UR; ++s) yn[s] = Ya32[(pa0 + (it + MT_UR + s) * GL + gl) & lma];
+                }
 #pragma unroll
                 for (int s = 0; s < MT_UR; ++s) {
                     const uint32_t t = (it + s) * GL + gl;
@@ -560,10 +569,17 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
             }
             const uint32_t gbits = (uint32_t)(warp + MT_WARPS * g) << lb;
             const uint32_t itn = (__reduce_max_sync(0xffffffffu, bcnt) + GL - 1) / GL;
+            uint32_t yn[MT_UR];
+#pragma unroll
+            for (int s = 0; s < MT_UR; ++s) yn[s] = Yb32[(pb0 + s * GL + gl) & lmb];
             for (uint32_t it = 0; it < itn; it += MT_UR) {
                 uint32_t yv[MT_UR];
 #pragma unroll
-                for (int s = 0; s < MT_UR; ++s) yv[s] = Yb32[(pb0 + (it + s) * GL + gl) & lmb];
+                for (int s = 0; s < MT_UR; ++s) yv[s] = yn[s];
+                if (it + MT_UR < itn) {
+#pragma unroll
+                    for (int s = 0; s < MT_UR; ++s) yn[s] = Yb32[(pb0 + (it + MT_UR + s) * GL + gl) & lmb];
+                }
 #pragma unroll
                 for (int s = 0; s < MT_UR; ++s) {
                     const uint32_t t = (it + s) * GL + gl;
