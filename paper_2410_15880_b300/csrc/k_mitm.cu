@@ -212,11 +212,22 @@ __global__ void __launch_bounds__(YM_THREADS) k_ymerge(const YJob* __restrict__ 
     const uint32_t o0 = (uint32_t)c * YM_TILE;
     const uint32_t a0 = J.splits[c], a1 = J.splits[c + 1], b0 = o0 - a0;
     const uint32_t na = a1 - a0;                  // nb = YM_TILE - na
-    for (uint32_t j = threadIdx.x; j < (uint32_t)YM_TILE; j += blockDim.x) {
-        if (j < na) { tin[j] = K[a0 + j]; min_[j] = M[a0 + j]; }
-        else {
-            const uint32_t q = (r + b0 + (j - na)) & nm;
-            tin[j] = K[q] + cs; min_[j] = M[q] | bit;
+    {
+        // all of this thread's loads are in flight before the first store
+        uint64_t kv[YM_PER];
+        uint32_t mv[YM_PER];
+#pragma unroll
+        for (int q = 0; q < YM_PER; ++q) {
+            const uint32_t j = threadIdx.x + (uint32_t)q * YM_THREADS;
+            const uint32_t src = j < na ? a0 + j : ((r + b0 + (j - na)) & nm);
+            kv[q] = K[src];
+            mv[q] = M[src];
+        }
+#pragma unroll
+        for (int q = 0; q < YM_PER; ++q) {
+            const uint32_t j = threadIdx.x + (uint32_t)q * YM_THREADS;
+            tin[j] = j < na ? kv[q] : kv[q] + cs;
+            min_[j] = j < na ? mv[q] : (mv[q] | bit);
         }
     }
     __syncthreads();
@@ -243,7 +254,12 @@ __global__ void __launch_bounds__(YM_THREADS) k_ymerge(const YJob* __restrict__ 
     uint64_t* KO = last ? J.ylist : J.kb[p ^ 1];
     uint32_t* MO = last ? J.ymask : J.mb[p ^ 1];
     if (!(last && J.ydir)) {
-        for (uint32_t j = threadIdx.x; j < (uint32_t)YM_TILE; j += blockDim.x) { KO[o0 + j] = tout[j]; MO[o0 + j] = mout[j]; }
+#pragma unroll
+        for (int q = 0; q < YM_PER; ++q) {
+            const uint32_t j = threadIdx.x + (uint32_t)q * YM_THREADS;
+            KO[o0 + j] = tout[j];
+            MO[o0 + j] = mout[j];
+        }
         return;
     }
     // the last level also writes the list's directory and positions (as k_ydir does):
