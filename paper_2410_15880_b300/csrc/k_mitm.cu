@@ -709,9 +709,11 @@ bool mitm_geometry(int n_a, int n_b, uint64_t W, MatchGeom* g) {
     if (nbl < 4) return false;
     const int fsh = su - nbl - 16;
     const uint32_t NB = 1u << d1;
-    uint32_t slab = NB / 256;
+    // the slab length of a lone problem (run_mitm chooses it per launch): up to
+    // MT_CH units, the stretch-search period, and at least 128 CTAs
+    uint32_t slab = NB / 128;
     if (slab < 1) slab = 1;
-    if (slab > 64) slab = 64;
+    if (slab > (uint32_t)MT_CH) slab = MT_CH;
     memset(g, 0, sizeof(*g));
     g->fused = true;
     g->optimistic = true;
@@ -796,11 +798,29 @@ cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev
     build_lists(yj.data(), (int)yj.size(), d_yj, s);
     if (ev_lists) cudaEventRecord(ev_lists, s);
     if (ev_lists2) cudaEventRecord(ev_lists2, s);
+    // CTAs of the costliest units first (keys per unit of both halves), so that
+    // the last wave holds the cheapest ones
+    std::vector<int> order(nF);
+    for (int i = 0; i < nF; ++i) order[i] = i;
+    auto unit_cost = [&](int i) {
+        return std::ldexp(1.0, F[i]->n_a - F[i]->d1) + std::ldexp(1.0, F[i]->n_b - F[i]->d1);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return unit_cost(x) > unit_cost(y); });
+    // slab length for this launch: the longest of 64, 32, 16, 8 units that still
+    // gives 20 waves of CTAs (one per SM), so that the last wave is a small share;
+    // a problem keeps at least 128 CTAs and at most its geometry's slab
+    double tot_units = 0;
+    for (int i = 0; i < nF; ++i) tot_units += std::ldexp(1.0, F[i]->d1);
+    int sg = 64;
+    while (sg > MT_CH && tot_units / sg < 20.0 * 148.0) sg /= 2;
     std::vector<MitmJob> mj(nF);
     int ctas = 0;
-    for (int i = 0; i < nF; ++i) {
-        const ProbJob& P = *F[i];
-        MitmJob& m = mj[i];
+    for (int oi = 0; oi < nF; ++oi) {
+        const ProbJob& P = *F[order[oi]];
+        MitmJob& m = mj[oi];
+        int slab = (1 << P.d1) / 128;
+        if (slab > sg) slab = sg;
+        if (slab < 1) slab = 1;
         memset(&m, 0, sizeof(m));
         m.ya = P.A.ylist; m.yb = P.B.ylist;
         m.ya32 = P.A.y32; m.yb32 = P.B.y32;
@@ -808,15 +828,16 @@ cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev
         m.da = P.A.ydir; m.db = P.B.ydir;
         m.w_a = P.w_a; m.w2_a = P.w2_a; m.w_b = P.w_b; m.w2_b = P.w2_b;
         m.n_a = P.n_a; m.n_b = P.n_b; m.l_a = P.A.l; m.l_b = P.B.l;
-        m.d1 = P.d1; m.nbl = P.nbl; m.slab = P.slab; m.wf = P.wf;
+        m.d1 = P.d1; m.nbl = P.nbl; m.slab = slab; m.wf = P.wf;
         m.cta_base = ctas;
         m.W = P.W; m.W2 = P.W2; m.Wc = P.Wc;
         m.cand = P.cand; m.cap = P.cap; m.ctr = P.ctr; m.err = P.A.err;
         m.hits = P.hits; m.nhits = P.ctr + 5; m.hcap = P.hcap;          // counters[5]: fingerprint hits
-        // key-range shard: slabs [lo, hi) of this problem's (1 << d1) / slab
-        const int slabs = (1 << P.d1) / P.slab;
+        // key-range shard: slabs [lo, hi) of this problem's (1 << d1) / slab,
+        // rounded up so that shard 0 always holds slab 0 (the trivial pair)
+        const int slabs = (1 << P.d1) / slab;
         const int ns = P.nshards > 1 ? P.nshards : 1, sh = P.nshards > 1 ? P.shard : 0;
-        const int lo = (int)((int64_t)slabs * sh / ns), hi = (int)((int64_t)slabs * (sh + 1) / ns);
+        const int lo = (int)(((int64_t)slabs * sh + ns - 1) / ns), hi = (int)(((int64_t)slabs * (sh + 1) + ns - 1) / ns);
         m.c_lo = lo;
         ctas += hi - lo;
     }
