@@ -257,23 +257,28 @@ def _marshal(polys, degrees=None):
 class PendingBatch:
     """A batch queued by Context.factor_batch_async.  result() waits for it
     (rfr_batch_wait) and returns what factor_batch would have; it may be
-    called again and returns the same list."""
+    called again and returns the same list.  The result arrays the library
+    writes into are held by the context until the batch has been waited for,
+    so dropping the handle early is safe: Context.close() then waits for the
+    batch and releases what it produced."""
 
     def __init__(self, ctx, n, outs, sts, ticket):
-        self._ctx, self._n, self._outs, self._sts, self._ticket = ctx, n, outs, sts, ticket
+        self._ctx, self._n, self._ticket = ctx, n, ticket
         self._res = [] if n == 0 else None
 
     def result(self, timeout_ms: int = -1) -> List[Result]:
         if self._res is None:
+            if not self._ctx._h or self._ticket not in self._ctx._inflight:
+                raise RFRError(-1, "rfr_batch_wait: the context was closed")
             rc = lib().rfr_batch_wait(self._ctx._h, self._ticket, int(timeout_ms))
             if rc == RFR_E_TIMEOUT:
                 raise RFRError(rc, "rfr_batch_wait")
+            outs, sts, n = self._ctx._inflight.pop(self._ticket)
             if rc != RFR_OK:
-                lib().rfr_factors_free_n(self._outs, self._n)
+                lib().rfr_factors_free_n(outs, n)
                 self._res = RFRError(rc, "rfr_factor_batch_async")
             else:
-                self._res = _to_results(self._n, self._sts, self._outs)
-            self._outs = self._sts = None
+                self._res = _to_results(n, sts, outs)
         if isinstance(self._res, RFRError):
             raise self._res
         return self._res
@@ -335,11 +340,15 @@ class Context:
             raise RFRError(st, "rfr_create")
         self._h = h
         self._keep = []
+        self._inflight = {}             # ticket -> (outs, statuses, n) of batches not yet waited for
 
     def close(self):
         if getattr(self, "_h", None):
-            lib().rfr_destroy(self._h)
+            lib().rfr_destroy(self._h)      # running batches finish, queued ones are dropped
             self._h = None
+            for outs, _sts, n in self._inflight.values():
+                lib().rfr_factors_free_n(outs, n)
+            self._inflight = {}
 
     def __enter__(self):
         return self
@@ -417,6 +426,7 @@ class Context:
         rc = lib().rfr_factor_batch_async(self._h, n, ptrs, degs_c, outs, sts, C.byref(t))
         if rc != RFR_OK:
             raise RFRError(rc, "rfr_factor_batch_async")
+        self._inflight[t.value] = (outs, sts, n)
         return PendingBatch(self, n, outs, sts, t.value)
 
     def factor_batch_sharded(self, polys: Sequence[Sequence[int]], shard: int, nshards: int, gather) -> List[Result]:

@@ -323,3 +323,24 @@ def test_async_wait_unknown_ticket_and_destroy_with_queued_batches():
             assert st == [0] * n
         L.rfr_factors_free_n(outs, n)
     assert 0 <= cancelled <= 6
+
+
+def test_async_handles_dropped_or_waited_after_close():
+    """A handle dropped before its result() leaves the result arrays with the
+    context (the workers still write into them), which releases them at
+    close(); result() after close() raises instead of touching freed state."""
+    import gc
+    from paper_2410_15880_b300 import Context, RFRError
+    recs = golden("cfg2")[:10]
+    polys = [r["coeffs"] for r in recs]
+    c = Context(device=0, max_inflight=2)
+    for _ in range(4):
+        c.factor_batch_async(polys)               # handle dropped at once
+    gc.collect()
+    kept = c.factor_batch_async(polys)
+    assert [x.factors for x in kept.result()] == [r["factors"] for r in recs]
+    late = c.factor_batch_async(polys)
+    c.close()
+    with pytest.raises(RFRError):
+        late.result()
+    assert [x.factors for x in kept.result()] == [r["factors"] for r in recs]   # already taken
