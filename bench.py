@@ -388,6 +388,25 @@ def degree120_leg(ctx, flush, steps, warmup=2):
             "matches_golden": (gold is not None and res[0].ok and res[0].factors == gold)}
 
 
+def tuned_summary(path):
+    """The layouts the autotuner picked during warm-up, from its cache file:
+    per (n_a, n_b) class the fused match's key-unit size and bin limit (or the
+    table match's low-list bits, bucket digit and CTAs per SM)."""
+    picked = {}
+    try:
+        for line in open(path):
+            f = line.rstrip("\n").split("\t")[-1].split()
+            if len(f) == 7:
+                na, nb, lmax, d1o, cps, ulog, nbl = map(int, f)
+                picked[f"{na}+{nb}"] = {"unit_keys_log2": ulog, "bins_log2_max": nbl, "table_l_max": lmax,
+                                       "table_d1_off": d1o, "table_cta_per_sm": cps}
+    except OSError:
+        pass
+    return {"on": True, "knobs": "fused match: key-unit size 2^12..2^14 half-a keys, bins per unit "
+                                 "2^12..2^13; table match: low-list bits, bucket digit, CTAs per SM; "
+                                 "timed per (n_a, n_b) class during warm-up", "picked": picked}
+
+
 def sharded_leg(ctx, polys, rank, world, steps, warmup, gather, golden=None, sync=None, barrier=None):
     """Key-range shard `rank` of `world` of one batch: every rank factors the
     same polynomials, its fused matches searching only its share of the key
@@ -527,8 +546,13 @@ def main():
 
     flush = torch.empty((256 << 20,), dtype=torch.uint8, device="cuda")     # larger than L2 (126 MB)
     match_path = {"auto": 0, "tables": 1, "splat": 2, "prune": 3}[a.match_path]
+    # the tuned layouts are read back from the cache file (a fresh one unless --tune-cache names one)
+    tune_cache = a.tune_cache
+    if not tune_cache and not a.no_autotune:
+        import tempfile
+        tune_cache = os.path.join(tempfile.mkdtemp(prefix="rfr_tune_"), "tune.txt")
     with Context(device=local, timing=True, root_mode=a.root_mode, autotune=not a.no_autotune,
-                 tune_cache_path=a.tune_cache, match_path=match_path, max_inflight=max(1, a.e2e_depth)) as ctx:
+                 tune_cache_path=tune_cache, match_path=match_path, max_inflight=max(1, a.e2e_depth)) as ctx:
         for i in range(a.warmup):
             flush.fill_(i & 255)                   # the flush kernel's first use loads it (not timed)
             torch.cuda.current_stream().synchronize()
@@ -701,9 +725,7 @@ def main():
         "config": {"workload": WORKLOAD_NAME[a.config], "polys_per_step": B,
                    "half_sums_per_step": half_sums, "parallelism": f"replicas x{world}",
                    "l2": "256 MiB buffer written before every timed step (L2 flush)", "root_mode": a.root_mode,
-                   "autotune": ("off" if a.no_autotune else
-                                "on; the fused match has no layout knobs, the autotuner tunes the table match "
-                                "(which takes only halves the fused match does not)"),
+                   "autotune": "off" if a.no_autotune else tuned_summary(tune_cache),
                    "match_path": a.match_path},
         "half_sums_per_s": half_sums * world * a.steps / (ms / 1e3),
         # what a design that keeps the sorted halves in HBM would need to move for the same

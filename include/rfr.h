@@ -79,9 +79,17 @@ typedef struct {
     uint64_t max_candidates;    /* per polynomial cap on candidate patterns (after the Tr_1/Tr_2 windows) */
     double   eps_override;      /* > 0: integrality window eps (fraction of 1) replacing the derived one */
     int      use_graphs;        /* 1: replay the batch prologue (copy in, validate, roots, weights,
-                                   plans out) as a captured CUDA graph per batch size */
-    int      autotune;          /* 1: time candidate layouts (low-list bits, bucket digit, CTAs per
-                                   SM) on the first problem of each (n_a, n_b) class and keep the best */
+                                   plans out) as a captured CUDA graph per batch size (host inputs),
+                                   and the match of a sub-batch of fused-match problems (job upload,
+                                   sorted lists, k_mitm, exact re-check, compaction) as a captured
+                                   graph per launch shape, captured when a shape occurs the second
+                                   time in a pipeline; caller batches only (blocking, device and
+                                   asynchronous calls), not the batches formed from the request
+                                   queue, whose compositions rarely recur */
+    int      autotune;          /* 1: time candidate layouts on the first problem of each (n_a, n_b)
+                                   class and keep the best: for the fused match the key-unit size
+                                   (2^12 .. 2^14 half-a keys per unit) and the bin limit, for the
+                                   table match the low-list bits, bucket digit and CTAs per SM */
     const char* tune_cache_path;/* NULL, or a text file that stores tuned layouts across runs (read at
                                    create, appended when a class is tuned); the string is copied */
     int      match_path;        /* RFR_MATCH_AUTO: halves of n_b <= 13 in one shared-memory kernel,
@@ -124,6 +132,8 @@ typedef struct {
     uint64_t d2h_bytes;         /* bytes the batch copied device -> host                     */
     uint32_t launches;          /* CUDA kernels the batch launched                           */
     uint32_t batch_size;        /* polynomials in the batch                                  */
+    uint32_t graphs;            /* captured CUDA graphs the batch replayed (prologue, match)  */
+    uint32_t reserved;
 } rfr_diag;
 
 /* A factorisation: n_factors monic irreducible factors in canonical order

@@ -57,7 +57,8 @@ class Diag(C.Structure):
                 ("cand_pre", C.c_uint64), ("cand_post", C.c_uint64), ("verified", C.c_uint64),
                 ("max_rel_residual", C.c_double), ("max_root_err", C.c_double),
                 ("stage_us", C.c_double * 8), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
-                ("launches", C.c_uint32), ("batch_size", C.c_uint32)]
+                ("launches", C.c_uint32), ("batch_size", C.c_uint32), ("graphs", C.c_uint32),
+                ("reserved", C.c_uint32)]
 
 
 class Factorization(C.Structure):

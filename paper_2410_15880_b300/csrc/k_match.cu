@@ -891,7 +891,7 @@ bool match_geometry(int n_a, int n_b, uint64_t W, int ctas_a, int ctas_b, MatchG
         fuse = FUSE_AUTO;
     }
     if (optimistic && (fuse == FUSE_ALWAYS || (fuse == FUSE_AUTO && n_a >= FUSED_MIN_NA))) {
-        if (mitm_geometry(n_a, n_b, W, g)) return true;
+        if (mitm_geometry(n_a, n_b, W, g, tp)) return true;
         if (fuse == FUSE_ALWAYS) return false;
     }
     g->fused = false;

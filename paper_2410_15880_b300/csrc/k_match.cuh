@@ -3,6 +3,7 @@
 #pragma once
 #include <cstdint>
 #include <mutex>
+#include <vector>
 #include <cuda_runtime.h>
 
 namespace rfr {
@@ -125,11 +126,17 @@ struct MatchGeom {
     bool prune;             // Algorithm B: no tables at all
 };
 
-// Layout knobs chosen by the autotuner (defaults: 16, 13, 16).
+// Layout knobs chosen by the autotuner.  Table match (defaults 16, 13, 16):
+// low-list bits, bucket digit, scatter CTAs per SM.  Fused match (defaults
+// 14, 13): the key-unit size, i.e. the mean number of half-a keys a CTA
+// holds in its shared-memory table at a time (2^unit_log), and the most bins
+// per unit (2^nbl_max).
 struct TuneParams {
     int l_max = 16;          // low-list bits (sorted list Y of up to 2^l_max sums)
     int d1_off = 13;         // bucket bits d1 = n_a - d1_off (mean table-a bucket 2^d1_off)
     int cta_per_sm = 16;     // scatter CTAs per SM over a sub-batch
+    int unit_log = 14;       // fused: units of 2^unit_log half-a keys on average (12 .. 14)
+    int nbl_max = 13;        // fused: at most 2^nbl_max bins per unit (10 .. 13)
 };
 
 // Which match a problem gets: tables in device memory, or the fused match
@@ -163,7 +170,8 @@ bool match_geometry(int n_a, int n_b, uint64_t W, int ctas_a, int ctas_b, MatchG
                     bool optimistic = true, const TuneParams* tp = nullptr, int fuse = FUSE_AUTO);
 
 // Geometry of the fused match; false if the halves or the window do not fit it.
-bool mitm_geometry(int n_a, int n_b, uint64_t W, MatchGeom* g);
+// tp (optional) gives the unit size and the bin limit.
+bool mitm_geometry(int n_a, int n_b, uint64_t W, MatchGeom* g, const TuneParams* tp = nullptr);
 size_t mitm_half_bytes(int l);
 uint64_t mitm_hit_cap(const MatchGeom& g);
 void mitm_layout_half(int l, char*& p, HalfJob* h);
@@ -173,6 +181,23 @@ void mitm_layout_half(int l, char*& p, HalfJob* h);
 cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev_yjobs, cudaStream_t s,
                      cudaEvent_t ev_lists = nullptr, cudaEvent_t ev_lists2 = nullptr);
 int mitm_launches(const ProbJob* const* F, int nF);
+// run_mitm in two parts, so that the launches can be captured in a CUDA graph
+// and replayed with new job records.  mitm_prepare (host only) writes the nF
+// MitmJob records (mitm_job_bytes(nF)) to mj_host and the 2 nF list-build
+// records (mitm_yjob_bytes(nF)) to yj_host and returns the launch shape;
+// mitm_issue launches the list build, k_mitm and k_mitm_check for records
+// already at dev_mjobs / dev_yjobs.  mitm_issue allocates nothing, sets no
+// attribute and does not synchronise, so it may run under stream capture
+// (ev_flags = cudaEventRecordExternal then records the two events in the graph).
+struct MitmShape {
+    int nF = 0, nh = 0, ctas = 0, dir_lmax = 0;
+    std::vector<int> ls;    // list bits of each half in launch order (descending)
+};
+cudaError_t mitm_prepare(const ProbJob* const* F, int nF, void* mj_host, void* yj_host, MitmShape* sh);
+cudaError_t mitm_issue(const MitmShape& sh, void* dev_mjobs, void* dev_yjobs, cudaStream_t s,
+                       cudaEvent_t ev_lists, cudaEvent_t ev_lists2, unsigned ev_flags);
+size_t mitm_job_bytes(int nF);
+size_t mitm_yjob_bytes(int nF);
 
 // Bytes of one problem's buffers for geometry g (uses g.hcap).
 size_t match_bytes(const MatchGeom& g);

@@ -667,23 +667,21 @@ cudaError_t mitm_attrs() {
     });
 }
 
-// Launch the list build for the jobs d_yj[0..nh), sorted by l descending (host
-// copy yj), then the directories of the jobs that have one.
-void build_lists(const YJob* yj, int nh, YJob* d_yj, cudaStream_t s) {
+// Launch the list build for the jobs d_yj[0..nh), whose list bits, in launch
+// order, are ls[0..nh) (descending), then the directories of the lists that
+// have one and were finished in shared memory (the longest of those has
+// dir_lmax bits; 0: none).
+void build_lists(const int* ls, int nh, int dir_lmax, YJob* d_yj, cudaStream_t s) {
     k_ybuild_smem<<<nh, YS_THREADS, YS_SMEM, s>>>(d_yj);
-    for (int i = YS_LOG; i < yj[0].l; ++i) {
+    for (int i = YS_LOG; i < ls[0]; ++i) {
         int nhi = 0;
-        while (nhi < nh && yj[nhi].l > i) ++nhi;
+        while (nhi < nh && ls[nhi] > i) ++nhi;
         const int cpl = (2 << i) / YM_TILE;
         k_ysplit<<<(nhi * (cpl + 1) + 127) / 128, 128, 0, s>>>(d_yj, nhi, i, cpl);
         k_ymerge<<<nhi * cpl, YM_THREADS, YM_SMEM, s>>>(d_yj, i, cpl);
     }
-    bool dir = false;                                          // lists finished in shared memory
-    int lmax_small = 0;
-    for (int h = 0; h < nh; ++h)
-        if (yj[h].ydir && yj[h].l <= YS_LOG) { dir = true; lmax_small = std::max(lmax_small, yj[h].l); }
-    if (dir) {
-        const int bx = (int)std::min<uint64_t>(((1ull << lmax_small) + 1 + 255) / 256, 4096);
+    if (dir_lmax > 0) {
+        const int bx = (int)std::min<uint64_t>(((1ull << dir_lmax) + 1 + 255) / 256, 4096);
         k_ydir<<<dim3(bx, nh), 256, 0, s>>>(d_yj);
     }
 }
@@ -692,11 +690,14 @@ int lsplit(int h) { return h <= 10 ? h : std::max(10, h - 7); }
 
 }  // namespace
 
-bool mitm_geometry(int n_a, int n_b, uint64_t W, MatchGeom* g) {
+bool mitm_geometry(int n_a, int n_b, uint64_t W, MatchGeom* g, const TuneParams* tp) {
     if (n_a < 2 || n_b < n_a || n_b > 32) return false;
     const int la = lsplit(n_a), lb = lsplit(n_b);
     if (la > L_MAX || lb > L_MAX || (1 << (n_a - la)) > MT_RUNS || (1 << (n_b - lb)) > MT_RUNS) return false;
-    int d1 = n_a - MT_UNIT_LOG;
+    // units of 2^ulog half-a keys on average (the table holds 1.5 x 2^14), at most 2^nbl_max bins
+    const int ulog = tp ? std::min(MT_UNIT_LOG, std::max(12, tp->unit_log)) : MT_UNIT_LOG;
+    const int nbl_max = tp ? std::min(MT_NBL, std::max(10, tp->nbl_max)) : MT_NBL;
+    int d1 = n_a - ulog;
     if (d1 < 2) d1 = 2;
     const int su = 64 - d1;
     // the lists hold exact sums: the coarse window only rounds up
@@ -704,7 +705,7 @@ bool mitm_geometry(int n_a, int n_b, uint64_t W, MatchGeom* g) {
     if (wc < W) return false;
     // a key's window (positions of 2^fsh, two more for the dropped carries) must
     // stay below half a bin of 2^16 positions: bin width 2^(su - nbl) > 4 Wc
-    int nbl = MT_NBL;
+    int nbl = nbl_max;
     while (nbl >= 4 && !(wc < (1ull << (su - nbl - 2)))) --nbl;
     if (nbl < 4) return false;
     const int fsh = su - nbl - 16;
@@ -768,13 +769,16 @@ int mitm_launches(const ProbJob* const* F, int nF) {
     return nF ? 4 + 2 * std::max(0, maxl - YS_LOG) : 0;
 }
 
-cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev_yjobs, cudaStream_t s,
-                     cudaEvent_t ev_lists, cudaEvent_t ev_lists2) {
+cudaError_t mitm_prepare(const ProbJob* const* F, int nF, void* mj_host, void* yj_host, MitmShape* sh) {
     static_assert(sizeof(MitmJob) <= sizeof(ProbJob), "MitmJob must fit a ProbJob slot");
     static_assert(sizeof(YJob) <= sizeof(HalfJob), "YJob must fit a HalfJob slot");
+    sh->nF = nF;
+    sh->nh = 2 * nF;
+    sh->ctas = 0;
+    sh->dir_lmax = 0;
+    sh->ls.clear();
     if (nF <= 0) return cudaSuccess;
-    cudaError_t e;
-    e = mitm_attrs();
+    const cudaError_t e = mitm_attrs();
     if (e != cudaSuccess) return e;
     std::vector<YJob> yj;
     yj.reserve(2 * (size_t)nF);
@@ -792,12 +796,11 @@ cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev
         }
     }
     std::stable_sort(yj.begin(), yj.end(), [](const YJob& a, const YJob& b) { return a.l > b.l; });
-    YJob* d_yj = (YJob*)dev_yjobs;
-    e = cudaMemcpyAsync(d_yj, yj.data(), sizeof(YJob) * yj.size(), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return e;
-    build_lists(yj.data(), (int)yj.size(), d_yj, s);
-    if (ev_lists) cudaEventRecord(ev_lists, s);
-    if (ev_lists2) cudaEventRecord(ev_lists2, s);
+    for (const YJob& y : yj) {
+        sh->ls.push_back(y.l);
+        if (y.ydir && y.l <= YS_LOG) sh->dir_lmax = std::max(sh->dir_lmax, std::max(1, y.l));
+    }
+    memcpy(yj_host, yj.data(), sizeof(YJob) * yj.size());
     // CTAs of the costliest units first (keys per unit of both halves), so that
     // the last wave holds the cheapest ones
     std::vector<int> order(nF);
@@ -813,11 +816,11 @@ cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev
     for (int i = 0; i < nF; ++i) tot_units += std::ldexp(1.0, F[i]->d1);
     int sg = 64;
     while (sg > MT_CH && tot_units / sg < 20.0 * 148.0) sg /= 2;
-    std::vector<MitmJob> mj(nF);
+    MitmJob* mj = (MitmJob*)mj_host;
     int ctas = 0;
     for (int oi = 0; oi < nF; ++oi) {
         const ProbJob& P = *F[order[oi]];
-        MitmJob& m = mj[oi];
+        MitmJob m;
         int slab = (1 << P.d1) / 128;
         if (slab > sg) slab = sg;
         if (slab < 1) slab = 1;
@@ -836,17 +839,44 @@ cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev
         // key-range shard: slabs [lo, hi) of this problem's (1 << d1) / slab,
         // rounded up so that shard 0 always holds slab 0 (the trivial pair)
         const int slabs = (1 << P.d1) / slab;
-        const int ns = P.nshards > 1 ? P.nshards : 1, sh = P.nshards > 1 ? P.shard : 0;
-        const int lo = (int)(((int64_t)slabs * sh + ns - 1) / ns), hi = (int)(((int64_t)slabs * (sh + 1) + ns - 1) / ns);
+        const int ns = P.nshards > 1 ? P.nshards : 1, shx = P.nshards > 1 ? P.shard : 0;
+        const int lo = (int)(((int64_t)slabs * shx + ns - 1) / ns), hi = (int)(((int64_t)slabs * (shx + 1) + ns - 1) / ns);
         m.c_lo = lo;
         ctas += hi - lo;
+        memcpy(&mj[oi], &m, sizeof(m));
     }
-    MitmJob* d_mj = (MitmJob*)dev_mjobs;
-    e = cudaMemcpyAsync(d_mj, mj.data(), sizeof(MitmJob) * nF, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return e;
-    if (ctas > 0) k_mitm<<<ctas, MT_THREADS, MT_SMEM, s>>>(d_mj, nF);
-    k_mitm_check<<<nF * 64, 256, 0, s>>>(d_mj, 64);
+    sh->ctas = ctas;
+    return cudaSuccess;
+}
+
+cudaError_t mitm_issue(const MitmShape& sh, void* dev_mjobs, void* dev_yjobs, cudaStream_t s,
+                       cudaEvent_t ev_lists, cudaEvent_t ev_lists2, unsigned ev_flags) {
+    if (sh.nF <= 0) return cudaSuccess;
+    build_lists(sh.ls.data(), sh.nh, sh.dir_lmax, (YJob*)dev_yjobs, s);
+    if (ev_lists) cudaEventRecordWithFlags(ev_lists, s, ev_flags);
+    if (ev_lists2) cudaEventRecordWithFlags(ev_lists2, s, ev_flags);
+    const MitmJob* d_mj = (const MitmJob*)dev_mjobs;
+    if (sh.ctas > 0) k_mitm<<<sh.ctas, MT_THREADS, MT_SMEM, s>>>(d_mj, sh.nF);
+    k_mitm_check<<<sh.nF * 64, 256, 0, s>>>(d_mj, 64);
     return cudaGetLastError();
+}
+
+size_t mitm_job_bytes(int nF) { return (size_t)nF * sizeof(MitmJob); }
+size_t mitm_yjob_bytes(int nF) { return (size_t)2 * nF * sizeof(YJob); }
+
+cudaError_t run_mitm(const ProbJob* const* F, int nF, void* dev_mjobs, void* dev_yjobs, cudaStream_t s,
+                     cudaEvent_t ev_lists, cudaEvent_t ev_lists2) {
+    if (nF <= 0) return cudaSuccess;
+    std::vector<MitmJob> mj(nF);
+    std::vector<YJob> yj(2 * (size_t)nF);
+    MitmShape sh;
+    cudaError_t e = mitm_prepare(F, nF, mj.data(), yj.data(), &sh);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(dev_yjobs, yj.data(), sizeof(YJob) * yj.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(dev_mjobs, mj.data(), sizeof(MitmJob) * nF, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    return mitm_issue(sh, dev_mjobs, dev_yjobs, s, ev_lists, ev_lists2, cudaEventRecordDefault);
 }
 
 }  // namespace rfr
@@ -883,6 +913,6 @@ extern "C" int rfr_stage_lowlist(const uint64_t* w, int l, int negate, uint64_t*
         y.splits = (uint32_t*)p;
     }
     if (cudaMemcpyAsync(d_yj, &y, sizeof(y), cudaMemcpyHostToDevice, s) != cudaSuccess) return RFR_E_CUDA;
-    build_lists(&y, 1, d_yj, s);
+    build_lists(&y.l, 1, 0, d_yj, s);
     return cudaGetLastError() == cudaSuccess ? RFR_OK : RFR_E_CUDA;
 }

@@ -85,6 +85,38 @@ struct Item {
     rfr_factors* out;
 };
 
+// Where a sub-batch's candidates are gathered (k_compact_desc reads it from the
+// match arena, so that a captured graph needs no kernel arguments that change).
+struct CompactDesc {
+    const uint64_t* cand;             // [np][cap] per-problem candidate buffers
+    uint64_t cap;
+    const unsigned long long* ctr;    // [np][8] counters
+    int np;
+    uint64_t* out;                    // [out_cap] compacted candidates
+    uint64_t out_cap;
+    uint64_t* offs;                   // [np + 1] their offsets
+};
+
+// Match arena of a sub-batch of np problems: the compaction descriptor, np
+// ProbJob slots, 2 np HalfJob slots, the counters [np][8] and the offsets
+// [np + 1].  Everything before the offsets is uploaded from the host image in
+// one copy (the counters as zeros); the layout for np fits in the one for any
+// larger np.
+struct ArenaLayout { size_t desc, jobs, halves, ctrs, offs, upload, total; };
+static ArenaLayout arena_layout(int np) {
+    auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    ArenaLayout L;
+    size_t p = 0;
+    L.desc = p;   p += a256(sizeof(CompactDesc));
+    L.jobs = p;   p += a256((size_t)np * sizeof(ProbJob));
+    L.halves = p; p += a256((size_t)2 * np * sizeof(HalfJob));
+    L.ctrs = p;   p += (size_t)np * 64;
+    L.offs = p;   p += ((size_t)np + 1) * 8;
+    L.upload = L.offs;
+    L.total = a256(p);
+    return L;
+}
+
 // Per-problem working state inside a batch.
 struct Work {
     int item;                // index into the batch's items
@@ -137,12 +169,40 @@ struct Pipeline {
     // captured prologue graphs (copy in, validate, roots, weights, plans out) per batch shape
     struct PrologueGraph { int B; int mode; double eps; cudaGraphExec_t exec; };
     std::vector<PrologueGraph> graphs;
+    // The match arena: a sub-batch's job records, counters, candidate offsets and
+    // compaction descriptor (arena_layout), at device addresses that stay fixed
+    // until the arena is regrown, and its pinned host image.  A sub-batch of
+    // fused problems uploads its records from the image in one copy, so a
+    // captured match graph replays with new records and no parameter updates.
+    char* d_arena = nullptr;
+    char* h_arena = nullptr;
+    // captured match graphs (record upload, sorted lists, k_mitm, k_mitm_check,
+    // compaction) by launch shape; a shape is captured the second time it
+    // occurs, so that shapes that never recur cost no capture
+    struct MatchGraph { std::vector<int> key; cudaGraphExec_t exec; uint64_t used; };
+    std::vector<MatchGraph> mgraphs;
+    std::deque<std::vector<int>> mseen;
+    uint64_t mclock = 0;
+    uint32_t graph_launches = 0;      // graphs launched by the running batch
+    // match graphs for this pipeline's batches: on for caller batches (blocking,
+    // device and asynchronous calls), whose shapes recur when a workload does;
+    // off for the batches continuous batching forms from the request queue,
+    // whose compositions rarely recur
+    bool match_graphs = true;
     void drop_graphs() {
         for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
         graphs.clear();
+        for (auto& g : mgraphs) cudaGraphExecDestroy(g.exec);
+        mgraphs.clear();
+        mseen.clear();
     }
     int issue_prologue(int B, const int64_t* d_co, const int32_t* d_dg, bool copy_in,
-                       uint64_t& h2d, uint64_t& d2h, uint32_t& launches);
+                       uint64_t& h2d, uint64_t& d2h, uint32_t& launches, unsigned ev_flags = cudaEventRecordDefault);
+    // The match of a sub-batch of np fused problems whose records are in the
+    // arena's host image (layout AL, launch shape sh): a replayed graph when
+    // the shape has one, else direct launches (capturing the shape on its
+    // second occurrence).
+    int run_match_graph(const MitmShape& sh, const ArenaLayout& AL, int np);
     bool init(Ctx* c);
     void destroy();
     bool reserve(int n);
@@ -239,11 +299,12 @@ void Pipeline::destroy() {
     if (s) cudaStreamSynchronize(s);
     drop_graphs();
     auto put = [&](void* p) { if (p) ctx->alloc.put(p, 0, s); };
-    put(d_coeffs); put(d_deg); put(d_roots); put(d_radius); put(d_rstat); put(d_plans);
+    put(d_coeffs); put(d_deg); put(d_roots); put(d_radius); put(d_rstat); put(d_plans); put(d_arena);
     if (s) cudaStreamSynchronize(s);
     if (h_coeffs) cudaFreeHost(h_coeffs);
     if (h_deg) cudaFreeHost(h_deg);
     if (h_plans) cudaFreeHost(h_plans);
+    if (h_arena) cudaFreeHost(h_arena);
     if (h_stage) cudaFreeHost(h_stage);
     h_stage = nullptr;
     h_stage_cap = 0;
@@ -258,17 +319,22 @@ bool Pipeline::reserve(int n) {
     cudaStreamSynchronize(s);
     drop_graphs();                      // they name the buffers freed below
     auto put = [&](void* p) { if (p) ctx->alloc.put(p, 0, s); };
-    put(d_coeffs); put(d_deg); put(d_roots); put(d_radius); put(d_rstat); put(d_plans);
+    put(d_coeffs); put(d_deg); put(d_roots); put(d_radius); put(d_rstat); put(d_plans); put(d_arena);
     if (h_coeffs) cudaFreeHost(h_coeffs);
     if (h_deg) cudaFreeHost(h_deg);
     if (h_plans) cudaFreeHost(h_plans);
+    if (h_arena) cudaFreeHost(h_arena);
+    h_arena = nullptr;
+    const size_t abytes = arena_layout(nc).total;
+    d_arena = (char*)ctx->alloc.get(abytes, s);
     d_coeffs = (int64_t*)ctx->alloc.get((size_t)nc * LDC * 8, s);
     d_deg = (int32_t*)ctx->alloc.get((size_t)nc * 4, s);
     d_roots = (double*)ctx->alloc.get((size_t)nc * DMAX * 32, s);
     d_radius = (double*)ctx->alloc.get((size_t)nc * DMAX * 8, s);
     d_rstat = (int32_t*)ctx->alloc.get((size_t)nc * 4, s);
     d_plans = (rfr_plan*)ctx->alloc.get((size_t)nc * sizeof(rfr_plan), s);
-    bool ok = d_coeffs && d_deg && d_roots && d_radius && d_rstat && d_plans;
+    bool ok = d_coeffs && d_deg && d_roots && d_radius && d_rstat && d_plans && d_arena;
+    ok = ok && cudaMallocHost(&h_arena, abytes) == cudaSuccess;
     ok = ok && cudaMallocHost(&h_coeffs, (size_t)nc * LDC * 8) == cudaSuccess;
     ok = ok && cudaMallocHost(&h_deg, (size_t)nc * 4) == cudaSuccess;
     ok = ok && cudaMallocHost(&h_plans, (size_t)nc * sizeof(rfr_plan)) == cudaSuccess;
@@ -281,10 +347,10 @@ bool Pipeline::reserve(int n) {
 // out[offs[i] ..); offs[np] = their total.  One block (the candidates are few);
 // nothing is copied when the total exceeds out_cap (the host then copies
 // problem by problem).
-__global__ void __launch_bounds__(256) k_compact_cands(const uint64_t* __restrict__ cand, uint64_t cap,
-                                                        const unsigned long long* __restrict__ ctr, int np,
-                                                        uint64_t* __restrict__ out, uint64_t out_cap,
-                                                        uint64_t* __restrict__ offs) {
+__device__ __forceinline__ void compact_cands(const uint64_t* __restrict__ cand, uint64_t cap,
+                                              const unsigned long long* __restrict__ ctr, int np,
+                                              uint64_t* __restrict__ out, uint64_t out_cap,
+                                              uint64_t* __restrict__ offs) {
     if (threadIdx.x == 0) {
         uint64_t o = 0;
         for (int i = 0; i < np; ++i) {
@@ -300,6 +366,19 @@ __global__ void __launch_bounds__(256) k_compact_cands(const uint64_t* __restric
         const uint64_t o = offs[i], n = offs[i + 1] - o;
         for (uint64_t j = threadIdx.x; j < n; j += blockDim.x) out[o + j] = cand[(uint64_t)i * cap + j];
     }
+}
+
+__global__ void __launch_bounds__(256) k_compact_cands(const uint64_t* __restrict__ cand, uint64_t cap,
+                                                        const unsigned long long* __restrict__ ctr, int np,
+                                                        uint64_t* __restrict__ out, uint64_t out_cap,
+                                                        uint64_t* __restrict__ offs) {
+    compact_cands(cand, cap, ctr, np, out, out_cap, offs);
+}
+
+// k_compact_cands for the sub-batch described at d (in the match arena).
+__global__ void __launch_bounds__(256) k_compact_desc(const CompactDesc* __restrict__ d) {
+    const CompactDesc D = *d;
+    compact_cands(D.cand, D.cap, D.ctr, D.np, D.out, D.out_cap, D.offs);
 }
 
 static double ms_between(cudaEvent_t a, cudaEvent_t b) {
@@ -340,9 +419,9 @@ static int part_ctas(int h, double share_total_elems, int cta_per_sm = 16) {
 }
 
 int Pipeline::issue_prologue(int B, const int64_t* d_co, const int32_t* d_dg, bool copy_in,
-                             uint64_t& h2d, uint64_t& d2h, uint32_t& launches) {
+                             uint64_t& h2d, uint64_t& d2h, uint32_t& launches, unsigned ev_flags) {
     Ctx& C = *ctx;
-    cudaEventRecord(ev[0], s);
+    cudaEventRecordWithFlags(ev[0], s, ev_flags);
     int rc = RFR_OK;
     if (copy_in) {
         rc = cuda_ok(cudaMemcpyAsync(d_coeffs, h_coeffs, (size_t)B * LDC * 8, cudaMemcpyHostToDevice, s));
@@ -352,10 +431,10 @@ int Pipeline::issue_prologue(int B, const int64_t* d_co, const int32_t* d_dg, bo
     if (rc == RFR_OK) rc = rfr_stage_validate(d_co, d_dg, B, d_rstat, s);
     if (rc == RFR_OK) rc = rfr_stage_roots(d_co, d_dg, B, C.cfg.root_mode, d_roots, d_radius, d_rstat, s);
     launches += 2;
-    cudaEventRecord(ev[1], s);
+    cudaEventRecordWithFlags(ev[1], s, ev_flags);
     if (rc == RFR_OK) rc = rfr_stage_weights(d_co, d_dg, B, d_roots, d_radius, d_rstat, C.cfg.eps_override, d_plans, s);
     launches += 1;
-    cudaEventRecord(ev[2], s);
+    cudaEventRecordWithFlags(ev[2], s, ev_flags);
     if (rc == RFR_OK) rc = cuda_ok(cudaMemcpyAsync(h_plans, d_plans, (size_t)B * sizeof(rfr_plan), cudaMemcpyDeviceToHost, s));
     d2h += (uint64_t)B * sizeof(rfr_plan);
     return rc;
@@ -418,14 +497,21 @@ static double time_layout(Ctx& C, cudaStream_t s, const rfr_plan& plan, const rf
     return best;
 }
 
-// Coordinate search over the layout knobs for one (n_a, n_b) class.
+// Coordinate search over the layout knobs for one (n_a, n_b) class: the key-unit
+// size and the bin limit for the fused match, the low-list bits, bucket digit and
+// CTAs per SM for the table match.
 static TuneParams tune_class(Ctx& C, cudaStream_t s, const rfr_plan& plan, const rfr_plan* dplan,
                              cudaEvent_t e0, cudaEvent_t e1) {
     TuneParams best;
-    MatchGeom g0;
-    if (match_geometry(plan.n_a, plan.n_b, plan.window, 1, 1, &g0, true) && g0.fused) return best;   // no table knobs
     double tbest = time_layout(C, s, plan, dplan, best, e0, e1);
     if (tbest < 0) return best;
+    MatchGeom g0;
+    if (match_geometry(plan.n_a, plan.n_b, plan.window, 1, 1, &g0, true) && g0.fused) {
+        const int uvals[] = {13, 12}, bvals[] = {12};
+        for (int v : uvals) { TuneParams t = best; t.unit_log = v; double m = time_layout(C, s, plan, dplan, t, e0, e1); if (m > 0 && m < tbest) { tbest = m; best = t; } }
+        for (int v : bvals) { TuneParams t = best; t.nbl_max = v; double m = time_layout(C, s, plan, dplan, t, e0, e1); if (m > 0 && m < tbest) { tbest = m; best = t; } }
+        return best;
+    }
     const int lvals[] = {15, 17}, dvals[] = {12}, cvals[] = {8, 32};
     for (int v : lvals) { TuneParams t = best; t.l_max = v; double m = time_layout(C, s, plan, dplan, t, e0, e1); if (m > 0 && m < tbest) { tbest = m; best = t; } }
     for (int v : dvals) { TuneParams t = best; t.d1_off = v; double m = time_layout(C, s, plan, dplan, t, e0, e1); if (m > 0 && m < tbest) { tbest = m; best = t; } }
@@ -442,7 +528,8 @@ static void tune_cache_load(Ctx& C) {
         std::string dev;
         int na, nb;
         TuneParams t;
-        if (std::getline(is, dev, '\t') && dev == C.device_name && (is >> na >> nb >> t.l_max >> t.d1_off >> t.cta_per_sm))
+        if (std::getline(is, dev, '\t') && dev == C.device_name &&
+            (is >> na >> nb >> t.l_max >> t.d1_off >> t.cta_per_sm >> t.unit_log >> t.nbl_max))
             C.tuned[{na, nb}] = t;
     }
 }
@@ -450,7 +537,62 @@ static void tune_cache_load(Ctx& C) {
 static void tune_cache_store(Ctx& C, int na, int nb, const TuneParams& t) {
     if (C.tune_path.empty()) return;
     std::ofstream f(C.tune_path, std::ios::app);
-    f << C.device_name << '\t' << na << ' ' << nb << ' ' << t.l_max << ' ' << t.d1_off << ' ' << t.cta_per_sm << '\n';
+    f << C.device_name << '\t' << na << ' ' << nb << ' ' << t.l_max << ' ' << t.d1_off << ' ' << t.cta_per_sm
+      << ' ' << t.unit_log << ' ' << t.nbl_max << '\n';
+}
+
+int Pipeline::run_match_graph(const MitmShape& sh, const ArenaLayout& AL, int np) {
+    char* d = d_arena;
+    auto issue = [&](unsigned flags) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(d, h_arena, AL.upload, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = mitm_issue(sh, d + AL.jobs, d + AL.halves, s, ev[4], ev[5], flags);
+        if (e == cudaSuccess) {
+            k_compact_desc<<<1, 256, 0, s>>>((const CompactDesc*)(d + AL.desc));
+            e = cudaGetLastError();
+        }
+        return e;
+    };
+    // the launch shape: everything the graph's nodes depend on besides the
+    // arena's addresses (fixed until a regrow, which drops the graphs)
+    std::vector<int> key{np, sh.nF, sh.nh, sh.ctas, sh.dir_lmax};
+    key.insert(key.end(), sh.ls.begin(), sh.ls.end());
+    MatchGraph* g = nullptr;
+    for (auto& x : mgraphs) if (x.key == key) g = &x;
+    if (!g) {
+        auto it = std::find(mseen.begin(), mseen.end(), key);
+        if (it == mseen.end()) {                      // first occurrence: launch directly
+            mseen.push_back(key);
+            if (mseen.size() > 64) mseen.pop_front();
+            return cuda_ok(issue(cudaEventRecordDefault));
+        }
+        mseen.erase(it);
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const cudaError_t e2 = issue(cudaEventRecordExternal);
+            e = cudaStreamEndCapture(s, &graph);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {                       // not captured: launch directly
+            cudaGetLastError();
+            if (exec) cudaGraphExecDestroy(exec);
+            return cuda_ok(issue(cudaEventRecordDefault));
+        }
+        if (mgraphs.size() >= 16) {                   // evict the least recently used
+            auto lru = std::min_element(mgraphs.begin(), mgraphs.end(),
+                                        [](const MatchGraph& a, const MatchGraph& b) { return a.used < b.used; });
+            cudaGraphExecDestroy(lru->exec);
+            mgraphs.erase(lru);
+        }
+        mgraphs.push_back({key, exec, 0});
+        g = &mgraphs.back();
+    }
+    g->used = ++mclock;
+    ++graph_launches;
+    return cuda_ok(cudaGraphLaunch(g->exec, s));
 }
 
 int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int32_t* dev_deg) {
@@ -460,6 +602,7 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
     auto t_host0 = std::chrono::steady_clock::now();
     uint64_t h2d = 0, d2h = 0;
     uint32_t launches = 0;
+    graph_launches = 0;
     std::vector<Work> work;
     // ---- host-side argument checks (host inputs); device inputs are checked by K-v
     for (size_t i = 0; i < items.size(); ++i) {
@@ -511,7 +654,7 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
             cudaGraph_t graph = nullptr;
             rc = cuda_ok(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
             if (rc == RFR_OK) {
-                const int rc2 = issue_prologue(B, d_co, d_dg, true, h0, d0, l0);
+                const int rc2 = issue_prologue(B, d_co, d_dg, true, h0, d0, l0, cudaEventRecordExternal);
                 rc = cuda_ok(cudaStreamEndCapture(s, &graph));
                 if (rc == RFR_OK) rc = rc2;
             }
@@ -523,6 +666,7 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
         h2d += (uint64_t)B * LDC * 8 + (uint64_t)B * 4;
         d2h += (uint64_t)B * sizeof(rfr_plan);
         launches += 3;
+        ++graph_launches;
         rc = cuda_ok(cudaGraphLaunch(exec, s));
     } else {
         rc = issue_prologue(B, d_co, d_dg, !device_in, h2d, d2h, launches);
@@ -695,14 +839,19 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
         std::vector<HalfJob> halves(2 * np);
         char* p = ws;
         auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
-        ProbJob* d_jobs = (ProbJob*)p; p += a256(np * sizeof(ProbJob));
-        HalfJob* d_halves = (HalfJob*)p; p += a256(2 * np * sizeof(HalfJob));
-        // counters [np][8] and the compacted candidates' offsets [np + 1], copied back together
-        unsigned long long* d_ctrs = (unsigned long long*)p; p += a256((size_t)np * 64 + ((size_t)np + 1) * 8);
-        uint64_t* d_offs = (uint64_t*)(d_ctrs + 8 * (size_t)np);
+        // job records, counters [np][8] and the compacted candidates' offsets [np + 1]
+        // (copied back together) live in the match arena
+        const ArenaLayout AL = arena_layout(np);
+        ProbJob* d_jobs = (ProbJob*)(d_arena + AL.jobs);
+        HalfJob* d_halves = (HalfJob*)(d_arena + AL.halves);
+        unsigned long long* d_ctrs = (unsigned long long*)(d_arena + AL.ctrs);
+        uint64_t* d_offs = (uint64_t*)(d_arena + AL.offs);
         uint64_t* d_cands = (uint64_t*)p; p += a256((size_t)np * cap * 8);     // [np][cap]
         uint64_t* d_compact = (uint64_t*)p; p += a256((size_t)out_cap * 8);
-        cudaMemsetAsync(d_ctrs, 0, (size_t)np * 64, s);
+        bool all_fused = true;
+        for (int i = 0; i < np; ++i) all_fused = all_fused && work[sub[i]].geom.fused;
+        const bool graphed = all_fused && C.cfg.use_graphs && match_graphs;
+        if (!graphed) cudaMemsetAsync(d_ctrs, 0, (size_t)np * 64, s);
         for (int i = 0; i < np; ++i) {
             Work& w = work[sub[i]];
             ProbJob& pj = jobs[i];
@@ -729,13 +878,28 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
         }
         h2d += (uint64_t)np * sizeof(ProbJob) + 2ull * np * sizeof(HalfJob);
         cudaEventRecord(ev[3], s);
-        int nl = 0;
-        rc = cuda_ok(run_match(jobs.data(), np, d_jobs, d_halves, halves.data(), s, ev[4], ev[5], &nl));
-        launches += (uint32_t)nl;
-        if (rc == RFR_OK) {
-            k_compact_cands<<<1, 256, 0, s>>>(d_cands, cap, d_ctrs, np, d_compact, out_cap, d_offs);
-            rc = cuda_ok(cudaGetLastError());
-            launches += 1;
+        if (graphed) {
+            // fused problems only: the records, with the compaction's descriptor and
+            // zeroed counters, go up in one copy from the arena's host image, and the
+            // launch sequence is a replayed graph once its shape has recurred
+            const CompactDesc cd{d_cands, cap, d_ctrs, np, d_compact, out_cap, d_offs};
+            memcpy(h_arena + AL.desc, &cd, sizeof(cd));
+            memset(h_arena + AL.ctrs, 0, (size_t)np * 64);
+            std::vector<const ProbJob*> F(np);
+            for (int i = 0; i < np; ++i) F[i] = &jobs[i];
+            MitmShape sh;
+            rc = cuda_ok(mitm_prepare(F.data(), np, h_arena + AL.jobs, h_arena + AL.halves, &sh));
+            if (rc == RFR_OK) rc = run_match_graph(sh, AL, np);
+            launches += (uint32_t)mitm_launches(F.data(), np) + 1;
+        } else {
+            int nl = 0;
+            rc = cuda_ok(run_match(jobs.data(), np, d_jobs, d_halves, halves.data(), s, ev[4], ev[5], &nl));
+            launches += (uint32_t)nl;
+            if (rc == RFR_OK) {
+                k_compact_cands<<<1, 256, 0, s>>>(d_cands, cap, d_ctrs, np, d_compact, out_cap, d_offs);
+                rc = cuda_ok(cudaGetLastError());
+                launches += 1;
+            }
         }
         cudaEventRecord(ev[6], s);
         // counters and offsets in one copy (pinned staging when available)
@@ -966,6 +1130,7 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
         dg.stage_us[3] = t_scatter * 1e3; dg.stage_us[4] = t_match * 1e3; dg.stage_us[5] = t_verify * 1e3;
         dg.stage_us[6] = t_dev * 1e3; dg.stage_us[7] = t_host * 1e3;
         dg.h2d_bytes = h2d; dg.d2h_bytes = d2h; dg.launches = launches; dg.batch_size = (uint32_t)B;
+        dg.graphs = graph_launches;
         if (w.status != RFR_OK) it.status = w.status;
     }
     return RFR_OK;
@@ -977,6 +1142,7 @@ static void run_batch_job(Ctx* C, Pipeline* P, BatchJob* J) {
     const int n = (int)J->rows.size();
     std::vector<Item> items(n);
     for (int i = 0; i < n; ++i) items[i] = {J->rows[i], J->degrees[i], RFR_OK, &J->outs[i]};
+    P->match_graphs = true;
     const int rc = n ? P->run(items) : RFR_OK;
     for (int i = 0; i < n; ++i) {
         const int st = rc == RFR_OK ? items[i].status : rc;
@@ -1030,6 +1196,7 @@ static void worker_loop(Ctx* C, Pipeline* P) {
         std::vector<Item> items(batch.size());
         for (size_t i = 0; i < batch.size(); ++i)
             items[i] = {batch[i]->coeffs.data(), batch[i]->degree, RFR_OK, &batch[i]->result};
+        P->match_graphs = false;
         int rc = batch.empty() ? RFR_OK : P->run(items);
         {
             std::lock_guard<std::mutex> lk(C->q_mu);
@@ -1178,13 +1345,15 @@ int rfr_set_allocator(rfr_ctx* x, rfr_alloc_fn a, rfr_free_fn f, void* user) {
     auto reset = [&](Pipeline& P) {
         cudaStreamSynchronize(P.s);
         auto put = [&](void* p) { if (p) C.alloc.put(p, 0, P.s); };
-        put(P.d_coeffs); put(P.d_deg); put(P.d_roots); put(P.d_radius); put(P.d_rstat); put(P.d_plans);
+        put(P.d_coeffs); put(P.d_deg); put(P.d_roots); put(P.d_radius); put(P.d_rstat); put(P.d_plans); put(P.d_arena);
         cudaStreamSynchronize(P.s);
         P.d_coeffs = nullptr; P.d_deg = nullptr; P.d_roots = nullptr; P.d_radius = nullptr; P.d_rstat = nullptr; P.d_plans = nullptr;
+        P.d_arena = nullptr;
         if (P.h_coeffs) cudaFreeHost(P.h_coeffs);
         if (P.h_deg) cudaFreeHost(P.h_deg);
         if (P.h_plans) cudaFreeHost(P.h_plans);
-        P.h_coeffs = nullptr; P.h_deg = nullptr; P.h_plans = nullptr;
+        if (P.h_arena) cudaFreeHost(P.h_arena);
+        P.h_coeffs = nullptr; P.h_deg = nullptr; P.h_plans = nullptr; P.h_arena = nullptr;
         P.cap = 0;
         P.drop_graphs();
     };

@@ -53,7 +53,7 @@ def test_host_only_calls(L):
 def test_struct_layout(L):
     import paper_2410_15880_b300._native as N
     assert N.PLAN_DTYPE.itemsize == 2512
-    assert ctypes.sizeof(N.Config) == 72 and ctypes.sizeof(N.Diag) == 176
+    assert ctypes.sizeof(N.Config) == 72 and ctypes.sizeof(N.Diag) == 184
 
 
 def test_create_without_gpu_fails_cleanly(L):

@@ -161,9 +161,44 @@ def test_autotune_and_graphs_do_not_change_results(tmp_path):
         check_batch(c, recs)
         check_batch(c, recs)                       # second pass uses the cache and the captured graph
     lines = open(cache).read().strip().splitlines()
-    assert len(lines) >= 2 and all(len(l.split("\t")[1].split()) == 5 for l in lines)
+    assert len(lines) >= 2 and all(len(l.split("\t")[1].split()) == 7 for l in lines)
     with Context(device=0, use_graphs=False, tune_cache_path=cache) as c:
         check_batch(c, recs)
+
+
+def test_match_graph_captured_on_second_occurrence_and_replayed():
+    """A batch whose problems all take the fused match: the first call launches
+    the match directly, the second captures its launch shape as a CUDA graph,
+    the third replays it.  Every call returns the goldens with the same
+    candidate counts, the stage timings recorded by the graph's event nodes are
+    positive, and a batch of another shape in between does not disturb it."""
+    import numpy as np
+    import torch
+    from paper_2410_15880_b300 import Context
+    recs = golden("cfg3")[:3] + golden("cfg2")[:5]
+    other = golden("cfg2")[5:9]
+    arr = np.zeros((len(recs), 129), dtype=np.int64)
+    for i, r in enumerate(recs):
+        arr[i, :len(r["coeffs"])] = r["coeffs"]
+    d_co = torch.from_numpy(arr).cuda()
+    d_dg = torch.tensor([len(r["coeffs"]) - 1 for r in recs], dtype=torch.int32, device="cuda")
+    with Context(device=0, timing=True) as c:
+        runs = []
+        for k in range(3):
+            runs.append(c.factor_batch_device(d_co, d_dg))
+            if k == 1:
+                check_batch(c, other)
+    with Context(device=0, timing=True) as c:
+        host = [check_batch(c, recs) for _ in range(3)]
+    assert [runs[k][0].diag["graphs"] for k in range(3)] == [0, 1, 1]
+    assert [host[k][0].diag["graphs"] for k in range(3)] == [1, 2, 2]     # prologue graph + match graph
+    for res in runs + host:
+        assert [x.factors for x in res] == [r["factors"] for r in recs]
+        assert [x.diag["cand_post"] for x in res] == [x.diag["cand_post"] for x in runs[0]]
+    for res in (runs[2], host[2]):
+        st = res[0].diag["stage_us"]
+        assert st[2] > 0 and st[4] > 0, list(st)           # sorted lists; match (event nodes of the graph)
+    assert host[2][0].diag["stage_us"][0] > 0                # roots (event nodes of the prologue graph)
 
 
 def test_tables_only_equals_fused():
