@@ -53,10 +53,14 @@ def parse():
     ap.add_argument("--root-mode", type=int, default=1,
                     help="0 = FP64 Aberth, 1 = FP32 bulk + FP64 (default)")
     ap.add_argument("--no-autotune", action="store_true", help="use the default match layout")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch the prologue and the match directly instead of replaying captured graphs")
     ap.add_argument("--match-path", default="auto", choices=["auto", "tables", "splat", "prune"],
                     help="rfr_config.match_path: automatic choice, table match only, the splat match "
                          "(Algorithm E) or the pruned search (Algorithm B)")
     ap.add_argument("--tune-cache", default="", help="file that stores tuned match layouts")
+    ap.add_argument("--degree60-steps", type=int, default=40,
+                    help="steps of the degree-60 sub-measurement (0: skip)")
     ap.add_argument("--degree120-steps", type=int, default=5,
                     help="timed steps of the degree-120 sub-measurement (0 = skip it)")
     ap.add_argument("--e2e-depth", type=int, default=E2E_DEPTH,
@@ -388,6 +392,66 @@ def degree120_leg(ctx, flush, steps, warmup=2):
             "matches_golden": (gold is not None and res[0].ok and res[0].factors == gold)}
 
 
+def degree60_leg(ctx, flush, steps, depth, warmup=5):
+    """The degree-60 workload (50 polynomials, halves of about 2^15 + 2^16
+    half-sums) through the same context: device-resident blocking calls timed
+    like the headline, and end to end from pinned host rows with `depth`
+    asynchronous batches in flight; both checked against the goldens."""
+    import numpy as np
+    import torch
+    insts = workload("cfg2", 0, 0)
+    arr = np.zeros((len(insts), 129), dtype=np.int64)
+    for i, inst in enumerate(insts):
+        arr[i, :len(inst.coeffs)] = inst.coeffs
+    d_co = torch.from_numpy(arr).cuda()
+    d_dg = torch.tensor([inst.degree for inst in insts], dtype=torch.int32, device="cuda")
+    h_co = torch.from_numpy(arr).pin_memory().numpy()
+    h_dg = np.array([inst.degree for inst in insts], dtype=np.int32)
+    gpath = os.path.join(ROOT, "tests", "golden", "cfg2.json")
+    gold = [g["factors"] for g in json.load(open(gpath))] if os.path.exists(gpath) else None
+    for i in range(warmup):
+        ctx.factor_batch_device(d_co, d_dg)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(steps):
+        flush.fill_(i & 255)
+        torch.cuda.current_stream().synchronize()
+        res = ctx.factor_batch_device(d_co, d_dg)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    d = res[0].diag
+
+    def pipelined(n):
+        pend, last = [], None
+        for i in range(n):
+            flush.fill_(i & 255)
+            torch.cuda.current_stream().synchronize()
+            pend.append(ctx.factor_batch_async(h_co, h_dg))
+            if len(pend) == depth or i == n - 1:
+                while pend and (len(pend) == depth or i == n - 1):
+                    last = pend.pop(0).result()
+        return last
+
+    pipelined(max(3, warmup))
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    r2 = pipelined(steps)
+    t1.record()
+    torch.cuda.synchronize()
+    ms_e2e = t0.elapsed_time(t1) / steps
+    ok = gold is not None and all(r.ok and r.factors == g for r, g in zip(res, gold)) and \
+        all(r.ok and r.factors == g for r, g in zip(r2, gold))
+    return {"workload": WORKLOAD_NAME["cfg2"], "steps": steps, "polys_per_step": len(insts),
+            "polys_per_s": len(insts) * 1e3 / ms, "ms_per_step": ms,
+            "e2e": {"polys_per_s": len(insts) * 1e3 / ms_e2e, "ms_per_step": ms_e2e,
+                    "api": f"rfr_factor_batch_async + rfr_batch_wait, {depth} batches in flight"},
+            "roots_ms": d["stage_us"][0] / 1e3, "match_ms": d["stage_us"][4] / 1e3,
+            "graphs_per_step": d["graphs"], "matches_golden": ok}
+
+
 def tuned_summary(path):
     """The layouts the autotuner picked during warm-up, from its cache file:
     per (n_a, n_b) class the fused match's key-unit size and bin limit (or the
@@ -552,7 +616,8 @@ def main():
         import tempfile
         tune_cache = os.path.join(tempfile.mkdtemp(prefix="rfr_tune_"), "tune.txt")
     with Context(device=local, timing=True, root_mode=a.root_mode, autotune=not a.no_autotune,
-                 tune_cache_path=tune_cache, match_path=match_path, max_inflight=max(1, a.e2e_depth)) as ctx:
+                 tune_cache_path=tune_cache, match_path=match_path, max_inflight=max(1, a.e2e_depth),
+                 use_graphs=not a.no_graphs) as ctx:
         for i in range(a.warmup):
             flush.fill_(i & 255)                   # the flush kernel's first use loads it (not timed)
             torch.cuda.current_stream().synchronize()
@@ -642,6 +707,10 @@ def main():
         deg120 = None
         if rank == 0 and world == 1 and a.config == "cfg3" and a.degree120_steps > 0:
             deg120 = degree120_leg(ctx, flush, a.degree120_steps)
+        # ---- the degree-60 workload (rank 0, default headline workload only)
+        deg60 = None
+        if rank == 0 and world == 1 and a.config == "cfg3" and a.degree60_steps > 0:
+            deg60 = degree60_leg(ctx, flush, a.degree60_steps, depth)
         # ---- one launch per polynomial (same inputs, host buffers)
         one_ms = None
         if rank == 0:
@@ -726,6 +795,9 @@ def main():
                    "half_sums_per_step": half_sums, "parallelism": f"replicas x{world}",
                    "l2": "256 MiB buffer written before every timed step (L2 flush)", "root_mode": a.root_mode,
                    "autotune": "off" if a.no_autotune else tuned_summary(tune_cache),
+                   "graphs": ("off" if a.no_graphs else
+                              f"on: {per_step[-1]['graphs']} replayed per device-resident step "
+                              "(the fused match's launch sequence; host inputs add the prologue)"),
                    "match_path": a.match_path},
         "half_sums_per_s": half_sums * world * a.steps / (ms / 1e3),
         # what a design that keeps the sorted halves in HBM would need to move for the same
@@ -762,6 +834,8 @@ def main():
     }
     if deg120 is not None:
         line["degree120"] = deg120
+    if deg60 is not None:
+        line["degree60"] = deg60
     if a.serving_requests > 0 and world == 1:
         line["serving"] = serving_leg(local, a.serving_requests, [float(x) for x in a.serving_loads.split(",")],
                                       trace_path=a.serving_trace)
