@@ -820,16 +820,25 @@ __global__ void __launch_bounds__(SMALL_THREADS, 2) k_small(const SmallJob* __re
 static const size_t SMALL_SMEM = ((size_t)1 << SMALL_MAX_H) * 8 + (size_t)pad32(1 << SUB_BITS) * 4;
 static PerDeviceOnce g_small_attr;
 
-cudaError_t run_small(const SmallJob* jobs, int np, SmallJob* dev_jobs, cudaStream_t s) {
-    if (np <= 0) return cudaSuccess;
-    cudaError_t e = g_small_attr.run([] {
+cudaError_t small_attrs() {
+    return g_small_attr.run([] {
         return cudaFuncSetAttribute(k_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMALL_SMEM);
     });
+}
+
+cudaError_t small_issue(const SmallJob* dev_jobs, int np, cudaStream_t s) {
+    if (np <= 0) return cudaSuccess;
+    k_small<<<np, SMALL_THREADS, SMALL_SMEM, s>>>(dev_jobs, np);
+    return cudaGetLastError();
+}
+
+cudaError_t run_small(const SmallJob* jobs, int np, SmallJob* dev_jobs, cudaStream_t s) {
+    if (np <= 0) return cudaSuccess;
+    cudaError_t e = small_attrs();
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(dev_jobs, jobs, sizeof(SmallJob) * np, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
-    k_small<<<np, SMALL_THREADS, SMALL_SMEM, s>>>(dev_jobs, np);
-    return cudaGetLastError();
+    return small_issue(dev_jobs, np, s);
 }
 
 // ---------------------------------------------------------------- host side

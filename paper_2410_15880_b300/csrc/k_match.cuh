@@ -110,6 +110,11 @@ struct SmallJob {
     unsigned long long* ctr;    // [6], as ProbJob
 };
 cudaError_t run_small(const SmallJob* jobs, int np, SmallJob* dev_jobs, cudaStream_t s);
+// run_small in two parts: the kernel attribute (once per device), and the
+// launch for records already at dev_jobs (no allocation or synchronisation,
+// so it may run under stream capture).
+cudaError_t small_attrs();
+cudaError_t small_issue(const SmallJob* dev_jobs, int np, cudaStream_t s);
 
 // Host-side sizing of one problem's match.
 struct MatchGeom {

@@ -24,6 +24,7 @@
 #include <cstring>
 #include <deque>
 #include <fstream>
+#include <functional>
 #include <map>
 #include <memory>
 #include <sstream>
@@ -203,6 +204,11 @@ struct Pipeline {
     // the shape has one, else direct launches (capturing the shape on its
     // second occurrence).
     int run_match_graph(const MitmShape& sh, const ArenaLayout& AL, int np);
+    // issue(flags) under the graph of `key` (replayed if captured; captured on
+    // the key's second occurrence; else launched directly).  issue must only
+    // enqueue work on s (it may run under stream capture) and records its
+    // events with `flags`.
+    int run_graphed(const std::vector<int>& key, const std::function<cudaError_t(unsigned)>& issue);
     bool init(Ctx* c);
     void destroy();
     bool reserve(int n);
@@ -541,21 +547,7 @@ static void tune_cache_store(Ctx& C, int na, int nb, const TuneParams& t) {
       << ' ' << t.unit_log << ' ' << t.nbl_max << '\n';
 }
 
-int Pipeline::run_match_graph(const MitmShape& sh, const ArenaLayout& AL, int np) {
-    char* d = d_arena;
-    auto issue = [&](unsigned flags) -> cudaError_t {
-        cudaError_t e = cudaMemcpyAsync(d, h_arena, AL.upload, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = mitm_issue(sh, d + AL.jobs, d + AL.halves, s, ev[4], ev[5], flags);
-        if (e == cudaSuccess) {
-            k_compact_desc<<<1, 256, 0, s>>>((const CompactDesc*)(d + AL.desc));
-            e = cudaGetLastError();
-        }
-        return e;
-    };
-    // the launch shape: everything the graph's nodes depend on besides the
-    // arena's addresses (fixed until a regrow, which drops the graphs)
-    std::vector<int> key{np, sh.nF, sh.nh, sh.ctas, sh.dir_lmax};
-    key.insert(key.end(), sh.ls.begin(), sh.ls.end());
+int Pipeline::run_graphed(const std::vector<int>& key, const std::function<cudaError_t(unsigned)>& issue) {
     MatchGraph* g = nullptr;
     for (auto& x : mgraphs) if (x.key == key) g = &x;
     if (!g) {
@@ -593,6 +585,23 @@ int Pipeline::run_match_graph(const MitmShape& sh, const ArenaLayout& AL, int np
     g->used = ++mclock;
     ++graph_launches;
     return cuda_ok(cudaGraphLaunch(g->exec, s));
+}
+
+int Pipeline::run_match_graph(const MitmShape& sh, const ArenaLayout& AL, int np) {
+    char* d = d_arena;
+    // the launch shape: everything the graph's nodes depend on besides the
+    // arena's addresses (fixed until a regrow, which drops the graphs)
+    std::vector<int> key{np, sh.nF, sh.nh, sh.ctas, sh.dir_lmax};
+    key.insert(key.end(), sh.ls.begin(), sh.ls.end());
+    return run_graphed(key, [&](unsigned flags) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(d, h_arena, AL.upload, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = mitm_issue(sh, d + AL.jobs, d + AL.halves, s, ev[4], ev[5], flags);
+        if (e == cudaSuccess) {
+            k_compact_desc<<<1, 256, 0, s>>>((const CompactDesc*)(d + AL.desc));
+            e = cudaGetLastError();
+        }
+        return e;
+    });
 }
 
 int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int32_t* dev_deg) {
@@ -700,17 +709,19 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
             auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
             const uint64_t out_cap = std::min<uint64_t>((uint64_t)ns * cap, 1ull << 18);
             const size_t cb = (size_t)ns * 64 + ((size_t)ns + 1) * 8;      // counters [ns][8], offsets [ns + 1]
-            const size_t bytes = a256((size_t)ns * sizeof(SmallJob)) + a256(cb) + a256((size_t)ns * cap * 8) +
-                                 a256((size_t)out_cap * 8);
+            const size_t bytes = a256((size_t)ns * cap * 8) + a256((size_t)out_cap * 8);
             char* ws = (char*)C.alloc.get(bytes, s);
             if (!ws) return RFR_E_OOM;
-            char* p = ws;
-            SmallJob* d_sj = (SmallJob*)p; p += a256((size_t)ns * sizeof(SmallJob));
-            unsigned long long* d_ctrs = (unsigned long long*)p; p += a256(cb);
-            uint64_t* d_offs = (uint64_t*)(d_ctrs + 8 * (size_t)ns);
-            uint64_t* d_cands = (uint64_t*)p; p += a256((size_t)ns * cap * 8);
-            uint64_t* d_compact = (uint64_t*)p;
-            cudaMemsetAsync(d_ctrs, 0, (size_t)ns * 64, s);
+            // job records, counters and offsets in the match arena (SmallJob records
+            // in its ProbJob slots), candidate buffers in the workspace
+            static_assert(sizeof(SmallJob) <= sizeof(ProbJob), "a SmallJob fits a ProbJob slot");
+            const ArenaLayout AL = arena_layout(ns);
+            SmallJob* d_sj = (SmallJob*)(d_arena + AL.jobs);
+            unsigned long long* d_ctrs = (unsigned long long*)(d_arena + AL.ctrs);
+            uint64_t* d_offs = (uint64_t*)(d_arena + AL.offs);
+            uint64_t* d_cands = (uint64_t*)ws;
+            uint64_t* d_compact = (uint64_t*)(ws + a256((size_t)ns * cap * 8));
+            const bool graphed = C.cfg.use_graphs && match_graphs;
             std::vector<SmallJob> sj(ns);
             for (int i = 0; i < ns; ++i) {
                 Work& w = work[small[i]];
@@ -723,12 +734,35 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
             }
             h2d += (uint64_t)ns * sizeof(SmallJob);
             cudaEventRecord(ev[5], s);
-            rc = cuda_ok(run_small(sj.data(), ns, d_sj, s));
-            launches += 1;
-            if (rc == RFR_OK) {
-                k_compact_cands<<<1, 256, 0, s>>>(d_cands, cap, d_ctrs, ns, d_compact, out_cap, d_offs);
-                rc = cuda_ok(cudaGetLastError());
+            if (graphed) {
+                // the records, the compaction's descriptor and zeroed counters go up in
+                // one copy from the arena's host image; k_small and the compaction are a
+                // replayed graph once the batch's small-problem count has recurred
+                const CompactDesc cd{d_cands, cap, d_ctrs, ns, d_compact, out_cap, d_offs};
+                memcpy(h_arena + AL.desc, &cd, sizeof(cd));
+                memcpy(h_arena + AL.jobs, sj.data(), sizeof(SmallJob) * ns);
+                memset(h_arena + AL.ctrs, 0, (size_t)ns * 64);
+                rc = cuda_ok(small_attrs());
+                if (rc == RFR_OK)
+                    rc = run_graphed({-1, ns}, [&](unsigned) -> cudaError_t {
+                        cudaError_t e = cudaMemcpyAsync(d_arena, h_arena, AL.upload, cudaMemcpyHostToDevice, s);
+                        if (e == cudaSuccess) e = small_issue(d_sj, ns, s);
+                        if (e == cudaSuccess) {
+                            k_compact_desc<<<1, 256, 0, s>>>((const CompactDesc*)(d_arena + AL.desc));
+                            e = cudaGetLastError();
+                        }
+                        return e;
+                    });
+                launches += 2;
+            } else {
+                cudaMemsetAsync(d_ctrs, 0, (size_t)ns * 64, s);
+                rc = cuda_ok(run_small(sj.data(), ns, d_sj, s));
                 launches += 1;
+                if (rc == RFR_OK) {
+                    k_compact_cands<<<1, 256, 0, s>>>(d_cands, cap, d_ctrs, ns, d_compact, out_cap, d_offs);
+                    rc = cuda_ok(cudaGetLastError());
+                    launches += 1;
+                }
             }
             cudaEventRecord(ev[6], s);
             std::vector<uint64_t> h_ctr(cb / 8);

@@ -171,7 +171,9 @@ def test_match_graph_captured_on_second_occurrence_and_replayed():
     the match directly, the second captures its launch shape as a CUDA graph,
     the third replays it.  Every call returns the goldens with the same
     candidate counts, the stage timings recorded by the graph's event nodes are
-    positive, and a batch of another shape in between does not disturb it."""
+    positive, and a batch of another shape in between does not disturb it.
+    Small problems (the shared-memory match) are captured and replayed the
+    same way."""
     import numpy as np
     import torch
     from paper_2410_15880_b300 import Context
@@ -190,8 +192,12 @@ def test_match_graph_captured_on_second_occurrence_and_replayed():
                 check_batch(c, other)
     with Context(device=0, timing=True) as c:
         host = [check_batch(c, recs) for _ in range(3)]
+        small = golden("cfg1")
+        assert all(r["n"] - 1 <= 26 for r in small)                 # halves of <= 13: the shared-memory match
+        tiny = [check_batch(c, small) for _ in range(3)]
     assert [runs[k][0].diag["graphs"] for k in range(3)] == [0, 1, 1]
     assert [host[k][0].diag["graphs"] for k in range(3)] == [1, 2, 2]     # prologue graph + match graph
+    assert [tiny[k][0].diag["graphs"] for k in range(3)] == [1, 2, 2]     # prologue graph + k_small graph
     for res in runs + host:
         assert [x.factors for x in res] == [r["factors"] for r in recs]
         assert [x.diag["cand_post"] for x in res] == [x.diag["cand_post"] for x in runs[0]]
@@ -199,6 +205,29 @@ def test_match_graph_captured_on_second_occurrence_and_replayed():
         st = res[0].diag["stage_us"]
         assert st[2] > 0 and st[4] > 0, list(st)           # sorted lists; match (event nodes of the graph)
     assert host[2][0].diag["stage_us"][0] > 0                # roots (event nodes of the prologue graph)
+
+
+def test_every_fused_layout_the_tuner_may_keep_gives_the_same_results(tmp_path):
+    """Each fused-match layout the autotuner times (key units of 2^12, 2^13 or
+    2^14 half-a keys, at most 2^12 or 2^13 bins per unit), forced through a
+    tune cache file, returns the goldens with the same exact candidate counts
+    as the default layout: the candidates are the pairs in the window, however
+    the key space is tiled."""
+    import torch
+    from paper_2410_15880_b300 import Context
+    recs = golden("cfg3")[:4] + golden("cfg2")[:8] + golden("cfg5")
+    with Context(device=0) as c:
+        base = check_batch(c, recs)
+    classes = sorted({(x.diag["n_a"], x.diag["n_b"]) for x in base if x.diag["n_a"] >= 14})
+    assert len(classes) >= 3
+    dev = torch.cuda.get_device_name(0)
+    for ulog, nbl in [(13, 13), (12, 13), (14, 12), (12, 12)]:
+        path = tmp_path / f"tune_{ulog}_{nbl}.txt"
+        path.write_text("".join(f"{dev}\t{na} {nb} 16 13 16 {ulog} {nbl}\n" for na, nb in classes))
+        with Context(device=0, tune_cache_path=str(path)) as c:
+            res = check_batch(c, recs)
+        assert [x.diag["cand_pre"] for x in res] == [x.diag["cand_pre"] for x in base], (ulog, nbl)
+        assert [x.diag["cand_post"] for x in res] == [x.diag["cand_post"] for x in base], (ulog, nbl)
 
 
 def test_tables_only_equals_fused():
