@@ -196,6 +196,7 @@ int mitm_launches(const ProbJob* const* F, int nF);
 // (ev_flags = cudaEventRecordExternal then records the two events in the graph).
 struct MitmShape {
     int nF = 0, nh = 0, ctas = 0, dir_lmax = 0;
+    int wrap = 0;           // some problem's key positions wrap (k_mitm<true>)
     std::vector<int> ls;    // list bits of each half in launch order (descending)
 };
 cudaError_t mitm_prepare(const ProbJob* const* F, int nF, void* mj_host, void* yj_host, MitmShape* sh);

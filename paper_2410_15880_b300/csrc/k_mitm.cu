@@ -62,10 +62,6 @@ constexpr int MT_HEADS = (1 << MT_NBL) + 4;                    // bins 0 .. 2^nb
 constexpr int MT_RUNS = 128;                                   // at most 128 runs per half
 constexpr int MT_RPW = MT_RUNS / MT_WARPS;                     // runs of each half per warp
 constexpr int GL = 32 / MT_RPW;                                // lanes walking one run together
-#ifndef RFR_MT_UR
-#define RFR_MT_UR 3
-#endif
-constexpr int MT_UR = RFR_MT_UR;                               // list loads per lane and block (the next block's in flight)
 constexpr int MT_CH = 8;                                       // units whose stretches are found together
 constexpr int MT_BM_LOG = 19;                                  // occupancy bitmap: about 2^19 cells per unit
 constexpr int MT_BMW = (1 << (MT_BM_LOG - 5)) + 4;             // + margin cells (16-byte multiple)
@@ -409,6 +405,10 @@ __device__ __noinline__ void mitm_stretches(uint32_t k, int su, uint64_t Wc, int
 // its list values y, and p = y32 + (x - lo + Off) >> fsh - c, where y32 holds
 // bits fsh.. of y and c in {0, 1} is the carry out of the low fsh bits, which
 // is not computed: positions may be one low, and the window wf counts that.
+// WRAP: some problem of the launch has fsh > 32, so positions are taken modulo
+// 2^(64 - fsh) (halves of fewer than 17 elements); otherwise the 32-bit sums
+// need no mask.
+template <bool WRAP>
 __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restrict__ js, int np) {
     extern __shared__ __align__(16) unsigned char mt_sm[];
     uint32_t* E = reinterpret_cast<uint32_t*>(mt_sm);                   // [CAP] fingerprint | next slot << 16
@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
     const uint64_t Wc = P.Wc;
     const int wf = P.wf;
     const int nbins = 1 << nbl;
-    const uint32_t kmask = fsh > 32 ? (1u << (64 - fsh)) - 1u : 0xffffffffu;   // positions modulo 2^(64 - fsh)
+    const uint32_t kmask = WRAP && fsh > 32 ? (1u << (64 - fsh)) - 1u : 0xffffffffu;   // positions modulo 2^(64 - fsh)
     // cells of 2^rsh positions, wider than a key's window of 2 wf + 1
     int rsh = nbl + 16 > MT_BM_LOG ? nbl + 16 - MT_BM_LOG : 0;
     while ((1 << rsh) <= 2 * wf + 1) ++rsh;
@@ -543,25 +543,23 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
         if (gl == 0) { rsb[warp * MT_RPW + g] = sbg; rp0[warp * MT_RPW + g] = pa0; }
         // ---- table a: every key of the unit, 8 lanes per run, 4 runs per warp
         {
-            // blocks of MT_UR positions per lane; the next block's loads are issued
-            // before this block's keys are inserted
-            const uint32_t itn = (__reduce_max_sync(0xffffffffu, acnt) + GL - 1) / GL;
-            uint32_t yn[MT_UR];
+            // blocks of 32 list positions per run, four per lane read as one 16-byte
+            // load from the 16-byte aligned start a_al <= pa0 (list lengths are
+            // multiples of 4, so an aligned group never straddles the wrap); the
+            // next block's load is issued before this block's keys are inserted
+            const uint32_t a_al = pa0 & ~3u, aoff = pa0 - a_al;
+            const uint32_t itn = (__reduce_max_sync(0xffffffffu, acnt + aoff) + 31) / 32;
+            const uint4* __restrict__ Ya4 = reinterpret_cast<const uint4*>(Ya32);
+            uint4 yn = Ya4[((a_al + 4 * gl) & lma) >> 2];
+            for (uint32_t it = 0; it < itn; ++it) {
+                const uint4 yv = yn;
+                if (it + 1 < itn) yn = Ya4[((a_al + (it + 1) * 32 + 4 * gl) & lma) >> 2];
+                const uint32_t y4[4] = {yv.x, yv.y, yv.z, yv.w};
 #pragma unroll
-            for (int s = 0; s < MT_UR; ++s) yn[s] = Ya32[(pa0 + s * GL + gl) & lma];
-            for (uint32_t it = 0; it < itn; it += MT_UR) {
-                uint32_t yv[MT_UR];
-#pragma unroll
-                for (int s = 0; s < MT_UR; ++s) yv[s] = yn[s];
-                if (it + MT_UR < itn) {
-#pragma unroll
-                    for (int s = 0; s < MT_UR; ++s) yn[s] = Ya32[(pa0 + (it + MT_UR + s) * GL + gl) & lma];
-                }
-#pragma unroll
-                for (int s = 0; s < MT_UR; ++s) {
-                    const uint32_t t = (it + s) * GL + gl;
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t t = it * 32 + 4 * gl + j - aoff;     // key index in the stretch
                     if (t < acnt) {
-                        const uint32_t p = (yv[s] + apx) & kmask;
+                        const uint32_t p = (y4[j] + apx) & kmask;
                         const uint32_t slot = sbg + t;
                         const uint32_t old = atomicExch(&head[min(p >> 16, (uint32_t)nbins)], slot);
                         E[slot] = (p & 0xffffu) | (old << 16);
@@ -584,26 +582,23 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
                 bpx = (uint32_t)((wxb[g] - lo + Off) >> fsh);
             }
             const uint32_t gbits = (uint32_t)(warp + MT_WARPS * g) << lb;
-            const uint32_t itn = (__reduce_max_sync(0xffffffffu, bcnt) + GL - 1) / GL;
-            uint32_t yn[MT_UR];
+            // blocks of 32 positions per run as in table a
+            const uint32_t b_al = pb0 & ~3u, boff = pb0 - b_al;
+            const uint32_t itn = (__reduce_max_sync(0xffffffffu, bcnt + boff) + 31) / 32;
+            const uint4* __restrict__ Yb4 = reinterpret_cast<const uint4*>(Yb32);
+            uint4 yn = Yb4[((b_al + 4 * gl) & lmb) >> 2];
+            for (uint32_t it = 0; it < itn; ++it) {
+                const uint4 yv = yn;
+                if (it + 1 < itn) yn = Yb4[((b_al + (it + 1) * 32 + 4 * gl) & lmb) >> 2];
+                const uint32_t y4[4] = {yv.x, yv.y, yv.z, yv.w};
 #pragma unroll
-            for (int s = 0; s < MT_UR; ++s) yn[s] = Yb32[(pb0 + s * GL + gl) & lmb];
-            for (uint32_t it = 0; it < itn; it += MT_UR) {
-                uint32_t yv[MT_UR];
-#pragma unroll
-                for (int s = 0; s < MT_UR; ++s) yv[s] = yn[s];
-                if (it + MT_UR < itn) {
-#pragma unroll
-                    for (int s = 0; s < MT_UR; ++s) yn[s] = Yb32[(pb0 + (it + MT_UR + s) * GL + gl) & lmb];
-                }
-#pragma unroll
-                for (int s = 0; s < MT_UR; ++s) {
-                    const uint32_t t = (it + s) * GL + gl;
-                    const uint32_t p = (yv[s] + bpx) & kmask;
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t r = it * 32 + 4 * gl + j;             // index from b_al
+                    const uint32_t p = (y4[j] + bpx) & kmask;
                     const uint32_t qc = p >> rsh;
                     const uint32_t wv = bm[min(qc >> 5, (uint32_t)(MT_BMW - 1))];
-                    const bool need = t < bcnt && ((wv >> (qc & 31)) & 1u);
-                    enqueue(need, p, gbits | ((pb0 + t) & lmb));
+                    const bool need = r - boff < bcnt && ((wv >> (qc & 31)) & 1u);
+                    enqueue(need, p, gbits | ((b_al + r) & lmb));
                 }
             }
         }
@@ -662,7 +657,8 @@ cudaError_t mitm_attrs() {
     return g_mitm_attr.run([] {
         cudaError_t e = cudaFuncSetAttribute(k_ybuild_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)YS_SMEM);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ymerge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)YM_SMEM);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mitm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MT_SMEM);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mitm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MT_SMEM);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mitm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MT_SMEM);
         return e;
     });
 }
@@ -776,6 +772,7 @@ cudaError_t mitm_prepare(const ProbJob* const* F, int nF, void* mj_host, void* y
     sh->nh = 2 * nF;
     sh->ctas = 0;
     sh->dir_lmax = 0;
+    sh->wrap = 0;
     sh->ls.clear();
     if (nF <= 0) return cudaSuccess;
     const cudaError_t e = mitm_attrs();
@@ -832,6 +829,7 @@ cudaError_t mitm_prepare(const ProbJob* const* F, int nF, void* mj_host, void* y
         m.w_a = P.w_a; m.w2_a = P.w2_a; m.w_b = P.w_b; m.w2_b = P.w2_b;
         m.n_a = P.n_a; m.n_b = P.n_b; m.l_a = P.A.l; m.l_b = P.B.l;
         m.d1 = P.d1; m.nbl = P.nbl; m.slab = slab; m.wf = P.wf;
+        if ((64 - P.d1) - P.nbl - 16 > 32) sh->wrap = 1;
         m.cta_base = ctas;
         m.W = P.W; m.W2 = P.W2; m.Wc = P.Wc;
         m.cand = P.cand; m.cap = P.cap; m.ctr = P.ctr; m.err = P.A.err;
@@ -856,7 +854,10 @@ cudaError_t mitm_issue(const MitmShape& sh, void* dev_mjobs, void* dev_yjobs, cu
     if (ev_lists) cudaEventRecordWithFlags(ev_lists, s, ev_flags);
     if (ev_lists2) cudaEventRecordWithFlags(ev_lists2, s, ev_flags);
     const MitmJob* d_mj = (const MitmJob*)dev_mjobs;
-    if (sh.ctas > 0) k_mitm<<<sh.ctas, MT_THREADS, MT_SMEM, s>>>(d_mj, sh.nF);
+    if (sh.ctas > 0) {
+        if (sh.wrap) k_mitm<true><<<sh.ctas, MT_THREADS, MT_SMEM, s>>>(d_mj, sh.nF);
+        else k_mitm<false><<<sh.ctas, MT_THREADS, MT_SMEM, s>>>(d_mj, sh.nF);
+    }
     k_mitm_check<<<sh.nF * 64, 256, 0, s>>>(d_mj, 64);
     return cudaGetLastError();
 }
