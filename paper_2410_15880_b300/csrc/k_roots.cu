@@ -289,16 +289,19 @@ k_aberth(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees
 }
 
 // Steps 3 and 4 take SL = 8 lanes per root, RPC roots of one polynomial per
-// CTA: blockIdx.x = problem * (DMAX / RPC) + chunk.  A polynomial is evaluated
-// by a split Horner scheme: lane l of a root sums the B = ceil((d+1)/SL)
-// coefficients k in [lB, lB + B) as q_l(z) = sum a_k z^(k - lB) (Horner), and
-// a shuffle tree forms p(z) = sum_l z^(lB) q_l(z) with the powers z^(sB),
-// s = 1, 2, 4.  The chain is about d / SL steps plus the power's log2 B
-// squarings, and the total work stays about d steps per root.
-constexpr int RPC = 16;                       // roots per CTA (RPC * SL threads)
-constexpr int RCHUNKS = DMAX / RPC;
+// CTA: blockIdx.x = problem * (DMAX / RPC) + chunk.  Both are bound by the
+// FP64 pipe of the SMs they run on, so a small batch takes 4 roots per CTA
+// (one warp; a degree-100 polynomial spread over 25 SMs) and a large one 16.
+// A polynomial is evaluated by a split Horner scheme: lane l of a root sums
+// the B = ceil((d+1)/SL) coefficients k in [lB, lB + B) as
+// q_l(z) = sum a_k z^(k - lB) (Horner), and a shuffle tree forms
+// p(z) = sum_l z^(lB) q_l(z) with the powers z^(sB), s = 1, 2, 4.  The chain
+// is about d / SL steps plus the power's log2 B squarings, and the total work
+// stays about d steps per root.
 struct RootWarp { int prob, d, i, lane; };
+template <int RPC>
 __device__ __forceinline__ bool root_warp(const int32_t* degrees, const int32_t* status, RootWarp* r) {
+    constexpr int RCHUNKS = DMAX / RPC;
     r->prob = blockIdx.x / RCHUNKS;
     r->d = degrees[r->prob];
     r->lane = threadIdx.x % SL;
@@ -378,12 +381,13 @@ __device__ double warp_poly_r(int n, double r, Coef c) {
 
 // Kernel 2: one Newton step per root with p evaluated in double-double (the
 // correction itself in FP64), so each root becomes a DD value.
+template <int RPC>
 __global__ void __launch_bounds__(RPC * SL)
 k_polish(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees,
          const int32_t* __restrict__ status, double* __restrict__ roots) {
     __shared__ double a[DMAX + 1];
     RootWarp R;
-    if (!root_warp(degrees, status, &R)) return;              // uniform over the CTA
+    if (!root_warp<RPC>(degrees, status, &R)) return;         // uniform over the CTA
     const int d = R.d, i = R.i;
     const int64_t* c = coeffs + (size_t)R.prob * LDC;
     for (int k = threadIdx.x; k <= d; k += blockDim.x) a[k] = (double)c[k];
@@ -415,6 +419,7 @@ k_polish(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees
 
 // Kernel 3: inclusion radius r_i = d |p(z_i)| / prod_{j != i} |z_i - z_j| with
 // |p(z_i)| from a double-double evaluation plus its error bound.
+template <int RPC>
 __global__ void __launch_bounds__(RPC * SL)
 k_radius(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees,
          const int32_t* __restrict__ status, const double* __restrict__ roots,
@@ -422,7 +427,7 @@ k_radius(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees
     __shared__ double a[DMAX + 1];
     __shared__ cx<double> z[DMAX];
     RootWarp R;
-    if (!root_warp(degrees, status, &R)) return;              // uniform over the CTA
+    if (!root_warp<RPC>(degrees, status, &R)) return;         // uniform over the CTA
     const int d = R.d, i = R.i;
     const int64_t* c = coeffs + (size_t)R.prob * LDC;
     const double* Rt = roots + (size_t)R.prob * DMAX * 4;
@@ -479,7 +484,12 @@ extern "C" int rfr_stage_roots(const int64_t* coeffs, const int32_t* degrees, in
     if (batch == 0) return RFR_OK;
     cudaStream_t s = (cudaStream_t)stream;
     k_aberth<<<batch, DMAX * SL, 0, s>>>(coeffs, degrees, root_mode, roots, status);
-    k_polish<<<batch * RCHUNKS, RPC * SL, 0, s>>>(coeffs, degrees, status, roots);
-    k_radius<<<batch * RCHUNKS, RPC * SL, 0, s>>>(coeffs, degrees, status, roots, radius);
+    if (batch <= 16) {
+        k_polish<4><<<batch * (DMAX / 4), 4 * SL, 0, s>>>(coeffs, degrees, status, roots);
+        k_radius<4><<<batch * (DMAX / 4), 4 * SL, 0, s>>>(coeffs, degrees, status, roots, radius);
+    } else {
+        k_polish<16><<<batch * (DMAX / 16), 16 * SL, 0, s>>>(coeffs, degrees, status, roots);
+        k_radius<16><<<batch * (DMAX / 16), 16 * SL, 0, s>>>(coeffs, degrees, status, roots, radius);
+    }
     return cudaGetLastError() == cudaSuccess ? RFR_OK : RFR_E_CUDA;
 }

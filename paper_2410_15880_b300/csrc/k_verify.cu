@@ -15,13 +15,16 @@
 
 namespace rfr {
 
-constexpr int VW = 4;                 // warps per CTA
 constexpr int QMAX = DMAX / 2 + 1;    // coefficients of a factor of degree <= 64
 
 __device__ __forceinline__ bool patbit(uint64_t lo, uint64_t hi, int k) {
     return k < 64 ? ((lo >> k) & 1ull) : ((hi >> (k - 64)) & 1ull);
 }
 
+// VW warps (jobs) per CTA.  A job is bound by the FP64 pipe of its SM (a warp's
+// FP64 instruction occupies it for many cycles on this GPU), so a small batch
+// of jobs runs one warp per CTA, spread over the SMs.
+template <int VW>
 __global__ void __launch_bounds__(VW * 32)
 k_verify(const int64_t* __restrict__ coeffs, const double* __restrict__ roots,
          const rfr_plan* __restrict__ plans, const int32_t* __restrict__ prob,
@@ -200,6 +203,9 @@ extern "C" int rfr_stage_verify(const int64_t* coeffs, const int32_t* degrees,
     (void)degrees;
     if (jobs < 0 || !coeffs || !roots || !plans || !prob || !pat_lo || !pat_hi || !result) return RFR_E_INVALID;
     if (jobs == 0) return RFR_OK;
-    k_verify<<<(jobs + VW - 1) / VW, VW * 32, 0, (cudaStream_t)stream>>>(coeffs, roots, plans, prob, pat_lo, pat_hi, jobs, result, coeffs_out);
+    if (jobs <= 4 * 148)
+        k_verify<1><<<jobs, 32, 0, (cudaStream_t)stream>>>(coeffs, roots, plans, prob, pat_lo, pat_hi, jobs, result, coeffs_out);
+    else
+        k_verify<4><<<(jobs + 3) / 4, 128, 0, (cudaStream_t)stream>>>(coeffs, roots, plans, prob, pat_lo, pat_hi, jobs, result, coeffs_out);
     return cudaGetLastError() == cudaSuccess ? RFR_OK : RFR_E_CUDA;
 }

@@ -24,11 +24,20 @@
 
 namespace rfr {
 
+// An unsigned key with the order of the finite double x (-0 and +0 equal), so
+// the canonical order is taken with integer compares instead of FP64 ones.
+__device__ __forceinline__ unsigned long long order_key(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x + 0.0);   // -0 + 0 = +0
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
 __global__ void __launch_bounds__(DMAX)
 k_weights(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees, const double* __restrict__ roots,
           const double* __restrict__ radius, const int32_t* __restrict__ root_status,
           double eps_override, rfr_plan* __restrict__ plans) {
     __shared__ double zx[DMAX], zy[DMAX], rr[DMAX];
+    __shared__ float zxf[DMAX], zyf[DMAX], rrf[DMAX], azf[DMAX];   // FP32 copies for the disc prefilter
+    __shared__ unsigned long long kx[DMAX], ky[DMAX];              // order-preserving keys of Re z, Im z
     __shared__ int cls[DMAX];        // 0 real, 1 upper, 2 lower
     __shared__ int partner[DMAX], taken[DMAX];
     __shared__ int s_err, s_r, s_c;
@@ -54,6 +63,14 @@ k_weights(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degree
         rr[i] = radius[(size_t)prob * DMAX + i];
         taken[i] = 0;
         partner[i] = -1;
+        zxf[i] = (float)zx[i];
+        zyf[i] = (float)zy[i];
+        azf[i] = fmaxf(fabsf(zxf[i]), fabsf(zyf[i]));
+        // the radius rounded up (infinite or NaN radii stay so: they fail the prefilter)
+        const float rf = (float)rr[i];
+        rrf[i] = rf * (1.f + 0x1p-20f) + 0x1p-149f;
+        kx[i] = order_key(zx[i]);
+        ky[i] = order_key(zy[i]);
     }
     if (i == 0) { s_err = 0; s_r = 0; s_c = 0; s_e1 = 0.0; s_e2 = 0.0; s_maxr = 0.0; s_res = 0.0; }
     __syncthreads();
@@ -90,9 +107,19 @@ k_weights(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degree
         double ri = rr[i];
         bool isolated = isfinite(ri), strong = true;
         // squared distances against squared radius sums (no square roots: FP64
-        // is this part's limit; an infinite or NaN radius fails both tests)
+        // is this part's limit; an infinite or NaN radius fails both tests).
+        // An FP32 prefilter settles the pairs that are far apart: the FP32
+        // difference of the FP32 copies is within 2^-22 (|z_i| + |z_j|) (max
+        // norm) of the exact one, so when |f|^2 exceeds (s3 + that)^2 with a
+        // 2^-20 margin, the roots are certainly more than s3 >= s1 apart and
+        // both tests pass; only near pairs take the FP64 test.
+        const float rif = rrf[i], azi = azf[i], zxi = zxf[i], zyi = zyf[i];
         for (int j = 0; j < d; ++j) {
             if (j == i) continue;
+            const float fx = zxi - zxf[j], fy = zyi - zyf[j];
+            const float d2f = fx * fx + fy * fy;
+            const float b = 3.f * rif + rrf[j] + 0x1p-22f * (azi + azf[j]);
+            if (d2f > b * b * (1.f + 0x1p-20f)) continue;
             const double dx = zx[i] - zx[j], dy = zy[i] - zy[j];
             const double d2 = dx * dx + dy * dy;
             const double s1 = ri + rr[j], s3 = 3.0 * ri + rr[j];
@@ -142,8 +169,8 @@ k_weights(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degree
         for (int j = 0; j < d; ++j) {
             if (j == i || cls[j] != cls[i]) continue;
             bool before = cls[i] == 0
-                ? (zx[j] < zx[i] || (zx[j] == zx[i] && j < i))
-                : (zx[j] < zx[i] || (zx[j] == zx[i] && (zy[j] < zy[i] || (zy[j] == zy[i] && j < i))));
+                ? (kx[j] < kx[i] || (kx[j] == kx[i] && j < i))
+                : (kx[j] < kx[i] || (kx[j] == kx[i] && (ky[j] < ky[i] || (ky[j] == ky[i] && j < i))));
             rank += before;
         }
         const int k = cls[i] == 0 ? rank : r + rank;
