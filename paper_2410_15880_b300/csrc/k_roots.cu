@@ -1,8 +1,11 @@
 // k_roots.cu — K-a: batched root finder (the "black box" of Section 2).
 //
-// Three kernels: k_aberth (one CTA per polynomial, SL = 8 lanes per root,
-// d <= 128) for steps 1-2; k_polish and k_radius (SL lanes per root, the
-// polynomial split over them, spread over the whole GPU) for steps 3 and 4.
+// Kernels: k_aberth (one CTA per polynomial, SL = 8 lanes per root,
+// d <= 128) for steps 1-2 (in FP32-bulk mode only the FP32 iterations and
+// the starting points); k_aberth64 (FP32-bulk mode: the FP64 iterations, one
+// polynomial per cluster of 4 CTAs); k_polish and k_radius (SL lanes per
+// root, the polynomial split over them, spread over the whole GPU) for steps
+// 3 and 4.
 // Every evaluation of p is a split Horner scheme over the root's SL lanes:
 // the dependent chain is about d / SL steps, and a CTA holds SL times the
 // warps of one thread per root, so the iteration is not latency-bound.
@@ -23,6 +26,7 @@
 //     |p(z_i)| enlarged by the DD evaluation's error bound.  When the discs
 //     D(z_i, r_i) are pairwise disjoint each holds exactly one root of p
 //     (the Weierstrass / Braess-Hadeler inclusion theorem).
+#include <cooperative_groups.h>
 #include "rfr_device.cuh"
 
 namespace rfr {
@@ -232,15 +236,15 @@ k_aberth(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees
     // Newton polygon: upper hull of (k, log2|a_k|) over a_k != 0.  The starting
     // points only steer the iteration, so the logs are taken once, in FP32.
     __shared__ float la[DMAX + 1];
-    for (int k = threadIdx.x; k <= d; k += blockDim.x) la[k] = a[k] != 0.0 ? log2f(fabsf(af[k])) : 0.f;
+    for (int k = threadIdx.x; k <= d; k += blockDim.x) la[k] = af[k] != 0.f ? log2f(fabsf(af[k])) : 0.f;
     __syncthreads();
     if (threadIdx.x == 0) {
         int km = 0;
-        while (km < d && a[km] == 0.0) ++km;
+        while (km < d && af[km] == 0.f) ++km;          // (float)a_k is 0 exactly when a_k is
         kmin = km;
         int h = 0;
         for (int k = km; k <= d; ++k) {
-            if (a[k] == 0.0) continue;
+            if (af[k] == 0.f) continue;
             const float yk = la[k];
             while (h >= 2) {
                 const int o = hull[h - 2], q = hull[h - 1];
@@ -268,20 +272,149 @@ k_aberth(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees
     }
     __syncthreads();
 
-    bool conv;
     if (root_mode == RFR_ROOTS_FP32_BULK) {
+        // the FP32 bulk; k_aberth64 finishes in FP64 with the polynomial spread
+        // over a cluster of CTAs, and sets the status
         aberth<float>(af, d, zf, 400);
-        if (i < d && lane == 0) z[i] = cxm<double>((double)zf[i].x, (double)zf[i].y);
-        __syncthreads();
-        conv = aberth<double>(a, d, z, 200);
-    } else {
-        conv = aberth<double>(a, d, z, 600);
+        if (i < d && lane == 0) {
+            double* out = roots + ((size_t)prob * DMAX + i) * 4;
+            out[0] = (double)zf[i].x; out[1] = 0.0; out[2] = (double)zf[i].y; out[3] = 0.0;
+        }
+        return;
     }
+    const bool conv = aberth<double>(a, d, z, 600);
     if (i < d && lane == 0) {
         double* out = roots + ((size_t)prob * DMAX + i) * 4;
         out[0] = z[i].x; out[1] = 0.0; out[2] = z[i].y; out[3] = 0.0;
     }
     if (threadIdx.x == 0) {
+        const bool suspect = pre == RFR_SF_SUSPECT;
+        status[prob] = conv ? (suspect ? RFR_SF_SUSPECT : RFR_OK)
+                            : (suspect ? RFR_E_NOT_SQUAREFREE : RFR_E_NO_CONVERGENCE);
+    }
+}
+
+// Kernel 1b (FP32-bulk mode): the FP64 Aberth iterations from k_aberth's FP32
+// roots, one polynomial per cluster of AC CTAs.  The FP64 evaluations are
+// bound by the FP64 pipe of the SM they run on (B300's FP64 rate is small),
+// so the polynomial's roots are dealt out over AC SMs: CTA r of the cluster
+// owns the roots i = r (mod AC).  Every CTA keeps all approximations in its
+// shared memory, double-buffered by iteration parity: an owner writes its new
+// z_i (FP64, and an FP32 copy for the Aberth sum) into buffer it+1 of every
+// CTA of the cluster through distributed shared memory, with its CTA's
+// "still moving" flag, and one cluster barrier per iteration makes them
+// visible.  The barrier also orders buffer reuse: buffer it & 1 is written
+// again in iteration it + 2, after every CTA has passed the barrier of
+// iteration it + 1, i.e. finished reading it.  All CTAs of a cluster read the
+// same flags, so they stop at the same iteration; nothing returns early
+// inside the loop.
+constexpr int AC = 4;                         // CTAs per polynomial
+constexpr int AR = DMAX / AC;                 // roots owned per CTA
+
+__global__ void __cluster_dims__(AC, 1, 1) __launch_bounds__(AR * SL)
+k_aberth64(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees,
+           double* __restrict__ roots, int32_t* __restrict__ status, int max_iter) {
+    namespace cg = cooperative_groups;
+    __shared__ double a[DMAX + 1];
+    __shared__ cx<double> zb[2][DMAX];
+    __shared__ cx<float> zfb[2][DMAX];
+    __shared__ int flag[2][AC];
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int prob = blockIdx.x / AC;
+    const int t = threadIdx.x / SL, lane = threadIdx.x % SL;
+    const int i = rank + AC * t;                              // the root this lane works on
+    const int d = degrees[prob];
+    const int pre = status[prob];
+    // uniform over the cluster: every CTA of it leaves here, or none does
+    if (pre < 0 || d < 1 || d > DMAX) return;
+    const int64_t* c = coeffs + (size_t)prob * LDC;
+    double* R = roots + (size_t)prob * DMAX * 4;
+    for (int k = threadIdx.x; k <= d; k += blockDim.x) a[k] = (double)c[k];
+    for (int k = threadIdx.x; k < d; k += blockDim.x) {
+        zb[0][k] = cxm<double>(R[4 * k], R[4 * k + 2]);
+        zfb[0][k] = cxm<float>((float)R[4 * k], (float)R[4 * k + 2]);
+    }
+    cx<double>* zr[AC];
+    cx<float>* zfr[AC];
+#pragma unroll
+    for (int q = 0; q < AC; ++q) {
+        zr[q] = cl.map_shared_rank(&zb[0][0], q);
+        zfr[q] = cl.map_shared_rank(&zfb[0][0], q);
+    }
+    int* fr = threadIdx.x < AC ? cl.map_shared_rank(&flag[0][0], (int)threadIdx.x) : nullptr;
+    // every CTA of the cluster has started (its shared memory may be written)
+    // and has loaded its copy before the first remote store
+    cl.sync();
+    bool done = i >= d;
+    bool conv = false;
+    int cur = 0;
+    for (int it = 0; it < max_iter; ++it) {
+        const int nxt = cur ^ 1;
+        const cx<double>* z = zb[cur];
+        const cx<float>* zf = zfb[cur];
+        const cx<double> zi = i < d ? z[i] : cxm<double>(0.0, 0.0);
+        cx<double> corr = cxm<double>(0.0, 0.0);
+        const unsigned am = __ballot_sync(0xffffffffu, !done);
+        if (!done) {
+            bool noise;
+            const cx<double> N = newton_ratio<double>(am, a, d, zi, &noise);
+            // the Aberth sum in FP32 (it only steers the step, as in aberth()):
+            // differences of the FP32 copies, except for roots so close that
+            // those lose their digits, which take the FP64 difference
+            const cx<float> zif = zf[i];
+            const float azi = fabsf(zif.x) + fabsf(zif.y);
+            float sx = 0.f, sy = 0.f;
+            for (int j = lane; j < d; j += SL) {
+                if (j == i) continue;
+                float dx = zif.x - zf[j].x, dy = zif.y - zf[j].y;
+                if (fabsf(dx) + fabsf(dy) < 0x1p-12f * (azi + fabsf(zf[j].x) + fabsf(zf[j].y))) {
+                    dx = (float)(zi.x - z[j].x);
+                    dy = (float)(zi.y - z[j].y);
+                }
+                const float m = dx * dx + dy * dy;
+                if (m > 0.f) {
+                    const float r = 1.f / m;
+                    sx += dx * r;
+                    sy -= dy * r;
+                }
+            }
+            for (int o = 1; o < SL; o <<= 1) {
+                sx += __shfl_xor_sync(am, sx, o, SL);
+                sy += __shfl_xor_sync(am, sy, o, SL);
+            }
+            const cx<double> S = cxm<double>((double)sx, (double)sy);
+            const cx<double> den = cxm<double>(1.0, 0.0) - N * S;
+            const cx<float> inv = crecip_f(cxm<float>((float)den.x, (float)den.y));
+            corr = N * cxm<double>((double)inv.x, (double)inv.y);
+            if (!(cabs2(corr) < 1e60) || (inv.x == 0.f && inv.y == 0.f)) corr = N;   // degenerate: Newton step
+            const double tol = 4.0 * eps_of<double>::v;
+            if (noise || cabs2(corr) <= tol * tol * cabs2(zi)) done = true;
+        }
+        // every owned root (moving or not) goes into buffer nxt of every CTA
+        if (i < d && lane == 0) {
+            const cx<double> zn = zi - corr;
+            const cx<float> znf = cxm<float>((float)zn.x, (float)zn.y);
+#pragma unroll
+            for (int q = 0; q < AC; ++q) {
+                zr[q][nxt * DMAX + i] = zn;
+                zfr[q][nxt * DMAX + i] = znf;
+            }
+        }
+        const int moving = __syncthreads_or(!done);
+        if (threadIdx.x < AC) fr[nxt * AC + rank] = moving;
+        cl.sync();
+        int any = 0;
+#pragma unroll
+        for (int q = 0; q < AC; ++q) any |= flag[nxt][q];
+        cur = nxt;
+        if (!any) { conv = true; break; }
+    }
+    if (i < d && lane == 0) {
+        double* out = R + (size_t)i * 4;
+        out[0] = zb[cur][i].x; out[1] = 0.0; out[2] = zb[cur][i].y; out[3] = 0.0;
+    }
+    if (rank == 0 && threadIdx.x == 0) {
         const bool suspect = pre == RFR_SF_SUSPECT;
         status[prob] = conv ? (suspect ? RFR_SF_SUSPECT : RFR_OK)
                             : (suspect ? RFR_E_NOT_SQUAREFREE : RFR_E_NO_CONVERGENCE);
@@ -484,6 +617,7 @@ extern "C" int rfr_stage_roots(const int64_t* coeffs, const int32_t* degrees, in
     if (batch == 0) return RFR_OK;
     cudaStream_t s = (cudaStream_t)stream;
     k_aberth<<<batch, DMAX * SL, 0, s>>>(coeffs, degrees, root_mode, roots, status);
+    if (root_mode == RFR_ROOTS_FP32_BULK) k_aberth64<<<batch * AC, AR * SL, 0, s>>>(coeffs, degrees, roots, status, 200);
     if (batch <= 16) {
         k_polish<4><<<batch * (DMAX / 4), 4 * SL, 0, s>>>(coeffs, degrees, status, roots);
         k_radius<4><<<batch * (DMAX / 4), 4 * SL, 0, s>>>(coeffs, degrees, status, roots, radius);
