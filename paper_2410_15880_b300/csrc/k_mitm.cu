@@ -322,19 +322,6 @@ __device__ __forceinline__ uint64_t mask_sum(const uint64_t* w, uint32_t m) {
     return s;
 }
 
-// Number of list entries below v: the directory narrows the search to the
-// entries of v's bucket (about one).
-__device__ __forceinline__ uint32_t dir_lower_bound(const uint64_t* __restrict__ Y, const uint32_t* __restrict__ D,
-                                                    int l, uint64_t v) {
-    const uint32_t q = (uint32_t)(v >> (64 - l));
-    uint32_t lo = D[q], hi = D[q + 1];
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (Y[mid] < v) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
 // The table-a keys of the bins around position pb (a half-b key with pattern
 // bits mb): those within wf are fingerprint hits.  A hit's table slot e gives
 // the half-a run (the last run whose slots start at or before e) and the list
@@ -378,24 +365,59 @@ __device__ __noinline__ void mitm_stretches(uint32_t k, int su, uint64_t Wc, int
                                             const uint64_t* Ya, const uint32_t* Da, int la,
                                             const uint64_t* Yb, const uint32_t* Db, int lb,
                                             const uint64_t* wxa, const uint64_t* wxb, uint32_t* wap, uint32_t* wbp) {
+    // A lane's (up to) four look-ups run in lockstep, so that their dependent
+    // L2 loads (two directory entries, then the bucket's entries) overlap
+    // instead of queueing one look-up behind the other.
+    constexpr int NS = (MT_APOS + MT_BPOS + 31) / 32;
     const int lane = threadIdx.x & 31;
     const uint64_t U = 1ull << su;
-    for (int e = lane; e < MT_APOS + MT_BPOS; e += 32) {
+    uint64_t val[NS];
+    uint32_t lo[NS], hi[NS];
+    const uint64_t* Y[NS];
+    uint32_t* out[NS];
+#pragma unroll
+    for (int m = 0; m < NS; ++m) {
+        const int e = lane + 32 * m;
+        out[m] = nullptr;
+        Y[m] = Ya;
+        val[m] = 0;
+        lo[m] = hi[m] = 0;
         if (e < MT_APOS) {
             const int i = e / (MT_CH + 1), v = e % (MT_CH + 1);
             if (i < qa) {
-                const uint64_t val = ((uint64_t)(k + v) << su) - wxa[i];
-                wap[e] = dir_lower_bound(Ya, Da, la, val);
+                val[m] = ((uint64_t)(k + v) << su) - wxa[i];
+                const uint32_t q = (uint32_t)(val[m] >> (64 - la));
+                lo[m] = Da[q]; hi[m] = Da[q + 1];
+                out[m] = wap + e;
             }
-        } else {
+        } else if (e < MT_APOS + MT_BPOS) {
             const int e2 = e - MT_APOS, i = e2 / (2 * MT_CH), v = (e2 % (2 * MT_CH)) >> 1, side = e2 & 1;
             if (i < qb) {
                 const uint64_t l0 = (uint64_t)(k + v) << su;
-                const uint64_t val = (side ? l0 + U + Wc : l0 - Wc) - wxb[i];
-                wbp[e2] = dir_lower_bound(Yb, Db, lb, val);
+                val[m] = (side ? l0 + U + Wc : l0 - Wc) - wxb[i];
+                const uint32_t q = (uint32_t)(val[m] >> (64 - lb));
+                Y[m] = Yb;
+                lo[m] = Db[q]; hi[m] = Db[q + 1];
+                out[m] = wbp + e2;
             }
         }
     }
+    // binary search of each bucket (lower bound of val): at most 32 halvings
+    for (int step = 0; step < 32; ++step) {
+        bool any = false;
+#pragma unroll
+        for (int m = 0; m < NS; ++m) {
+            if (lo[m] < hi[m]) {
+                const uint32_t mid = (lo[m] + hi[m]) >> 1;
+                if (Y[m][mid] < val[m]) lo[m] = mid + 1; else hi[m] = mid;
+                any = true;
+            }
+        }
+        if (!any) break;
+    }
+#pragma unroll
+    for (int m = 0; m < NS; ++m)
+        if (out[m]) *out[m] = lo[m];
     __syncwarp();
 }
 
