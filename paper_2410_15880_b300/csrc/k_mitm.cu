@@ -547,6 +547,10 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
             gpre += i < g ? ci : 0u;
             wtot += ci;
         }
+        // table a's first block of positions is loaded before the barrier, so the
+        // load overlaps the barrier wait and the slot prefix sum
+        const uint32_t a_al = pa0 & ~3u, aoff = pa0 - a_al;
+        uint4 yn = reinterpret_cast<const uint4*>(Ya32)[((a_al + 4 * gl) & lma) >> 2];
         if (lane == 0) s_tot[warp] = wtot;
         __syncthreads();
         // slot base of this warp: table-a keys of the lower warps
@@ -569,10 +573,8 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
             // load from the 16-byte aligned start a_al <= pa0 (list lengths are
             // multiples of 4, so an aligned group never straddles the wrap); the
             // next block's load is issued before this block's keys are inserted
-            const uint32_t a_al = pa0 & ~3u, aoff = pa0 - a_al;
             const uint32_t itn = (__reduce_max_sync(0xffffffffu, acnt + aoff) + 31) / 32;
             const uint4* __restrict__ Ya4 = reinterpret_cast<const uint4*>(Ya32);
-            uint4 yn = Ya4[((a_al + 4 * gl) & lma) >> 2];
             for (uint32_t it = 0; it < itn; ++it) {
                 const uint4 yv = yn;
                 if (it + 1 < itn) yn = Ya4[((a_al + (it + 1) * 32 + 4 * gl) & lma) >> 2];
@@ -592,7 +594,6 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
                 }
             }
         }
-        __syncthreads();
         // ---- half b: keys in [lo - Wc, hi + Wc), each looked up in the table
         {
             uint32_t pb0 = 0, bcnt = 0, bpx = 0;
@@ -609,6 +610,9 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
             const uint32_t itn = (__reduce_max_sync(0xffffffffu, bcnt + boff) + 31) / 32;
             const uint4* __restrict__ Yb4 = reinterpret_cast<const uint4*>(Yb32);
             uint4 yn = Yb4[((b_al + 4 * gl) & lmb) >> 2];
+            // the table and bitmap are complete past this barrier; half b's stretch
+            // and first block were read before it, overlapping the wait
+            __syncthreads();
             for (uint32_t it = 0; it < itn; ++it) {
                 const uint4 yv = yn;
                 if (it + 1 < itn) yn = Yb4[((b_al + (it + 1) * 32 + 4 * gl) & lmb) >> 2];
