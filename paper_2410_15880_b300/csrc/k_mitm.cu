@@ -157,11 +157,12 @@ __global__ void __launch_bounds__(YS_THREADS) k_ybuild_smem(const YJob* __restri
 // Level i >= 13 (2^i entries -> 2^(i+1)) for every half with l > i; cpl CTAs per
 // half, each writing a tile of YM_TILE outputs.  The CTA finds where its tile
 // starts and ends on the merge path (precomputed by k_ysplit), reads the two
-// input stretches into shared memory with coalesced loads, merges them there
-// (YM_PER outputs per thread) and writes the tile back coalesced.  The last
-// level writes the list itself.
+// input stretches into shared memory with coalesced loads and merges them there,
+// YM_PER consecutive outputs per thread kept in registers (the two merge heads
+// too, so each output costs one key load) and written with 16-byte stores.  The
+// last level writes the list itself, its 32-bit positions and its directory.
 constexpr int YM_TILE = YM_THREADS * YM_PER;
-constexpr size_t YM_SMEM = (size_t)2 * YM_TILE * (8 + 4);
+constexpr size_t YM_SMEM = (size_t)YM_TILE * (8 + 4);
 
 __device__ __forceinline__ uint32_t merge_split(const uint64_t* __restrict__ K, uint32_t n, uint32_t r,
                                                 uint64_t c, uint32_t d) {
@@ -193,9 +194,7 @@ __global__ void __launch_bounds__(128) k_ysplit(const YJob* __restrict__ js, int
 __global__ void __launch_bounds__(YM_THREADS) k_ymerge(const YJob* __restrict__ js, int i, int cpl) {
     extern __shared__ __align__(16) uint64_t ym_sm[];
     uint64_t* tin = ym_sm;                        // [YM_TILE]: the stretch of K, then of the shifted copy
-    uint64_t* tout = ym_sm + YM_TILE;             // [YM_TILE]: merged tile
-    uint32_t* min_ = reinterpret_cast<uint32_t*>(ym_sm + 2 * YM_TILE);
-    uint32_t* mout = min_ + YM_TILE;
+    uint32_t* min_ = reinterpret_cast<uint32_t*>(ym_sm + YM_TILE);   // [YM_TILE]: their masks
     const YJob& J = js[blockIdx.x / cpl];
     const int c = blockIdx.x % cpl;
     const uint32_t n = 1u << i, nm = n - 1;
@@ -237,44 +236,69 @@ __global__ void __launch_bounds__(YM_THREADS) k_ymerge(const YJob* __restrict__ 
         if (A[mid] <= Bv[dl - mid - 1]) lo = mid + 1; else hi = mid;
     }
     uint32_t ia = lo, ib = dl - lo;
-    for (int q = 0; q < YM_PER; ++q) {
-        const uint64_t ka = ia < na ? A[ia] : ~0ull;
-        const uint64_t kb = ib < nb ? Bv[ib] : ~0ull;
-        const bool ta = ib >= nb || (ia < na && ka <= kb);
-        tout[dl + q] = ta ? ka : kb;
-        mout[dl + q] = ta ? min_[ia] : min_[na + ib];
-        if (ta) ++ia; else ++ib;
-    }
-    __syncthreads();
     const bool last = i == J.l - 1;
     uint64_t* KO = last ? J.ylist : J.kb[p ^ 1];
     uint32_t* MO = last ? J.ymask : J.mb[p ^ 1];
+    uint64_t ka = ia < na ? A[ia] : 0ull, kb = ib < nb ? Bv[ib] : 0ull;
     if (!(last && J.ydir)) {
+        // outputs dl .. dl + 7 straight from registers: 64 B of keys, 32 B of masks
+        uint64_t kq[YM_PER];
+        uint32_t mq[YM_PER];
 #pragma unroll
         for (int q = 0; q < YM_PER; ++q) {
-            const uint32_t j = threadIdx.x + (uint32_t)q * YM_THREADS;
-            KO[o0 + j] = tout[j];
-            MO[o0 + j] = mout[j];
+            const bool ta = ib >= nb || (ia < na && ka <= kb);
+            kq[q] = ta ? ka : kb;
+            mq[q] = ta ? min_[ia] : min_[na + ib];
+            if (ta) { ++ia; ka = ia < na ? A[ia] : 0ull; } else { ++ib; kb = ib < nb ? Bv[ib] : 0ull; }
         }
+        ulonglong2* k2 = reinterpret_cast<ulonglong2*>(KO + o0 + dl);
+#pragma unroll
+        for (int q = 0; q < YM_PER / 2; ++q) k2[q] = make_ulonglong2(kq[2 * q], kq[2 * q + 1]);
+        uint4* m4 = reinterpret_cast<uint4*>(MO + o0 + dl);
+#pragma unroll
+        for (int q = 0; q < YM_PER / 4; ++q) m4[q] = make_uint4(mq[4 * q], mq[4 * q + 1], mq[4 * q + 2], mq[4 * q + 3]);
         return;
     }
     // the last level also writes the list's directory and positions (as k_ydir does):
-    // D[q] = j for every q in (Y[j-1] >> (64-l), Y[j] >> (64-l)], the entry before the
-    // tile being the larger of the two inputs' last entries taken before it
+    // D[q] = j for every q in (Y[j-1] >> (64-l), Y[j] >> (64-l)]
     const int sh = 64 - J.l;
     const uint32_t N = 2u * n;
-    const uint64_t pa = a0 ? K[a0 - 1] : 0ull, pb = b0 ? K[(r + b0 - 1) & nm] + cs : 0ull;
-    const uint64_t prev = !a0 ? pb : (!b0 ? pa : (pa > pb ? pa : pb));
-    for (uint32_t j = threadIdx.x; j < (uint32_t)YM_TILE; j += blockDim.x) {
-        const uint32_t d = o0 + j;
-        const uint64_t v = tout[j];
-        KO[d] = v;
-        MO[d] = mout[j];
-        J.y32[d] = (uint32_t)(v >> J.fsh);
-        const uint64_t qp = d ? ((j ? tout[j - 1] : prev) >> sh) + 1 : 0ull;
-        for (uint64_t q = qp; q <= (v >> sh); ++q) J.ydir[q] = d;
+    uint64_t pv;                                  // the output before this thread's first
+    if (dl == 0) {                                // the tile's: the larger of the two inputs' last entries before it
+        const uint64_t pa = a0 ? K[a0 - 1] : 0ull, pb = b0 ? K[(r + b0 - 1) & nm] + cs : 0ull;
+        pv = !a0 ? pb : (!b0 ? pa : (pa > pb ? pa : pb));
+    } else {
+        const uint64_t xa = ia ? A[ia - 1] : 0ull, xb = ib ? Bv[ib - 1] : 0ull;
+        pv = !ia ? xb : (!ib ? xa : (xa > xb ? xa : xb));
+    }
+    uint64_t kq[YM_PER];
+    uint32_t mq[YM_PER];
+#pragma unroll
+    for (int q = 0; q < YM_PER; ++q) {
+        const bool ta = ib >= nb || (ia < na && ka <= kb);
+        kq[q] = ta ? ka : kb;
+        mq[q] = ta ? min_[ia] : min_[na + ib];
+        if (ta) { ++ia; ka = ia < na ? A[ia] : 0ull; } else { ++ib; kb = ib < nb ? Bv[ib] : 0ull; }
+    }
+    ulonglong2* k2 = reinterpret_cast<ulonglong2*>(KO + o0 + dl);
+#pragma unroll
+    for (int q = 0; q < YM_PER / 2; ++q) k2[q] = make_ulonglong2(kq[2 * q], kq[2 * q + 1]);
+    uint4* m4 = reinterpret_cast<uint4*>(MO + o0 + dl);
+    uint4* y4 = reinterpret_cast<uint4*>(J.y32 + o0 + dl);
+#pragma unroll
+    for (int q = 0; q < YM_PER / 4; ++q) {
+        m4[q] = make_uint4(mq[4 * q], mq[4 * q + 1], mq[4 * q + 2], mq[4 * q + 3]);
+        y4[q] = make_uint4((uint32_t)(kq[4 * q] >> J.fsh), (uint32_t)(kq[4 * q + 1] >> J.fsh),
+                           (uint32_t)(kq[4 * q + 2] >> J.fsh), (uint32_t)(kq[4 * q + 3] >> J.fsh));
+    }
+#pragma unroll
+    for (int q = 0; q < YM_PER; ++q) {
+        const uint32_t d = o0 + dl + q;
+        const uint64_t v = kq[q];
+        const uint64_t qp = d ? ((q ? kq[q - 1] : pv) >> sh) + 1 : 0ull;
+        for (uint64_t x = qp; x <= (v >> sh); ++x) J.ydir[x] = d;
         if (d == N - 1)
-            for (uint64_t q = (v >> sh) + 1; q <= N; ++q) J.ydir[q] = N;
+            for (uint64_t x = (v >> sh) + 1; x <= N; ++x) J.ydir[x] = N;
     }
 }
 
