@@ -607,13 +607,16 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
                 for (int j = 0; j < 4; ++j) {
                     const uint32_t t = it * 32 + 4 * gl + j - aoff;     // key index in the stretch
                     if (t < acnt) {
+                        // a key of the unit sits at p in [coff - 1, 2^(nbl+16) + coff - 1]
+                        // (coff = 2^rsh > 2 wf + 1, rsh <= 16), so p >> 16 <= nbins, p >= wf,
+                        // and (p + wf) >> (rsh + 5) < MT_BMW: the indices need no clamp
                         const uint32_t p = (y4[j] + apx) & kmask;
                         const uint32_t slot = sbg + t;
-                        const uint32_t old = atomicExch(&head[min(p >> 16, (uint32_t)nbins)], slot);
+                        const uint32_t old = atomicExch(&head[p >> 16], slot);
                         E[slot] = (p & 0xffffu) | (old << 16);
                         const uint32_t q0 = (p - (uint32_t)wf) >> rsh, q1 = (p + (uint32_t)wf) >> rsh;
-                        atomicOr(&bm[min(q0 >> 5, (uint32_t)(MT_BMW - 1))], (q1 != q0 ? 3u : 1u) << (q0 & 31));
-                        if (q1 != q0 && (q0 & 31) == 31) atomicOr(&bm[min(q1 >> 5, (uint32_t)(MT_BMW - 1))], 1u);
+                        atomicOr(&bm[q0 >> 5], (q1 != q0 ? 3u : 1u) << (q0 & 31));
+                        if (q1 != q0 && (q0 & 31) == 31) atomicOr(&bm[q1 >> 5], 1u);
                     }
                 }
             }
