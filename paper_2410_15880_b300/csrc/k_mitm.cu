@@ -758,6 +758,17 @@ bool mitm_geometry(int n_a, int n_b, uint64_t W, MatchGeom* g, const TuneParams*
     while (nbl >= 4 && !(wc < (1ull << (su - nbl - 2)))) --nbl;
     if (nbl < 4) return false;
     const int fsh = su - nbl - 16;
+    // k_mitm indexes its table heads and bitmap words from a half-a key's position
+    // p in [coff - 1, 2^(nbl+16) + coff - 1] without clamps: check those bounds
+    // for this geometry (cells of 2^rsh positions, as the kernel derives them)
+    {
+        const uint64_t wfh = (wc >> fsh) + 2;
+        int rsh = nbl + 16 > MT_BM_LOG ? nbl + 16 - MT_BM_LOG : 0;
+        while ((1ull << rsh) <= 2 * wfh + 1) ++rsh;
+        const uint64_t coff = 1ull << rsh, pmax = (1ull << (nbl + 16)) + coff - 1;
+        if ((pmax >> 16) > (1ull << nbl) || coff - 1 < wfh || ((pmax + wfh) >> rsh >> 5) >= (uint64_t)MT_BMW)
+            return false;
+    }
     const uint32_t NB = 1u << d1;
     // the slab length of a lone problem (run_mitm chooses it per launch): up to
     // MT_CH units, the stretch-search period, and at least 128 CTAs

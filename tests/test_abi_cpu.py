@@ -74,6 +74,9 @@ def test_stage_argument_checks(L):
     assert L.rfr_stage_match_fused_workspace(1, 2) == 0    # the fused match needs two elements per half
     assert L.rfr_stage_match_fused_workspace(12, 33) == 0  # and at most 32
     assert L.rfr_stage_match_fused_workspace(26, 27) > (1 << 20) * (8 + 4 + 4 + 4)   # lists, masks, directory, positions
+    # the host-side bound check of the fused geometry (k_mitm indexes its table
+    # and bitmap without clamps) accepts every pair of half sizes it takes
+    assert all(L.rfr_stage_match_fused_workspace(a, b) > 0 for a in range(2, 33) for b in range(a, 33))
     assert L.rfr_stage_splat_cells(-1) == 0 and L.rfr_stage_splat_cells(31) == 0
     assert L.rfr_stage_splat_cells(10) == (2 << 10) + 4096 + 32   # home cells, overflow cells, descriptor
     assert L.rfr_stage_splat(None, 40, None, 0, None, None) == -1
