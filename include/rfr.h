@@ -83,9 +83,9 @@ typedef struct {
                                    and the match of a sub-batch of fused-match problems (job upload,
                                    sorted lists, k_mitm, exact re-check, compaction) as a captured
                                    graph per launch shape, captured when a shape occurs the second
-                                   time in a pipeline; caller batches only (blocking, device and
-                                   asynchronous calls), not the batches formed from the request
-                                   queue, whose compositions rarely recur */
+                                   time in a pipeline; both for caller batches only (blocking,
+                                   device and asynchronous calls), not the batches formed from the
+                                   request queue, whose sizes and compositions rarely recur */
     int      autotune;          /* 1: time candidate layouts on the first problem of each (n_a, n_b)
                                    class and keep the best: for the fused match the key-unit size
                                    (2^12 .. 2^14 half-a keys per unit) and the bin limit, for the

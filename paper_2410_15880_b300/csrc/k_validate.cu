@@ -64,7 +64,9 @@ __device__ bool coprime_mod(const int64_t* c, int d, uint64_t* a, uint64_t* b, i
     uint64_t* A = a;
     uint64_t* B = b;
     while (db > 0) {
-        // A <- A mod B by pseudo-division
+        // A <- A mod B by pseudo-division; every thread then finds the new degree
+        // itself (the leading term is cancelled, and lower ones vanish only by
+        // chance), so a step takes two barriers
         while (da >= db) {
             const uint64_t la = A[da], lb = B[db];
             const int sh = da - db;
@@ -72,18 +74,17 @@ __device__ bool coprime_mod(const int64_t* c, int d, uint64_t* a, uint64_t* b, i
             const int k = t;
             if (k <= da) {
                 v = F::mul(lb, A[k]);
-                if (k >= sh && k - sh <= db) v = (v + L - F::mul(la, B[k - sh])) % L;
+                if (k >= sh && k - sh <= db) {
+                    v += L - F::mul(la, B[k - sh]);          // both terms below L: one subtraction reduces
+                    if (v >= L) v -= L;
+                }
             }
             __syncthreads();
             if (k <= da) A[k] = v;
             __syncthreads();
-            if (t == 0) {
-                int nd = da - 1;
-                while (nd >= 0 && A[nd] == 0) --nd;
-                s_deg[0] = nd;
-            }
-            __syncthreads();
-            da = s_deg[0];
+            int nd = da - 1;
+            while (nd >= 0 && A[nd] == 0) --nd;
+            da = nd;
         }
         // swap roles
         uint64_t* T = A; A = B; B = T;

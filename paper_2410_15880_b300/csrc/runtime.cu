@@ -185,10 +185,10 @@ struct Pipeline {
     std::deque<std::vector<int>> mseen;
     uint64_t mclock = 0;
     uint32_t graph_launches = 0;      // graphs launched by the running batch
-    // match graphs for this pipeline's batches: on for caller batches (blocking,
-    // device and asynchronous calls), whose shapes recur when a workload does;
-    // off for the batches continuous batching forms from the request queue,
-    // whose compositions rarely recur
+    // graphs (prologue and match) for this pipeline's batches: on for caller
+    // batches (blocking, device and asynchronous calls), whose shapes recur when
+    // a workload does; off for the batches continuous batching forms from the
+    // request queue, whose sizes and compositions rarely recur
     bool match_graphs = true;
     void drop_graphs() {
         for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
@@ -652,8 +652,10 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
     }
     cur_coeffs = d_co;
     cur_deg = d_dg;
-    if (!device_in && C.cfg.use_graphs) {
+    if (!device_in && C.cfg.use_graphs && match_graphs) {
         // the prologue's shape depends only on B and the root settings: replay a captured graph
+        // (caller batches only: the request queue forms batches of every size, and a capture
+        // per size costs more than the launches it saves)
         cudaGraphExec_t exec = nullptr;
         for (auto& g : graphs)
             if (g.B == B && g.mode == C.cfg.root_mode && g.eps == C.cfg.eps_override) exec = g.exec;
