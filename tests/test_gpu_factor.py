@@ -96,6 +96,8 @@ def test_serving_alone_and_in_mix():
         alone = srv.factor(recs[5]["coeffs"])
     for r, x in zip(recs, out):
         assert x.ok and x.factors == r["factors"], r["name"]
+    # batches formed from the request queue launch directly: no graph is captured on the request path
+    assert all(x.diag["graphs"] == 0 for x in out)
     mixed = out[5]
     assert alone.factors == mixed.factors
     assert alone.diag["n"] == mixed.diag["n"] and alone.diag["window"] == mixed.diag["window"]
