@@ -196,7 +196,8 @@ int mitm_launches(const ProbJob* const* F, int nF);
 // (ev_flags = cudaEventRecordExternal then records the two events in the graph).
 struct MitmShape {
     int nF = 0, nh = 0, ctas = 0, dir_lmax = 0;
-    int wrap = 0;           // some problem's key positions wrap (k_mitm<true>)
+    int wrap = 0;           // some problem's key positions wrap (k_mitm<true, .>)
+    int wide = 0;           // some problem's position lists exceed 32 MB: 16-byte position loads
     std::vector<int> ls;    // list bits of each half in launch order (descending)
 };
 cudaError_t mitm_prepare(const ProbJob* const* F, int nF, void* mj_host, void* yj_host, MitmShape* sh);

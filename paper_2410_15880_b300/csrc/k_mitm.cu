@@ -451,10 +451,30 @@ __device__ __noinline__ void mitm_stretches(uint32_t k, int su, uint64_t Wc, int
 // its list values y, and p = y32 + (x - lo + Off) >> fsh - c, where y32 holds
 // bits fsh.. of y and c in {0, 1} is the carry out of the low fsh bits, which
 // is not computed: positions may be one low, and the window wf counts that.
+// PV list positions read per lane with one load (8 or 16 bytes), so a run's
+// keys go in blocks of GL * PV from the PV-aligned start of its stretch (list
+// lengths are powers of two, so an aligned group never straddles the wrap).
+template <int PV> struct PosVec;
+template <> struct PosVec<2> {
+    __device__ __forceinline__ static void load(const uint32_t* y, uint32_t i, uint32_t (&v)[2]) {
+        const uint2 t = reinterpret_cast<const uint2*>(y)[i >> 1];
+        v[0] = t.x; v[1] = t.y;
+    }
+};
+template <> struct PosVec<4> {
+    __device__ __forceinline__ static void load(const uint32_t* y, uint32_t i, uint32_t (&v)[4]) {
+        const uint4 t = reinterpret_cast<const uint4*>(y)[i >> 2];
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+};
+
 // WRAP: some problem of the launch has fsh > 32, so positions are taken modulo
 // 2^(64 - fsh) (halves of fewer than 17 elements); otherwise the 32-bit sums
 // need no mask.
-template <bool WRAP>
+// PV: positions per lane and load (PosVec): 2 while the launch's lists stay in
+// L2 (finer blocks, fewer idle lanes at the end of a stretch), 4 when they
+// stream from DRAM (whole 128-byte lines per group of lanes).
+template <bool WRAP, int PV>
 __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restrict__ js, int np) {
     extern __shared__ __align__(16) unsigned char mt_sm[];
     uint32_t* E = reinterpret_cast<uint32_t*>(mt_sm);                   // [CAP] fingerprint | next slot << 16
@@ -573,8 +593,10 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
         }
         // table a's first block of positions is loaded before the barrier, so the
         // load overlaps the barrier wait and the slot prefix sum
-        const uint32_t a_al = pa0 & ~3u, aoff = pa0 - a_al;
-        uint4 yn = reinterpret_cast<const uint4*>(Ya32)[((a_al + 4 * gl) & lma) >> 2];
+        constexpr uint32_t BS = GL * PV;                              // keys of a run per block
+        const uint32_t a_al = pa0 & ~(uint32_t)(PV - 1), aoff = pa0 - a_al;
+        uint32_t yn[PV];
+        PosVec<PV>::load(Ya32, (a_al + PV * gl) & lma, yn);
         if (lane == 0) s_tot[warp] = wtot;
         __syncthreads();
         // slot base of this warp: table-a keys of the lower warps
@@ -593,19 +615,18 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
         if (gl == 0) { rsb[warp * MT_RPW + g] = sbg; rp0[warp * MT_RPW + g] = pa0; }
         // ---- table a: every key of the unit, 8 lanes per run, 4 runs per warp
         {
-            // blocks of 32 list positions per run, four per lane read as one 16-byte
-            // load from the 16-byte aligned start a_al <= pa0 (list lengths are
-            // multiples of 4, so an aligned group never straddles the wrap); the
-            // next block's load is issued before this block's keys are inserted
-            const uint32_t itn = (__reduce_max_sync(0xffffffffu, acnt + aoff) + 31) / 32;
-            const uint4* __restrict__ Ya4 = reinterpret_cast<const uint4*>(Ya32);
+            // blocks of BS list positions per run, PV per lane read with one load
+            // from the aligned start a_al <= pa0; the next block's load is issued
+            // before this block's keys are inserted
+            const uint32_t itn = (__reduce_max_sync(0xffffffffu, acnt + aoff) + BS - 1) / BS;
             for (uint32_t it = 0; it < itn; ++it) {
-                const uint4 yv = yn;
-                if (it + 1 < itn) yn = Ya4[((a_al + (it + 1) * 32 + 4 * gl) & lma) >> 2];
-                const uint32_t y4[4] = {yv.x, yv.y, yv.z, yv.w};
+                uint32_t y4[PV];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const uint32_t t = it * 32 + 4 * gl + j - aoff;     // key index in the stretch
+                for (int j = 0; j < PV; ++j) y4[j] = yn[j];
+                if (it + 1 < itn) PosVec<PV>::load(Ya32, (a_al + (it + 1) * BS + PV * gl) & lma, yn);
+#pragma unroll
+                for (int j = 0; j < PV; ++j) {
+                    const uint32_t t = it * BS + PV * gl + j - aoff;     // key index in the stretch
                     if (t < acnt) {
                         // a key of the unit sits at p in [coff - 1, 2^(nbl+16) + coff - 1]
                         // (coff = 2^rsh > 2 wf + 1, rsh <= 16), so p >> 16 <= nbins, p >= wf,
@@ -632,21 +653,22 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_mitm(const MitmJob* __restric
                 bpx = (uint32_t)((wxb[g] - lo + Off) >> fsh);
             }
             const uint32_t gbits = (uint32_t)(warp + MT_WARPS * g) << lb;
-            // blocks of 32 positions per run as in table a
-            const uint32_t b_al = pb0 & ~3u, boff = pb0 - b_al;
-            const uint32_t itn = (__reduce_max_sync(0xffffffffu, bcnt + boff) + 31) / 32;
-            const uint4* __restrict__ Yb4 = reinterpret_cast<const uint4*>(Yb32);
-            uint4 yn = Yb4[((b_al + 4 * gl) & lmb) >> 2];
+            // blocks of BS positions per run as in table a
+            const uint32_t b_al = pb0 & ~(uint32_t)(PV - 1), boff = pb0 - b_al;
+            const uint32_t itn = (__reduce_max_sync(0xffffffffu, bcnt + boff) + BS - 1) / BS;
+            uint32_t yn[PV];
+            PosVec<PV>::load(Yb32, (b_al + PV * gl) & lmb, yn);
             // the table and bitmap are complete past this barrier; half b's stretch
             // and first block were read before it, overlapping the wait
             __syncthreads();
             for (uint32_t it = 0; it < itn; ++it) {
-                const uint4 yv = yn;
-                if (it + 1 < itn) yn = Yb4[((b_al + (it + 1) * 32 + 4 * gl) & lmb) >> 2];
-                const uint32_t y4[4] = {yv.x, yv.y, yv.z, yv.w};
+                uint32_t y4[PV];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const uint32_t r = it * 32 + 4 * gl + j;             // index from b_al
+                for (int j = 0; j < PV; ++j) y4[j] = yn[j];
+                if (it + 1 < itn) PosVec<PV>::load(Yb32, (b_al + (it + 1) * BS + PV * gl) & lmb, yn);
+#pragma unroll
+                for (int j = 0; j < PV; ++j) {
+                    const uint32_t r = it * BS + PV * gl + j;            // index from b_al
                     const uint32_t p = (y4[j] + bpx) & kmask;
                     const uint32_t qc = p >> rsh;
                     const uint32_t wv = bm[min(qc >> 5, (uint32_t)(MT_BMW - 1))];
@@ -710,8 +732,10 @@ cudaError_t mitm_attrs() {
     return g_mitm_attr.run([] {
         cudaError_t e = cudaFuncSetAttribute(k_ybuild_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)YS_SMEM);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ymerge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)YM_SMEM);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mitm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MT_SMEM);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mitm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MT_SMEM);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mitm<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MT_SMEM);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mitm<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MT_SMEM);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mitm<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MT_SMEM);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mitm<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MT_SMEM);
         return e;
     });
 }
@@ -837,6 +861,7 @@ cudaError_t mitm_prepare(const ProbJob* const* F, int nF, void* mj_host, void* y
     sh->ctas = 0;
     sh->dir_lmax = 0;
     sh->wrap = 0;
+    sh->wide = 0;
     sh->ls.clear();
     if (nF <= 0) return cudaSuccess;
     const cudaError_t e = mitm_attrs();
@@ -894,6 +919,8 @@ cudaError_t mitm_prepare(const ProbJob* const* F, int nF, void* mj_host, void* y
         m.n_a = P.n_a; m.n_b = P.n_b; m.l_a = P.A.l; m.l_b = P.B.l;
         m.d1 = P.d1; m.nbl = P.nbl; m.slab = slab; m.wf = P.wf;
         if ((64 - P.d1) - P.nbl - 16 > 32) sh->wrap = 1;
+        // position lists of more than 32 MB per problem stream from DRAM: 16-byte loads
+        if ((((size_t)1 << P.A.l) + ((size_t)1 << P.B.l)) * 4 > ((size_t)32 << 20)) sh->wide = 1;
         m.cta_base = ctas;
         m.W = P.W; m.W2 = P.W2; m.Wc = P.Wc;
         m.cand = P.cand; m.cap = P.cap; m.ctr = P.ctr; m.err = P.A.err;
@@ -919,8 +946,13 @@ cudaError_t mitm_issue(const MitmShape& sh, void* dev_mjobs, void* dev_yjobs, cu
     if (ev_lists2) cudaEventRecordWithFlags(ev_lists2, s, ev_flags);
     const MitmJob* d_mj = (const MitmJob*)dev_mjobs;
     if (sh.ctas > 0) {
-        if (sh.wrap) k_mitm<true><<<sh.ctas, MT_THREADS, MT_SMEM, s>>>(d_mj, sh.nF);
-        else k_mitm<false><<<sh.ctas, MT_THREADS, MT_SMEM, s>>>(d_mj, sh.nF);
+        if (sh.wide) {
+            if (sh.wrap) k_mitm<true, 4><<<sh.ctas, MT_THREADS, MT_SMEM, s>>>(d_mj, sh.nF);
+            else k_mitm<false, 4><<<sh.ctas, MT_THREADS, MT_SMEM, s>>>(d_mj, sh.nF);
+        } else {
+            if (sh.wrap) k_mitm<true, 2><<<sh.ctas, MT_THREADS, MT_SMEM, s>>>(d_mj, sh.nF);
+            else k_mitm<false, 2><<<sh.ctas, MT_THREADS, MT_SMEM, s>>>(d_mj, sh.nF);
+        }
     }
     k_mitm_check<<<sh.nF * 64, 256, 0, s>>>(d_mj, 64);
     return cudaGetLastError();

@@ -591,7 +591,7 @@ int Pipeline::run_match_graph(const MitmShape& sh, const ArenaLayout& AL, int np
     char* d = d_arena;
     // the launch shape: everything the graph's nodes depend on besides the
     // arena's addresses (fixed until a regrow, which drops the graphs)
-    std::vector<int> key{np, sh.nF, sh.nh, sh.ctas, sh.dir_lmax, sh.wrap};
+    std::vector<int> key{np, sh.nF, sh.nh, sh.ctas, sh.dir_lmax, sh.wrap, sh.wide};
     key.insert(key.end(), sh.ls.begin(), sh.ls.end());
     return run_graphed(key, [&](unsigned flags) -> cudaError_t {
         cudaError_t e = cudaMemcpyAsync(d, h_arena, AL.upload, cudaMemcpyHostToDevice, s);
