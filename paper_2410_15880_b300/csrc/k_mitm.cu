@@ -46,8 +46,8 @@ namespace {
 constexpr int YS_LOG = 13;                                     // list levels built in shared memory
 constexpr int YS_THREADS = 1024;
 constexpr size_t YS_SMEM = ((size_t)2 << YS_LOG) * (8 + 4);    // two (key, mask) buffers of 2^13 entries
-constexpr int YM_THREADS = 256;
-constexpr int YM_PER = 4;                                      // merge outputs per thread (1024-output tiles)
+constexpr int YM_THREADS = 128;
+constexpr int YM_PER = 4;                                      // merge outputs per thread (512-output tiles)
 constexpr int L_MAX = 25;                                      // list bits (2^7 runs of a 32-element half)
 
 #ifndef RFR_MT_THREADS
