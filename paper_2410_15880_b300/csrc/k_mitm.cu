@@ -163,7 +163,6 @@ __global__ void __launch_bounds__(YS_THREADS) k_ybuild_smem(const YJob* __restri
 // last level writes the list itself, its 32-bit positions and its directory.
 constexpr int YM_TILE = YM_THREADS * YM_PER;
 constexpr size_t YM_SMEM = (size_t)YM_TILE * (8 + 4);
-static_assert(YM_PER % 4 == 0, "a thread's outputs go out in 16-byte groups (four masks, two keys)");
 
 __device__ __forceinline__ uint32_t merge_split(const uint64_t* __restrict__ K, uint32_t n, uint32_t r,
                                                 uint64_t c, uint32_t d) {
