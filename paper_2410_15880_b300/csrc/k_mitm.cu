@@ -848,9 +848,15 @@ void mitm_layout_half(int l, char*& p, HalfJob* h) {
 }
 
 int mitm_launches(const ProbJob* const* F, int nF) {
+    // k_ybuild_smem, two per merge level, k_ydir when a list ends in shared
+    // memory, k_mitm (when it has CTAs, which every fused problem gives) and k_mitm_check
     int maxl = 0;
-    for (int i = 0; i < nF; ++i) maxl = std::max(maxl, std::max(F[i]->A.l, F[i]->B.l));
-    return nF ? 4 + 2 * std::max(0, maxl - YS_LOG) : 0;
+    bool dir = false;
+    for (int i = 0; i < nF; ++i) {
+        maxl = std::max(maxl, std::max(F[i]->A.l, F[i]->B.l));
+        dir = dir || (F[i]->A.ydir && F[i]->A.l <= YS_LOG) || (F[i]->B.ydir && F[i]->B.l <= YS_LOG);
+    }
+    return nF ? 3 + 2 * std::max(0, maxl - YS_LOG) + (dir ? 1 : 0) : 0;
 }
 
 cudaError_t mitm_prepare(const ProbJob* const* F, int nF, void* mj_host, void* yj_host, MitmShape* sh) {

@@ -436,7 +436,8 @@ int Pipeline::issue_prologue(int B, const int64_t* d_co, const int32_t* d_dg, bo
     }
     if (rc == RFR_OK) rc = rfr_stage_validate(d_co, d_dg, B, d_rstat, s);
     if (rc == RFR_OK) rc = rfr_stage_roots(d_co, d_dg, B, C.cfg.root_mode, d_roots, d_radius, d_rstat, s);
-    launches += 2;
+    // k_validate; k_aberth (+ k_aberth64 in FP32-bulk mode), k_polish, k_radius
+    launches += C.cfg.root_mode == RFR_ROOTS_FP32_BULK ? 5 : 4;
     cudaEventRecordWithFlags(ev[1], s, ev_flags);
     if (rc == RFR_OK) rc = rfr_stage_weights(d_co, d_dg, B, d_roots, d_radius, d_rstat, C.cfg.eps_override, d_plans, s);
     launches += 1;
@@ -676,7 +677,7 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
         }
         h2d += (uint64_t)B * LDC * 8 + (uint64_t)B * 4;
         d2h += (uint64_t)B * sizeof(rfr_plan);
-        launches += 3;
+        launches += C.cfg.root_mode == RFR_ROOTS_FP32_BULK ? 6 : 5;     // the prologue's kernels (as issue_prologue)
         ++graph_launches;
         rc = cuda_ok(cudaGraphLaunch(exec, s));
     } else {
