@@ -20,8 +20,10 @@
 //     A root stops moving when its correction is below 4 ulp or |p(z_i)| is
 //     below the rounding-error bound of its evaluation.  In FP32-bulk mode
 //     the same iteration runs in FP32 first and FP64 finishes it.
-//  3. One Newton step with p evaluated in double-double arithmetic (the
-//     correction itself in FP64), so each root is kept as a DD value.
+//  3. A Newton step with p evaluated in double-double arithmetic (the
+//     correction itself in FP64), so each root is kept as a DD value; a root
+//     whose step was not tiny against the distance to its nearest neighbour
+//     (close roots) takes up to four more.
 //  4. Inclusion radius: r_i = d |p(z_i)| / prod_{j != i} |z_i - z_j|, with
 //     |p(z_i)| enlarged by the DD evaluation's error bound.  When the discs
 //     D(z_i, r_i) are pairwise disjoint each holds exactly one root of p
@@ -512,40 +514,70 @@ __device__ double warp_poly_r(int n, double r, Coef c) {
     return q;
 }
 
-// Kernel 2: one Newton step per root with p evaluated in double-double (the
-// correction itself in FP64), so each root becomes a DD value.
+// Kernel 2: Newton steps with p evaluated in double-double (the correction
+// itself in FP64), so each root becomes a DD value: one step, or up to five
+// for a root close to another (below).
 template <int RPC>
 __global__ void __launch_bounds__(RPC * SL)
 k_polish(const int64_t* __restrict__ coeffs, const int32_t* __restrict__ degrees,
          const int32_t* __restrict__ status, double* __restrict__ roots) {
     __shared__ double a[DMAX + 1];
+    __shared__ cx<float> zs[DMAX];                           // FP32 copies of the roots
     RootWarp R;
     if (!root_warp<RPC>(degrees, status, &R)) return;         // uniform over the CTA
     const int d = R.d, i = R.i;
     const int64_t* c = coeffs + (size_t)R.prob * LDC;
+    const double* Rt = roots + (size_t)R.prob * DMAX * 4;
     for (int k = threadIdx.x; k <= d; k += blockDim.x) a[k] = (double)c[k];
+    for (int k = threadIdx.x; k < d; k += blockDim.x) zs[k] = cxm<float>((float)Rt[4 * k], (float)Rt[4 * k + 2]);
     __syncthreads();
     // lanes of roots past the degree compute on the last root and write nothing
     // (every lane of the warp takes part in the shuffles)
     const bool live = i < d;
-    double* out = roots + ((size_t)R.prob * DMAX + (live ? i : d - 1)) * 4;
-    cdd Z = cdd_make(out[0], out[2]);
-    // one Newton step from the FP64 Aberth root (error ~1e-16 |z|) squares the
-    // error; the inclusion radius computed afterwards certifies what it reached
-    const cx<double> zh = cxm<double>(Z.re.hi, Z.im.hi);
-    const bool rev = cabsv(zh) > 1.0;
-    // |z| > 1: P(w) = w^d p(1/w) = sum_m a_{d-m} w^m at w = 1/z.  The evaluation
-    // is the same call either way (the lanes of a warp hold different roots).
-    const cdd X = rev ? cdd_inv(Z) : Z;
-    const cx<double> xh = cxm<double>(X.re.hi, X.im.hi);
-    const cdd P = warp_poly_dd(d, X, [&](int k) { return a[rev ? d - k : k]; });
-    const cx<double> dP = warp_poly_c(d - 1, xh, [&](int m) { return (double)(m + 1) * a[rev ? d - m - 1 : m + 1]; });
-    const cx<double> Ph = cxm<double>(P.re.hi, P.im.hi);
-    cx<double> N = rev ? cdivv(zh * Ph, cscale(Ph, (double)d) - xh * dP) : cdivv(Ph, dP);
+    const int ii = live ? i : d - 1;
+    double* out = roots + ((size_t)R.prob * DMAX + ii) * 4;
+    cdd Z = {{out[0], out[1]}, {out[2], out[3]}};
+    // squared distance to the nearest other root (FP32, lanes over j)
+    float dmin2 = INFINITY;
+    for (int j = R.lane; j < d; j += SL) {
+        if (j == ii) continue;
+        const float dx = zs[ii].x - zs[j].x, dy = zs[ii].y - zs[j].y;
+        dmin2 = fminf(dmin2, dx * dx + dy * dy);
+    }
+    for (int o = SL / 2; o; o >>= 1) dmin2 = fminf(dmin2, __shfl_xor_sync(0xffffffffu, dmin2, o, SL));
+    // Newton steps with p in double-double (the correction itself in FP64).
+    // From the FP64 Aberth root (error ~1e-16 |z|) one step squares the error,
+    // and that is the common case.  A root whose step was not tiny against the
+    // distance to its nearest neighbour (close roots, where the FP64 root is
+    // accurate only to a fraction of that distance) takes further steps, each
+    // squaring its error, up to five in all.  The inclusion radius computed
+    // afterwards certifies what they reached.
+    for (int step = 0; step < 5; ++step) {
+        const cx<double> zh = cxm<double>(Z.re.hi, Z.im.hi);
+        const bool rev = cabsv(zh) > 1.0;
+        // |z| > 1: P(w) = w^d p(1/w) = sum_m a_{d-m} w^m at w = 1/z.  The evaluation
+        // is the same call either way (the lanes of a warp hold different roots).
+        const cdd X = rev ? cdd_inv(Z) : Z;
+        const cx<double> xh = cxm<double>(X.re.hi, X.im.hi);
+        const cdd P = warp_poly_dd(d, X, [&](int k) { return a[rev ? d - k : k]; });
+        const cx<double> dP = warp_poly_c(d - 1, xh, [&](int m) { return (double)(m + 1) * a[rev ? d - m - 1 : m + 1]; });
+        const cx<double> Ph = cxm<double>(P.re.hi, P.im.hi);
+        cx<double> N = rev ? cdivv(zh * Ph, cscale(Ph, (double)d) - xh * dP) : cdivv(Ph, dP);
+        if (R.lane == 0) {
+            if (!(cabsv(N) < 1e300)) N = newton_ratio_serial(a, d, zh);   // degenerate: plain FP64 Newton ratio
+            Z.re = dd_add_d(Z.re, -N.x);
+            Z.im = dd_add_d(Z.im, -N.y);
+        }
+        // the root's lanes take the new approximation and its step size from its first lane
+        Z.re.hi = __shfl_sync(0xffffffffu, Z.re.hi, 0, SL);
+        Z.re.lo = __shfl_sync(0xffffffffu, Z.re.lo, 0, SL);
+        Z.im.hi = __shfl_sync(0xffffffffu, Z.im.hi, 0, SL);
+        Z.im.lo = __shfl_sync(0xffffffffu, Z.im.lo, 0, SL);
+        const double n2 = __shfl_sync(0xffffffffu, cabs2(N), 0, SL);
+        const bool more = live && n2 > 1e-12 * (double)dmin2;      // |step| > 1e-6 x nearest distance
+        if (!__any_sync(0xffffffffu, more)) break;
+    }
     if (R.lane == 0 && live) {
-        if (!(cabsv(N) < 1e300)) N = newton_ratio_serial(a, d, zh);   // degenerate: plain FP64 Newton ratio
-        Z.re = dd_add_d(Z.re, -N.x);
-        Z.im = dd_add_d(Z.im, -N.y);
         out[0] = Z.re.hi; out[1] = Z.re.lo; out[2] = Z.im.hi; out[3] = Z.im.lo;
     }
 }

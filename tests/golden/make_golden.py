@@ -43,6 +43,16 @@ def _special():
     out.append(Instance([-2, 1], "special", None, tags={"name": "linear"}))
     out.append(Instance([1, 1, 1], "special", None, tags={"name": "quadratic_pair"}))
     out.append(Instance(prod([[-2, 0, 1], [-3, 0, 1], [1, 1, 1]]), "special", None, tags={"name": "sqrt2_sqrt3_cyclo3"}))
+    # close roots: +-sqrt(2000001) and +-sqrt(2000002) lie 3.5e-4 apart (2.5e-7 relative, a few
+    # FP32 ulps), alone and beside a random degree-54 factor (about 32 elements: the fused match)
+    import numpy as np
+    from workloads import random_monic
+    q1, q2 = [-2000001, 0, 1], [-2000002, 0, 1]
+    f54 = random_monic(np.random.default_rng(20261204), 54, -100, 100)
+    out.append(Instance(prod([q1, q2]), "special", [q1, q2], tags={"name": "close_quadratics"}))
+    out.append(Instance(prod([q1, q2, f54]), "special", [q1, q2, f54], tags={"name": "close_quadratics_deg58"}))
+    # Mignotte's x^16 - 2 (5x - 1)^2: two real roots near 1/5 about 5^-9 apart
+    out.append(Instance([-2, 20, -50] + [0] * 13 + [1], "special", None, tags={"name": "mignotte_16"}))
     return out
 
 

@@ -87,6 +87,22 @@ def test_error_statuses(ctx):
     assert ctx.factor([1, 0, 0, 0, 1]).factors == [[1, 0, 0, 0, 1]]    # x^4+1 irreducible over Z
 
 
+def test_root_cluster_below_fp64_resolution_is_reported():
+    """x^24 - 2 (5x - 1)^2 (Mignotte) has two real roots near 1/5 about 1.6e-9
+    apart, closer than its FP64 root finder can resolve them (its error there is
+    about 1e-16 |p| / |p'|, near 1e-6), so the inclusion discs cannot be
+    separated: the call must then report RFR_E_ROOTS, never a wrong list (it is
+    irreducible, which the oracle proves; this build reports RFR_E_ROOTS).  Two
+    roots 3.5e-4 apart at 1414 (the special goldens close_quadratics*) are
+    resolved by the further double-double Newton steps."""
+    from paper_2410_15880_b300 import Context
+    from paper_2410_15880_b300._native import status_name
+    p = [-2, 20, -50] + [0] * 21 + [1]
+    with Context(device=0) as c:
+        x = c.factor(p)
+    assert (x.ok and x.factors == [p]) or (status_name(x.status) == "RFR_E_ROOTS" and not x.factors)
+
+
 def test_serving_alone_and_in_mix():
     from paper_2410_15880_b300 import Context
     recs = golden("cfg4_sample")
