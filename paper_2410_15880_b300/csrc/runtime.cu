@@ -96,14 +96,20 @@ struct CompactDesc {
     uint64_t* out;                    // [out_cap] compacted candidates
     uint64_t out_cap;
     uint64_t* offs;                   // [np + 1] their offsets
+    uint64_t* inl;                    // [INL] the first INL compacted candidates, beside the offsets
 };
 
+// Candidates that come back in the same copy as the counters (a sub-batch with
+// at most this many needs no second copy and synchronisation).
+constexpr uint64_t INL = 512;
+
 // Match arena of a sub-batch of np problems: the compaction descriptor, np
-// ProbJob slots, 2 np HalfJob slots, the counters [np][8] and the offsets
-// [np + 1].  Everything before the offsets is uploaded from the host image in
-// one copy (the counters as zeros); the layout for np fits in the one for any
-// larger np.
-struct ArenaLayout { size_t desc, jobs, halves, ctrs, offs, upload, total; };
+// ProbJob slots, 2 np HalfJob slots, the counters [np][8], the offsets
+// [np + 1] and the first INL compacted candidates.  Everything before the
+// offsets is uploaded from the host image in one copy (the counters as zeros);
+// the counters, offsets and inline candidates come back in one copy.  The
+// layout for np fits in the one for any larger np.
+struct ArenaLayout { size_t desc, jobs, halves, ctrs, offs, inl, upload, total; };
 static ArenaLayout arena_layout(int np) {
     auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
     ArenaLayout L;
@@ -113,6 +119,7 @@ static ArenaLayout arena_layout(int np) {
     L.halves = p; p += a256((size_t)2 * np * sizeof(HalfJob));
     L.ctrs = p;   p += (size_t)np * 64;
     L.offs = p;   p += ((size_t)np + 1) * 8;
+    L.inl = p;    p += INL * 8;
     L.upload = L.offs;
     L.total = a256(p);
     return L;
@@ -356,7 +363,7 @@ bool Pipeline::reserve(int n) {
 __device__ __forceinline__ void compact_cands(const uint64_t* __restrict__ cand, uint64_t cap,
                                               const unsigned long long* __restrict__ ctr, int np,
                                               uint64_t* __restrict__ out, uint64_t out_cap,
-                                              uint64_t* __restrict__ offs) {
+                                              uint64_t* __restrict__ offs, uint64_t* __restrict__ inl) {
     if (threadIdx.x == 0) {
         uint64_t o = 0;
         for (int i = 0; i < np; ++i) {
@@ -370,21 +377,25 @@ __device__ __forceinline__ void compact_cands(const uint64_t* __restrict__ cand,
     if (offs[np] > out_cap) return;
     for (int i = 0; i < np; ++i) {
         const uint64_t o = offs[i], n = offs[i + 1] - o;
-        for (uint64_t j = threadIdx.x; j < n; j += blockDim.x) out[o + j] = cand[(uint64_t)i * cap + j];
+        for (uint64_t j = threadIdx.x; j < n; j += blockDim.x) {
+            const uint64_t v = cand[(uint64_t)i * cap + j];
+            out[o + j] = v;
+            if (o + j < INL) inl[o + j] = v;
+        }
     }
 }
 
 __global__ void __launch_bounds__(256) k_compact_cands(const uint64_t* __restrict__ cand, uint64_t cap,
                                                         const unsigned long long* __restrict__ ctr, int np,
                                                         uint64_t* __restrict__ out, uint64_t out_cap,
-                                                        uint64_t* __restrict__ offs) {
-    compact_cands(cand, cap, ctr, np, out, out_cap, offs);
+                                                        uint64_t* __restrict__ offs, uint64_t* __restrict__ inl) {
+    compact_cands(cand, cap, ctr, np, out, out_cap, offs, inl);
 }
 
 // k_compact_cands for the sub-batch described at d (in the match arena).
 __global__ void __launch_bounds__(256) k_compact_desc(const CompactDesc* __restrict__ d) {
     const CompactDesc D = *d;
-    compact_cands(D.cand, D.cap, D.ctr, D.np, D.out, D.out_cap, D.offs);
+    compact_cands(D.cand, D.cap, D.ctr, D.np, D.out, D.out_cap, D.offs, D.inl);
 }
 
 static double ms_between(cudaEvent_t a, cudaEvent_t b) {
@@ -741,7 +752,7 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
                 // the records, the compaction's descriptor and zeroed counters go up in
                 // one copy from the arena's host image; k_small and the compaction are a
                 // replayed graph once the batch's small-problem count has recurred
-                const CompactDesc cd{d_cands, cap, d_ctrs, ns, d_compact, out_cap, d_offs};
+                const CompactDesc cd{d_cands, cap, d_ctrs, ns, d_compact, out_cap, d_offs, (uint64_t*)(d_arena + AL.inl)};
                 memcpy(h_arena + AL.desc, &cd, sizeof(cd));
                 memcpy(h_arena + AL.jobs, sj.data(), sizeof(SmallJob) * ns);
                 memset(h_arena + AL.ctrs, 0, (size_t)ns * 64);
@@ -762,24 +773,29 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
                 rc = cuda_ok(run_small(sj.data(), ns, d_sj, s));
                 launches += 1;
                 if (rc == RFR_OK) {
-                    k_compact_cands<<<1, 256, 0, s>>>(d_cands, cap, d_ctrs, ns, d_compact, out_cap, d_offs);
+                    k_compact_cands<<<1, 256, 0, s>>>(d_cands, cap, d_ctrs, ns, d_compact, out_cap, d_offs,
+                                                      (uint64_t*)(d_arena + AL.inl));
                     rc = cuda_ok(cudaGetLastError());
                     launches += 1;
                 }
             }
             cudaEventRecord(ev[6], s);
-            std::vector<uint64_t> h_ctr(cb / 8);
-            char* hs = stage(cb);
-            if (rc == RFR_OK) rc = cuda_ok(cudaMemcpyAsync(hs ? (void*)hs : (void*)h_ctr.data(), d_ctrs, cb, cudaMemcpyDeviceToHost, s));
-            d2h += cb;
+            // counters, offsets and the first INL candidates in one copy
+            const size_t cbx = cb + INL * 8;
+            std::vector<uint64_t> h_ctr(cbx / 8);
+            char* hs = stage(cbx);
+            if (rc == RFR_OK) rc = cuda_ok(cudaMemcpyAsync(hs ? (void*)hs : (void*)h_ctr.data(), d_ctrs, cbx, cudaMemcpyDeviceToHost, s));
+            d2h += cbx;
             if (rc == RFR_OK) rc = cuda_ok(cudaStreamSynchronize(s));
-            if (rc == RFR_OK && hs) memcpy(h_ctr.data(), hs, cb);
+            if (rc == RFR_OK && hs) memcpy(h_ctr.data(), hs, cbx);
             if (timing && rc == RFR_OK) t_match += ms_between(ev[5], ev[6]);
             const uint64_t* h_offs = h_ctr.data() + 8 * (size_t)ns;
             const uint64_t total = rc == RFR_OK ? h_offs[ns] : 0;
             const bool compacted = total <= out_cap;
             char* hc = nullptr;
-            if (rc == RFR_OK && compacted && total) {
+            if (rc == RFR_OK && compacted && total <= INL) {
+                hc = (char*)(h_ctr.data() + cb / 8);          // came back with the counters
+            } else if (rc == RFR_OK && compacted && total) {
                 hc = stage((size_t)total * 8);
                 rc = hc ? cuda_ok(cudaMemcpyAsync(hc, d_compact, total * 8, cudaMemcpyDeviceToHost, s)) : RFR_E_OOM;
                 d2h += total * 8;
@@ -919,7 +935,7 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
             // fused problems only: the records, with the compaction's descriptor and
             // zeroed counters, go up in one copy from the arena's host image, and the
             // launch sequence is a replayed graph once its shape has recurred
-            const CompactDesc cd{d_cands, cap, d_ctrs, np, d_compact, out_cap, d_offs};
+            const CompactDesc cd{d_cands, cap, d_ctrs, np, d_compact, out_cap, d_offs, (uint64_t*)(d_arena + AL.inl)};
             memcpy(h_arena + AL.desc, &cd, sizeof(cd));
             memset(h_arena + AL.ctrs, 0, (size_t)np * 64);
             std::vector<const ProbJob*> F(np);
@@ -933,20 +949,22 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
             rc = cuda_ok(run_match(jobs.data(), np, d_jobs, d_halves, halves.data(), s, ev[4], ev[5], &nl));
             launches += (uint32_t)nl;
             if (rc == RFR_OK) {
-                k_compact_cands<<<1, 256, 0, s>>>(d_cands, cap, d_ctrs, np, d_compact, out_cap, d_offs);
+                k_compact_cands<<<1, 256, 0, s>>>(d_cands, cap, d_ctrs, np, d_compact, out_cap, d_offs,
+                                                  (uint64_t*)(d_arena + AL.inl));
                 rc = cuda_ok(cudaGetLastError());
                 launches += 1;
             }
         }
         cudaEventRecord(ev[6], s);
-        // counters and offsets in one copy (pinned staging when available)
-        const size_t cb = (size_t)np * 64 + ((size_t)np + 1) * 8;
-        std::vector<uint64_t> h_ctr(cb / 8);
-        char* hs = stage(cb);
-        if (rc == RFR_OK) rc = cuda_ok(cudaMemcpyAsync(hs ? (void*)hs : (void*)h_ctr.data(), d_ctrs, cb, cudaMemcpyDeviceToHost, s));
-        d2h += cb;
+        // counters, offsets and the first INL compacted candidates in one copy
+        // (pinned staging when available)
+        const size_t cb = (size_t)np * 64 + ((size_t)np + 1) * 8, cbx = cb + INL * 8;
+        std::vector<uint64_t> h_ctr(cbx / 8);
+        char* hs = stage(cbx);
+        if (rc == RFR_OK) rc = cuda_ok(cudaMemcpyAsync(hs ? (void*)hs : (void*)h_ctr.data(), d_ctrs, cbx, cudaMemcpyDeviceToHost, s));
+        d2h += cbx;
         if (rc == RFR_OK) rc = cuda_ok(cudaStreamSynchronize(s));
-        if (rc == RFR_OK && hs) memcpy(h_ctr.data(), hs, cb);
+        if (rc == RFR_OK && hs) memcpy(h_ctr.data(), hs, cbx);
         const uint64_t* h_offs = h_ctr.data() + 8 * (size_t)np;
         const uint64_t total = rc == RFR_OK ? h_offs[np] : 0;
         const bool compacted = total <= out_cap;
@@ -955,9 +973,12 @@ int Pipeline::run(std::vector<Item>& items, const int64_t* dev_coeffs, const int
             t_scatter += ms_between(ev[4], ev[5]);
             t_match += ms_between(ev[5], ev[6]);
         }
-        // all candidates in one copy when they were compacted, else problem by problem
+        // all candidates in one copy when they were compacted (none when they came
+        // back with the counters), else problem by problem
         char* hc = nullptr;
-        if (rc == RFR_OK && compacted && total) {
+        if (rc == RFR_OK && compacted && total <= INL) {
+            hc = (char*)(h_ctr.data() + cb / 8);
+        } else if (rc == RFR_OK && compacted && total) {
             hc = stage((size_t)total * 8);
             rc = hc ? cuda_ok(cudaMemcpyAsync(hc, d_compact, total * 8, cudaMemcpyDeviceToHost, s)) : RFR_E_OOM;
             d2h += total * 8;
